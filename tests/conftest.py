@@ -1,0 +1,21 @@
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built extension")
+    config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
+
+
+@pytest.fixture(scope="session")
+def paper():
+    with open(os.path.join(ROOT, "tests", "golden", "paper_values.json")) as f:
+        d = json.load(f)
+    return {k: v["value"] for k, v in d.items() if not k.startswith("_")}
