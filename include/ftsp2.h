@@ -1,0 +1,252 @@
+/*
+ * ftsp2.h -- C ABI of the GB300 (sm_103a) machine-learned finite-temperature
+ * SP2 hot path (arXiv 2605.08523).
+ *
+ * Given dense symmetric Hamiltonians H (one large matrix or a ragged batch),
+ * a chemical potential mu and an electronic temperature kT per instance, the
+ * library
+ *   (a1) bounds each spectrum with Gershgorin circles (Appendix A),
+ *   (a2) maps (H, beta, mu) onto a trained model (beta0, mu0) by the affine
+ *        rescaling of Sec. III A (Eqs. H', mu', beta', H0), choosing the flip
+ *        of Eq. flip and a model whose region of validity (Eq. conditions)
+ *        contains (beta', mu'),
+ *   (a3) runs the L-layer learned recursion x <- a x^2 + b x + c, A <- A + d x
+ *        (Eq. mlsp2) on the matrix, one symmetric square per layer on the
+ *        tensor cores,
+ *   (a4) returns D = A + X (or I - (A + X) when flipped) with Tr D and
+ *        ||D||_F^2 (Eq. tr(D^2)),
+ *   (a5, a6) runs the entropy recursion (Eqs. entropy expansion and
+ *        entropy expansion-s) and returns S = 4 ln2 (Tr F - Tr F^2),
+ * and (a7) trains the per-layer coefficients by Levenberg-Marquardt on scalar
+ * samples (Sec. II C).
+ *
+ * Conventions shared by every entry point
+ *   - Energies are in eV with k_B absorbed: beta = 1/kT.  S is returned per
+ *     spin channel in units of k_B.
+ *   - Matrices are row-major.  H is FP64 and must be symmetric; every element
+ *     is read.  D is FP32.
+ *   - Pointers named d... are device pointers; all others are host pointers.
+ *     The caller owns every buffer; the library never allocates device memory
+ *     in these calls (model sets are the one library-owned allocation).
+ *   - Every launch goes to the caller's stream (`stream`, a cudaStream_t
+ *     passed as void*; NULL = legacy default stream) and the call returns
+ *     without synchronising, unless FTSP2_SYNC is set in `flags`, in which case
+ *     it synchronises the stream and returns the worst per-instance status.
+ *     Without FTSP2_SYNC only host-side argument errors and launch errors are
+ *     returned; device-detected conditions (validity, non-finite input,
+ *     timeouts) are left in the per-instance records.
+ *   - Calls that share a workspace must not overlap on the GPU.
+ */
+#ifndef FTSP2_H
+#define FTSP2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FTSP2_OK = 0,
+    FTSP2_E_ARG = -1,          /* bad argument detected on the host           */
+    FTSP2_E_CUDA = -2,         /* a CUDA runtime/driver call failed           */
+    FTSP2_E_WORKSPACE = -3,    /* workspace too small or misaligned           */
+    FTSP2_E_VALIDITY = -4,     /* beta' beyond every model's region of validity */
+    FTSP2_E_NONFINITE = -5,    /* NaN/Inf in H, mu or kT                       */
+    FTSP2_E_TIMEOUT = -6,      /* a bounded device-side wait gave up           */
+    FTSP2_E_NOMODEL = -7,      /* empty or inconsistent model set              */
+    FTSP2_E_UNSUPPORTED = -8   /* device is not sm_103 / mode not built        */
+} ftsp2_status;
+
+/* Arithmetic of the layer products X^2 (Sec. IV A): every mode keeps the state
+ * in FP32 and accumulates in FP32; they differ in how X is split into
+ * tensor-core operands. */
+typedef enum {
+    FTSP2_FP32 = 0,    /* CUDA-core FP32 FMA products (no tensor cores)        */
+    FTSP2_TF32X3 = 1,  /* X = hi + lo in TF32, 3 products (hi hi, hi lo, lo hi)  */
+    FTSP2_BF16X3 = 2,  /* X = b0 + b1 + b2 in BF16, 6 products (terms >= 2^-16)  */
+    FTSP2_FP16X2 = 3   /* X = hi + lo in FP16 with a per-layer power-of-two
+                          scale, 3 products (the paper's Eq. emulated matmul)  */
+} ftsp2_mode;
+
+/* flags */
+#define FTSP2_SYNC          0x1  /* synchronise and return the worst status   */
+#define FTSP2_CLAMP         0x2  /* outside validity: lower beta' to the largest
+                                    valid value of the largest-beta0 model, as
+                                    the paper's Appendix A program does (this
+                                    changes the temperature); default: status
+                                    FTSP2_E_VALIDITY and no result           */
+#define FTSP2_REFINE1       0x4  /* last layer in FTSP2_FP32 arithmetic       */
+#define FTSP2_REFINE2       0x8  /* last two layers in FTSP2_FP32 arithmetic  */
+
+/* One Hamiltonian of a (ragged) batch.  H_b starts at dH + offset and is
+ * n x n row-major; D_b starts at dD + offset.  Offsets are in elements. */
+typedef struct {
+    int32_t n;          /* order, >= 1                                        */
+    int32_t reserved;
+    int64_t offset;     /* element offset into dH and dD                      */
+    double mu;          /* chemical potential (eV)                            */
+    double kT;          /* electronic temperature (eV), > 0                   */
+} ftsp2_instance;
+
+/* One trained model (Sec. III A 2, "a set of models").  theta holds L rows
+ * (a, b, c, d) = (theta_i1, theta_i2, theta_i3, theta_i4) of Eq. mlsp2, acting
+ * on the layer-0 input x0 = H0 without an inner flip and approximating
+ * 1/(1 + exp(-beta0 (x - mu0))) on [0, 1].  theta_entropy holds L_entropy rows
+ * of the entropy recursion (Eq. entropy expansion) or is NULL to reuse theta
+ * (the theta_fermi strategy).  alpha is the entropy input scale of
+ * Eq. entropy expansion.  All pointers are host pointers, copied at creation. */
+typedef struct {
+    int32_t L;
+    int32_t L_entropy;
+    double beta0;
+    double mu0;
+    double alpha;
+    const double* theta;
+    const double* theta_entropy;
+} ftsp2_table;
+
+typedef struct ftsp2_model_set ftsp2_model_set;   /* opaque */
+
+/* Per-instance record written by ftsp2_rescale / ftsp2_density /
+ * ftsp2_entropy (device memory, 64 bytes each). */
+typedef struct {
+    double e_min, e_max;   /* Gershgorin bounds (Appendix A)                  */
+    double mu_p;           /* mu' after the flip (Eq. mu', Eq. flip)          */
+    double beta_p;         /* beta' (after clamping, if any)                  */
+    double scale;          /* X0 = mu0 I + scale (mu I - H): scale = +-beta_eff/beta0 */
+    int32_t flip;          /* 1 if Eq. flip was applied (mu' > 1/2)           */
+    int32_t model;         /* index into the model set, -1 if none is valid   */
+    int32_t status;        /* ftsp2_status of this instance                   */
+    int32_t layers;        /* layers run for this instance                    */
+    int32_t valid;         /* 1 if inside the chosen model's region          */
+    int32_t reserved;
+} ftsp2_rescale_rec;
+
+/* ---- model sets -------------------------------------------------------- */
+
+/* Copies `ntab` tables to the device (one cudaMalloc, owned by the set) and
+ * precomputes the per-layer constants the kernels use.  Tables must satisfy
+ * 1 <= L <= 64, beta0 > 0, 0 < mu0 < 1.  Returns FTSP2_E_NOMODEL for ntab < 1. */
+ftsp2_status ftsp2_model_set_create(const ftsp2_table* tabs, int ntab, ftsp2_model_set** out);
+
+/* Model set holding the 26-layer table printed in the paper's Appendix A
+ * (beta0 = 1500, mu0 = 1/3; theta_fermi entropy with alpha = 0.842704). */
+ftsp2_status ftsp2_model_set_builtin(ftsp2_model_set** out);
+
+void ftsp2_model_set_destroy(ftsp2_model_set* set);
+
+/* Number of tables and the largest layer count in the set. */
+ftsp2_status ftsp2_model_set_info(const ftsp2_model_set* set, int* ntab, int* max_layers);
+
+/* ---- workspace ------------------------------------------------------------ */
+
+/* Bytes of device workspace needed by a density/entropy call with these
+ * instances and mode.  `want` = 1 density, 2 entropy, 3 both. */
+ftsp2_status ftsp2_workspace_size(const ftsp2_instance* inst, int nb, ftsp2_mode mode,
+                                  int want, size_t* bytes);
+
+/* ---- the hot path ------------------------------------------------------------ */
+
+/* Bytes of device workspace ftsp2_rescale needs for nb instances (any
+ * workspace sized by ftsp2_workspace_size for the same instances also fits). */
+ftsp2_status ftsp2_rescale_workspace_size(int nb, size_t* bytes);
+
+/* (a1)+(a2) only: Gershgorin bounds, normalisation, flip, validity and model
+ * choice for every instance; writes dRec[nb].  dInst is a device copy of inst
+ * (same contents; the kernels read it, the host plans from inst).  ws must be
+ * 1024-byte aligned and hold ftsp2_rescale_workspace_size(nb) bytes. */
+ftsp2_status ftsp2_rescale(const double* dH, const ftsp2_instance* inst,
+                           const ftsp2_instance* dInst, int nb,
+                           const ftsp2_model_set* set, int flags,
+                           ftsp2_rescale_rec* dRec, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/* (a1)-(a4): density matrices.  dD receives D_b at its offset (full symmetric
+ * matrix, FP32).  dTrace (nullable) receives 2 doubles per instance:
+ * Tr D_b and ||D_b||_F^2 (Eq. tr(D^2)), accumulated in FP64.  dRec receives
+ * the per-instance records.  ws must hold ftsp2_workspace_size(..., want=1)
+ * bytes and be 1024-byte aligned. */
+ftsp2_status ftsp2_density(const double* dH, const ftsp2_instance* inst,
+                           const ftsp2_instance* dInst, int nb,
+                           const ftsp2_model_set* set, ftsp2_mode mode, int flags,
+                           float* dD, double* dTrace, ftsp2_rescale_rec* dRec,
+                           void* ws, size_t ws_bytes, void* stream);
+
+/* (a1), (a2), (a5), (a6): entropies only.  dS receives one double per
+ * instance: S_b = 4 ln2 (Tr F - Tr F^2), F = A_S + Y (Eq. entropy expansion-s,
+ * taken with the sign that makes S >= 0). */
+ftsp2_status ftsp2_entropy(const double* dH, const ftsp2_instance* inst,
+                           const ftsp2_instance* dInst, int nb,
+                           const ftsp2_model_set* set, ftsp2_mode mode, int flags,
+                           double* dS, ftsp2_rescale_rec* dRec,
+                           void* ws, size_t ws_bytes, void* stream);
+
+/* (a1)-(a6) in one pass: both recursions share the bounds and the rescale and
+ * run as two problems of the same grouped launch per layer (Alg. 2 runs them
+ * in one loop).  Any of dD, dTrace, dS may be NULL (dD and dS not both). */
+ftsp2_status ftsp2_density_entropy(const double* dH, const ftsp2_instance* inst,
+                                   const ftsp2_instance* dInst, int nb,
+                                   const ftsp2_model_set* set, ftsp2_mode mode, int flags,
+                                   float* dD, double* dTrace, double* dS,
+                                   ftsp2_rescale_rec* dRec,
+                                   void* ws, size_t ws_bytes, void* stream);
+
+/* ---- training (a7) -------------------------------------------------------------- */
+
+typedef struct {
+    int32_t iterations;     /* LM iterations run                               */
+    int32_t accepted;       /* accepted steps                                  */
+    double cost0, cost;     /* 0.5 sum r^2 at start and end                    */
+    double max_err;         /* max |model - target| on the samples              */
+    double lambda;          /* final damping                                    */
+} ftsp2_train_report;
+
+#define FTSP2_TARGET_FERMI   0  /* 1/(1 + exp(-beta0 (x - mu0)))                */
+#define FTSP2_TARGET_ENTROPY 1  /* s(beta0 (x - mu0)) of Eq. entropy, model
+                                   4 ln2 F (1 - F) with x0 = alpha (x - mu0) + mu0 */
+
+/* Levenberg-Marquardt with optional geodesic acceleration (Sec. II C 2) on
+ * nsamples scalar samples.  dX (device, nsamples doubles) holds the sample
+ * points in [0, 1] (fixed for the whole fit, Sec. II C 1); dWork must hold
+ * ftsp2_train_workspace_size(nsamples, L) bytes.  theta_init (host, L*4) is
+ * the starting table; theta_out (host, L*4) receives the result.  Residuals,
+ * Jacobian rows and the reductions J^T J, J^T r run on the GPU in FP64; the
+ * damped normal equations are solved on the host by Cholesky in FP64.
+ * accel != 0 enables geodesic acceleration.  Synchronous on `stream`. */
+size_t ftsp2_train_workspace_size(int nsamples, int L);
+ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, double alpha,
+                                const double* dX, int nsamples, int iterations, int accel,
+                                const double* theta_init, double* theta_out,
+                                ftsp2_train_report* rep, void* dWork, size_t work_bytes,
+                                void* stream);
+
+/* Building blocks of one LM iteration, exposed for parity tests.
+ * ftsp2_train_residual_jacobian: residuals dR[nsamples] = model(theta) - target
+ * and (if dM != NULL) the augmented Jacobian dM[(4L+1) * nsamples],
+ * parameter-major: dM[j * nsamples + s] = d model(x_s) / d theta_j for the
+ * flattened table (a_0, b_0, c_0, d_0, a_1, ...), j < 4L, by reverse
+ * accumulation, and dM[4L * nsamples + s] = r_s.  theta is a host array.
+ * ftsp2_train_normal_equations: dG[(4L+1)^2] = M^T M (row-major), i.e.
+ * [[J^T J, J^T r], [r^T J, r^T r]], reduced in FP64 in a fixed order; dWork
+ * must hold ftsp2_train_workspace_size(nsamples, L) bytes. */
+ftsp2_status ftsp2_train_residual_jacobian(int target, double beta0, double mu0, int L,
+                                           double alpha, const double* theta,
+                                           const double* dX, int nsamples,
+                                           double* dR, double* dM, void* stream);
+ftsp2_status ftsp2_train_normal_equations(const double* dM, int nsamples, int L, double* dG,
+                                          void* dWork, size_t work_bytes, void* stream);
+
+/* ---- misc ---------------------------------------------------------------- */
+
+const char* ftsp2_status_string(ftsp2_status s);
+
+/* Number of kernels this library launched since load (all entry points). */
+uint64_t ftsp2_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTSP2_H */

@@ -1,0 +1,265 @@
+"""GB300-native machine-learned finite-temperature SP2 (arXiv 2605.08523).
+
+Python binding of the C ABI in ``include/ftsp2.h`` (ctypes; see ``_lib``).
+PyTorch provides device memory and streams only; every step of the hot path
+(Gershgorin bounds, rescale, the learned recursion on the tensor cores, the
+traces and the entropy) runs in the library's CUDA kernels.  There is no CPU
+fallback: without the built library or a GB300 every call raises.
+
+Main entry points (same names as the C functions, torch tensors in place of
+device pointers):
+
+* ``ModelSet`` -- ``ftsp2_model_set_create`` / ``ftsp2_model_set_builtin``
+* ``Solver``   -- a planned batch: workspace, device descriptors, outputs;
+                  ``Solver.run()`` issues ``ftsp2_density_entropy`` (or the
+                  density-only / entropy-only variants) without allocating.
+* ``ftsp2_rescale``, ``ftsp2_train_coeffs``, ``ftsp2_train_residual_jacobian``,
+  ``ftsp2_train_normal_equations``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (BF16X3, CLAMP, FP16X2, FP32, MODES, REFINE1, REFINE2, SYNC, TARGET_ENTROPY,
+                   TARGET_FERMI, TF32X3, Ftsp2Error, Instance, RescaleRec, Table, TrainReport, check,
+                   lib, status_string)
+
+__all__ = ["ModelSet", "Solver", "ftsp2_rescale", "ftsp2_train_coeffs", "ftsp2_train_residual_jacobian",
+           "ftsp2_train_normal_equations", "kernel_launch_count", "MODES", "FP32", "TF32X3", "BF16X3",
+           "FP16X2", "SYNC", "CLAMP", "REFINE1", "REFINE2", "TARGET_FERMI", "TARGET_ENTROPY",
+           "Ftsp2Error", "status_string", "lib", "REC_DTYPE"]
+
+REC_DTYPE = np.dtype([("e_min", "f8"), ("e_max", "f8"), ("mu_p", "f8"), ("beta_p", "f8"), ("scale", "f8"),
+                      ("flip", "i4"), ("model", "i4"), ("status", "i4"), ("layers", "i4"), ("valid", "i4"),
+                      ("reserved", "i4")])
+INST_DTYPE = np.dtype([("n", "i4"), ("reserved", "i4"), ("offset", "i8"), ("mu", "f8"), ("kT", "f8")])
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def kernel_launch_count() -> int:
+    return int(lib().ftsp2_kernel_launch_count())
+
+
+class ModelSet:
+    """A set of trained tables (Sec. III A 2).  ``tables`` is a list of dicts
+    with keys theta ((L, 4) rows a, b, c, d), beta0, mu0, alpha and optionally
+    theta_entropy; ``None`` gives the paper's printed 26-layer table."""
+
+    def __init__(self, tables=None):
+        self._h = C.c_void_p()
+        self._keep = []
+        if tables is None:
+            check(lib().ftsp2_model_set_builtin(C.byref(self._h)), "ftsp2_model_set_builtin")
+            self.tables = None
+            return
+        arr = (Table * len(tables))()
+        for i, t in enumerate(tables):
+            th = np.ascontiguousarray(np.asarray(t["theta"], dtype=np.float64).reshape(-1, 4))
+            self._keep.append(th)
+            arr[i].L = th.shape[0]
+            arr[i].beta0 = float(t["beta0"])
+            arr[i].mu0 = float(t["mu0"])
+            arr[i].alpha = float(t.get("alpha", 0.842704))
+            arr[i].theta = th.ctypes.data_as(C.POINTER(C.c_double))
+            te = t.get("theta_entropy")
+            if te is not None:
+                te = np.ascontiguousarray(np.asarray(te, dtype=np.float64).reshape(-1, 4))
+                self._keep.append(te)
+                arr[i].L_entropy = te.shape[0]
+                arr[i].theta_entropy = te.ctypes.data_as(C.POINTER(C.c_double))
+            else:
+                arr[i].L_entropy = 0
+                arr[i].theta_entropy = None
+        check(lib().ftsp2_model_set_create(arr, len(tables), C.byref(self._h)), "ftsp2_model_set_create")
+        self.tables = tables
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        n, L = C.c_int(), C.c_int()
+        check(lib().ftsp2_model_set_info(self._h, C.byref(n), C.byref(L)), "ftsp2_model_set_info")
+        return n.value, L.value
+
+    def close(self):
+        if self._h:
+            lib().ftsp2_model_set_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _instances(ns, mus, kTs, offsets=None):
+    nb = len(ns)
+    host = (Instance * nb)()
+    offs = []
+    o = 0
+    for b in range(nb):
+        off = o if offsets is None else int(offsets[b])
+        host[b].n = int(ns[b])
+        host[b].offset = off
+        host[b].mu = float(mus[b])
+        host[b].kT = float(kTs[b])
+        offs.append(off)
+        o += int(ns[b]) * int(ns[b])
+    return host, offs, o
+
+
+class Solver:
+    """One planned (ragged) batch on the current CUDA device.
+
+    ns, mus, kTs: per-instance order, chemical potential (eV) and temperature
+    (eV).  Matrices are packed back to back (offset_b = sum_{b'<b} n_b'^2) in a
+    flat FP64 tensor.  want: 1 density, 2 entropy, 3 both.  Allocates the
+    workspace, the device descriptor copy and the outputs once; ``run`` then
+    only launches kernels (safe to capture in a CUDA graph)."""
+
+    def __init__(self, ns, mus, kTs, model_set: ModelSet, mode="fp16x2", want=3, flags=0, device=None):
+        torch = _torch()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        self.want = int(want)
+        self.flags = int(flags)
+        self.ms = model_set
+        self.nb = len(ns)
+        self.host_inst, self.offsets, self.total = _instances(ns, mus, kTs)
+        self.ns = [int(n) for n in ns]
+        raw = np.frombuffer(bytes(self.host_inst), dtype=INST_DTYPE)
+        self.d_inst = torch.from_numpy(raw.view(np.uint8).copy()).to(self.device)
+        wsz = C.c_size_t()
+        check(lib().ftsp2_workspace_size(self.host_inst, self.nb, self.mode, self.want, C.byref(wsz)),
+              "ftsp2_workspace_size")
+        self.ws_bytes = wsz.value
+        self._ws_raw = torch.empty(self.ws_bytes + 1024, dtype=torch.uint8, device=self.device)
+        base = self._ws_raw.data_ptr()
+        self.ws_ptr = (base + 1023) // 1024 * 1024
+        self.D = torch.empty(self.total, dtype=torch.float32, device=self.device) if want & 1 else None
+        self.trace = torch.empty((self.nb, 2), dtype=torch.float64, device=self.device) if want & 1 else None
+        self.S = torch.empty(self.nb, dtype=torch.float64, device=self.device) if want & 2 else None
+        self.rec = torch.empty(self.nb * 64, dtype=torch.uint8, device=self.device)
+
+    def set_mu_kT(self, mus, kTs):
+        """Change the per-instance mu and kT (host and device copies)."""
+        for b in range(self.nb):
+            self.host_inst[b].mu = float(mus[b])
+            self.host_inst[b].kT = float(kTs[b])
+        raw = np.frombuffer(bytes(self.host_inst), dtype=np.uint8).copy()
+        self.d_inst.copy_(_torch().from_numpy(raw))
+
+    def run(self, H, stream=None, sync=False):
+        """Launch the hot path on the flat FP64 device tensor H (length
+        sum n_b^2).  Returns the status of the call (host-side errors raise)."""
+        torch = _torch()
+        if H.dtype != torch.float64 or not H.is_cuda or H.numel() < self.total:
+            raise ValueError("H must be a CUDA float64 tensor with sum(n^2) elements")
+        flags = self.flags | (SYNC if sync else 0)
+        L = lib()
+        args_common = (_ptr(H), self.host_inst, _ptr(self.d_inst), self.nb, self.ms.handle, self.mode, flags)
+        if self.want == 1:
+            st = L.ftsp2_density(*args_common, _ptr(self.D), _ptr(self.trace), _ptr(self.rec),
+                                 C.c_void_p(self.ws_ptr), self.ws_bytes, _stream(stream))
+        elif self.want == 2:
+            st = L.ftsp2_entropy(*args_common, _ptr(self.S), _ptr(self.rec), C.c_void_p(self.ws_ptr),
+                                 self.ws_bytes, _stream(stream))
+        else:
+            st = L.ftsp2_density_entropy(*args_common, _ptr(self.D), _ptr(self.trace), _ptr(self.S),
+                                         _ptr(self.rec), C.c_void_p(self.ws_ptr), self.ws_bytes, _stream(stream))
+        if st in (_lib.E_ARG, _lib.E_CUDA, _lib.E_WORKSPACE, _lib.E_NOMODEL, _lib.E_UNSUPPORTED):
+            raise Ftsp2Error(st, "ftsp2 hot path")
+        return st
+
+    def records(self):
+        raw = self.rec.cpu().numpy()
+        return raw.view(REC_DTYPE)
+
+    def matrix(self, b):
+        n, o = self.ns[b], self.offsets[b]
+        return self.D[o:o + n * n].view(n, n)
+
+
+def ftsp2_rescale(H, ns, mus, kTs, model_set: ModelSet, flags=0, stream=None):
+    """(a1)+(a2) only; returns the per-instance records (numpy structured)."""
+    torch = _torch()
+    host, offs, total = _instances(ns, mus, kTs)
+    nb = len(ns)
+    raw = np.frombuffer(bytes(host), dtype=np.uint8).copy()
+    d_inst = torch.from_numpy(raw).to(H.device)
+    rec = torch.empty(nb * 64, dtype=torch.uint8, device=H.device)
+    wsz = C.c_size_t()
+    check(lib().ftsp2_rescale_workspace_size(nb, C.byref(wsz)), "ftsp2_rescale_workspace_size")
+    ws = torch.empty(wsz.value + 1024, dtype=torch.uint8, device=H.device)
+    wp = (ws.data_ptr() + 1023) // 1024 * 1024
+    st = lib().ftsp2_rescale(_ptr(H), host, _ptr(d_inst), nb, model_set.handle, int(flags) | SYNC, _ptr(rec),
+                             C.c_void_p(wp), wsz.value, _stream(stream))
+    if st in (_lib.E_ARG, _lib.E_CUDA, _lib.E_WORKSPACE, _lib.E_NOMODEL, _lib.E_UNSUPPORTED):
+        raise Ftsp2Error(st, "ftsp2_rescale")
+    return rec.cpu().numpy().view(REC_DTYPE)
+
+
+def ftsp2_train_residual_jacobian(target, beta0, mu0, theta, x, alpha=1.0, with_jacobian=True, stream=None):
+    """Residuals r (ns,) and augmented Jacobian M ((4L+1), ns) on the GPU."""
+    torch = _torch()
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1, 4))
+    L = th.shape[0]
+    ns = x.numel()
+    r = torch.empty(ns, dtype=torch.float64, device=x.device)
+    M = torch.empty((4 * L + 1, ns), dtype=torch.float64, device=x.device) if with_jacobian else None
+    check(lib().ftsp2_train_residual_jacobian(int(target), float(beta0), float(mu0), L, float(alpha),
+                                              th.ctypes.data_as(C.POINTER(C.c_double)), _ptr(x), ns, _ptr(r),
+                                              _ptr(M), _stream(stream)), "ftsp2_train_residual_jacobian")
+    return r, M
+
+
+def ftsp2_train_normal_equations(M, L, stream=None):
+    """G = M^T M ((4L+1) x (4L+1)) on the GPU, FP64, fixed reduction order."""
+    torch = _torch()
+    ns = M.shape[1]
+    m = 4 * L + 1
+    G = torch.empty((m, m), dtype=torch.float64, device=M.device)
+    wb = lib().ftsp2_train_workspace_size(ns, L)
+    ws = torch.empty(wb, dtype=torch.uint8, device=M.device)
+    check(lib().ftsp2_train_normal_equations(_ptr(M), ns, L, _ptr(G), _ptr(ws), wb, _stream(stream)),
+          "ftsp2_train_normal_equations")
+    return G
+
+
+def ftsp2_train_coeffs(target, beta0, mu0, theta_init, x, iterations=100, accel=True, alpha=1.0, stream=None):
+    """Levenberg-Marquardt fit on the GPU (Sec. II C).  x: CUDA float64 samples.
+    Returns (theta (L, 4) numpy, report dict)."""
+    torch = _torch()
+    th0 = np.ascontiguousarray(np.asarray(theta_init, dtype=np.float64).reshape(-1, 4))
+    L = th0.shape[0]
+    ns = x.numel()
+    out = np.zeros_like(th0)
+    wb = lib().ftsp2_train_workspace_size(ns, L)
+    ws = torch.empty(wb, dtype=torch.uint8, device=x.device)
+    rep = TrainReport()
+    check(lib().ftsp2_train_coeffs(int(target), float(beta0), float(mu0), L, float(alpha), _ptr(x), ns,
+                                   int(iterations), int(bool(accel)),
+                                   th0.ctypes.data_as(C.POINTER(C.c_double)),
+                                   out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep), _ptr(ws), wb,
+                                   _stream(stream)), "ftsp2_train_coeffs")
+    return out, dict(iterations=rep.iterations, accepted=rep.accepted, cost0=rep.cost0, cost=rep.cost,
+                     max_err=rep.max_err, lam=rep.lam)

@@ -1,0 +1,156 @@
+// Epilogue of one layer of the centred recursion, shared by the tensor-core
+// and the CUDA-core layer kernels.  For an owned element (r, c), r <= c:
+//   Z_{k+1} = a_k (Z_k^2)_{rc} + (b_k + 2 a_k tau_k) (Z_k)_{rc}     (centred Eq. mlsp2)
+//   A_{k+1} = A_k + d_k (Z_k)_{rc}
+// then either the next layer's operands are written at (r, c) and (c, r), or,
+// at the last layer, D = G + f0 I (Appendix A output, flipped as I - (A + X)
+// when Eq. flip was used) is written and the FP64 partial sums of G are formed.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "ftsp2_internal.h"
+
+namespace ftsp2 {
+
+// Is tile `t` active in this launch?  Returns local layer k and chain kind.
+__device__ __forceinline__ bool tile_active(const LayerArgs& a, const Tile& t, int& k) {
+    const ftsp2_rescale_rec& rec = a.rec[t.inst];
+    if (rec.status != FTSP2_OK || rec.model < 0) return false;
+    const int start = (a.iw[t.inst].start_layer >> (16 * t.chain)) & 0xffff;
+    k = a.gl - start;
+    return k >= 0;
+}
+
+// ----------------------------------------------------------------------------------
+// Epilogue on one row segment of 16 columns (shared logic of the centred update).
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ void store_operand(int fmt, uint8_t* base, size_t plane, size_t idx, float zs) {
+    switch (fmt) {
+        case OP_F32:
+            reinterpret_cast<float*>(base)[idx] = zs;
+            break;
+        case OP_TF32X3: {
+            uint32_t hb;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(zs));
+            const float h = __uint_as_float(hb);
+            reinterpret_cast<float*>(base)[idx] = h;
+            reinterpret_cast<float*>(base)[plane + idx] = zs - h;
+            break;
+        }
+        case OP_BF16X3: {
+            const __nv_bfloat16 b0 = __float2bfloat16_rn(zs);
+            const float r1 = zs - __bfloat162float(b0);
+            const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
+            __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(base);
+            p[idx] = b0;
+            p[plane + idx] = b1;
+            p[2 * plane + idx] = b2;
+            break;
+        }
+        case OP_F16X2: {
+            const __half h = __float2half_rn(zs);
+            const __half l = __float2half_rn(zs - __half2float(h));
+            __half* p = reinterpret_cast<__half*>(base);
+            p[idx] = h;
+            p[plane + idx] = l;
+            break;
+        }
+    }
+}
+
+struct EpiCtx {
+    int n, P, chain, kind, flip, last, next_fmt;
+    float mul;            // multiplier of the product: a_k, times 2^(-2 e_k) for scaled FP16 operands
+    size_t slab;          // b * P * P
+    int64_t doff;         // D offset
+    DevLayer L;
+    double cdiag;         // f0 (or 1 - f0 when flipped) added on the diagonal of D
+};
+
+// Process row r, columns c0 .. c0 + W - 1 (c0 % 4 == 0, c0 + W <= P) with
+// accumulator values v[W].  Accumulates (diagonal sum, weighted square sum) of the
+// centred output G into tr / sq at the last layer.
+template <int W>
+__device__ __forceinline__ void epi_segment(const LayerArgs& a, const EpiCtx& e, int r, int c0,
+                                            const float* v, double& tr, double& sq) {
+    if (r >= e.n) return;
+    float* Zr = a.Z[e.chain] + e.slab + (size_t)r * e.P + c0;
+    float* Ar = a.A[e.chain] + e.slab + (size_t)r * e.P + c0;
+    float z[W], ac[W];
+#pragma unroll
+    for (int i = 0; i < W / 4; ++i) {
+        const float4 zz = reinterpret_cast<const float4*>(Zr)[i];
+        const float4 aa = reinterpret_cast<const float4*>(Ar)[i];
+        z[4 * i + 0] = zz.x; z[4 * i + 1] = zz.y; z[4 * i + 2] = zz.z; z[4 * i + 3] = zz.w;
+        ac[4 * i + 0] = aa.x; ac[4 * i + 1] = aa.y; ac[4 * i + 2] = aa.z; ac[4 * i + 3] = aa.w;
+    }
+    float zn[W], an[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        zn[j] = fmaf(e.mul, v[j], e.L.bp * z[j]);
+        an[j] = fmaf(e.L.d, z[j], ac[j]);
+    }
+    if (!e.last) {
+#pragma unroll
+        for (int i = 0; i < W / 4; ++i) {
+            reinterpret_cast<float4*>(Zr)[i] = make_float4(zn[4 * i], zn[4 * i + 1], zn[4 * i + 2], zn[4 * i + 3]);
+            reinterpret_cast<float4*>(Ar)[i] = make_float4(an[4 * i], an[4 * i + 1], an[4 * i + 2], an[4 * i + 3]);
+        }
+        uint8_t* ob = a.opw[e.chain];
+        const float os = e.next_fmt == OP_F16X2 ? e.L.out_scale : 1.f;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int c = c0 + j;
+            if (c < e.n && r <= c) {
+                const float zs = zn[j] * os;
+                store_operand(e.next_fmt, ob, a.plane_elems, e.slab + (size_t)r * e.P + c, zs);
+                if (c != r) store_operand(e.next_fmt, ob, a.plane_elems, e.slab + (size_t)c * e.P + r, zs);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int c = c0 + j;
+            if (c < e.n && r <= c) {
+                const float g = an[j] + zn[j];
+                if (e.kind == CHAIN_FERMI && a.D) {
+                    float dv;
+                    if (e.flip) dv = (r == c ? (float)e.cdiag : 0.f) - g;
+                    else dv = g + (r == c ? (float)e.cdiag : 0.f);
+                    a.D[e.doff + (int64_t)r * e.n + c] = dv;
+                    if (c != r) a.D[e.doff + (int64_t)c * e.n + r] = dv;
+                }
+                const double gd = (double)g;
+                if (r == c) {
+                    tr += gd;
+                    sq += gd * gd;
+                } else {
+                    sq += 2.0 * gd * gd;
+                }
+            }
+        }
+    }
+}
+
+// `scaled_in`: the products were formed from power-of-two scaled FP16 operands.
+__device__ __forceinline__ void make_ctx(const LayerArgs& a, const Tile& t, int k, EpiCtx& e, bool scaled_in) {
+    const ftsp2_instance in = a.inst[t.inst];
+    const ftsp2_rescale_rec& rec = a.rec[t.inst];
+    const DevModel& M = a.models[rec.model];
+    e.n = in.n;
+    e.P = a.P;
+    e.chain = t.chain;
+    e.kind = a.chain_kind[t.chain];
+    e.flip = rec.flip;
+    e.last = a.last;
+    e.next_fmt = a.next_fmt;
+    e.slab = (size_t)t.inst * a.P * a.P;
+    e.doff = in.offset;
+    e.L = a.layers[(e.kind == CHAIN_ENTROPY ? M.offS : M.off) + k];
+    e.cdiag = rec.flip ? 1.0 - M.f0 : M.f0;
+    e.mul = scaled_in ? e.L.acc_mul : e.L.a;
+}
+
+}  // namespace ftsp2

@@ -1,0 +1,880 @@
+// C ABI of the ftsp2 library: model sets, workspace planning, the launch
+// sequence of the hot path, and the Levenberg-Marquardt driver of the
+// training path.  Host code only; kernels live in k_*.cu.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "ftsp2_internal.h"
+
+namespace ftsp2 {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------------------
+// device checks and the driver's tensor-map encoder
+// ------------------------------------------------------------------------------
+struct DeviceInfo {
+    int sms = 0;
+    int major = 0, minor = 0;
+};
+
+static ftsp2_status device_info(DeviceInfo& di) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FTSP2_E_CUDA;
+    static std::mutex mu;
+    static int cached_dev = -1;
+    static DeviceInfo cached;
+    std::lock_guard<std::mutex> lk(mu);
+    if (cached_dev != dev) {
+        cudaDeviceProp p;
+        if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return FTSP2_E_CUDA;
+        cached.sms = p.multiProcessorCount;
+        cached.major = p.major;
+        cached.minor = p.minor;
+        cached_dev = dev;
+    }
+    di = cached;
+    if (di.major != 10 || di.minor != 3) return FTSP2_E_UNSUPPORTED;
+    return FTSP2_OK;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2-D map over a stack of nb padded P x P slabs (rows = nb * P), element type
+// `dt`, box {box_k elements, box_rows rows}, 128-byte swizzle.
+static bool encode_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int esize, int P, int nb, int box_k,
+                       int box_rows) {
+    auto fn = encoder();
+    if (!fn) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)P, (cuuint64_t)nb * (cuuint64_t)P};
+    cuuint64_t gstride[1] = {(cuuint64_t)P * (cuuint64_t)esize};
+    cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, dt, 2, base, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------------------------
+// model sets
+// ------------------------------------------------------------------------------
+struct HostModel {
+    int L = 0, LS = 0;
+    double beta0 = 0, mu0 = 0, alpha = 0;
+    std::vector<double> th, thS;
+};
+
+}  // namespace ftsp2
+
+struct ftsp2_model_set {
+    std::vector<ftsp2::HostModel> host;
+    ftsp2::DevModel* d_models[2] = {nullptr, nullptr};   // [plain, fp16-scaled]
+    ftsp2::DevLayer* d_layers[2] = {nullptr, nullptr};
+    void* d_mem = nullptr;
+    int Lmax = 0;
+    int device = -1;
+};
+
+namespace ftsp2 {
+
+// Trajectory of the centre and the per-layer constants of one chain.
+// x0range: interval of layer-0 inputs the chain sees (subset of [0, 1]).
+static void chain_constants(const std::vector<double>& th, int L, double mu0, double lo, double hi, bool scaled,
+                            std::vector<DevLayer>& out, double& f0, float& scale0) {
+    std::vector<double> tau(L + 1);
+    tau[0] = mu0;
+    for (int k = 0; k < L; ++k) {
+        const double a = th[4 * k], b = th[4 * k + 1], c = th[4 * k + 2];
+        tau[k + 1] = a * tau[k] * tau[k] + b * tau[k] + c;
+    }
+    f0 = tau[L];
+    for (int k = 0; k < L; ++k) f0 += th[4 * k + 3] * tau[k];
+    // spectral radius bound of the centred state: max over inputs of |x_k - tau_k|
+    const int G = 20001;
+    std::vector<double> x(G);
+    for (int i = 0; i < G; ++i) x[i] = lo + (hi - lo) * (double)i / (G - 1);
+    std::vector<int> e(L + 1, 0);
+    for (int k = 0; k <= L; ++k) {
+        double m = 0.0;
+        for (int i = 0; i < G; ++i) m = std::max(m, std::fabs(x[i] - tau[k]));
+        if (scaled && m > 0.0) {
+            int ek = (int)std::floor(std::log2(16384.0 / (1.25 * m)));
+            e[k] = std::min(40, std::max(-20, ek));
+        }
+        if (k < L) {
+            const double a = th[4 * k], b = th[4 * k + 1], c = th[4 * k + 2];
+            for (int i = 0; i < G; ++i) x[i] = a * x[i] * x[i] + b * x[i] + c;
+        }
+    }
+    out.resize(L);
+    for (int k = 0; k < L; ++k) {
+        const double a = th[4 * k], b = th[4 * k + 1], d = th[4 * k + 3];
+        DevLayer dl;
+        dl.a = (float)a;
+        dl.acc_mul = (float)(a * std::ldexp(1.0, -2 * e[k]));
+        dl.bp = (float)(b + 2.0 * a * tau[k]);
+        dl.d = (float)d;
+        dl.in_scale = (float)std::ldexp(1.0, e[k]);
+        dl.out_scale = (float)std::ldexp(1.0, e[k + 1]);
+        dl.pad0 = dl.pad1 = 0.f;
+        out[k] = dl;
+    }
+    scale0 = (float)std::ldexp(1.0, e[0]);
+}
+
+static ftsp2_status upload_models(ftsp2_model_set* s) {
+    const int nm = (int)s->host.size();
+    std::vector<DevModel> dm[2];
+    std::vector<DevLayer> dl[2];
+    for (int v = 0; v < 2; ++v) {
+        const bool scaled = v == 1;
+        for (int m = 0; m < nm; ++m) {
+            const HostModel& h = s->host[m];
+            DevModel M;
+            M.beta0 = h.beta0;
+            M.mu0 = h.mu0;
+            M.alpha = h.alpha;
+            M.L = h.L;
+            M.LS = h.LS;
+            std::vector<DevLayer> lf, ls;
+            chain_constants(h.th, h.L, h.mu0, 0.0, 1.0, scaled, lf, M.f0, M.scale0);
+            const double ylo = h.mu0 + h.alpha * (0.0 - h.mu0), yhi = h.mu0 + h.alpha * (1.0 - h.mu0);
+            chain_constants(h.thS.empty() ? h.th : h.thS, h.LS, h.mu0, std::min(ylo, yhi), std::max(ylo, yhi),
+                            scaled, ls, M.g0, M.scale0S);
+            M.off = (int)dl[v].size();
+            dl[v].insert(dl[v].end(), lf.begin(), lf.end());
+            M.offS = (int)dl[v].size();
+            dl[v].insert(dl[v].end(), ls.begin(), ls.end());
+            dm[v].push_back(M);
+        }
+    }
+    const size_t bm = sizeof(DevModel) * nm, bl = sizeof(DevLayer) * dl[0].size();
+    const size_t total = 2 * (bm + bl) + 256;
+    if (cudaMalloc(&s->d_mem, total) != cudaSuccess) return FTSP2_E_CUDA;
+    uint8_t* p = static_cast<uint8_t*>(s->d_mem);
+    for (int v = 0; v < 2; ++v) {
+        s->d_models[v] = reinterpret_cast<DevModel*>(p);
+        p += bm;
+        s->d_layers[v] = reinterpret_cast<DevLayer*>(p);
+        p += bl;
+        if (cudaMemcpy(s->d_models[v], dm[v].data(), bm, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(s->d_layers[v], dl[v].data(), bl, cudaMemcpyHostToDevice) != cudaSuccess)
+            return FTSP2_E_CUDA;
+    }
+    cudaGetDevice(&s->device);
+    return FTSP2_OK;
+}
+
+// Table printed in the paper's Appendix A (beta0 = 1500, mu0 = 1/3):
+// rows (a, b, c, d) of Eq. mlsp2.
+static const double kPrinted[26][4] = {
+    {-1.353996666080607e+00, +2.437540893737664e+00, -2.038466804171965e-01, +1.291156147536192e-11},
+    {+1.608677030263155e+00, -2.987544634415441e-01, -6.746741346599809e-02, -7.006084032292678e-12},
+    {-2.351636735892118e+00, +2.613813908880740e+00, -2.081115324436639e-03, -6.572840812953572e-13},
+    {+1.810031371507046e+00, -3.733036049410451e-02, -5.442179841399564e-02, +4.318503541775794e-11},
+    {-2.732204264661287e+00, +2.825886342002125e+00, +8.167975559885774e-03, -1.662456055798004e-11},
+    {-1.873987421378235e+00, +2.138798318408699e+00, +3.573114610928145e-02, +4.542623791264443e-12},
+    {+1.402261079424850e+00, +4.890736627204146e-02, -4.237220339751432e-02, +2.424648524635838e-11},
+    {+1.713089400763156e+00, -1.034037621506357e-01, -2.438094942357169e-02, +7.873381643056254e-11},
+    {-3.252595736449542e+00, +2.628649626717414e+00, +3.165347918592593e-02, -6.312379678783267e-11},
+    {-1.878046620274372e+00, +2.074880349608742e+00, +3.449163838903798e-02, -6.649574392039178e-11},
+    {+1.310464008049612e+00, +5.496499701340592e-02, +3.310087064751345e-03, +2.825980776677432e-10},
+    {+1.563608995897714e+00, -8.606990671650539e-03, -1.301065468049911e-02, -1.424083924407828e-07},
+    {-3.038983738437103e+00, +2.477686862799397e+00, +2.636871201950337e-02, -1.330100571490071e-07},
+    {-1.699377329573085e+00, +2.076565284757246e+00, +3.442469802192470e-02, +4.896446563691430e-03},
+    {+1.256940670391469e+00, +5.777573303514125e-02, +4.902596975631270e-02, -2.302054912581413e-03},
+    {-1.390281989291434e+00, +1.966243706278270e+00, +1.910503489826946e-02, +1.606259300834474e-02},
+    {+1.172415492052006e+00, +2.982302801604828e-02, +4.530045685625948e-02, -1.539021333689731e-02},
+    {+1.351448045975672e+00, +5.773064380022182e-02, +3.753306163777001e-02, -1.276795931125504e-01},
+    {-1.212734900653146e+00, +1.861660915086903e+00, +1.242573869144004e-02, -1.100276149057915e-01},
+    {+8.610663421144649e-01, +1.048747203546148e-02, +4.701135000272372e-02, -4.946843804326570e-02},
+    {-1.369173339062334e+00, +1.699077704335121e+00, -7.732969926664974e-03, -1.761228530611925e-01},
+    {-1.452079661340262e+00, +1.993171071701545e+00, -1.661115887219701e-02, -5.688902388963853e-01},
+    {+1.347262922911275e+00, +2.198074427424086e-02, +1.995615256168758e-01, +5.964487309001580e-01},
+    {-1.114238353358810e+00, +1.896937623313116e+00, -7.280733281872145e-02, +1.530915295291056e+00},
+    {+9.411010738180853e-01, -1.554719335561439e-01, +6.584253835393120e-02, -2.059339861429303e-01},
+    {+8.321693583250559e-01, +5.698259888759222e-01, -4.234806053199446e-01, +5.698259888760550e-01},
+};
+
+// ------------------------------------------------------------------------------
+// workspace planning
+// ------------------------------------------------------------------------------
+static int fmt_of_mode(int mode) {
+    switch (mode) {
+        case FTSP2_FP16X2: return OP_F16X2;
+        case FTSP2_BF16X3: return OP_BF16X3;
+        case FTSP2_TF32X3: return OP_TF32X3;
+        default: return OP_F32;
+    }
+}
+static int op_bytes(int fmt) {
+    switch (fmt) {
+        case OP_F16X2: return 4;
+        case OP_BF16X3: return 6;
+        case OP_TF32X3: return 8;
+        default: return 4;
+    }
+}
+static int refine_layers(int flags) { return (flags & FTSP2_REFINE2) ? 2 : ((flags & FTSP2_REFINE1) ? 1 : 0); }
+
+static int host_tiles_of(int n, int BN) {
+    const int q = BN / kTileM;
+    const int nI = (n + kTileM - 1) / kTileM;
+    const int nJ = (n + BN - 1) / BN;
+    int c = 0;
+    for (int J = 0; J < nJ; ++J) c += std::min(q * (J + 1), nI);
+    return c;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want, int flags, Layout& L) {
+    if (!inst || nb < 1) return FTSP2_E_ARG;
+    if (mode < FTSP2_FP32 || mode > FTSP2_FP16X2) return FTSP2_E_ARG;
+    if (want < 1 || want > 3) return FTSP2_E_ARG;
+    int maxn = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (inst[b].n < 1 || inst[b].offset < 0) return FTSP2_E_ARG;
+        maxn = std::max(maxn, inst[b].n);
+    }
+    const int P = (int)align_up((size_t)maxn, kPad);
+    const int nch = want == 3 ? 2 : 1;
+    const bool simt_main = mode == FTSP2_FP32;
+    const int BN = simt_main ? 128 : tc_block_n(mode);
+    const bool refine = !simt_main && refine_layers(flags) > 0;
+    long long nt = 0, ntr = 0;
+    for (int b = 0; b < nb; ++b) {
+        nt += host_tiles_of(inst[b].n, BN);
+        if (refine) ntr += host_tiles_of(inst[b].n, 128);
+    }
+    nt *= nch;
+    ntr *= nch;
+    if (nt > (1ll << 30)) return FTSP2_E_ARG;
+    L.P = P;
+    L.nb = nb;
+    L.nchains = nch;
+    L.ntiles = (int)nt;
+    L.ntiles_ref = (int)ntr;
+    L.BN = BN;
+    L.plane_elems = (size_t)nb * P * P;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 1024);
+        return o;
+    };
+    L.status = take(256);
+    L.inst_work = take(sizeof(InstWork) * nb);
+    L.tiles = take(sizeof(Tile) * nt);
+    L.tiles_ref = refine ? take(sizeof(Tile) * ntr) : 0;
+    L.partials = take(sizeof(double) * 8 * std::max<long long>(nt, ntr));
+    const int fmt = fmt_of_mode(mode);
+    for (int c = 0; c < kMaxChains; ++c) {
+        L.Z[c] = L.A[c] = L.OP[c][0] = L.OP[c][1] = L.OPR[c][0] = L.OPR[c][1] = 0;
+    }
+    for (int c = 0; c < nch; ++c) {
+        L.Z[c] = take(4 * L.plane_elems);
+        L.A[c] = take(4 * L.plane_elems);
+        L.OP[c][0] = take((size_t)op_bytes(fmt) * L.plane_elems);
+        L.OP[c][1] = take((size_t)op_bytes(fmt) * L.plane_elems);
+        if (refine) {
+            L.OPR[c][0] = take(4 * L.plane_elems);
+            L.OPR[c][1] = take(4 * L.plane_elems);
+        }
+    }
+    L.total = off;
+    return FTSP2_OK;
+}
+
+static ftsp2_status from_cuda(cudaError_t e) { return e == cudaSuccess ? FTSP2_OK : FTSP2_E_CUDA; }
+
+// The launch sequence of (a1)-(a6).
+static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp2_instance* dInst, int nb,
+                        const ftsp2_model_set* set, int mode, int flags, int want, float* dD, double* dTrace,
+                        double* dS, ftsp2_rescale_rec* dRec, void* ws, size_t ws_bytes, void* stream) {
+    if (!set || set->host.empty()) return FTSP2_E_NOMODEL;
+    if (!dH || !dInst || !dRec || !ws) return FTSP2_E_ARG;
+    if ((want & 1) && !dD && !dTrace) return FTSP2_E_ARG;
+    if ((want & 2) && !dS) return FTSP2_E_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % 1024 != 0) return FTSP2_E_WORKSPACE;
+    DeviceInfo di;
+    ftsp2_status st = device_info(di);
+    if (st != FTSP2_OK) return st;
+    Layout L;
+    st = plan(inst, nb, mode, want, flags, L);
+    if (st != FTSP2_OK) return st;
+    if (ws_bytes < L.total) return FTSP2_E_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t* W = static_cast<uint8_t*>(ws);
+    const bool scaled = mode == FTSP2_FP16X2;
+    const DevModel* models = set->d_models[scaled ? 1 : 0];
+    const DevLayer* layers = set->d_layers[scaled ? 1 : 0];
+    const int Lmax = set->Lmax;
+    const int R = mode == FTSP2_FP32 ? 0 : refine_layers(flags);
+    const int refine_from = Lmax - R;       // global layers >= this run in FP32
+    const bool all_simt = mode == FTSP2_FP32;
+    const int fmt = fmt_of_mode(mode);
+    int maxn = 0;
+    for (int b = 0; b < nb; ++b) maxn = std::max(maxn, inst[b].n);
+
+    int kinds[kMaxChains] = {CHAIN_FERMI, CHAIN_ENTROPY};
+    if (want == 2) kinds[0] = CHAIN_ENTROPY;
+
+    int* dstatus = reinterpret_cast<int*>(W + L.status);
+    InstWork* iw = reinterpret_cast<InstWork*>(W + L.inst_work);
+    Tile* tiles = reinterpret_cast<Tile*>(W + L.tiles);
+    Tile* tiles_ref = L.ntiles_ref ? reinterpret_cast<Tile*>(W + L.tiles_ref) : nullptr;
+    double* partials = reinterpret_cast<double*>(W + L.partials);
+
+    SetupArgs sa;
+    sa.H = dH;
+    sa.inst = dInst;
+    sa.nb = nb;
+    sa.P = L.P;
+    sa.Lmax = Lmax;
+    sa.nchains = L.nchains;
+    sa.BN = L.BN;
+    sa.BN_ref = 128;
+    sa.models = models;
+    sa.nmodels = (int)set->host.size();
+    sa.flags = flags;
+    sa.chain_kind[0] = kinds[0];
+    sa.chain_kind[1] = kinds[1];
+    sa.iw = iw;
+    sa.tiles = tiles;
+    sa.tiles_ref = tiles_ref;
+    sa.rec = dRec;
+    sa.status = dstatus;
+    launch_prep(sa, s);
+    launch_gershgorin(sa, maxn, s);
+    launch_decide(sa, s);
+
+    InitArgs ia;
+    ia.H = dH;
+    ia.inst = dInst;
+    ia.rec = dRec;
+    ia.models = models;
+    ia.iw = iw;
+    ia.nb = nb;
+    ia.P = L.P;
+    ia.nchains = L.nchains;
+    ia.plane_elems = L.plane_elems;
+    ia.main_fmt = fmt;
+    ia.refine_from = all_simt ? 0 : refine_from;
+    for (int c = 0; c < kMaxChains; ++c) {
+        ia.chain_kind[c] = kinds[c];
+        ia.Z[c] = c < L.nchains ? reinterpret_cast<float*>(W + L.Z[c]) : nullptr;
+        ia.A[c] = c < L.nchains ? reinterpret_cast<float*>(W + L.A[c]) : nullptr;
+        for (int p = 0; p < 2; ++p) {
+            ia.OP[c][p] = c < L.nchains ? W + L.OP[c][p] : nullptr;
+            ia.OPR[c][p] = (c < L.nchains && L.OPR[c][p]) ? reinterpret_cast<float*>(W + L.OPR[c][p]) : nullptr;
+        }
+    }
+    launch_init(ia, maxn, s);
+
+    // tensor maps of both parities (tensor-core layers only)
+    TmaMaps maps[2];
+    if (!all_simt && refine_from > 0) {
+        const CUtensorMapDataType dt = fmt == OP_F16X2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                       : fmt == OP_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        const int es = fmt == OP_TF32X3 ? 4 : 2;
+        const int nsplit = fmt == OP_BF16X3 ? 3 : 2;
+        const int bke = 128 / es;
+        std::memset(maps, 0, sizeof(maps));
+        for (int p = 0; p < 2; ++p)
+            for (int c = 0; c < L.nchains; ++c)
+                for (int sp = 0; sp < nsplit; ++sp) {
+                    void* base = W + L.OP[c][p] + (size_t)sp * es * L.plane_elems;
+                    if (!encode_map(&maps[p].a[c][sp], base, dt, es, L.P, nb, bke, kTileM) ||
+                        !encode_map(&maps[p].b[c][sp], base, dt, es, L.P, nb, bke, L.BN))
+                        return FTSP2_E_CUDA;
+                }
+    }
+
+    LayerArgs la;
+    std::memset(&la, 0, sizeof(la));
+    la.inst = dInst;
+    la.rec = dRec;
+    la.iw = iw;
+    la.models = models;
+    la.layers = layers;
+    la.P = L.P;
+    la.Lmax = Lmax;
+    la.nchains = L.nchains;
+    la.plane_elems = L.plane_elems;
+    la.D = dD;
+    la.partials = partials;
+    la.status = dstatus;
+    for (int c = 0; c < kMaxChains; ++c) {
+        la.chain_kind[c] = kinds[c];
+        la.Z[c] = c < L.nchains ? reinterpret_cast<float*>(W + L.Z[c]) : nullptr;
+        la.A[c] = c < L.nchains ? reinterpret_cast<float*>(W + L.A[c]) : nullptr;
+    }
+    auto is_simt = [&](int g) { return all_simt || g >= refine_from; };
+    int last_table = 0;
+    for (int g = 0; g < Lmax; ++g) {
+        const bool simt = is_simt(g);
+        const bool next_simt = g + 1 < Lmax && is_simt(g + 1);
+        la.gl = g;
+        la.last = g == Lmax - 1;
+        la.next_fmt = next_simt ? OP_F32 : fmt;
+        for (int c = 0; c < L.nchains; ++c) {
+            const int rp = g & 1, wp = (g + 1) & 1;
+            if (simt) la.opr[c] = all_simt ? W + L.OP[c][rp] : W + L.OPR[c][rp];
+            else la.opr[c] = W + L.OP[c][rp];
+            if (next_simt) la.opw[c] = all_simt ? W + L.OP[c][wp] : W + L.OPR[c][wp];
+            else la.opw[c] = W + L.OP[c][wp];
+        }
+        if (dD == nullptr && la.last) la.D = nullptr;
+        cudaError_t e;
+        if (simt) {
+            const bool use_ref = !all_simt;
+            la.tiles = use_ref ? tiles_ref : tiles;
+            la.ntiles = use_ref ? L.ntiles_ref : L.ntiles;
+            const int grid = std::max(1, std::min(la.ntiles, di.sms * 4));
+            e = launch_layer_simt(la, grid, s);
+            last_table = use_ref ? 1 : 0;
+        } else {
+            la.tiles = tiles;
+            la.ntiles = L.ntiles;
+            const int grid = std::max(1, std::min(la.ntiles, di.sms));
+            e = launch_layer_tc(mode, la, maps[g & 1], grid, s);
+            last_table = 0;
+        }
+        if (e != cudaSuccess) return FTSP2_E_CUDA;
+    }
+    FinalArgs fa;
+    fa.inst = dInst;
+    fa.rec = dRec;
+    fa.models = models;
+    fa.iw = iw;
+    fa.partials = partials;
+    fa.table = last_table;
+    fa.nb = nb;
+    fa.nchains = L.nchains;
+    fa.chain_kind[0] = kinds[0];
+    fa.chain_kind[1] = kinds[1];
+    fa.trace = (want & 1) ? dTrace : nullptr;
+    fa.S = (want & 2) ? dS : nullptr;
+    fa.status = dstatus;
+    launch_finalize(fa, s);
+    if (cudaGetLastError() != cudaSuccess) return FTSP2_E_CUDA;
+    if (flags & FTSP2_SYNC) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return FTSP2_E_CUDA;
+        std::vector<ftsp2_rescale_rec> h(nb);
+        if (cudaMemcpy(h.data(), dRec, sizeof(ftsp2_rescale_rec) * nb, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return FTSP2_E_CUDA;
+        int worst = FTSP2_OK;
+        for (auto& r : h)
+            if (r.status != FTSP2_OK) worst = r.status;
+        return (ftsp2_status)worst;
+    }
+    return FTSP2_OK;
+}
+
+// ------------------------------------------------------------------------------
+// training driver
+// ------------------------------------------------------------------------------
+struct TrainLayout {
+    size_t M, R, Rh, G, part, apart, v, out, amax;
+    size_t total;
+    int nchunks;
+};
+
+static TrainLayout train_layout(int ns, int L) {
+    TrainLayout t;
+    const int np = 4 * L, m = np + 1;
+    t.nchunks = 64;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    t.M = take(sizeof(double) * (size_t)m * ns);
+    t.R = take(sizeof(double) * ns);
+    t.Rh = take(sizeof(double) * ns);
+    t.G = take(sizeof(double) * (size_t)m * m);
+    t.part = take(sizeof(double) * (size_t)t.nchunks * m * m);
+    t.apart = take(sizeof(double) * (size_t)((ns + 255) / 256) * np);
+    t.v = take(sizeof(double) * np);
+    t.out = take(sizeof(double) * np);
+    t.amax = take(sizeof(double) * 80);
+    t.total = off;
+    return t;
+}
+
+// Cholesky solve of (A) x = b for a symmetric positive definite A (n x n, FP64).
+static bool chol_solve(std::vector<double> A, int n, const std::vector<double>& b, std::vector<double>& x) {
+    for (int j = 0; j < n; ++j) {
+        double d = A[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+        if (!(d > 0.0) || !std::isfinite(d)) return false;
+        d = std::sqrt(d);
+        A[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double s = A[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) s -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+            A[(size_t)i * n + j] = s / d;
+        }
+    }
+    x = b;
+    for (int i = 0; i < n; ++i) {
+        double s = x[i];
+        for (int k = 0; k < i; ++k) s -= A[(size_t)i * n + k] * x[k];
+        x[i] = s / A[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int k = i + 1; k < n; ++k) s -= A[(size_t)k * n + i] * x[k];
+        x[i] = s / A[(size_t)i * n + i];
+    }
+    return true;
+}
+
+}  // namespace ftsp2
+
+using namespace ftsp2;
+
+extern "C" {
+
+const char* ftsp2_status_string(ftsp2_status s) {
+    switch (s) {
+        case FTSP2_OK: return "ok";
+        case FTSP2_E_ARG: return "invalid argument";
+        case FTSP2_E_CUDA: return "CUDA error";
+        case FTSP2_E_WORKSPACE: return "workspace too small or misaligned";
+        case FTSP2_E_VALIDITY: return "beta' outside every model's region of validity";
+        case FTSP2_E_NONFINITE: return "non-finite input or result";
+        case FTSP2_E_TIMEOUT: return "device-side wait timed out";
+        case FTSP2_E_NOMODEL: return "no model";
+        case FTSP2_E_UNSUPPORTED: return "unsupported device or mode";
+    }
+    return "unknown status";
+}
+
+uint64_t ftsp2_kernel_launch_count(void) { return g_launches.load(); }
+
+ftsp2_status ftsp2_model_set_create(const ftsp2_table* tabs, int ntab, ftsp2_model_set** out) {
+    if (!out) return FTSP2_E_ARG;
+    *out = nullptr;
+    if (!tabs || ntab < 1) return FTSP2_E_NOMODEL;
+    auto* s = new ftsp2_model_set();
+    for (int i = 0; i < ntab; ++i) {
+        const ftsp2_table& t = tabs[i];
+        const int LS = t.theta_entropy ? t.L_entropy : t.L;
+        if (t.L < 1 || t.L > kMaxLayers || LS < 1 || LS > kMaxLayers || !t.theta || !(t.beta0 > 0) ||
+            !(t.mu0 > 0 && t.mu0 < 1) || !std::isfinite(t.alpha)) {
+            delete s;
+            return FTSP2_E_ARG;
+        }
+        HostModel h;
+        h.L = t.L;
+        h.LS = LS;
+        h.beta0 = t.beta0;
+        h.mu0 = t.mu0;
+        h.alpha = t.alpha;
+        h.th.assign(t.theta, t.theta + 4 * t.L);
+        if (t.theta_entropy) h.thS.assign(t.theta_entropy, t.theta_entropy + 4 * LS);
+        for (double v : h.th)
+            if (!std::isfinite(v)) { delete s; return FTSP2_E_ARG; }
+        for (double v : h.thS)
+            if (!std::isfinite(v)) { delete s; return FTSP2_E_ARG; }
+        s->Lmax = std::max(s->Lmax, std::max(h.L, h.LS));
+        s->host.push_back(std::move(h));
+    }
+    const ftsp2_status st = upload_models(s);
+    if (st != FTSP2_OK) {
+        ftsp2_model_set_destroy(s);
+        return st;
+    }
+    *out = s;
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_model_set_builtin(ftsp2_model_set** out) {
+    ftsp2_table t;
+    t.L = 26;
+    t.L_entropy = 0;
+    t.beta0 = 1500.0;
+    t.mu0 = 1.0 / 3.0;
+    t.alpha = 0.842704;
+    t.theta = &kPrinted[0][0];
+    t.theta_entropy = nullptr;
+    return ftsp2_model_set_create(&t, 1, out);
+}
+
+void ftsp2_model_set_destroy(ftsp2_model_set* s) {
+    if (!s) return;
+    if (s->d_mem) cudaFree(s->d_mem);
+    delete s;
+}
+
+ftsp2_status ftsp2_model_set_info(const ftsp2_model_set* s, int* ntab, int* max_layers) {
+    if (!s) return FTSP2_E_ARG;
+    if (ntab) *ntab = (int)s->host.size();
+    if (max_layers) *max_layers = s->Lmax;
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_workspace_size(const ftsp2_instance* inst, int nb, ftsp2_mode mode, int want, size_t* bytes) {
+    if (!bytes) return FTSP2_E_ARG;
+    Layout L;
+    // sized for the largest refinement setting so one workspace serves every flag
+    const ftsp2_status st = plan(inst, nb, mode, want, FTSP2_REFINE2, L);
+    if (st != FTSP2_OK) return st;
+    *bytes = L.total;
+    return FTSP2_OK;
+}
+
+static size_t rescale_ws_bytes(int nb) { return 1024 + align_up(sizeof(InstWork) * (size_t)nb, 1024); }
+
+ftsp2_status ftsp2_rescale_workspace_size(int nb, size_t* bytes) {
+    if (!bytes || nb < 1) return FTSP2_E_ARG;
+    *bytes = rescale_ws_bytes(nb);
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_rescale(const double* dH, const ftsp2_instance* inst, const ftsp2_instance* dInst, int nb,
+                           const ftsp2_model_set* set, int flags, ftsp2_rescale_rec* dRec, void* ws,
+                           size_t ws_bytes, void* stream) {
+    if (!set || set->host.empty()) return FTSP2_E_NOMODEL;
+    if (!dH || !inst || !dInst || !dRec || nb < 1 || !ws) return FTSP2_E_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % 1024 != 0 || ws_bytes < rescale_ws_bytes(nb)) return FTSP2_E_WORKSPACE;
+    DeviceInfo di;
+    ftsp2_status st = device_info(di);
+    if (st != FTSP2_OK) return st;
+    int maxn = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (inst[b].n < 1 || inst[b].offset < 0) return FTSP2_E_ARG;
+        maxn = std::max(maxn, inst[b].n);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t* W = static_cast<uint8_t*>(ws);
+    SetupArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
+    sa.H = dH;
+    sa.inst = dInst;
+    sa.nb = nb;
+    sa.Lmax = set->Lmax;
+    sa.nchains = 1;
+    sa.BN = 128;
+    sa.models = set->d_models[0];
+    sa.nmodels = (int)set->host.size();
+    sa.flags = flags;
+    sa.chain_kind[0] = CHAIN_FERMI;
+    sa.iw = reinterpret_cast<InstWork*>(W + 1024);
+    sa.tiles = nullptr;
+    sa.tiles_ref = nullptr;
+    sa.rec = dRec;
+    sa.status = reinterpret_cast<int*>(W);
+    launch_prep(sa, s);
+    launch_gershgorin(sa, maxn, s);
+    launch_decide(sa, s);
+    if (cudaGetLastError() != cudaSuccess) return FTSP2_E_CUDA;
+    if (flags & FTSP2_SYNC) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return FTSP2_E_CUDA;
+        std::vector<ftsp2_rescale_rec> h(nb);
+        if (cudaMemcpy(h.data(), dRec, sizeof(ftsp2_rescale_rec) * nb, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return FTSP2_E_CUDA;
+        int worst = FTSP2_OK;
+        for (auto& r : h)
+            if (r.status != FTSP2_OK) worst = r.status;
+        return (ftsp2_status)worst;
+    }
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_density(const double* dH, const ftsp2_instance* inst, const ftsp2_instance* dInst, int nb,
+                           const ftsp2_model_set* set, ftsp2_mode mode, int flags, float* dD, double* dTrace,
+                           ftsp2_rescale_rec* dRec, void* ws, size_t ws_bytes, void* stream) {
+    return run(dH, inst, dInst, nb, set, mode, flags, 1, dD, dTrace, nullptr, dRec, ws, ws_bytes, stream);
+}
+
+ftsp2_status ftsp2_entropy(const double* dH, const ftsp2_instance* inst, const ftsp2_instance* dInst, int nb,
+                           const ftsp2_model_set* set, ftsp2_mode mode, int flags, double* dS,
+                           ftsp2_rescale_rec* dRec, void* ws, size_t ws_bytes, void* stream) {
+    return run(dH, inst, dInst, nb, set, mode, flags, 2, nullptr, nullptr, dS, dRec, ws, ws_bytes, stream);
+}
+
+ftsp2_status ftsp2_density_entropy(const double* dH, const ftsp2_instance* inst, const ftsp2_instance* dInst,
+                                   int nb, const ftsp2_model_set* set, ftsp2_mode mode, int flags, float* dD,
+                                   double* dTrace, double* dS, ftsp2_rescale_rec* dRec, void* ws, size_t ws_bytes,
+                                   void* stream) {
+    if (!dS) return ftsp2_density(dH, inst, dInst, nb, set, mode, flags, dD, dTrace, dRec, ws, ws_bytes, stream);
+    if (!dD && !dTrace)
+        return ftsp2_entropy(dH, inst, dInst, nb, set, mode, flags, dS, dRec, ws, ws_bytes, stream);
+    return run(dH, inst, dInst, nb, set, mode, flags, 3, dD, dTrace, dS, dRec, ws, ws_bytes, stream);
+}
+
+size_t ftsp2_train_workspace_size(int nsamples, int L) {
+    if (nsamples < 1 || L < 1 || L > kMaxLayers) return 0;
+    return train_layout(nsamples, L).total;
+}
+
+static ftsp2_status load_theta(int L, const double* theta, ThetaParam& tp) {
+    if (!theta || L < 1 || L > kMaxLayers) return FTSP2_E_ARG;
+    std::memset(&tp, 0, sizeof(tp));
+    for (int i = 0; i < 4 * L; ++i) {
+        if (!std::isfinite(theta[i])) return FTSP2_E_ARG;
+        tp.v[i] = theta[i];
+    }
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_train_residual_jacobian(int target, double beta0, double mu0, int L, double alpha,
+                                           const double* theta, const double* dX, int nsamples, double* dR,
+                                           double* dJ, void* stream) {
+    // dJ: the augmented parameter-major Jacobian M
+    if ((target != FTSP2_TARGET_FERMI && target != FTSP2_TARGET_ENTROPY) || !dX || !dR || nsamples < 1)
+        return FTSP2_E_ARG;
+    ThetaParam tp;
+    ftsp2_status st = load_theta(L, theta, tp);
+    if (st != FTSP2_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = dJ ? launch_train_fwd_jac(target, beta0, mu0, L, alpha, tp, dX, nsamples, dR, dJ, s)
+                       : launch_train_residual(target, beta0, mu0, L, alpha, tp, dX, nsamples, dR, s);
+    return from_cuda(e);
+}
+
+ftsp2_status ftsp2_train_normal_equations(const double* dM, int nsamples, int L, double* dG, void* dWork,
+                                          size_t work_bytes, void* stream) {
+    if (!dM || !dG || !dWork || nsamples < 1 || L < 1 || L > kMaxLayers) return FTSP2_E_ARG;
+    const TrainLayout tl = train_layout(nsamples, L);
+    if (work_bytes < tl.total) return FTSP2_E_WORKSPACE;
+    double* dPart = reinterpret_cast<double*>(static_cast<uint8_t*>(dWork) + tl.part);
+    return from_cuda(launch_train_gram(dM, nsamples, 4 * L, dG, dPart, tl.nchunks, static_cast<cudaStream_t>(stream)));
+}
+
+ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, double alpha, const double* dX,
+                                int nsamples, int iterations, int accel, const double* theta_init,
+                                double* theta_out, ftsp2_train_report* rep, void* dWork, size_t work_bytes,
+                                void* stream) {
+    if ((target != FTSP2_TARGET_FERMI && target != FTSP2_TARGET_ENTROPY) || !dX || nsamples < 1 || !theta_out ||
+        !dWork || iterations < 0)
+        return FTSP2_E_ARG;
+    ThetaParam tp;
+    ftsp2_status st = load_theta(L, theta_init, tp);
+    if (st != FTSP2_OK) return st;
+    const TrainLayout tl = train_layout(nsamples, L);
+    if (work_bytes < tl.total) return FTSP2_E_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t* W = static_cast<uint8_t*>(dWork);
+    double* dM = reinterpret_cast<double*>(W + tl.M);
+    double* dRr = reinterpret_cast<double*>(W + tl.R);
+    double* dRh = reinterpret_cast<double*>(W + tl.Rh);
+    double* dG = reinterpret_cast<double*>(W + tl.G);
+    double* dPart = reinterpret_cast<double*>(W + tl.part);
+    double* dAp = reinterpret_cast<double*>(W + tl.apart);
+    double* dV = reinterpret_cast<double*>(W + tl.v);
+    double* dOut = reinterpret_cast<double*>(W + tl.out);
+    double* dAm = reinterpret_cast<double*>(W + tl.amax);
+    const int np = 4 * L, m = np + 1;
+    std::vector<double> G((size_t)m * m), Gc((size_t)m * m);
+
+    auto eval = [&](const ThetaParam& t, std::vector<double>& g) -> ftsp2_status {
+        if (launch_train_fwd_jac(target, beta0, mu0, L, alpha, t, dX, nsamples, dRr, dM, s) != cudaSuccess)
+            return FTSP2_E_CUDA;
+        if (launch_train_gram(dM, nsamples, np, dG, dPart, tl.nchunks, s) != cudaSuccess) return FTSP2_E_CUDA;
+        if (cudaMemcpyAsync(g.data(), dG, sizeof(double) * m * m, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return FTSP2_E_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return FTSP2_E_CUDA;
+        return FTSP2_OK;
+    };
+
+    st = eval(tp, G);
+    if (st != FTSP2_OK) return st;
+    double cost = 0.5 * G[(size_t)np * m + np];
+    const double cost0 = cost;
+    double lam = 1e-3;
+    int accepted = 0, it = 0;
+    const double h = 0.1;
+    std::vector<double> JTJ((size_t)np * np), g(np), Md((size_t)np * np), v, a, rhs(np);
+    for (it = 0; it < iterations; ++it) {
+        for (int i = 0; i < np; ++i) {
+            for (int j = 0; j < np; ++j) JTJ[(size_t)i * np + j] = G[(size_t)i * m + j];
+            g[i] = G[(size_t)i * m + np];
+        }
+        Md = JTJ;
+        for (int i = 0; i < np; ++i) Md[(size_t)i * np + i] += lam * JTJ[(size_t)i * np + i];
+        for (int i = 0; i < np; ++i) rhs[i] = -g[i];
+        if (!chol_solve(Md, np, rhs, v)) {
+            lam = std::min(lam * 10.0, 1e12);
+            continue;
+        }
+        ThetaParam cand = tp;
+        std::vector<double> step = v;
+        if (accel) {
+            ThetaParam th_h = tp;
+            for (int i = 0; i < np; ++i) th_h.v[i] += h * v[i];
+            if (launch_train_residual(target, beta0, mu0, L, alpha, th_h, dX, nsamples, dRh, s) != cudaSuccess ||
+                cudaMemcpyAsync(dV, v.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                launch_train_accel(dM, dV, dRh, h, nsamples, np, dAp, dOut, s) != cudaSuccess ||
+                cudaMemcpyAsync(rhs.data(), dOut, sizeof(double) * np, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return FTSP2_E_CUDA;
+            for (int i = 0; i < np; ++i) rhs[i] = -rhs[i];
+            if (chol_solve(Md, np, rhs, a)) {
+                double na = 0, nv = 0;
+                for (int i = 0; i < np; ++i) {
+                    na += a[i] * a[i];
+                    nv += v[i] * v[i];
+                }
+                if (2.0 * std::sqrt(na) <= 0.75 * std::sqrt(nv))
+                    for (int i = 0; i < np; ++i) step[i] = v[i] + 0.5 * a[i];
+            }
+        }
+        for (int i = 0; i < np; ++i) cand.v[i] += step[i];
+        st = eval(cand, Gc);
+        if (st != FTSP2_OK) return st;
+        const double cc = 0.5 * Gc[(size_t)np * m + np];
+        if (std::isfinite(cc) && cc < cost) {
+            tp = cand;
+            G.swap(Gc);
+            cost = cc;
+            lam = std::max(lam / 10.0, 1e-12);
+            ++accepted;
+        } else {
+            lam = std::min(lam * 10.0, 1e12);
+        }
+    }
+    // residuals at the final table and their max
+    if (launch_train_residual(target, beta0, mu0, L, alpha, tp, dX, nsamples, dRr, s) != cudaSuccess ||
+        launch_train_absmax(dRr, nsamples, dAm + 8, dAm, s) != cudaSuccess)
+        return FTSP2_E_CUDA;
+    double mx = 0;
+    if (cudaMemcpyAsync(&mx, dAm, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return FTSP2_E_CUDA;
+    for (int i = 0; i < np; ++i) theta_out[i] = tp.v[i];
+    if (rep) {
+        rep->iterations = it;
+        rep->accepted = accepted;
+        rep->cost0 = cost0;
+        rep->cost = cost;
+        rep->max_err = mx;
+        rep->lambda = lam;
+    }
+    return FTSP2_OK;
+}
+
+}  // extern "C"

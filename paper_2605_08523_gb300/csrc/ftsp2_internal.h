@@ -1,0 +1,266 @@
+// Internal declarations shared by the ftsp2 CUDA translation units.
+//
+// Centred recursion.  Every matrix chain is run in the variable
+// Z_k = X_k - tau_k I, where tau_k is the image of the model's mu0 under the
+// first k layers of the scalar recursion (tau_0 = mu0).  Substituting
+// X_k = Z_k + tau_k I into Eq. mlsp2 gives, exactly,
+//     Z_{k+1} = a_k Z_k^2 + (b_k + 2 a_k tau_k) Z_k           (no constant)
+//     A_{k+1} = A_k + d_k Z_k          (the constant sum_k d_k tau_k moves
+//                                         to the output)
+//     D = A_L + Z_L + f0 I,  f0 = P_theta(mu0) = tau_L + sum_k d_k tau_k.
+// The layer-0 state is Z_0 = H0 - mu0 I = scale (mu I - H) (Eq. H0 with the
+// normalisation of Eqs. H', mu', beta' substituted; no division by the
+// spectral width).  The products then only see deviations from the point
+// where the Fermi function is steep, which keeps FP32 rounding far below the
+// beta0/4 slope amplification that a plain X_k^2 suffers.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include "../../include/ftsp2.h"
+
+namespace ftsp2 {
+
+constexpr int kMaxLayers = 64;
+constexpr int kMaxChains = 2;
+constexpr int kTileM = 128;                  // tensor-core tile rows (UMMA M)
+constexpr int kPad = 128;                    // matrix pitch granularity (elements)
+constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;   // 4 s
+
+enum ChainKind : int { CHAIN_FERMI = 0, CHAIN_ENTROPY = 1 };
+
+// Operand formats written for the next layer.
+enum OpFmt : int { OP_F32 = 0, OP_TF32X3 = 1, OP_BF16X3 = 2, OP_F16X2 = 3 };
+
+// Per layer constants of the centred recursion (float: what the epilogue uses).
+struct DevLayer {
+    float acc_mul;    // a_k * 2^(-2 e_k): undoes the operand scale of FP16 splits
+    float bp;         // b_k + 2 a_k tau_k
+    float d;          // d_k
+    float out_scale;  // 2^(e_{k+1}): scale of the operands written for layer k+1
+    float in_scale;   // 2^(e_k)
+    float a;          // a_k
+    float pad0, pad1;
+};
+
+struct DevModel {
+    double beta0, mu0, alpha;
+    double f0;        // Fermi chain output at mu0
+    double g0;        // entropy chain output at the centre mu0
+    int L;            // Fermi chain layers
+    int LS;           // entropy chain layers
+    int off;          // first DevLayer of the Fermi chain (FP16 scales)
+    int offS;         // first DevLayer of the entropy chain
+    float scale0;     // 2^(e_0) of the Fermi chain (FP16 operands of Z_0)
+    float scale0S;    // 2^(e_0) of the entropy chain
+};
+
+// One output tile of one grouped layer launch.
+struct Tile {
+    int inst;
+    int I;            // 128-row block
+    int J;            // BN-column block
+    int chain;
+};
+
+// Per-instance bookkeeping written by the setup kernels (workspace).
+struct InstWork {
+    unsigned long long kmin, kmax;   // order-preserving keys of e_min / e_max
+    int tile_start[2][kMaxChains];   // [tensor-core table, 128x128 table][chain]
+    int tile_count[2][kMaxChains];
+    int start_layer;                 // per chain, 16 bits each: first global layer
+    int nonfinite;
+};
+
+struct Layout {
+    // all offsets in bytes from the workspace base
+    size_t inst_work, tiles, tiles_ref, partials, status;
+    size_t Z[kMaxChains], A[kMaxChains], OP[kMaxChains][2], OPR[kMaxChains][2];
+    size_t total;
+    size_t plane_elems;   // nb * P * P
+    int P, nb, nchains, ntiles, ntiles_ref, BN;
+};
+
+// --- setup / bandwidth kernels (k_setup.cu) --------------------------------
+struct SetupArgs {
+    const double* H;
+    const ftsp2_instance* inst;
+    int nb, P, Lmax, nchains, BN, BN_ref;
+    const DevModel* models;
+    int nmodels;
+    int flags;
+    int chain_kind[kMaxChains];
+    InstWork* iw;
+    Tile* tiles;
+    Tile* tiles_ref;
+    ftsp2_rescale_rec* rec;
+    int* status;
+};
+
+void launch_prep(const SetupArgs& a, cudaStream_t s);
+void launch_gershgorin(const SetupArgs& a, int max_n, cudaStream_t s);
+void launch_decide(const SetupArgs& a, cudaStream_t s);
+
+struct InitArgs {
+    const double* H;
+    const ftsp2_instance* inst;
+    const ftsp2_rescale_rec* rec;
+    const DevModel* models;
+    const InstWork* iw;
+    int nb, P, nchains;
+    int chain_kind[kMaxChains];
+    float* Z[kMaxChains];
+    float* A[kMaxChains];
+    uint8_t* OP[kMaxChains][2];    // operands in the main format
+    float* OPR[kMaxChains][2];     // FP32 operands of refinement layers (nullable)
+    int main_fmt;                  // format of the main layers (OP_F32 in FTSP2_FP32 mode)
+    int refine_from;               // global layers >= refine_from run in FP32 on OPR
+    size_t plane_elems;
+};
+void launch_init(const InitArgs& a, int max_n, cudaStream_t s);
+
+struct FinalArgs {
+    const ftsp2_instance* inst;
+    ftsp2_rescale_rec* rec;
+    const DevModel* models;
+    const InstWork* iw;
+    const double* partials;   // [tile][4 quarters][2]
+    int table;                // tile table used by the last layer (0 main, 1 128x128)
+    int nb, nchains;
+    int chain_kind[kMaxChains];
+    double* trace;            // nullable, [nb][2]
+    double* S;                // nullable, [nb]
+    const int* status;
+};
+void launch_finalize(const FinalArgs& a, cudaStream_t s);
+
+// --- layer kernels -------------------------------------------------------------
+struct LayerArgs {
+    const Tile* tiles;
+    int ntiles;
+    const ftsp2_instance* inst;
+    const ftsp2_rescale_rec* rec;
+    const InstWork* iw;
+    const DevModel* models;
+    const DevLayer* layers;
+    int P, Lmax, gl, last, nchains;
+    int chain_kind[kMaxChains];
+    int next_fmt;
+    float* Z[kMaxChains];
+    float* A[kMaxChains];
+    const uint8_t* opr[kMaxChains];   // read operands (plane 0 base) - SIMT path
+    uint8_t* opw[kMaxChains];         // write operands (plane 0 base)
+    size_t plane_elems;
+    float* D;
+    double* partials;
+    int* status;
+};
+
+struct TmaMaps {
+    CUtensorMap a[kMaxChains][3];   // boxes of 128 rows (A operand)
+    CUtensorMap b[kMaxChains][3];   // boxes of BN rows (B operand)
+};
+
+// Tensor-core layer (k_layer_tc.cu); mode in {TF32X3, BF16X3, FP16X2}.
+int tc_block_n(int mode);
+int tc_smem_bytes(int mode);
+cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, int grid,
+                            cudaStream_t s);
+// CUDA-core FP32 layer (k_layer_simt.cu), 128 x 128 tiles.
+cudaError_t launch_layer_simt(const LayerArgs& a, int grid, cudaStream_t s);
+
+// --- training (k_train.cu) -----------------------------------------------------
+struct ThetaParam {
+    double v[4 * kMaxLayers];
+};
+cudaError_t launch_train_fwd_jac(int target, double beta0, double mu0, int L, double alpha,
+                                 const ThetaParam& th, const double* dX, int ns,
+                                 double* dR, double* dM, cudaStream_t s);
+cudaError_t launch_train_residual(int target, double beta0, double mu0, int L, double alpha,
+                                  const ThetaParam& th, const double* dX, int ns,
+                                  double* dR, cudaStream_t s);
+cudaError_t launch_train_gram(const double* dM, int ns, int np, double* dG, double* dScratch,
+                              int nchunks, cudaStream_t s);
+cudaError_t launch_train_accel(const double* dM, const double* dV, const double* dRh, double h,
+                               int ns, int np, double* dPart, double* dOut, cudaStream_t s);
+cudaError_t launch_train_absmax(const double* dR, int ns, double* dPart, double* dOut,
+                                cudaStream_t s);
+
+void count_launch(int n = 1);
+
+}  // namespace ftsp2
+
+// ---------------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace ftsp2 {
+
+__device__ __forceinline__ unsigned long long dkey(double x) {
+    // order-preserving map of doubles onto unsigned 64-bit integers
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dunkey(unsigned long long k) {
+    unsigned long long b = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait on an mbarrier phase with a time limit.  On timeout the CTA-wide abort
+// flag and the global status word are set and false is returned; every role
+// then leaves its loop.  Also returns false when another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* gstatus) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > kWaitTimeoutNs) {
+                *abort_flag = 1;
+                atomicExch(gstatus, (int)FTSP2_E_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+}  // namespace ftsp2
+#endif

@@ -1,0 +1,100 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads,
+exports every function include/ftsp2.h declares, and the ctypes struct layouts
+match the C compiler's."""
+import ctypes as C
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ftsp2.h")
+
+
+@pytest.fixture(scope="module")
+def built():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2605_08523_gb300 as ft
+    return ft
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(ftsp2_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ftsp2_rescale", "ftsp2_density", "ftsp2_entropy", "ftsp2_train_coeffs"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    lib = built.lib()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding declares a signature for each of them
+    from paper_2605_08523_gb300 import _lib
+    assert set(declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_status_strings(built):
+    for code in range(0, -9, -1):
+        assert built.status_string(code) != "unknown status"
+
+
+def test_struct_layouts_match_c(tmp_path):
+    from paper_2605_08523_gb300 import _lib
+    prog = tmp_path / "layout.c"
+    prog.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "ftsp2.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(ftsp2_instance), offsetof(ftsp2_instance, offset),
+         offsetof(ftsp2_instance, mu), offsetof(ftsp2_instance, kT));
+  printf("%zu %zu %zu %zu\\n", sizeof(ftsp2_table), offsetof(ftsp2_table, beta0),
+         offsetof(ftsp2_table, theta), offsetof(ftsp2_table, theta_entropy));
+  printf("%zu %zu %zu %zu\\n", sizeof(ftsp2_rescale_rec), offsetof(ftsp2_rescale_rec, flip),
+         offsetof(ftsp2_rescale_rec, status), offsetof(ftsp2_rescale_rec, valid));
+  printf("%zu %zu %zu %zu\\n", sizeof(ftsp2_train_report), offsetof(ftsp2_train_report, cost0),
+         offsetof(ftsp2_train_report, max_err), offsetof(ftsp2_train_report, lambda));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    I, T, R, P = _lib.Instance, _lib.Table, _lib.RescaleRec, _lib.TrainReport
+    assert out[0].split() == [str(v) for v in (C.sizeof(I), I.offset.offset, I.mu.offset, I.kT.offset)]
+    assert out[1].split() == [str(v) for v in (C.sizeof(T), T.beta0.offset, T.theta.offset, T.theta_entropy.offset)]
+    assert out[2].split() == [str(v) for v in (C.sizeof(R), R.flip.offset, R.status.offset, R.valid.offset)]
+    assert out[3].split() == [str(v) for v in (C.sizeof(P), P.cost0.offset, P.max_err.offset, P.lam.offset)]
+
+
+def test_builtin_table_matches_oracle_copy():
+    # The library and the oracle each carry their own copy of the printed
+    # Appendix A table; they must agree digit for digit.
+    from oracle import tables
+    src = open(os.path.join(ROOT, "paper_2605_08523_gb300", "csrc", "ftsp2_api.cu")).read()
+    block = src[src.index("kPrinted[26][4]"):]
+    block = block[:block.index("};")]
+    nums = [float(v) for v in re.findall(r"[-+]\d\.\d+e[-+]\d+", block)]
+    flat = [v for row in tables.PRINTED_B1500 for v in row]
+    assert nums == flat
+
+
+def test_product_path_fails_loudly_without_library(tmp_path):
+    # A copy of the binding pointed at a missing library must raise, not fall back.
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2605_08523_gb300 import _lib\n"
+            "_lib.LIB_PATH = '/nonexistent/libftsp2.so'\n"
+            "_lib._lib = None\n"
+            "try:\n    _lib.lib()\nexcept RuntimeError as e:\n    print('raised')\n") % ROOT
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert "raised" in out.stdout
