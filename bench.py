@@ -1,0 +1,420 @@
+"""Benchmark of the MLSP2 hot path (density matrix + entropy) on GB300.
+
+Workload (the headline configuration): one dense symmetric H, n = 4096, 3D
+cubic tight-binding lattice 16 x 16 x 16 with open boundaries, on-site
+U(-1, 1) eV, hopping -1 eV, plus symmetrised 0.01 N(0, 1) dense noise;
+kT = 0.1 eV, mu at half filling; the paper's 26-layer table (beta0 = 1500,
+mu0 = 1/3); density and entropy chains; FP16x2 split-precision tensor-core
+layers with FP32 accumulation.
+
+A step is one pass of the whole hot path (Gershgorin bounds, rescale, both
+26-layer recursions, traces, entropy) over the resident input.  Inputs and
+the per-step working set (~0.7 GB) are larger than the 129 MB L2, so no
+explicit flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (the path has no
+exchange step); value = solves of all ranks / max wall time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "density-matrix solves/s and TFLOP/s vs plain FP32 recursion at <=1e-6 error"
+LN2 = math.log(2.0)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--dims", default="16,16,16")
+    p.add_argument("--kT", type=float, default=0.1)
+    p.add_argument("--mode", default="fp16x2")
+    p.add_argument("--no-baselines", action="store_true")
+    p.add_argument("--seed", type=int, default=0)
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(dims, seed):
+    import workloads as wl
+    return wl.lattice_3d(dims, seed)
+
+
+def fermi_t(t):
+    import torch
+    return torch.where(t > 0, torch.exp(-t) / (1 + torch.exp(-t)), 1 / (1 + torch.exp(t)))
+
+
+def entropy_t(t):
+    import torch
+    a = t.abs()
+    e = torch.exp(-a)
+    return torch.log1p(e) + a * e / (1 + e)
+
+
+def eig_reference_gpu(Hd, kT, n):
+    """FP64 eigendecomposition baseline on the GPU: eps, V; mu at half filling;
+    D_ref = V f V^T, S_ref = sum s(eps)."""
+    import torch
+    eps, V = torch.linalg.eigh(Hd)
+    lo, hi = float(eps[0]) - 1.0, float(eps[-1]) + 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if float(fermi_t((eps - mid) / kT).sum()) > n / 2:
+            hi = mid
+        else:
+            lo = mid
+    mu = 0.5 * (lo + hi)
+    f = fermi_t((eps - mu) / kT)
+    D = (V * f[None, :]) @ V.T
+    S = float(entropy_t((eps - mu) / kT).sum())
+    return mu, D, S, eps, V
+
+
+def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
+    """Baseline (i): the plain FP32 recursion of Alg. 2 with torch.matmul
+    (TF32 disabled): X and Y chains, 26 layers each."""
+    import torch
+    n = Hd.shape[0]
+    W = emax - emin
+    beta = 1.0 / kT
+    I = torch.eye(n, dtype=torch.float32, device=Hd.device)
+    Hp = (emax * I.double() - Hd) / W
+    mup = (emax - mu) / W
+    betap = W * beta
+    flip = mup > 0.5
+    if flip:
+        Hp = I.double() - Hp
+        mup = 1 - mup
+    X = ((betap / beta0) * (Hp - mup * I.double()) + mu0 * I.double()).float()
+    Y = alpha * X + (1 - alpha) * mu0 * I
+    AD = torch.zeros_like(X)
+    AS = torch.zeros_like(X)
+    for a, b, c, d in theta:
+        AD += d * X
+        X = a * (X @ X) + b * X + c * I
+        AS += d * Y
+        Y = a * (Y @ Y) + b * Y + c * I
+    D = AD + X
+    if flip:
+        D = I - D
+    F = AS + Y
+    S = 4 * LN2 * (float(torch.trace(F.double())) - float((F.double() ** 2).sum()))
+    return D, S
+
+
+def cuda_time(fn, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0 / reps
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle (eigendecomposition definition of D and S)
+    timed on the host cores, on a bounded sample of the workload."""
+    import numpy as np
+    from oracle import fermi
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    dims = tuple(int(x) for x in args.dims.split(","))
+    n = dims[0] * dims[1] * dims[2]
+    sdims = (dims[0] // 2, dims[1], dims[2]) if n > 2048 else dims
+    ns = sdims[0] * sdims[1] * sdims[2]
+    H = make_workload(sdims, args.seed)
+    eps = np.linalg.eigvalsh(H)
+    mu = fermi.mu_at_filling(eps, args.kT, ns / 2)
+    for _ in range(min(args.warmup, 1)):
+        fermi.eig_reference(H, mu, args.kT)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        fermi.eig_reference(H, mu, args.kT)
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    scale = (ns / n) ** 3
+    value = scale / t
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1000 / scale,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "cfg1 lattice %dx%dx%d n=%d kT=%g mu=half filling" % (dims + (n, args.kT)),
+                       "n": n, "kT": args.kT},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": "oracle.fermi.eig_reference (numpy eigh + V f V^T + S) on the "
+                                       "%dx%dx%d lattice (n=%d) of the same family, scaled to n=%d by n^3"
+                                       % (sdims + (ns, n))},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(H, mu, kT, n):
+    """The oracle (eigendecomposition definition) timed once on the host cores."""
+    from oracle import fermi
+    t0 = time.perf_counter()
+    fermi.eig_reference(H, mu, kT)
+    t = time.perf_counter() - t0
+    return {"value": 1.0 / t, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one oracle.fermi.eig_reference solve (numpy eigh + V f V^T + S) of the full n=%d H "
+                      "(%.1f s)" % (n, t)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2605_08523_gb300 as ft
+    from paper_2605_08523_gb300 import build as ftbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    if rank == 0:
+        ftbuild.build()
+    if world > 1:
+        dist.barrier()
+    ft.lib()
+    dims = tuple(int(x) for x in args.dims.split(","))
+    n = dims[0] * dims[1] * dims[2]
+    kT = args.kT
+    H = make_workload(dims, args.seed + rank)
+    Hd = torch.from_numpy(H.ravel().copy()).cuda()
+    Hm = Hd.view(n, n)
+
+    # mu at half filling from the FP64 GPU eigendecomposition (baseline ii)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    mu, Dref, Sref, eps, V = eig_reference_gpu(Hm, kT, n)
+    ms = ft.ModelSet()
+    solver = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3)
+    for _ in range(args.warmup):
+        solver.run(Hd)
+    torch.cuda.synchronize()
+    rec = solver.records()[0]
+    if rec["status"] != 0:
+        raise SystemExit("hot path status %d (%s)" % (rec["status"], ft.status_string(int(rec["status"]))))
+
+    # ---- timed region (device-resident inputs) ----
+    L = int(rec["layers"])
+    ft.profile_layers(True)
+    ft.profile_read()
+    launches0 = ft.kernel_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            solver.run(Hd)
+        ev1.record()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = ft.kernel_launch_count() - launches0
+    layer_ms, layer_n = ft.profile_read()
+    ft.profile_layers(False)
+    t_step = ev0.elapsed_time(ev1) / 1000.0 / args.steps
+    tmax = torch.tensor([t_step], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    t_step = float(tmax)
+    value = world / t_step
+    alg_flops = 2 * L * float(n) ** 3          # L symmetric squares (n^3) per chain, 2 chains
+    # ---- accuracy of this run's output ----
+    D = solver.matrix(0).double()
+    err_D = float((D - Dref).abs().max())
+    S = float(solver.S[0])
+    err_S = abs(S - Sref) / n
+    trD = float(solver.trace[0, 0])
+
+    # ---- end to end through the public API with host buffers ----
+    Hh = torch.from_numpy(H.ravel().copy()).pin_memory()
+    Dh = torch.empty(n * n, dtype=torch.float32).pin_memory()
+    Sh = torch.empty(1, dtype=torch.float64).pin_memory()
+    Th = torch.empty(2, dtype=torch.float64).pin_memory()
+    Hdev = torch.empty_like(Hd)
+
+    def e2e_step():
+        Hdev.copy_(Hh, non_blocking=True)
+        solver.run(Hdev)
+        Dh.copy_(solver.D, non_blocking=True)
+        Sh.copy_(solver.S, non_blocking=True)
+        Th.copy_(solver.trace[0], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    t_e2e = cuda_time(e2e_step, e2e_steps)
+    h2d = n * n * 8
+    d2h = n * n * 4 + 8 + 16
+
+    # ---- dominant kernel roofline ----
+    pk, pk_kind = peaks()
+    layer_avg = layer_ms / max(1, layer_n) / 1000.0
+    alg_per_launch = 2 * float(n) ** 3
+    achieved = alg_per_launch / layer_avg / 1e12 if layer_avg > 0 else None
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    # hardware tensor flops actually issued per launch: triangle tiles x 3 products
+    BN = 256 if args.mode in ("fp16x2", "tf32x3") else 128
+    nI, nJ, q = math.ceil(n / 128), math.ceil(n / BN), BN // 128
+    tiles = sum(min(q * (J + 1), nI) for J in range(nJ))
+    nprod = {"fp16x2": 3, "tf32x3": 3, "bf16x3": 6}.get(args.mode, 1)
+    hw_per_launch = 2 * tiles * 128 * BN * n * 2 * nprod
+    hw_achieved = hw_per_launch / layer_avg / 1e12 if layer_avg > 0 else None
+    hw_peak = peak if args.mode in ("fp16x2", "bf16x3") else peak / 2.0
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        key = "layer_tc_%s_n%d" % (args.mode, n)
+        traffic = tr.get(key)
+    except Exception:
+        pass
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp16x2-split/fp32-accum" if args.mode == "fp16x2" else args.mode,
+        "data": "synthetic",
+        "config": {"workload": "cfg1 lattice %dx%dx%d n=%d kT=%g mu=half filling, density+entropy, "
+                               "printed 26-layer table" % (dims + (n, kT)),
+                   "n": n, "kT": kT, "mu": mu, "layers": L, "mode": args.mode, "chains": 2,
+                   "l2": "inputs and working set larger than L2 (no flush)", "parallelism": "replicas"},
+        "tflops_alg": alg_flops / t_step / 1e12 * world,
+        "accuracy": {"max_abs_D_minus_Dref": err_D, "abs_S_minus_Sref_per_n": err_S, "trD": trD,
+                     "trD_ref": n / 2, "S": S, "S_ref": Sref},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": "layer_tc_kernel<%s>" % args.mode.upper(),
+                     "per_launch_alg_flops": alg_per_launch, "avg_launch_ms": layer_avg * 1000,
+                     "peak_kind": "bf16_tflops_sustained (%s)" % pk_kind,
+                     "hw_tensor_tflops": hw_achieved, "hw_frac": (hw_achieved / hw_peak) if hw_achieved else None},
+        "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+
+    if not args.no_baselines:
+        # baseline (i): plain FP32 recursion with torch.matmul, TF32 off
+        theta = [tuple(r) for r in ms.table(0)[0]]
+        emin, emax = float(rec["e_min"]), float(rec["e_max"])
+        out = {}
+
+        def fp32_step():
+            out["r"] = plain_fp32_recursion(Hm, mu, kT, theta, 1500.0, 1 / 3, 0.842704, emin, emax)
+
+        fp32_step()
+        t32 = cuda_time(fp32_step, 2)
+        D32, S32 = out["r"]
+        t64 = cuda_time(lambda: eig_reference_gpu(Hm, kT, n), 1)
+        result["baselines"] = {
+            "plain_fp32_recursion": {"solves_per_s": 1 / t32, "max_abs_D_minus_Dref": float((D32.double() - Dref).abs().max()),
+                                     "abs_S_minus_Sref_per_n": abs(S32 - Sref) / n,
+                                     "math": "torch.matmul fp32, allow_tf32=False"},
+            "fp64_eigh_gpu": {"solves_per_s": 1 / t64, "how": "torch.linalg.eigh float64 + V f V^T + S"},
+            "speedup_vs_fp32_recursion": value / world * t32,
+            "speedup_vs_fp64_eigh": value / world * t64,
+        }
+    if rank == 0 and world == 1 and not args.no_baselines:
+        result["cpu_baseline"] = cpu_baseline(H, mu, kT, n)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

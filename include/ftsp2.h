@@ -140,6 +140,11 @@ void ftsp2_model_set_destroy(ftsp2_model_set* set);
 /* Number of tables and the largest layer count in the set. */
 ftsp2_status ftsp2_model_set_info(const ftsp2_model_set* set, int* ntab, int* max_layers);
 
+/* Copy of table `idx` of the set: *L layers, theta_out (host, room for 4*64
+ * doubles) receives the rows (a, b, c, d); any output pointer may be NULL. */
+ftsp2_status ftsp2_model_set_table(const ftsp2_model_set* set, int idx, int* L, double* theta_out,
+                                   double* beta0, double* mu0, double* alpha);
+
 /* ---- workspace ------------------------------------------------------------ */
 
 /* Bytes of device workspace needed by a density/entropy call with these
@@ -237,6 +242,16 @@ ftsp2_status ftsp2_train_residual_jacobian(int target, double beta0, double mu0,
                                            double* dR, double* dM, void* stream);
 ftsp2_status ftsp2_train_normal_equations(const double* dM, int nsamples, int L, double* dG,
                                           void* dWork, size_t work_bytes, void* stream);
+
+/* ---- measurement support ------------------------------------------------- */
+
+/* While enabled, every tensor-core layer launch is bracketed by a CUDA event
+ * pair recorded on the caller's stream (host-side events, created on demand;
+ * not usable during stream capture).  ftsp2_profile_read synchronises those
+ * events and returns the summed layer-kernel time (ms) and the number of
+ * launches measured since the last read, then clears the record. */
+ftsp2_status ftsp2_profile_layers(int enable);
+ftsp2_status ftsp2_profile_read(double* total_ms, uint64_t* launches);
 
 /* ---- misc ---------------------------------------------------------------- */
 

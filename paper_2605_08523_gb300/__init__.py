@@ -28,7 +28,7 @@ from ._lib import (BF16X3, CLAMP, FP16X2, FP32, MODES, REFINE1, REFINE2, SYNC, T
                    lib, status_string)
 
 __all__ = ["ModelSet", "Solver", "ftsp2_rescale", "ftsp2_train_coeffs", "ftsp2_train_residual_jacobian",
-           "ftsp2_train_normal_equations", "kernel_launch_count", "MODES", "FP32", "TF32X3", "BF16X3",
+           "ftsp2_train_normal_equations", "kernel_launch_count", "profile_layers", "profile_read", "MODES", "FP32", "TF32X3", "BF16X3",
            "FP16X2", "SYNC", "CLAMP", "REFINE1", "REFINE2", "TARGET_FERMI", "TARGET_ENTROPY",
            "Ftsp2Error", "status_string", "lib", "REC_DTYPE"]
 
@@ -55,6 +55,18 @@ def _stream(stream=None):
 
 def kernel_launch_count() -> int:
     return int(lib().ftsp2_kernel_launch_count())
+
+
+def profile_layers(enable: bool):
+    """Bracket every tensor-core layer launch with CUDA events (ftsp2_profile_layers)."""
+    check(lib().ftsp2_profile_layers(int(bool(enable))), "ftsp2_profile_layers")
+
+
+def profile_read():
+    """(summed layer-kernel ms, launches) since the last read (ftsp2_profile_read)."""
+    ms, n = C.c_double(), C.c_uint64()
+    check(lib().ftsp2_profile_read(C.byref(ms), C.byref(n)), "ftsp2_profile_read")
+    return ms.value, int(n.value)
 
 
 class ModelSet:
@@ -98,6 +110,15 @@ class ModelSet:
         n, L = C.c_int(), C.c_int()
         check(lib().ftsp2_model_set_info(self._h, C.byref(n), C.byref(L)), "ftsp2_model_set_info")
         return n.value, L.value
+
+    def table(self, idx=0):
+        """(theta (L, 4), beta0, mu0, alpha) of table idx (ftsp2_model_set_table)."""
+        L = C.c_int()
+        th = (C.c_double * 256)()
+        b0, m0, al = C.c_double(), C.c_double(), C.c_double()
+        check(lib().ftsp2_model_set_table(self._h, int(idx), C.byref(L), th, C.byref(b0), C.byref(m0),
+                                          C.byref(al)), "ftsp2_model_set_table")
+        return np.array(th[:4 * L.value]).reshape(-1, 4), b0.value, m0.value, al.value
 
     def close(self):
         if self._h:

@@ -54,6 +54,8 @@ SIGNATURES = {
     "ftsp2_model_set_builtin": (_I, [C.POINTER(_VP)]),
     "ftsp2_model_set_destroy": (None, [_VP]),
     "ftsp2_model_set_info": (_I, [_VP, C.POINTER(_I), C.POINTER(_I)]),
+    "ftsp2_model_set_table": (_I, [_VP, _I, C.POINTER(_I), C.POINTER(_D), C.POINTER(_D), C.POINTER(_D),
+                                   C.POINTER(_D)]),
     "ftsp2_workspace_size": (_I, [_PINST, _I, _I, _I, C.POINTER(_SZ)]),
     "ftsp2_rescale_workspace_size": (_I, [_I, C.POINTER(_SZ)]),
     "ftsp2_rescale": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _VP, _VP, _SZ, _VP]),
@@ -65,6 +67,8 @@ SIGNATURES = {
                                 C.POINTER(TrainReport), _VP, _SZ, _VP]),
     "ftsp2_train_residual_jacobian": (_I, [_I, _D, _D, _I, _D, C.POINTER(_D), _VP, _I, _VP, _VP, _VP]),
     "ftsp2_train_normal_equations": (_I, [_VP, _I, _I, _VP, _VP, _SZ, _VP]),
+    "ftsp2_profile_layers": (_I, [_I]),
+    "ftsp2_profile_read": (_I, [C.POINTER(_D), C.POINTER(C.c_uint64)]),
     "ftsp2_status_string": (C.c_char_p, [_I]),
     "ftsp2_kernel_launch_count": (C.c_uint64, []),
 }

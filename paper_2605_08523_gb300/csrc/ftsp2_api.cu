@@ -15,6 +15,11 @@ namespace ftsp2 {
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
+// event pairs around tensor-core layer launches (measurement support)
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_events;
+
 // ------------------------------------------------------------------------------
 // device checks and the driver's tensor-map encoder
 // ------------------------------------------------------------------------------
@@ -457,7 +462,21 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
             la.tiles = tiles;
             la.ntiles = L.ntiles;
             const int grid = std::max(1, std::min(la.ntiles, di.sms));
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            {
+                std::lock_guard<std::mutex> lk(g_prof_mu);
+                if (g_prof_on && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+                    cudaEventRecord(e0, s);
+                } else {
+                    e0 = e1 = nullptr;
+                }
+            }
             e = launch_layer_tc(mode, la, maps[g & 1], grid, s);
+            if (e0) {
+                cudaEventRecord(e1, s);
+                std::lock_guard<std::mutex> lk(g_prof_mu);
+                g_prof_events.emplace_back(e0, e1);
+            }
             last_table = 0;
         }
         if (e != cudaSuccess) return FTSP2_E_CUDA;
@@ -574,6 +593,34 @@ const char* ftsp2_status_string(ftsp2_status s) {
 
 uint64_t ftsp2_kernel_launch_count(void) { return g_launches.load(); }
 
+ftsp2_status ftsp2_profile_layers(int enable) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = enable != 0;
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_profile_read(double* total_ms, uint64_t* launches) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    double sum = 0.0;
+    uint64_t n = 0;
+    ftsp2_status st = FTSP2_OK;
+    for (auto& pr : g_prof_events) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(pr.second) != cudaSuccess || cudaEventElapsedTime(&ms, pr.first, pr.second) != cudaSuccess)
+            st = FTSP2_E_CUDA;
+        else {
+            sum += ms;
+            ++n;
+        }
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    g_prof_events.clear();
+    if (total_ms) *total_ms = sum;
+    if (launches) *launches = n;
+    return st;
+}
+
 ftsp2_status ftsp2_model_set_create(const ftsp2_table* tabs, int ntab, ftsp2_model_set** out) {
     if (!out) return FTSP2_E_ARG;
     *out = nullptr;
@@ -633,6 +680,18 @@ ftsp2_status ftsp2_model_set_info(const ftsp2_model_set* s, int* ntab, int* max_
     if (!s) return FTSP2_E_ARG;
     if (ntab) *ntab = (int)s->host.size();
     if (max_layers) *max_layers = s->Lmax;
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_model_set_table(const ftsp2_model_set* s, int idx, int* L, double* theta_out, double* beta0,
+                                   double* mu0, double* alpha) {
+    if (!s || idx < 0 || idx >= (int)s->host.size()) return FTSP2_E_ARG;
+    const HostModel& h = s->host[idx];
+    if (L) *L = h.L;
+    if (theta_out) std::copy(h.th.begin(), h.th.end(), theta_out);
+    if (beta0) *beta0 = h.beta0;
+    if (mu0) *mu0 = h.mu0;
+    if (alpha) *alpha = h.alpha;
     return FTSP2_OK;
 }
 
