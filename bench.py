@@ -38,7 +38,7 @@ LN2 = math.log(2.0)
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--dims", default="16,16,16")
@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--mode", default="fp16x2")
     p.add_argument("--no-baselines", action="store_true")
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--mu", type=float, default=None,
+                   help="skip the GPU eigendecomposition and use this mu (profiling runs)")
     return p.parse_args()
 
 
@@ -75,7 +77,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -276,7 +278,10 @@ def main():
 
     # mu at half filling from the FP64 GPU eigendecomposition (baseline ii)
     torch.backends.cuda.matmul.allow_tf32 = False
-    mu, Dref, Sref, eps, V = eig_reference_gpu(Hm, kT, n)
+    if args.mu is None:
+        mu, Dref, Sref, eps, V = eig_reference_gpu(Hm, kT, n)
+    else:
+        mu, Dref, Sref = args.mu, None, None
     ms = ft.ModelSet()
     solver = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3)
     for _ in range(args.warmup):
@@ -315,9 +320,9 @@ def main():
     alg_flops = 2 * L * float(n) ** 3          # L symmetric squares (n^3) per chain, 2 chains
     # ---- accuracy of this run's output ----
     D = solver.matrix(0).double()
-    err_D = float((D - Dref).abs().max())
     S = float(solver.S[0])
-    err_S = abs(S - Sref) / n
+    err_D = float((D - Dref).abs().max()) if Dref is not None else None
+    err_S = abs(S - Sref) / n if Sref is not None else None
     trD = float(solver.trace[0, 0])
 
     # ---- end to end through the public API with host buffers ----
