@@ -240,9 +240,9 @@ static int op_bytes(int fmt) {
 }
 static int refine_layers(int flags) { return (flags & FTSP2_REFINE2) ? 2 : ((flags & FTSP2_REFINE1) ? 1 : 0); }
 
-static int host_tiles_of(int n, int BN) {
-    const int q = BN / kTileM;
-    const int nI = (n + kTileM - 1) / kTileM;
+static int host_tiles_of(int n, int BM, int BN) {
+    const int q = BN / BM;
+    const int nI = (n + BM - 1) / BM;
     const int nJ = (n + BN - 1) / BN;
     int c = 0;
     for (int J = 0; J < nJ; ++J) c += std::min(q * (J + 1), nI);
@@ -264,11 +264,12 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
     const int nch = want == 3 ? 2 : 1;
     const bool simt_main = mode == FTSP2_FP32;
     const int BN = simt_main ? 128 : tc_block_n(mode);
+    const int BM = simt_main ? 128 : tc_block_m(mode);
     const bool refine = !simt_main && refine_layers(flags) > 0;
     long long nt = 0, ntr = 0;
     for (int b = 0; b < nb; ++b) {
-        nt += host_tiles_of(inst[b].n, BN);
-        if (refine) ntr += host_tiles_of(inst[b].n, 128);
+        nt += host_tiles_of(inst[b].n, BM, BN);
+        if (refine) ntr += host_tiles_of(inst[b].n, 128, 128);
     }
     nt *= nch;
     ntr *= nch;
@@ -279,6 +280,7 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
     L.ntiles = (int)nt;
     L.ntiles_ref = (int)ntr;
     L.BN = BN;
+    L.BM = BM;
     L.plane_elems = (size_t)nb * P * P;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -290,7 +292,7 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
     L.inst_work = take(sizeof(InstWork) * nb);
     L.tiles = take(sizeof(Tile) * nt);
     L.tiles_ref = refine ? take(sizeof(Tile) * ntr) : 0;
-    L.partials = take(sizeof(double) * 8 * std::max<long long>(nt, ntr));
+    L.partials = take(sizeof(double) * 2 * kPartialSlots * std::max<long long>(nt, ntr));
     const int fmt = fmt_of_mode(mode);
     for (int c = 0; c < kMaxChains; ++c) {
         L.Z[c] = L.A[c] = L.OP[c][0] = L.OP[c][1] = L.OPR[c][0] = L.OPR[c][1] = 0;
@@ -357,7 +359,9 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     sa.Lmax = Lmax;
     sa.nchains = L.nchains;
     sa.BN = L.BN;
+    sa.BM = L.BM;
     sa.BN_ref = 128;
+    sa.BM_ref = 128;
     sa.models = models;
     sa.nmodels = (int)set->host.size();
     sa.flags = flags;
@@ -409,9 +413,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
             for (int c = 0; c < L.nchains; ++c)
                 for (int sp = 0; sp < nsplit; ++sp) {
                     void* base = W + L.OP[c][p] + (size_t)sp * es * L.plane_elems;
-                    if (!encode_map(&maps[p].a[c][sp], base, dt, es, L.P, nb, bke, kTileM) ||
-                        !encode_map(&maps[p].b[c][sp], base, dt, es, L.P, nb, bke, L.BN))
-                        return FTSP2_E_CUDA;
+                    if (!encode_map(&maps[p].a[c][sp], base, dt, es, L.P, nb, bke, kTileM)) return FTSP2_E_CUDA;
                 }
     }
 
@@ -461,7 +463,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         } else {
             la.tiles = tiles;
             la.ntiles = L.ntiles;
-            const int grid = std::max(1, std::min(la.ntiles, di.sms));
+            const int npairs = std::max(1, std::min(la.ntiles, di.sms / 2));
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             {
                 std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -471,7 +473,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
                     e0 = e1 = nullptr;
                 }
             }
-            e = launch_layer_tc(mode, la, maps[g & 1], grid, s);
+            e = launch_layer_tc(mode, la, maps[g & 1], npairs, s);
             if (e0) {
                 cudaEventRecord(e1, s);
                 std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -737,6 +739,7 @@ ftsp2_status ftsp2_rescale(const double* dH, const ftsp2_instance* inst, const f
     sa.Lmax = set->Lmax;
     sa.nchains = 1;
     sa.BN = 128;
+    sa.BM = 128;
     sa.models = set->d_models[0];
     sa.nmodels = (int)set->host.size();
     sa.flags = flags;

@@ -28,6 +28,7 @@ constexpr int kMaxLayers = 64;
 constexpr int kMaxChains = 2;
 constexpr int kTileM = 128;                  // tensor-core tile rows (UMMA M)
 constexpr int kPad = 128;                    // matrix pitch granularity (elements)
+constexpr int kPartialSlots = 16;            // FP64 partial-sum slots per tile (last layer)
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;   // 4 s
 
 enum ChainKind : int { CHAIN_FERMI = 0, CHAIN_ENTROPY = 1 };
@@ -61,7 +62,7 @@ struct DevModel {
 // One output tile of one grouped layer launch.
 struct Tile {
     int inst;
-    int I;            // 128-row block
+    int I;            // BM-row block
     int J;            // BN-column block
     int chain;
 };
@@ -81,14 +82,14 @@ struct Layout {
     size_t Z[kMaxChains], A[kMaxChains], OP[kMaxChains][2], OPR[kMaxChains][2];
     size_t total;
     size_t plane_elems;   // nb * P * P
-    int P, nb, nchains, ntiles, ntiles_ref, BN;
+    int P, nb, nchains, ntiles, ntiles_ref, BN, BM;
 };
 
 // --- setup / bandwidth kernels (k_setup.cu) --------------------------------
 struct SetupArgs {
     const double* H;
     const ftsp2_instance* inst;
-    int nb, P, Lmax, nchains, BN, BN_ref;
+    int nb, P, Lmax, nchains, BM, BN, BM_ref, BN_ref;
     const DevModel* models;
     int nmodels;
     int flags;
@@ -160,14 +161,15 @@ struct LayerArgs {
 };
 
 struct TmaMaps {
-    CUtensorMap a[kMaxChains][3];   // boxes of 128 rows (A operand)
-    CUtensorMap b[kMaxChains][3];   // boxes of BN rows (B operand)
+    CUtensorMap a[kMaxChains][3];   // [chain][split plane], boxes of 128 rows x 128 bytes
 };
 
 // Tensor-core layer (k_layer_tc.cu); mode in {TF32X3, BF16X3, FP16X2}.
 int tc_block_n(int mode);
+int tc_block_m(int mode);
 int tc_smem_bytes(int mode);
-cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, int grid,
+// npairs: CTA pairs (clusters of 2) of the persistent grid
+cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, int npairs,
                             cudaStream_t s);
 // CUDA-core FP32 layer (k_layer_simt.cu), 128 x 128 tiles.
 cudaError_t launch_layer_simt(const LayerArgs& a, int grid, cudaStream_t s);

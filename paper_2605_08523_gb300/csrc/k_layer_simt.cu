@@ -81,10 +81,10 @@ __global__ void __launch_bounds__(256) layer_simt_kernel(const __grid_constant__
                 red[tid >> 5][1] = sq;
             }
             __syncthreads();
-            if (tid < 4) {
-                // four slots per tile, as the tensor-core kernel writes
-                a.partials[((size_t)t * 4 + tid) * 2 + 0] = red[2 * tid][0] + red[2 * tid + 1][0];
-                a.partials[((size_t)t * 4 + tid) * 2 + 1] = red[2 * tid][1] + red[2 * tid + 1][1];
+            if (tid < kPartialSlots) {
+                // one slot per warp; the remaining slots of the tile hold zeros
+                a.partials[((size_t)t * kPartialSlots + tid) * 2 + 0] = tid < 8 ? red[tid][0] : 0.0;
+                a.partials[((size_t)t * kPartialSlots + tid) * 2 + 1] = tid < 8 ? red[tid][1] : 0.0;
             }
             __syncthreads();
         }

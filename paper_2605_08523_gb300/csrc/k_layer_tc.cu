@@ -2,26 +2,39 @@
 // (instance, chain) of a grouped launch, on the 5th-generation tensor cores.
 //
 // The product of a layer is the symmetric square Z^2 of the centred state.
-// Only output tiles that touch the upper triangle are computed; each element
-// (r, c) with r <= c is produced once and written to (r, c) and (c, r).  Since
-// Z is symmetric, (Z^2)_{rc} = sum_k Z_{rk} Z_{ck}: both MMA operands are
-// K-major row panels of the same matrix, loaded by TMA with 128-byte swizzle.
+// Output tiles are 256 x 256 and only those touching the upper triangle are
+// computed (I <= J); each element (r, c) with r <= c is produced once and
+// written to (r, c) and (c, r).  Since Z is symmetric, (Z^2)_{rc} =
+// sum_k Z_{rk} Z_{ck}: both MMA operands are K-major row panels of the same
+// matrix, loaded by TMA with 128-byte swizzle.
 //
 // Split precision (Sec. IV A, Eq. emulated matmul, generalised): Z is stored as
 // NSPLIT low-precision planes Z = sum_s Z_s and the products Z_s Z_t with
-// s + t small enough are accumulated into one FP32 TMEM accumulator:
+// s + t small enough are accumulated in FP32:
 //   FP16X2: (0,0) (0,1) (1,0)    TF32X3: same      BF16X3: + (0,2) (2,0) (1,1)
 // (the paper's two GEMMs plus a transpose-add become three products on the
-// triangle, which costs 1.5 n^3 MACs instead of 2 n^3).
+// triangle: 1.5 n^3 MACs instead of 2 n^3).
 //
-// Warp roles (192 threads, one CTA per SM, persistent over the tile list):
-//   warp 0 lane 0: TMA producer (STAGES-deep ring of K-slices)
-//   warp 1 lane 0: tcgen05.mma issuer; warp 1 also allocates TMEM
-//   warps 2-5    : epilogue, one 32-lane TMEM quarter each, double-buffered
-//                  accumulators so the epilogue of tile t overlaps the MMAs of
-//                  tile t+1.
-// Every wait is bounded (ftsp2::mbar_wait): on timeout the CTA sets
-// FTSP2_E_TIMEOUT in the status word and all roles leave their loops.
+// CTA pairs (cta_group::2).  A cluster of two CTAs computes one 256 x 256 tile
+// with M = 256 MMAs issued by the even CTA: CTA r loads its own 128 rows of
+// the A panel and its 128-row half of the B panel, so each SM fills and reads
+// half of B.  Both CTAs' TMA loads complete on the even CTA's "full" barrier;
+// the MMA commit is multicast to both CTAs' "empty" and "tfull" barriers; the
+// odd CTA's epilogue warps release accumulators on the even CTA's "tempty".
+//
+// Chunked accumulation.  Every 256 elements of K the MMAs switch to the other
+// of two TMEM accumulators and the epilogue adds the finished chunk into FP32
+// registers; the tensor core's internal accumulation then spans 256 products
+// per chunk instead of all n, which keeps the FP32 accumulation error of the
+// long sums near that of a short dot product.
+//
+// Warp roles (320 threads per CTA, persistent over the pair-tile list):
+//   warp 0 lane 0 : TMA producer (STAGES-deep ring of 128-byte K-slices)
+//   warp 1        : TMEM allocation; lane 0 of the even CTA issues tcgen05.mma
+//   warps 2..9    : epilogue; warp w reads TMEM lane quarter w % 4 and column
+//                   half (w - 2) / 4 of the CTA's 128 x 256 accumulator.
+// Every wait is bounded: on timeout the CTA sets FTSP2_E_TIMEOUT in the status
+// word and all roles leave their loops.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -35,28 +48,35 @@ struct TcCfg;
 
 template <>
 struct TcCfg<FTSP2_FP16X2> {
-    static constexpr int NSPLIT = 2, ESIZE = 2, BKE = 64, BN = 256, STAGES = 2, NPROD = 3;
+    static constexpr int NSPLIT = 2, ESIZE = 2, STAGES = 3, NPROD = 3, CK = 4;
     static constexpr uint32_t ATYPE = 0;      // f16
     static constexpr bool TF32 = false;
 };
 template <>
 struct TcCfg<FTSP2_BF16X3> {
-    static constexpr int NSPLIT = 3, ESIZE = 2, BKE = 64, BN = 128, STAGES = 2, NPROD = 6;
+    static constexpr int NSPLIT = 3, ESIZE = 2, STAGES = 2, NPROD = 6, CK = 4;
     static constexpr uint32_t ATYPE = 1;      // bf16
     static constexpr bool TF32 = false;
 };
 template <>
 struct TcCfg<FTSP2_TF32X3> {
-    static constexpr int NSPLIT = 2, ESIZE = 4, BKE = 32, BN = 256, STAGES = 2, NPROD = 3;
+    static constexpr int NSPLIT = 2, ESIZE = 4, STAGES = 3, NPROD = 3, CK = 8;
     static constexpr uint32_t ATYPE = 2;      // tf32
     static constexpr bool TF32 = true;
 };
+
+constexpr int kPairRows = 256;       // rows of a pair tile (M of the 2-CTA MMA)
+constexpr int kBN = 256;             // columns of a tile (N)
+constexpr int kCtaRows = 128;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kTbufBytes = 16 * 32 * 4;    // per-warp transpose buffer
 
 __device__ __constant__ int kProdA[6] = {0, 0, 1, 0, 2, 1};
 __device__ __constant__ int kProdB[6] = {0, 1, 0, 2, 0, 1};
 
 // Instruction descriptor of tcgen05.mma kind::f16 / kind::tf32: D in FP32,
-// A and B K-major, M = 128, N = BN.
+// A and B K-major, M x N.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t atype, int M, int N) {
     return (1u << 4)                       // D format: F32
            | (atype << 7) | (atype << 10)  // A, B formats
@@ -76,34 +96,90 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
-                                            int y) {
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the same shared variable in CTA `rank`
+__device__ __forceinline__ uint32_t map_to(uint32_t local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ void remote_arrive(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void remote_expect_tx(uint32_t cluster_addr, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(cluster_addr),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool try_wait_cluster(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* gstatus) {
+    if (try_wait_cluster(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (try_wait_cluster(bar, parity)) return true;
+        if ((it & 63u) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > kWaitTimeoutNs) {
+                *abort_flag = 1;
+                atomicExch(gstatus, (int)FTSP2_E_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// TMA 2-D tile load into this CTA's shared memory, completing on an mbarrier
+// that may live in the peer CTA of the pair.
+__device__ __forceinline__ void tma_load_pair(uint32_t dst, const CUtensorMap* map, uint32_t bar_cluster, int x,
+                                              int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
         "%4}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(x), "r"(y)
         : "memory");
 }
 
 template <bool TF32>
-__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
-                                     uint32_t accumulate) {
+__device__ __forceinline__ void umma_pair(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                          uint32_t accumulate) {
     if constexpr (TF32) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
             "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
     } else {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
             "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
     }
 }
 
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
+// arrive (once) on the barrier at this shared offset in both CTAs of the pair
+// when all previously issued MMAs of this thread have completed
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+    const uint16_t mask = 0x3;
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(mask)
+        : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
@@ -124,20 +200,215 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // ----------------------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(192, 1)
+// Next-layer operand stores of one 32-row x 16-column block held by a warp
+// (lane = row).  Direct stores at (r, c) as 16-element vectors; the mirror
+// (c, r) goes through a per-warp shared transpose buffer so that each lane
+// stores 16 consecutive elements of one mirrored row.
+// ----------------------------------------------------------------------------------
+template <int FMT>
+struct OpFmtT;
+template <>
+struct OpFmtT<OP_F16X2> {
+    static constexpr int NPL = 2, ESZ = 2;
+    __device__ static void split(float z, uint32_t* o) {
+        const __half h = __float2half_rn(z);
+        const __half l = __float2half_rn(z - __half2float(h));
+        o[0] = __half_as_ushort(h);
+        o[1] = __half_as_ushort(l);
+    }
+};
+template <>
+struct OpFmtT<OP_BF16X3> {
+    static constexpr int NPL = 3, ESZ = 2;
+    __device__ static void split(float z, uint32_t* o) {
+        const __nv_bfloat16 b0 = __float2bfloat16_rn(z);
+        const float r1 = z - __bfloat162float(b0);
+        const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
+        o[0] = __bfloat16_as_ushort(b0);
+        o[1] = __bfloat16_as_ushort(b1);
+        o[2] = __bfloat16_as_ushort(b2);
+    }
+};
+template <>
+struct OpFmtT<OP_TF32X3> {
+    static constexpr int NPL = 2, ESZ = 4;
+    __device__ static void split(float z, uint32_t* o) {
+        uint32_t hb;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(z));
+        o[0] = hb;
+        o[1] = __float_as_uint(z - __uint_as_float(hb));
+    }
+};
+template <>
+struct OpFmtT<OP_F32> {
+    static constexpr int NPL = 1, ESZ = 4;
+    __device__ static void split(float z, uint32_t* o) { o[0] = __float_as_uint(z); }
+};
+
+template <int ESZ>
+__device__ __forceinline__ void store16(uint8_t* dst, const uint32_t* v) {
+    if constexpr (ESZ == 2) {
+        uint4 a, b;
+        a.x = v[0] | (v[1] << 16); a.y = v[2] | (v[3] << 16); a.z = v[4] | (v[5] << 16); a.w = v[6] | (v[7] << 16);
+        b.x = v[8] | (v[9] << 16); b.y = v[10] | (v[11] << 16); b.z = v[12] | (v[13] << 16); b.w = v[14] | (v[15] << 16);
+        reinterpret_cast<uint4*>(dst)[0] = a;
+        reinterpret_cast<uint4*>(dst)[1] = b;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            reinterpret_cast<uint4*>(dst)[i] = make_uint4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    }
+}
+template <int ESZ>
+__device__ __forceinline__ void store1(uint8_t* dst, uint32_t v) {
+    if constexpr (ESZ == 2) *reinterpret_cast<uint16_t*>(dst) = (uint16_t)v;
+    else *reinterpret_cast<uint32_t*>(dst) = v;
+}
+template <int ESZ>
+__device__ __forceinline__ uint32_t load1(const uint8_t* src) {
+    if constexpr (ESZ == 2) return (uint32_t)*reinterpret_cast<const uint16_t*>(src);
+    else return *reinterpret_cast<const uint32_t*>(src);
+}
+
+template <int FMT>
+__device__ __forceinline__ void store_block(const LayerArgs& a, const EpiCtx& e, int R0, int r, int c0,
+                                            const float* zs, uint8_t* tbuf, int lane) {
+    using F = OpFmtT<FMT>;
+    constexpr int ESZ = F::ESZ;
+    uint8_t* const base = a.opw[e.chain];
+    const size_t plane_bytes = a.plane_elems * ESZ;
+    const bool row_ok = r < e.n;
+    const bool full_direct = row_ok && r <= c0 && c0 + 15 < e.n;
+    const int j = lane >> 1, half = lane & 1;
+    const int cm = c0 + j;                 // mirrored row handled by this lane
+    const int rr0 = R0 + 16 * half;        // its first column
+    const bool full_mirror = cm < e.n && rr0 + 15 < cm && rr0 + 15 < e.n;
+#pragma unroll
+    for (int p = 0; p < F::NPL; ++p) {
+        uint32_t sp[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            uint32_t o[F::NPL];
+            F::split(zs[jj], o);
+            sp[jj] = o[p];
+        }
+        uint8_t* pb = base + p * plane_bytes + (e.slab + (size_t)r * e.P + c0) * ESZ;
+        if (full_direct) {
+            store16<ESZ>(pb, sp);
+        } else if (row_ok) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj)
+                if (c0 + jj < e.n && r <= c0 + jj) store1<ESZ>(pb + jj * ESZ, sp[jj]);
+        }
+        // mirror (c, r) for r < c through tbuf[jj][lane] = element (r, c0 + jj)
+        __syncwarp();
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) store1<ESZ>(tbuf + (jj * 32 + lane) * ESZ, sp[jj]);
+        __syncwarp();
+        uint8_t* mb = base + p * plane_bytes + (e.slab + (size_t)cm * e.P + rr0) * ESZ;
+        const uint8_t* src = tbuf + (j * 32 + 16 * half) * ESZ;
+        if (full_mirror) {
+            uint32_t v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = load1<ESZ>(src + i * ESZ);
+            store16<ESZ>(mb, v);
+        } else if (cm < e.n) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int rr = rr0 + i;
+                if (rr < e.n && rr < cm) store1<ESZ>(mb + i * ESZ, load1<ESZ>(src + i * ESZ));
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Centred update of a 16-column group for this lane's row, then operand stores
+// in format OUTFMT, or, for OUTFMT == kLastLayer, the output D and the partial
+// sums.  v holds the 16 accumulated products.
+constexpr int kLastLayer = -1;
+
+template <int OUTFMT>
+__device__ __forceinline__ void epi_group(const LayerArgs& a, const EpiCtx& e, int R0, int r, int c0, const float* v,
+                                          uint8_t* tbuf, int lane, double& tr, double& sq) {
+    constexpr bool LAST = OUTFMT == kLastLayer;
+    const bool row_ok = r < e.n;
+    float zn[16];
+    if (row_ok) {
+        float* Zr = a.Z[e.chain] + e.slab + (size_t)r * e.P + c0;
+        float* Ar = a.A[e.chain] + e.slab + (size_t)r * e.P + c0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 zz = reinterpret_cast<const float4*>(Zr)[i];
+            const float4 aa = reinterpret_cast<const float4*>(Ar)[i];
+            const float z4[4] = {zz.x, zz.y, zz.z, zz.w};
+            const float a4[4] = {aa.x, aa.y, aa.z, aa.w};
+            float an4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                zn[4 * i + u] = fmaf(e.mul, v[4 * i + u], e.L.bp * z4[u]);
+                an4[u] = fmaf(e.L.d, z4[u], a4[u]);
+            }
+            if constexpr (!LAST) {
+                reinterpret_cast<float4*>(Zr)[i] = make_float4(zn[4 * i], zn[4 * i + 1], zn[4 * i + 2], zn[4 * i + 3]);
+                reinterpret_cast<float4*>(Ar)[i] = make_float4(an4[0], an4[1], an4[2], an4[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) zn[4 * i + u] += an4[u];     // G = A_L + Z_L
+            }
+        }
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) zn[jj] = 0.f;
+    }
+    if constexpr (!LAST) {
+        if constexpr (OUTFMT == OP_F16X2) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) zn[jj] *= e.L.out_scale;
+        }
+        store_block<(OUTFMT < 0 ? OP_F32 : OUTFMT)>(a, e, R0, r, c0, zn, tbuf, lane);
+    } else if (row_ok) {
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            const int c = c0 + jj;
+            if (c < e.n && r <= c) {
+                const float g = zn[jj];
+                if (e.kind == CHAIN_FERMI && a.D) {
+                    float dv;
+                    if (e.flip) dv = (r == c ? (float)e.cdiag : 0.f) - g;
+                    else dv = g + (r == c ? (float)e.cdiag : 0.f);
+                    a.D[e.doff + (int64_t)r * e.n + c] = dv;
+                    if (c != r) a.D[e.doff + (int64_t)c * e.n + r] = dv;
+                }
+                const double gd = (double)g;
+                if (r == c) {
+                    tr += gd;
+                    sq += gd * gd;
+                } else {
+                    sq += 2.0 * gd * gd;
+                }
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// OUTFMT: operand format written for the next layer, or kLastLayer.
+template <int MODE, int OUTFMT>
+__global__ void __launch_bounds__(kThreads, 1)
     layer_tc_kernel(const __grid_constant__ LayerArgs a, const __grid_constant__ TmaMaps maps) {
     using C = TcCfg<MODE>;
-    constexpr int BN = C::BN;
-    constexpr int A_PLANE = kTileM * 128;
-    constexpr int B_PLANE = BN * 128;
-    constexpr int STAGE_BYTES = C::NSPLIT * (A_PLANE + B_PLANE);
-    constexpr int KSTEPS = 4;                 // 128-byte slice / 32 bytes per MMA
-    constexpr uint32_t IDESC = make_idesc(C::ATYPE, kTileM, BN);
-    constexpr uint32_t TMEM_COLS = 2 * BN;
+    constexpr int BKE = 128 / C::ESIZE;                // K elements per 128-byte slice
+    constexpr int PLANE = kCtaRows * 128;              // bytes of one 128-row slice
+    constexpr int STAGE_BYTES = C::NSPLIT * 2 * PLANE; // A and B-half planes of this CTA
+    constexpr int KSTEPS = 4;                          // 128-byte slice / 32 bytes per MMA
+    constexpr uint32_t IDESC = make_idesc(C::ATYPE, kPairRows, kBN);
+    constexpr uint32_t TMEM_COLS = 2 * kBN;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* tbuf_all = smem + C::STAGES * STAGE_BYTES;
     __shared__ __align__(8) uint64_t full_bar[C::STAGES];
     __shared__ __align__(8) uint64_t empty_bar[C::STAGES];
     __shared__ __align__(8) uint64_t tfull_bar[2];
@@ -146,56 +417,59 @@ __global__ void __launch_bounds__(192, 1)
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
-            mbar_init(&full_bar[s], 1);
+            mbar_init(&full_bar[s], 2);          // one expect_tx arrival per CTA
             mbar_init(&empty_bar[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&tfull_bar[s], 1);
-            mbar_init(&tempty_bar[s], 4);
+            mbar_init(&tempty_bar[s], 2 * kEpiWarps);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                      "r"(TMEM_COLS)
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer ----------------
+            // ---------------- TMA producer (both CTAs) ----------------
             int stage = 0;
             uint32_t phase = 0;
-            for (int t = blockIdx.x; t < a.ntiles && !abort_flag; t += gridDim.x) {
+            for (int t = pair; t < a.ntiles && !abort_flag; t += npairs) {
                 const Tile tl = a.tiles[t];
                 int k;
                 if (!tile_active(a, tl, k)) continue;
                 const int n = a.inst[tl.inst].n;
-                const int nk = (n + C::BKE - 1) / C::BKE;
-                const int rowA = tl.inst * a.P + tl.I * kTileM;
-                const int rowB = tl.inst * a.P + tl.J * BN;
+                const int nk = (n + BKE - 1) / BKE;
+                const int rowA = tl.inst * a.P + tl.I * kPairRows + (int)rank * kCtaRows;
+                const int rowB = tl.inst * a.P + tl.J * kBN + (int)rank * kCtaRows;
                 bool ok = true;
                 for (int kb = 0; kb < nk; ++kb) {
-                    if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, a.status)) {
+                    if (!wait_bar(&empty_bar[stage], phase ^ 1u, &abort_flag, a.status)) {
                         ok = false;
                         break;
                     }
-                    const uint32_t fb = smem_u32(&full_bar[stage]);
-                    mbar_expect_tx(&full_bar[stage], STAGE_BYTES);
+                    const uint32_t fb = map_to(smem_u32(&full_bar[stage]), 0);
+                    remote_expect_tx(fb, STAGE_BYTES);
                     uint8_t* sbase = smem + stage * STAGE_BYTES;
 #pragma unroll
                     for (int s = 0; s < C::NSPLIT; ++s) {
-                        tma_load_2d(smem_u32(sbase + s * A_PLANE), &maps.a[tl.chain][s], fb, kb * C::BKE, rowA);
-                        tma_load_2d(smem_u32(sbase + C::NSPLIT * A_PLANE + s * B_PLANE), &maps.b[tl.chain][s], fb,
-                                    kb * C::BKE, rowB);
+                        tma_load_pair(smem_u32(sbase + s * PLANE), &maps.a[tl.chain][s], fb, kb * BKE, rowA);
+                        tma_load_pair(smem_u32(sbase + (C::NSPLIT + s) * PLANE), &maps.a[tl.chain][s], fb,
+                                      kb * BKE, rowB);
                     }
                     if (++stage == C::STAGES) {
                         stage = 0;
@@ -207,119 +481,145 @@ __global__ void __launch_bounds__(192, 1)
         }
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) {
-            // ---------------- MMA issuer ----------------
+        if (lane == 0 && rank == 0) {
+            // ---------------- MMA issuer (even CTA) ----------------
             int stage = 0;
             uint32_t phase = 0;
             int buf = 0;
             uint32_t aphase = 0;
-            for (int t = blockIdx.x; t < a.ntiles && !abort_flag; t += gridDim.x) {
+            bool ok = true;
+            for (int t = pair; t < a.ntiles && ok && !abort_flag; t += npairs) {
                 const Tile tl = a.tiles[t];
                 int k;
                 if (!tile_active(a, tl, k)) continue;
                 const int n = a.inst[tl.inst].n;
-                const int nk = (n + C::BKE - 1) / C::BKE;
-                if (!mbar_wait(&tempty_bar[buf], aphase ^ 1u, &abort_flag, a.status)) break;
-                tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(buf * BN);
-                bool ok = true;
-                for (int kb = 0; kb < nk; ++kb) {
-                    if (!mbar_wait(&full_bar[stage], phase, &abort_flag, a.status)) {
+                const int nk = (n + BKE - 1) / BKE;
+                for (int kc = 0; kc < nk && ok; kc += C::CK) {
+                    if (!wait_bar(&tempty_bar[buf], aphase ^ 1u, &abort_flag, a.status)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sb = smem_u32(smem + stage * STAGE_BYTES);
+                    const uint32_t dt = tmem + (uint32_t)(buf * kBN);
+                    const int kend = min(nk, kc + C::CK);
+                    for (int kb = kc; kb < kend; ++kb) {
+                        if (!wait_bar(&full_bar[stage], phase, &abort_flag, a.status)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sb = smem_u32(smem + stage * STAGE_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < KSTEPS; ++kk) {
+                        for (int kk = 0; kk < KSTEPS; ++kk) {
 #pragma unroll
-                        for (int p = 0; p < C::NPROD; ++p) {
-                            const uint32_t sa = sb + kProdA[p] * A_PLANE + kk * 32;
-                            const uint32_t sbb = sb + C::NSPLIT * A_PLANE + kProdB[p] * B_PLANE + kk * 32;
-                            umma<C::TF32>(dt, sdesc_sw128(sa), sdesc_sw128(sbb), IDESC,
-                                          (kb | kk | p) != 0 ? 1u : 0u);
+                            for (int p = 0; p < C::NPROD; ++p) {
+                                const uint32_t sa = sb + kProdA[p] * PLANE + kk * 32;
+                                const uint32_t sbb = sb + (C::NSPLIT + kProdB[p]) * PLANE + kk * 32;
+                                umma_pair<C::TF32>(dt, sdesc_sw128(sa), sdesc_sw128(sbb), IDESC,
+                                                   ((kb - kc) | kk | p) != 0 ? 1u : 0u);
+                            }
+                        }
+                        umma_commit_pair(smem_u32(&empty_bar[stage]));
+                        if (++stage == C::STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
                         }
                     }
-                    umma_commit(smem_u32(&empty_bar[stage]));
-                    if (++stage == C::STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
+                    if (!ok) break;
+                    umma_commit_pair(smem_u32(&tfull_bar[buf]));
+                    if (++buf == 2) {
+                        buf = 0;
+                        aphase ^= 1u;
                     }
-                }
-                if (!ok) break;
-                umma_commit(smem_u32(&tfull_bar[buf]));
-                if (++buf == 2) {
-                    buf = 0;
-                    aphase ^= 1u;
                 }
             }
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue (warps 2..5) ----------------
-        const int q = warp & 3;                // TMEM lane quarter of this warp
+        // ---------------- epilogue (warps 2..9, both CTAs) ----------------
+        const int q = warp & 3;                  // TMEM lane quarter
+        const int hcol = (warp - 2) >> 2;        // column half of the 256-column tile
+        uint8_t* tbuf = tbuf_all + (warp - 2) * kTbufBytes;
+        const uint32_t tempty_leader0 = map_to(smem_u32(&tempty_bar[0]), 0);
+        const uint32_t tempty_leader1 = map_to(smem_u32(&tempty_bar[1]), 0);
         int buf = 0;
         uint32_t aphase = 0;
-        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        bool ok = true;
+        for (int t = pair; t < a.ntiles && ok; t += npairs) {
             const Tile tl = a.tiles[t];
             int k;
             if (!tile_active(a, tl, k)) continue;
-            if (!mbar_wait(&tfull_bar[buf], aphase, &abort_flag, a.status)) break;
-            tc_fence_after();
             EpiCtx e;
             make_ctx(a, tl, k, e, MODE == FTSP2_FP16X2);
-            const int r = tl.I * kTileM + q * 32 + lane;
-            const int rmin = tl.I * kTileM + q * 32;
-            double tr = 0.0, sq = 0.0;
-            for (int cc = 0; cc < BN / 16; ++cc) {
-                const int c0 = tl.J * BN + cc * 16;
-                if (c0 >= e.n) break;                 // warp-uniform
-                if (c0 + 15 < rmin) continue;         // whole chunk below the diagonal
-                if (rmin >= e.n) break;
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + cc * 16), v);
-                epi_segment<16>(a, e, r, c0, v, tr, sq);
+            const int nk = (e.n + BKE - 1) / BKE;
+            const int R0 = tl.I * kPairRows + (int)rank * kCtaRows + q * 32;   // first row of this warp
+            const int r = R0 + lane;
+            const int C0 = tl.J * kBN + hcol * 128;                            // first column of this warp
+            float acc[128];
+#pragma unroll
+            for (int i = 0; i < 128; ++i) acc[i] = 0.f;
+            for (int kc = 0; kc < nk; kc += C::CK) {
+                if (!wait_bar(&tfull_bar[buf], aphase, &abort_flag, a.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                    const int c0 = C0 + 16 * g;
+                    if (c0 < e.n && c0 + 15 >= R0 && R0 < e.n) {
+                        float v[16];
+                        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * kBN + hcol * 128 + 16 * g), v);
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) acc[16 * g + jj] += v[jj];
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) remote_arrive(buf ? tempty_leader1 : tempty_leader0);
+                if (++buf == 2) {
+                    buf = 0;
+                    aphase ^= 1u;
+                }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty_bar[buf]);
-            if (a.last) {
+            if (!ok) break;
+            double tr = 0.0, sq = 0.0;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const int c0 = C0 + 16 * g;
+                if (c0 < e.n && c0 + 15 >= R0 && R0 < e.n)
+                    epi_group<OUTFMT>(a, e, R0, r, c0, &acc[16 * g], tbuf, lane, tr, sq);
+            }
+            if constexpr (OUTFMT == kLastLayer) {
                 for (int o = 16; o > 0; o >>= 1) {
                     tr += __shfl_xor_sync(0xffffffffu, tr, o);
                     sq += __shfl_xor_sync(0xffffffffu, sq, o);
                 }
                 if (lane == 0) {
-                    a.partials[((size_t)t * 4 + q) * 2 + 0] = tr;
-                    a.partials[((size_t)t * 4 + q) * 2 + 1] = sq;
+                    const int slot = (int)rank * kEpiWarps + (warp - 2);
+                    a.partials[((size_t)t * kPartialSlots + slot) * 2 + 0] = tr;
+                    a.partials[((size_t)t * kPartialSlots + slot) * 2 + 1] = sq;
                 }
-            }
-            if (++buf == 2) {
-                buf = 0;
-                aphase ^= 1u;
             }
         }
     }
+    __syncwarp();
     tc_fence_before();
     __syncthreads();
+    cluster_sync();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
 
-int tc_block_n(int mode) {
-    switch (mode) {
-        case FTSP2_FP16X2: return TcCfg<FTSP2_FP16X2>::BN;
-        case FTSP2_BF16X3: return TcCfg<FTSP2_BF16X3>::BN;
-        case FTSP2_TF32X3: return TcCfg<FTSP2_TF32X3>::BN;
-    }
-    return 0;
-}
+int tc_block_n(int) { return kBN; }
+int tc_block_m(int) { return kPairRows; }
 
 template <int MODE>
 static int smem_of() {
     using C = TcCfg<MODE>;
-    return C::STAGES * C::NSPLIT * (kTileM * 128 + C::BN * 128) + 1024;
+    return C::STAGES * C::NSPLIT * 2 * kCtaRows * 128 + kEpiWarps * kTbufBytes + 1024;
 }
 
 int tc_smem_bytes(int mode) {
@@ -331,25 +631,45 @@ int tc_smem_bytes(int mode) {
     return 0;
 }
 
-template <int MODE>
-static cudaError_t launch_mode(const LayerArgs& a, const TmaMaps& maps, int grid, cudaStream_t s) {
+template <int MODE, int OUTFMT>
+static cudaError_t launch_variant(const LayerArgs& a, const TmaMaps& maps, int npairs, cudaStream_t s) {
     const int smem = smem_of<MODE>();
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(layer_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(layer_tc_kernel<MODE, OUTFMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    layer_tc_kernel<MODE><<<grid, 192, smem, s>>>(a, maps);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * npairs, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, layer_tc_kernel<MODE, OUTFMT>, a, maps);
     count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
-cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, int grid, cudaStream_t s) {
+template <int MODE, int MAINFMT>
+static cudaError_t launch_mode(const LayerArgs& a, const TmaMaps& maps, int npairs, cudaStream_t s) {
+    if (a.last) return launch_variant<MODE, kLastLayer>(a, maps, npairs, s);
+    if (a.next_fmt == OP_F32) return launch_variant<MODE, OP_F32>(a, maps, npairs, s);
+    return launch_variant<MODE, MAINFMT>(a, maps, npairs, s);
+}
+
+cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, int npairs, cudaStream_t s) {
     switch (mode) {
-        case FTSP2_FP16X2: return launch_mode<FTSP2_FP16X2>(a, maps, grid, s);
-        case FTSP2_BF16X3: return launch_mode<FTSP2_BF16X3>(a, maps, grid, s);
-        case FTSP2_TF32X3: return launch_mode<FTSP2_TF32X3>(a, maps, grid, s);
+        case FTSP2_FP16X2: return launch_mode<FTSP2_FP16X2, OP_F16X2>(a, maps, npairs, s);
+        case FTSP2_BF16X3: return launch_mode<FTSP2_BF16X3, OP_BF16X3>(a, maps, npairs, s);
+        case FTSP2_TF32X3: return launch_mode<FTSP2_TF32X3, OP_TF32X3>(a, maps, npairs, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -22,16 +22,16 @@ namespace ftsp2 {
 // (I < q (J + 1), q = BN / 128).  Chain-major order: all tiles of chain 0, then
 // chain 1; inside a chain, instance by instance.
 // ------------------------------------------------------------------------------
-__device__ __forceinline__ int tiles_of(int n, int BN) {
-    const int q = BN / kTileM;
-    const int nI = (n + kTileM - 1) / kTileM;
+__device__ __forceinline__ int tiles_of(int n, int BM, int BN) {
+    const int q = BN / BM;
+    const int nI = (n + BM - 1) / BM;
     const int nJ = (n + BN - 1) / BN;
     int c = 0;
     for (int J = 0; J < nJ; ++J) c += min(q * (J + 1), nI);
     return c;
 }
 
-__device__ void block_exclusive_scan_fill(const ftsp2_instance* inst, int nb, int BN, int nchains,
+__device__ void block_exclusive_scan_fill(const ftsp2_instance* inst, int nb, int BM, int BN, int nchains,
                                           InstWork* iw, Tile* tiles, int table) {
     __shared__ int tot[1024];
     __shared__ int chain_total;
@@ -40,7 +40,7 @@ __device__ void block_exclusive_scan_fill(const ftsp2_instance* inst, int nb, in
     const int b0 = min(nb, threadIdx.x * chunk);
     const int b1 = min(nb, b0 + chunk);
     int s = 0;
-    for (int b = b0; b < b1; ++b) s += tiles_of(inst[b].n, BN);
+    for (int b = b0; b < b1; ++b) s += tiles_of(inst[b].n, BM, BN);
     tot[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -53,15 +53,15 @@ __device__ void block_exclusive_scan_fill(const ftsp2_instance* inst, int nb, in
         chain_total = acc;
     }
     __syncthreads();
-    const int q = BN / kTileM;
+    const int q = BN / BM;
     for (int c = 0; c < nchains; ++c) {
         int pos = c * chain_total + tot[threadIdx.x];
         for (int b = b0; b < b1; ++b) {
             const int n = inst[b].n;
-            const int nI = (n + kTileM - 1) / kTileM;
+            const int nI = (n + BM - 1) / BM;
             const int nJ = (n + BN - 1) / BN;
             iw[b].tile_start[table][c] = pos;
-            iw[b].tile_count[table][c] = tiles_of(n, BN);
+            iw[b].tile_count[table][c] = tiles_of(n, BM, BN);
             for (int J = 0; J < nJ; ++J)
                 for (int I = 0; I < min(q * (J + 1), nI); ++I) tiles[pos++] = Tile{b, I, J, c};
         }
@@ -77,8 +77,8 @@ __global__ void prep_kernel(SetupArgs a) {
         a.iw[b].start_layer = 0;
     }
     if (threadIdx.x == 0) *a.status = 0;
-    if (a.tiles) block_exclusive_scan_fill(a.inst, a.nb, a.BN, a.nchains, a.iw, a.tiles, 0);
-    if (a.tiles_ref) block_exclusive_scan_fill(a.inst, a.nb, a.BN_ref, a.nchains, a.iw, a.tiles_ref, 1);
+    if (a.tiles) block_exclusive_scan_fill(a.inst, a.nb, a.BM, a.BN, a.nchains, a.iw, a.tiles, 0);
+    if (a.tiles_ref) block_exclusive_scan_fill(a.inst, a.nb, a.BM_ref, a.BN_ref, a.nchains, a.iw, a.tiles_ref, 1);
 }
 
 void launch_prep(const SetupArgs& a, cudaStream_t s) {
@@ -371,7 +371,7 @@ void launch_init(const InitArgs& a, int max_n, cudaStream_t s) {
 
 // ------------------------------------------------------------------------------
 // finalize: one warp per instance.  Per chain the last layer left, per tile and
-// per 32-row quarter, two FP64 sums of the centred output G = A_L + Z_L:
+// per epilogue warp (kPartialSlots slots), two FP64 sums of the centred output G = A_L + Z_L:
 // sum of the diagonal and sum of squares over the full matrix.  With
 // D = G + f0 I (flipped: (1 - f0) I - G):
 //   Tr D = n f0 + Tr G,  ||D||^2 = ||G||^2 + 2 f0 Tr G + n f0^2   (no flip)
@@ -391,9 +391,9 @@ __global__ void finalize_kernel(FinalArgs a) {
     for (int ch = 0; ch < a.nchains; ++ch) {
         double tr = 0.0, sq = 0.0;
         const int t0 = a.iw[b].tile_start[a.table][ch], tc = a.iw[b].tile_count[a.table][ch];
-        for (int t = lane; t < tc * 4; t += 32) {
-            tr += a.partials[(size_t)(t0 * 4 + t) * 2 + 0];
-            sq += a.partials[(size_t)(t0 * 4 + t) * 2 + 1];
+        for (int t = lane; t < tc * kPartialSlots; t += 32) {
+            tr += a.partials[(size_t)(t0 * kPartialSlots + t) * 2 + 0];
+            sq += a.partials[(size_t)(t0 * kPartialSlots + t) * 2 + 1];
         }
         for (int o = 16; o > 0; o >>= 1) {
             tr += __shfl_xor_sync(0xffffffffu, tr, o);
