@@ -183,6 +183,18 @@ def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
     return D, S
 
 
+def aggregate(t_step_local: float, world: int, device=None):
+    """Whole-job throughput of independent replicas: every rank processed one
+    solve per step, so value = world / (max over ranks of the step time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_step_local], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t)
+    return world / tmax, tmax
+
+
 def cuda_time(fn, reps):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -311,12 +323,7 @@ def main():
     launches = ft.kernel_launch_count() - launches0
     layer_ms, layer_n = ft.profile_read()
     ft.profile_layers(False)
-    t_step = ev0.elapsed_time(ev1) / 1000.0 / args.steps
-    tmax = torch.tensor([t_step], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    t_step = float(tmax)
-    value = world / t_step
+    value, t_step = aggregate(ev0.elapsed_time(ev1) / 1000.0 / args.steps, world, device="cuda")
     alg_flops = 2 * L * float(n) ** 3          # L symmetric squares (n^3) per chain, 2 chains
     # ---- accuracy of this run's output ----
     D = solver.matrix(0).double()
