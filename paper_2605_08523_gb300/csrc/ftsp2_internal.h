@@ -20,7 +20,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
-#include "../../include/ftsp2.h"
+#include "ftsp2.h"
 
 namespace ftsp2 {
 
@@ -28,7 +28,7 @@ constexpr int kMaxLayers = 64;
 constexpr int kMaxChains = 2;
 constexpr int kTileM = 128;                  // tensor-core tile rows (UMMA M)
 constexpr int kPad = 128;                    // matrix pitch granularity (elements)
-constexpr int kPartialSlots = 16;            // FP64 partial-sum slots per tile (last layer)
+constexpr int kPartialSlots = 32;            // FP64 partial-sum slots per tile (last layer)
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;   // 4 s
 
 enum ChainKind : int { CHAIN_FERMI = 0, CHAIN_ENTROPY = 1 };

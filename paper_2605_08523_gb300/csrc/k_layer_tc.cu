@@ -68,9 +68,12 @@ struct TcCfg<FTSP2_TF32X3> {
 constexpr int kPairRows = 256;       // rows of a pair tile (M of the 2-CTA MMA)
 constexpr int kBN = 256;             // columns of a tile (N)
 constexpr int kCtaRows = 128;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kTbufBytes = 16 * 32 * 4;    // per-warp transpose buffer
+constexpr int kEpiCols = kBN / (kEpiWarps / 4);   // columns per epilogue warp (64)
+constexpr int kGrp = 8;                            // columns per epilogue group
+constexpr int kTbufBytes = kGrp * 32 * 4;          // per-warp transpose buffer
+static_assert(kPartialSlots == 2 * kEpiWarps, "one partial-sum slot per epilogue warp of the pair");
 
 __device__ __constant__ int kProdA[6] = {0, 0, 1, 0, 2, 1};
 __device__ __constant__ int kProdB[6] = {0, 1, 0, 2, 0, 1};
@@ -247,17 +250,14 @@ struct OpFmtT<OP_F32> {
 };
 
 template <int ESZ>
-__device__ __forceinline__ void store16(uint8_t* dst, const uint32_t* v) {
+__device__ __forceinline__ void store8(uint8_t* dst, const uint32_t* v) {
     if constexpr (ESZ == 2) {
-        uint4 a, b;
+        uint4 a;
         a.x = v[0] | (v[1] << 16); a.y = v[2] | (v[3] << 16); a.z = v[4] | (v[5] << 16); a.w = v[6] | (v[7] << 16);
-        b.x = v[8] | (v[9] << 16); b.y = v[10] | (v[11] << 16); b.z = v[12] | (v[13] << 16); b.w = v[14] | (v[15] << 16);
-        reinterpret_cast<uint4*>(dst)[0] = a;
-        reinterpret_cast<uint4*>(dst)[1] = b;
+        *reinterpret_cast<uint4*>(dst) = a;
     } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            reinterpret_cast<uint4*>(dst)[i] = make_uint4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        reinterpret_cast<uint4*>(dst)[0] = make_uint4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<uint4*>(dst)[1] = make_uint4(v[4], v[5], v[6], v[7]);
     }
 }
 template <int ESZ>
@@ -271,6 +271,10 @@ __device__ __forceinline__ uint32_t load1(const uint8_t* src) {
     else return *reinterpret_cast<const uint32_t*>(src);
 }
 
+// Operand stores of one 32-row x 8-column block held by a warp (lane = row r,
+// columns c0 .. c0 + 7): direct stores at (r, c) as one 8-element vector per
+// plane; the mirror (c, r) goes through a per-warp shared transpose buffer so
+// that lane l stores 8 consecutive elements of mirrored row c0 + l / 4.
 template <int FMT>
 __device__ __forceinline__ void store_block(const LayerArgs& a, const EpiCtx& e, int R0, int r, int c0,
                                             const float* zs, uint8_t* tbuf, int lane) {
@@ -278,44 +282,44 @@ __device__ __forceinline__ void store_block(const LayerArgs& a, const EpiCtx& e,
     constexpr int ESZ = F::ESZ;
     uint8_t* const base = a.opw[e.chain];
     const size_t plane_bytes = a.plane_elems * ESZ;
+    uint32_t sp[F::NPL][kGrp];
+#pragma unroll
+    for (int jj = 0; jj < kGrp; ++jj) {
+        uint32_t o[F::NPL];
+        F::split(zs[jj], o);
+#pragma unroll
+        for (int p = 0; p < F::NPL; ++p) sp[p][jj] = o[p];
+    }
     const bool row_ok = r < e.n;
-    const bool full_direct = row_ok && r <= c0 && c0 + 15 < e.n;
-    const int j = lane >> 1, half = lane & 1;
-    const int cm = c0 + j;                 // mirrored row handled by this lane
-    const int rr0 = R0 + 16 * half;        // its first column
-    const bool full_mirror = cm < e.n && rr0 + 15 < cm && rr0 + 15 < e.n;
+    const bool full_direct = row_ok && r <= c0 && c0 + kGrp - 1 < e.n;
+    const int jm = lane >> 2, qm = lane & 3;
+    const int cm = c0 + jm;                 // mirrored row handled by this lane
+    const int rr0 = R0 + 8 * qm;            // its first column
+    const bool full_mirror = cm < e.n && rr0 + 7 < cm && rr0 + 7 < e.n;
 #pragma unroll
     for (int p = 0; p < F::NPL; ++p) {
-        uint32_t sp[16];
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-            uint32_t o[F::NPL];
-            F::split(zs[jj], o);
-            sp[jj] = o[p];
-        }
         uint8_t* pb = base + p * plane_bytes + (e.slab + (size_t)r * e.P + c0) * ESZ;
         if (full_direct) {
-            store16<ESZ>(pb, sp);
+            store8<ESZ>(pb, sp[p]);
         } else if (row_ok) {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj)
-                if (c0 + jj < e.n && r <= c0 + jj) store1<ESZ>(pb + jj * ESZ, sp[jj]);
+            for (int jj = 0; jj < kGrp; ++jj)
+                if (c0 + jj < e.n && r <= c0 + jj) store1<ESZ>(pb + jj * ESZ, sp[p][jj]);
         }
-        // mirror (c, r) for r < c through tbuf[jj][lane] = element (r, c0 + jj)
         __syncwarp();
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) store1<ESZ>(tbuf + (jj * 32 + lane) * ESZ, sp[jj]);
+        for (int jj = 0; jj < kGrp; ++jj) store1<ESZ>(tbuf + (jj * 32 + lane) * ESZ, sp[p][jj]);
         __syncwarp();
         uint8_t* mb = base + p * plane_bytes + (e.slab + (size_t)cm * e.P + rr0) * ESZ;
-        const uint8_t* src = tbuf + (j * 32 + 16 * half) * ESZ;
+        const uint8_t* src = tbuf + (jm * 32 + 8 * qm) * ESZ;
         if (full_mirror) {
-            uint32_t v[16];
+            uint32_t v[kGrp];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = load1<ESZ>(src + i * ESZ);
-            store16<ESZ>(mb, v);
+            for (int i = 0; i < kGrp; ++i) v[i] = load1<ESZ>(src + i * ESZ);
+            store8<ESZ>(mb, v);
         } else if (cm < e.n) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
+            for (int i = 0; i < kGrp; ++i) {
                 const int rr = rr0 + i;
                 if (rr < e.n && rr < cm) store1<ESZ>(mb + i * ESZ, load1<ESZ>(src + i * ESZ));
             }
@@ -324,9 +328,9 @@ __device__ __forceinline__ void store_block(const LayerArgs& a, const EpiCtx& e,
     __syncwarp();
 }
 
-// Centred update of a 16-column group for this lane's row, then operand stores
+// Centred update of an 8-column group for this lane's row, then operand stores
 // in format OUTFMT, or, for OUTFMT == kLastLayer, the output D and the partial
-// sums.  v holds the 16 accumulated products.
+// sums.  v holds the 8 accumulated products.
 constexpr int kLastLayer = -1;
 
 template <int OUTFMT>
@@ -334,43 +338,42 @@ __device__ __forceinline__ void epi_group(const LayerArgs& a, const EpiCtx& e, i
                                           uint8_t* tbuf, int lane, double& tr, double& sq) {
     constexpr bool LAST = OUTFMT == kLastLayer;
     const bool row_ok = r < e.n;
-    float zn[16];
+    float zn[kGrp];
     if (row_ok) {
         float* Zr = a.Z[e.chain] + e.slab + (size_t)r * e.P + c0;
         float* Ar = a.A[e.chain] + e.slab + (size_t)r * e.P + c0;
+        const float4 z0 = reinterpret_cast<const float4*>(Zr)[0], z1 = reinterpret_cast<const float4*>(Zr)[1];
+        const float4 a0 = reinterpret_cast<const float4*>(Ar)[0], a1 = reinterpret_cast<const float4*>(Ar)[1];
+        const float z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+        const float ac[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        float an[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float4 zz = reinterpret_cast<const float4*>(Zr)[i];
-            const float4 aa = reinterpret_cast<const float4*>(Ar)[i];
-            const float z4[4] = {zz.x, zz.y, zz.z, zz.w};
-            const float a4[4] = {aa.x, aa.y, aa.z, aa.w};
-            float an4[4];
+        for (int u = 0; u < 8; ++u) {
+            zn[u] = fmaf(e.mul, v[u], e.L.bp * z[u]);
+            an[u] = fmaf(e.L.d, z[u], ac[u]);
+        }
+        if constexpr (!LAST) {
+            reinterpret_cast<float4*>(Zr)[0] = make_float4(zn[0], zn[1], zn[2], zn[3]);
+            reinterpret_cast<float4*>(Zr)[1] = make_float4(zn[4], zn[5], zn[6], zn[7]);
+            reinterpret_cast<float4*>(Ar)[0] = make_float4(an[0], an[1], an[2], an[3]);
+            reinterpret_cast<float4*>(Ar)[1] = make_float4(an[4], an[5], an[6], an[7]);
+        } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                zn[4 * i + u] = fmaf(e.mul, v[4 * i + u], e.L.bp * z4[u]);
-                an4[u] = fmaf(e.L.d, z4[u], a4[u]);
-            }
-            if constexpr (!LAST) {
-                reinterpret_cast<float4*>(Zr)[i] = make_float4(zn[4 * i], zn[4 * i + 1], zn[4 * i + 2], zn[4 * i + 3]);
-                reinterpret_cast<float4*>(Ar)[i] = make_float4(an4[0], an4[1], an4[2], an4[3]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) zn[4 * i + u] += an4[u];     // G = A_L + Z_L
-            }
+            for (int u = 0; u < 8; ++u) zn[u] += an[u];     // G = A_L + Z_L
         }
     } else {
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) zn[jj] = 0.f;
+        for (int jj = 0; jj < kGrp; ++jj) zn[jj] = 0.f;
     }
     if constexpr (!LAST) {
         if constexpr (OUTFMT == OP_F16X2) {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) zn[jj] *= e.L.out_scale;
+            for (int jj = 0; jj < kGrp; ++jj) zn[jj] *= e.L.out_scale;
         }
         store_block<(OUTFMT < 0 ? OP_F32 : OUTFMT)>(a, e, R0, r, c0, zn, tbuf, lane);
     } else if (row_ok) {
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
+        for (int jj = 0; jj < kGrp; ++jj) {
             const int c = c0 + jj;
             if (c < e.n && r <= c) {
                 const float g = zn[jj];
@@ -390,6 +393,16 @@ __device__ __forceinline__ void epi_group(const LayerArgs& a, const EpiCtx& e, i
                 }
             }
         }
+    }
+}
+
+// Pull this lane's row segment of Z and A into L2 ahead of the final epilogue.
+__device__ __forceinline__ void prefetch_state(const LayerArgs& a, const EpiCtx& e, int r, int C0) {
+    if (r < e.n && C0 < e.n && C0 + kEpiCols - 1 >= r) {
+        const float* z = a.Z[e.chain] + e.slab + (size_t)r * e.P + C0;
+        const float* ac = a.A[e.chain] + e.slab + (size_t)r * e.P + C0;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(z), "r"(kEpiCols * 4) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ac), "r"(kEpiCols * 4) : "memory");
     }
 }
 
@@ -536,9 +549,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue (warps 2..9, both CTAs) ----------------
+        // ---------------- epilogue (warps 2..17, both CTAs) ----------------
         const int q = warp & 3;                  // TMEM lane quarter
-        const int hcol = (warp - 2) >> 2;        // column half of the 256-column tile
+        const int cq = (warp - 2) >> 2;          // column quarter of the 256-column tile
         uint8_t* tbuf = tbuf_all + (warp - 2) * kTbufBytes;
         const uint32_t tempty_leader0 = map_to(smem_u32(&tempty_bar[0]), 0);
         const uint32_t tempty_leader1 = map_to(smem_u32(&tempty_bar[1]), 0);
@@ -554,24 +567,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int nk = (e.n + BKE - 1) / BKE;
             const int R0 = tl.I * kPairRows + (int)rank * kCtaRows + q * 32;   // first row of this warp
             const int r = R0 + lane;
-            const int C0 = tl.J * kBN + hcol * 128;                            // first column of this warp
-            float acc[128];
+            const int C0 = tl.J * kBN + cq * kEpiCols;                         // first column of this warp
+            const bool warp_live = C0 < e.n && C0 + kEpiCols - 1 >= R0 && R0 < e.n;
+            float acc[kEpiCols];
 #pragma unroll
-            for (int i = 0; i < 128; ++i) acc[i] = 0.f;
+            for (int i = 0; i < kEpiCols; ++i) acc[i] = 0.f;
+            const int kpre = max(0, nk - 2 * C::CK);      // prefetch the state one chunk ahead of the end
             for (int kc = 0; kc < nk; kc += C::CK) {
+                if (kc <= kpre && kpre < kc + C::CK) prefetch_state(a, e, r, C0);
                 if (!wait_bar(&tfull_bar[buf], aphase, &abort_flag, a.status)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
+                if (warp_live) {
 #pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    const int c0 = C0 + 16 * g;
-                    if (c0 < e.n && c0 + 15 >= R0 && R0 < e.n) {
-                        float v[16];
-                        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * kBN + hcol * 128 + 16 * g), v);
+                    for (int g = 0; g < kEpiCols / 16; ++g) {
+                        const int c0 = C0 + 16 * g;
+                        if (c0 < e.n && c0 + 15 >= R0) {
+                            float v[16];
+                            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * kBN + cq * kEpiCols + 16 * g),
+                                      v);
 #pragma unroll
-                        for (int jj = 0; jj < 16; ++jj) acc[16 * g + jj] += v[jj];
+                            for (int jj = 0; jj < 16; ++jj) acc[16 * g + jj] += v[jj];
+                        }
                     }
                 }
                 tc_fence_before();
@@ -584,11 +603,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok) break;
             double tr = 0.0, sq = 0.0;
+            if (warp_live) {
 #pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const int c0 = C0 + 16 * g;
-                if (c0 < e.n && c0 + 15 >= R0 && R0 < e.n)
-                    epi_group<OUTFMT>(a, e, R0, r, c0, &acc[16 * g], tbuf, lane, tr, sq);
+                for (int g = 0; g < kEpiCols / kGrp; ++g) {
+                    const int c0 = C0 + kGrp * g;
+                    if (c0 < e.n && c0 + kGrp - 1 >= R0)
+                        epi_group<OUTFMT>(a, e, R0, r, c0, &acc[kGrp * g], tbuf, lane, tr, sq);
+                }
             }
             if constexpr (OUTFMT == kLastLayer) {
                 for (int o = 16; o > 0; o >>= 1) {
