@@ -198,6 +198,35 @@ ftsp2_status ftsp2_density_entropy(const double* dH, const ftsp2_instance* inst,
                                    ftsp2_rescale_rec* dRec,
                                    void* ws, size_t ws_bytes, void* stream);
 
+/* Density without allocation.  Same computation and arguments as
+ * ftsp2_density, but the workspace comes from an 8 MiB array inside the
+ * library's device image instead of from the caller.  It is meant for callers
+ * that cannot allocate device memory where they need D: code running while a
+ * stream is being captured into a CUDA graph, plug-ins whose host application
+ * owns all device memory, loops that must not pay for cudaMalloc.  (The paper
+ * has no counterpart; this is an interface convenience of this library.)
+ *   - Allocates nothing: no cudaMalloc, no cudaFree, no host buffers.  The
+ *     model set must have been created beforehand.
+ *   - Limit: the batch must fit the 8 MiB array.  It needs about
+ *     nb * P^2 * (8 + 2 b) bytes plus a few KiB of bookkeeping, where P is the
+ *     largest n rounded up to 128 and b the operand bytes per element (4 for
+ *     FTSP2_FP16X2 and FTSP2_FP32, 6 for FTSP2_BF16X3, 8 for FTSP2_TF32X3;
+ *     FTSP2_REFINE1/2 add 8).  A single FP16X2 instance fits up to n = 640.
+ *     Larger batches are rejected with FTSP2_E_WORKSPACE before any launch.
+ *     FTSP2_SYNC is refused (FTSP2_E_ARG); read dRec instead.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind; each call
+ *     rewrites everything it reads before reading it.  Calls that overlap on
+ *     the GPU (other streams, other host threads) race on the array: serialise
+ *     them. */
+ftsp2_status ftsp2_density_noalloc(const double* dH, const ftsp2_instance* inst,
+                                   const ftsp2_instance* dInst, int nb,
+                                   const ftsp2_model_set* set, ftsp2_mode mode, int flags,
+                                   float* dD, double* dTrace, ftsp2_rescale_rec* dRec,
+                                   void* stream);
+
 /* ---- training (a7) -------------------------------------------------------------- */
 
 typedef struct {

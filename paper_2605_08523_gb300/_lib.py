@@ -62,6 +62,7 @@ SIGNATURES = {
     "ftsp2_density": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "ftsp2_entropy": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _SZ, _VP]),
     "ftsp2_density_entropy": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "ftsp2_density_noalloc": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP]),
     "ftsp2_train_workspace_size": (_SZ, [_I, _I]),
     "ftsp2_train_coeffs": (_I, [_I, _D, _D, _I, _D, _VP, _I, _I, _I, C.POINTER(_D), C.POINTER(_D),
                                 C.POINTER(TrainReport), _VP, _SZ, _VP]),

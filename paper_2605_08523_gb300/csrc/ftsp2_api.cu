@@ -788,6 +788,69 @@ ftsp2_status ftsp2_density_entropy(const double* dH, const ftsp2_instance* inst,
     return run(dH, inst, dInst, nb, set, mode, flags, 3, dD, dTrace, dS, dRec, ws, ws_bytes, stream);
 }
 
+}  // extern "C"
+
+namespace ftsp2 {
+
+// ---- density without any allocation ------------------------------------------
+//
+// Some callers cannot allocate device memory at the point where they need a
+// density matrix: code that runs while a stream is being captured into a CUDA
+// graph (an allocation there breaks or invalidates the capture), plug-ins that
+// live inside a host application owning every device allocation, and
+// real-time loops that forbid the cost and possible synchronisation of
+// cudaMalloc.  ftsp2_density_noalloc serves them: it runs the same kernels as
+// ftsp2_density but takes its scratch (the workspace of ftsp2_density) from
+// the fixed device array below instead of from the caller.
+
+// 8 MiB of scratch in the library image.  Every GPU that loads the library
+// holds this array until the process exits.
+constexpr size_t kNoallocScratchBytes = size_t(8) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// Device address of the array on the current device.  In host code the name
+// g_noalloc_scratch is only a host-side stand-in, so the address is looked up
+// with cudaGetSymbolAddress once per device (with that device current) and
+// cached; the lookup allocates nothing.
+static ftsp2_status noalloc_scratch(void** ws, size_t* bytes) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static void* addr[kMaxDevices] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FTSP2_E_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return FTSP2_E_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FTSP2_E_CUDA;
+        addr[dev] = p;
+    }
+    // the hot path wants a 1024-byte aligned workspace
+    const uintptr_t base = reinterpret_cast<uintptr_t>(addr[dev]);
+    const uintptr_t aligned = (base + 1023) & ~uintptr_t(1023);
+    *ws = reinterpret_cast<void*>(aligned);
+    *bytes = kNoallocScratchBytes - (size_t)(aligned - base);
+    return FTSP2_OK;
+}
+
+}  // namespace ftsp2
+
+extern "C" {
+
+ftsp2_status ftsp2_density_noalloc(const double* dH, const ftsp2_instance* inst, const ftsp2_instance* dInst,
+                                   int nb, const ftsp2_model_set* set, ftsp2_mode mode, int flags, float* dD,
+                                   double* dTrace, ftsp2_rescale_rec* dRec, void* stream) {
+    // FTSP2_SYNC would need a host buffer for the records: not offered here.
+    if (flags & FTSP2_SYNC) return FTSP2_E_ARG;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    const ftsp2_status st = noalloc_scratch(&ws, &ws_bytes);
+    if (st != FTSP2_OK) return st;
+    // run() checks the plan against ws_bytes and returns FTSP2_E_WORKSPACE,
+    // before launching anything, when the batch needs more scratch than the array.
+    return run(dH, inst, dInst, nb, set, mode, flags, 1, dD, dTrace, nullptr, dRec, ws, ws_bytes, stream);
+}
+
 size_t ftsp2_train_workspace_size(int nsamples, int L) {
     if (nsamples < 1 || L < 1 || L > kMaxLayers) return 0;
     return train_layout(nsamples, L).total;
