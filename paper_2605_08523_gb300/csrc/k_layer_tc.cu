@@ -75,8 +75,9 @@ constexpr int kGrp = 8;                            // columns per epilogue group
 constexpr int kTbufBytes = kGrp * 32 * 4;          // per-warp transpose buffer
 static_assert(kPartialSlots == 2 * kEpiWarps, "one partial-sum slot per epilogue warp of the pair");
 
-__device__ __constant__ int kProdA[6] = {0, 0, 1, 0, 2, 1};
-__device__ __constant__ int kProdB[6] = {0, 1, 0, 2, 0, 1};
+// split planes (s, t) of the products Z_s Z_t, in issue order
+__host__ __device__ constexpr int prod_a(int p) { return p == 2 ? 1 : (p == 4 ? 2 : (p == 5 ? 1 : 0)); }
+__host__ __device__ constexpr int prod_b(int p) { return p == 1 ? 1 : (p == 3 ? 2 : (p == 5 ? 1 : 0)); }
 
 // Instruction descriptor of tcgen05.mma kind::f16 / kind::tf32: D in FP32,
 // A and B K-major, M x N.
@@ -185,8 +186,8 @@ __device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
+// 32 lanes x 16 columns of FP32 from TMEM into registers (no wait)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
         "%12, %13, %14, %15}, [%16];"
@@ -194,10 +195,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -501,6 +500,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             int buf = 0;
             uint32_t aphase = 0;
             bool ok = true;
+            // descriptors differ only in the start-address field (bits 0-13,
+            // address >> 4); all operand slices lie inside this CTA's window
+            const uint64_t desc0 = sdesc_sw128(smem_u32(smem));
             for (int t = pair; t < a.ntiles && ok && !abort_flag; t += npairs) {
                 const Tile tl = a.tiles[t];
                 int k;
@@ -521,15 +523,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sb = smem_u32(smem + stage * STAGE_BYTES);
+                        const uint64_t ds = desc0 + (uint64_t)((stage * STAGE_BYTES) >> 4);
+                        const uint32_t first = kb == kc ? 0u : 1u;
 #pragma unroll
                         for (int kk = 0; kk < KSTEPS; ++kk) {
 #pragma unroll
                             for (int p = 0; p < C::NPROD; ++p) {
-                                const uint32_t sa = sb + kProdA[p] * PLANE + kk * 32;
-                                const uint32_t sbb = sb + (C::NSPLIT + kProdB[p]) * PLANE + kk * 32;
-                                umma_pair<C::TF32>(dt, sdesc_sw128(sa), sdesc_sw128(sbb), IDESC,
-                                                   ((kb - kc) | kk | p) != 0 ? 1u : 0u);
+                                const uint64_t da = ds + (uint64_t)((prod_a(p) * PLANE + kk * 32) >> 4);
+                                const uint64_t db = ds + (uint64_t)(((C::NSPLIT + prod_b(p)) * PLANE + kk * 32) >> 4);
+                                umma_pair<C::TF32>(dt, da, db, IDESC, (kk == 0 && p == 0) ? first : 1u);
                             }
                         }
                         umma_commit_pair(smem_u32(&empty_bar[stage]));
@@ -581,15 +583,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 if (warp_live) {
+                    // two 16-column loads in flight per wait
 #pragma unroll
-                    for (int g = 0; g < kEpiCols / 16; ++g) {
-                        const int c0 = C0 + 16 * g;
-                        if (c0 < e.n && c0 + 15 >= R0) {
-                            float v[16];
-                            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * kBN + cq * kEpiCols + 16 * g),
-                                      v);
+                    for (int g = 0; g < kEpiCols / 16; g += 2) {
+                        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * kBN + cq * kEpiCols + 16 * g);
+                        uint32_t v0[16], v1[16];
+                        tmem_ld16(ta, v0);
+                        tmem_ld16(ta + 16, v1);
+                        tmem_wait_ld();
 #pragma unroll
-                            for (int jj = 0; jj < 16; ++jj) acc[16 * g + jj] += v[jj];
+                        for (int jj = 0; jj < 16; ++jj) {
+                            acc[16 * g + jj] += __uint_as_float(v0[jj]);
+                            acc[16 * g + 16 + jj] += __uint_as_float(v1[jj]);
                         }
                     }
                 }
