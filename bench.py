@@ -183,6 +183,21 @@ def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
     return D, S
 
 
+# (mode, n, sha256[:16] of the layer-kernel sources) -> dram read + write bytes
+# of one layer launch (both chains), from the ncu capture summarised in
+# profiles/layer_tc_fp16x2_n4096.md
+MEASURED_TRAFFIC = {("fp16x2", 4096, "b813375eda399c75"): 428.024320e6 + 256.838912e6}
+
+
+def kernel_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("k_layer_tc.cu", "epilogue.cuh", "ftsp2_internal.h"):
+        with open(os.path.join(ROOT, "paper_2605_08523_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def aggregate(t_step_local: float, world: int, device=None):
     """Whole-job throughput of independent replicas: every rank processed one
     solve per step, so value = world / (max over ranks of the step time)."""
@@ -367,14 +382,10 @@ def main():
     hw_per_launch = 2 * tiles * 128 * BN * n * 2 * nprod
     hw_achieved = hw_per_launch / layer_avg / 1e12 if layer_avg > 0 else None
     hw_peak = peak if args.mode in ("fp16x2", "bf16x3") else peak / 2.0
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            tr = json.load(f)
-        key = "layer_tc_%s_n%d" % (args.mode, n)
-        traffic = tr.get(key)
-    except Exception:
-        pass
+    # DRAM bytes per launch from one ncu capture (profiles/layer_tc_fp16x2_n4096.md),
+    # valid only while the kernel sources are the ones that were profiled
+    ksha = kernel_sha()
+    traffic = MEASURED_TRAFFIC.get((args.mode, n, ksha))
 
     result = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -390,7 +401,7 @@ def main():
                      "trD_ref": n / 2, "S": S, "S_ref": Sref},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": "layer_tc_kernel<%s>" % args.mode.upper(),
+                     "kernel": "layer_tc_kernel<%s>" % args.mode.upper(), "kernel_sha": ksha,
                      "per_launch_alg_flops": alg_per_launch, "avg_launch_ms": layer_avg * 1000,
                      "peak_kind": "bf16_tflops_sustained (%s)" % pk_kind,
                      "hw_tensor_tflops": hw_achieved, "hw_frac": (hw_achieved / hw_peak) if hw_achieved else None},

@@ -102,6 +102,19 @@ class ModelSet:
         check(lib().ftsp2_model_set_create(arr, len(tables), C.byref(self._h)), "ftsp2_model_set_create")
         self.tables = tables
 
+    @classmethod
+    def from_json(cls, paths):
+        """Model set from table files written by train_tables (keys beta0, mu0,
+        alpha, theta and optionally theta_entropy)."""
+        import json
+        tabs = []
+        for p in paths:
+            with open(p) as f:
+                d = json.load(f)
+            tabs.append(dict(theta=d["theta"], beta0=d["beta0"], mu0=d["mu0"], alpha=d.get("alpha", 0.842704),
+                             theta_entropy=d.get("theta_entropy")))
+        return cls(tabs)
+
     @property
     def handle(self):
         return self._h

@@ -4,7 +4,8 @@
 // epilogue as the tensor-core kernel; the operand is the full symmetric FP32
 // matrix Z_k (written for this layer by the previous layer's epilogue).
 // Classic register-blocked tile product: 256 threads, 8 x 8 outputs each,
-// K-slices of 16 staged through shared memory (transposed, K-major rows).
+// K-slices of 16 staged through shared memory (transposed, K-major rows),
+// sums taken over 128-element K chunks.
 #include "epilogue.cuh"
 #include "ftsp2_internal.h"
 
@@ -26,11 +27,13 @@ __global__ void __launch_bounds__(256) layer_simt_kernel(const __grid_constant__
         const int n = a.inst[tl.inst].n;
         const float* Op = reinterpret_cast<const float*>(a.opr[tl.chain]) + (size_t)tl.inst * a.P * a.P;
         const int rowA = tl.I * SB, rowB = tl.J * SB;
-        float acc[8][8];
+        // products are summed over 128-element K chunks in `part` and the
+        // chunks are added into `acc` (shorter FP32 accumulation runs)
+        float acc[8][8], part[8][8];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+            for (int j = 0; j < 8; ++j) acc[i][j] = part[i][j] = 0.f;
         const int nk = (n + SK - 1) / SK;
         // loader mapping: 128 rows x 16 columns = 512 float4; 2 per thread
         for (int kb = 0; kb < nk; ++kb) {
@@ -58,9 +61,18 @@ __global__ void __launch_bounds__(256) layer_simt_kernel(const __grid_constant__
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(ra[i], rb[j], acc[i][j]);
+                    for (int j = 0; j < 8; ++j) part[i][j] = fmaf(ra[i], rb[j], part[i][j]);
             }
             __syncthreads();
+            if ((kb & 7) == 7 || kb == nk - 1) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        acc[i][j] += part[i][j];
+                        part[i][j] = 0.f;
+                    }
+            }
         }
         EpiCtx e;
         make_ctx(a, tl, k, e, false);

@@ -370,7 +370,7 @@ void launch_init(const InitArgs& a, int max_n, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------------
-// finalize: one warp per instance.  Per chain the last layer left, per tile and
+// finalize: one block per instance.  Per chain the last layer left, per tile and
 // per epilogue warp (kPartialSlots slots), two FP64 sums of the centred output G = A_L + Z_L:
 // sum of the diagonal and sum of squares over the full matrix.  With
 // D = G + f0 I (flipped: (1 - f0) I - G):
@@ -379,11 +379,13 @@ void launch_init(const InitArgs& a, int max_n, cudaStream_t s) {
 // and for the entropy chain F = G + g0 I:
 //   S = 4 ln2 (Tr F - ||F||^2) = 4 ln2 (n g0 (1 - g0) + (1 - 2 g0) Tr G - ||G||^2).
 // ------------------------------------------------------------------------------
-__global__ void finalize_kernel(FinalArgs a) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= a.nb) return;
-    const int b = warp;
+__global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a) {
+    // one block per instance; each chain's partial sums are reduced by a
+    // fixed assignment of slots to threads and a fixed tree, so the result
+    // does not depend on scheduling
+    const int b = blockIdx.x;
+    if (b >= a.nb) return;
+    __shared__ double s_tr[256], s_sq[256];
     ftsp2_rescale_rec rec = a.rec[b];
     const int gstat = *a.status;
     const int n = a.inst[b].n;
@@ -391,15 +393,24 @@ __global__ void finalize_kernel(FinalArgs a) {
     for (int ch = 0; ch < a.nchains; ++ch) {
         double tr = 0.0, sq = 0.0;
         const int t0 = a.iw[b].tile_start[a.table][ch], tc = a.iw[b].tile_count[a.table][ch];
-        for (int t = lane; t < tc * kPartialSlots; t += 32) {
+        for (int t = threadIdx.x; t < tc * kPartialSlots; t += blockDim.x) {
             tr += a.partials[(size_t)(t0 * kPartialSlots + t) * 2 + 0];
             sq += a.partials[(size_t)(t0 * kPartialSlots + t) * 2 + 1];
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            tr += __shfl_xor_sync(0xffffffffu, tr, o);
-            sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        s_tr[threadIdx.x] = tr;
+        s_sq[threadIdx.x] = sq;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                s_tr[threadIdx.x] += s_tr[threadIdx.x + o];
+                s_sq[threadIdx.x] += s_sq[threadIdx.x + o];
+            }
+            __syncthreads();
         }
-        if (lane != 0) continue;
+        tr = s_tr[0];
+        sq = s_sq[0];
+        __syncthreads();
+        if (threadIdx.x != 0) continue;
         const bool ok = rec.status == FTSP2_OK && rec.model >= 0 && gstat == 0;
         if (a.chain_kind[ch] == CHAIN_FERMI) {
             double trD = qnan, frD = qnan;
@@ -428,16 +439,14 @@ __global__ void finalize_kernel(FinalArgs a) {
             if (a.S) a.S[b] = S;
         }
     }
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
         if (gstat != 0 && rec.status == FTSP2_OK) rec.status = gstat;
         a.rec[b].status = rec.status;
     }
 }
 
 void launch_finalize(const FinalArgs& a, cudaStream_t s) {
-    const int threads = 128;
-    const int blocks = (a.nb * 32 + threads - 1) / threads;
-    finalize_kernel<<<blocks, threads, 0, s>>>(a);
+    finalize_kernel<<<a.nb, 256, 0, s>>>(a);
     count_launch();
 }
 

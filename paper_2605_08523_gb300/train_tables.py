@@ -1,0 +1,89 @@
+"""Train coefficient tables on the GPU with the library's own trainer and write
+them as JSON (usage: ``python -m paper_2605_08523_gb300.train_tables OUTDIR``).
+
+Two groups of tables:
+
+* ``entropy_b1500_L26``: an entropy table (theta_entropy, Sec. II B) for the
+  26-layer Fermi table printed in the paper's Appendix A, started from those
+  Fermi weights (the paper's own recipe for theta_entropy) with
+  alpha = 0.842704;
+* the training sweep of L in {16, 24, 32} layers at scaled temperatures
+  kT0 in [0.005, 0.05] (beta0 in {20, 50, 100, 200}, mu0 = 1/3): a Fermi table
+  from the SP2 initial guess, then an entropy table started from it.
+
+Every fit uses 1e5 fixed samples from p ~ 1 + |f'| (training.sample_points) and
+Levenberg-Marquardt with geodesic acceleration (ftsp2_train_coeffs).  The max
+error of each table is measured on a uniform grid of 2e6 points in [0, 1].
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+from . import training
+
+ALPHA = 0.842704
+MU0 = 1.0 / 3.0
+
+
+def max_error(ft, target, beta0, mu0, theta, alpha, grid=2_000_001):
+    import torch
+    x = torch.linspace(0.0, 1.0, grid, dtype=torch.float64, device="cuda")
+    r, _ = ft.ftsp2_train_residual_jacobian(target, beta0, mu0, theta, x, alpha=alpha, with_jacobian=False)
+    return float(r.abs().max())
+
+
+def fit(ft, target, beta0, L, init, iterations, alpha=1.0, nsamples=100_000):
+    t0 = time.time()
+    th, rep = training.train_table(ft, target, beta0, MU0, L, alpha=alpha, iterations=iterations,
+                                   nsamples=nsamples, theta_init=init)
+    rep["seconds"] = time.time() - t0
+    rep["max_err_grid"] = max_error(ft, target, beta0, MU0, th, alpha)
+    return th, rep
+
+
+def main(outdir: str, iterations: int = 800, quick: bool = False):
+    import paper_2605_08523_gb300 as ft
+    from .build import build
+    build()
+    os.makedirs(outdir, exist_ok=True)
+    out = {}
+    # entropy table for the printed Fermi table
+    ms = ft.ModelSet()
+    printed, b0, m0, _ = ms.table(0)
+    th_s, rep_s = fit(ft, ft.TARGET_ENTROPY, b0, 26, printed, 4 * iterations, alpha=ALPHA)
+    out["entropy_b1500_L26"] = dict(beta0=b0, mu0=m0, alpha=ALPHA, L=26, theta=printed.tolist(),
+                                    theta_entropy=th_s.tolist(),
+                                    fit=dict(max_err_fermi=max_error(ft, ft.TARGET_FERMI, b0, m0, printed, 1.0),
+                                             max_err_entropy=rep_s["max_err_grid"],
+                                             max_err_entropy_theta_fermi=max_error(ft, ft.TARGET_ENTROPY, b0, m0,
+                                                                                   printed, ALPHA)),
+                                    train=dict(entropy=rep_s, samples=100_000, density="1+|f'|"))
+    print("entropy_b1500_L26", out["entropy_b1500_L26"]["fit"], flush=True)
+    betas = [20.0, 200.0] if quick else [20.0, 50.0, 100.0, 200.0]
+    for beta0 in betas:
+        for L in (16, 24, 32):
+            th, rep = fit(ft, ft.TARGET_FERMI, beta0, L, None, iterations)
+            ths, reps = fit(ft, ft.TARGET_ENTROPY, beta0, L, th, iterations, alpha=ALPHA)
+            name = "b%d_L%d" % (int(beta0), L)
+            out[name] = dict(beta0=beta0, mu0=MU0, alpha=ALPHA, L=L, theta=th.tolist(), theta_entropy=ths.tolist(),
+                             fit=dict(max_err_fermi=rep["max_err_grid"], max_err_entropy=reps["max_err_grid"],
+                                      max_err_sp2_init=max_error(ft, ft.TARGET_FERMI, beta0, MU0,
+                                                                 training.sp2_init(L, beta0, MU0), 1.0),
+                                      layer_count=training.layer_count(beta0)),
+                             train=dict(fermi=rep, entropy=reps, samples=100_000, density="1+|f'|"))
+            print(name, out[name]["fit"], flush=True)
+    for name, d in out.items():
+        with open(os.path.join(outdir, name + ".json"), "w") as f:
+            json.dump(d, f, indent=1)
+    return out
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else "tables_out",
+         iterations=int(sys.argv[2]) if len(sys.argv) > 2 else 800,
+         quick="--quick" in sys.argv)
