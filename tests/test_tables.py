@@ -1,0 +1,64 @@
+"""The coefficient tables shipped in paper_2605_08523_gb300/tables (written by
+the library's GPU trainer, paper_2605_08523_gb300.train_tables): metadata, and
+their fit error re-measured with the oracle's scalar recursion against the
+target functions (the tables are outputs under test; the expected values are
+the logistic and entropy definitions).  CPU only."""
+import glob
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import tables, train
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+FILES = sorted(glob.glob(os.path.join(ROOT, "paper_2605_08523_gb300", "tables", "*.json")))
+
+
+def load(name):
+    with open(os.path.join(ROOT, "paper_2605_08523_gb300", "tables", name + ".json")) as f:
+        return json.load(f)
+
+
+def test_tables_present():
+    names = {os.path.basename(f)[:-5] for f in FILES}
+    assert "entropy_b1500_L26" in names
+    for b in (20, 50, 100, 200):
+        for L in (16, 24, 32):
+            assert "b%d_L%d" % (b, L) in names
+
+
+@pytest.mark.parametrize("path", FILES, ids=[os.path.basename(f) for f in FILES])
+def test_table_fit_errors(path):
+    d = json.load(open(path))
+    th = np.array(d["theta"])
+    ths = np.array(d["theta_entropy"])
+    assert th.shape == (d["L"], 4) and ths.shape == (d["L"], 4)
+    b0, m0, al = d["beta0"], d["mu0"], d["alpha"]
+    ef = train.max_error(th, "fermi", b0, m0, 1.0, grid=400001)
+    es = train.max_error(ths, "entropy", b0, m0, al, grid=400001)
+    # the recorded GPU figures agree with the oracle's evaluation
+    assert ef == pytest.approx(d["fit"]["max_err_fermi"], rel=0.05, abs=1e-9)
+    assert es == pytest.approx(d["fit"]["max_err_entropy"], rel=0.05, abs=1e-9)
+
+
+def test_entropy_table_for_printed_weights():
+    d = load("entropy_b1500_L26")
+    assert np.array_equal(np.array(d["theta"]), np.array(tables.PRINTED_B1500))
+    es = train.max_error(np.array(d["theta_entropy"]), "entropy", 1500.0, 1 / 3, 0.842704, grid=2_000_001)
+    e_fermi = train.max_error(np.array(d["theta"]), "entropy", 1500.0, 1 / 3, 0.842704, grid=2_000_001)
+    # Table entropy: theta_fermi 1.24e-3; training theta_entropy improves it by orders of magnitude
+    assert abs(e_fermi - 1.24e-3) < 1e-5
+    assert es < 1e-6
+
+
+def test_training_sweep_layer_count():
+    # Eq. layer count: beta0 = 200 needs n_l = 18.5 layers, so 16 layers
+    # underfit while 24 and 32 reach ~1e-6; every trained table beats its SP2
+    # initial guess by orders of magnitude (what the learned part gains).
+    e = {(b, L): load("b%d_L%d" % (b, L))["fit"] for b in (20, 50, 100, 200) for L in (16, 24, 32)}
+    assert e[(200, 16)]["max_err_fermi"] > 5 * e[(200, 24)]["max_err_fermi"]
+    for k, f in e.items():
+        assert f["max_err_fermi"] < 1e-3 * f["max_err_sp2_init"], k
+        assert f["max_err_fermi"] < 3e-5, k
