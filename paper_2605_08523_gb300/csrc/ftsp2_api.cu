@@ -238,6 +238,8 @@ static int op_bytes(int fmt) {
         default: return 4;
     }
 }
+constexpr int kShortChunkLayers = 6;
+
 static int refine_layers(int flags) { return (flags & FTSP2_REFINE2) ? 2 : ((flags & FTSP2_REFINE1) ? 1 : 0); }
 
 static int host_tiles_of(int n, int BM, int BN) {
@@ -443,6 +445,11 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         const bool next_simt = g + 1 < Lmax && is_simt(g + 1);
         la.gl = g;
         la.last = g == Lmax - 1;
+        // The last layers run with 64-element accumulation chunks: their rounding
+        // reaches the output undamped (earlier errors are contracted by the
+        // saturating layers), and the entropy is linear in it for occupations
+        // near 0 and 1.
+        la.chunk_elems = g >= Lmax - kShortChunkLayers ? 64 : 0;
         la.next_fmt = next_simt ? OP_F32 : fmt;
         for (int c = 0; c < L.nchains; ++c) {
             const int rp = g & 1, wp = (g + 1) & 1;

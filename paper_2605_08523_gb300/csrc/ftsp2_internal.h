@@ -150,6 +150,7 @@ struct LayerArgs {
     int P, Lmax, gl, last, nchains;
     int chain_kind[kMaxChains];
     int next_fmt;
+    int chunk_elems;                  // K elements per TMEM accumulation chunk (0: kernel default)
     float* Z[kMaxChains];
     float* A[kMaxChains];
     const uint8_t* opr[kMaxChains];   // read operands (plane 0 base) - SIMT path

@@ -22,8 +22,8 @@
 // the MMA commit is multicast to both CTAs' "empty" and "tfull" barriers; the
 // odd CTA's epilogue warps release accumulators on the even CTA's "tempty".
 //
-// Chunked accumulation.  Every 128 elements of K (CK slices) the MMAs switch
-// to the other of two TMEM accumulators and the epilogue adds the finished
+// Chunked accumulation.  Every 128 elements of K (CK slices; a launch may ask
+// for shorter chunks) the MMAs switch to the other of two TMEM accumulators and the epilogue adds the finished
 // chunk into FP32 registers; the tensor core's internal accumulation then
 // spans 128 products per chunk instead of all n.  Measured at n = 4096 with the
 // printed table (density, FP16X2): chunks of 256 / 128 / 64 elements give
@@ -435,6 +435,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
+    // K slices per accumulation chunk: the default 128 elements, or a shorter
+    // chunk requested for this launch (a.chunk_elems)
+    const int ck = max(1, (a.chunk_elems > 0 ? a.chunk_elems : C::CK * BKE) / BKE);
     const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -514,14 +517,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!tile_active(a, tl, k)) continue;
                 const int n = a.inst[tl.inst].n;
                 const int nk = (n + BKE - 1) / BKE;
-                for (int kc = 0; kc < nk && ok; kc += C::CK) {
+                for (int kc = 0; kc < nk && ok; kc += ck) {
                     if (!wait_bar(&tempty_bar[buf], aphase ^ 1u, &abort_flag, a.status)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t dt = tmem + (uint32_t)(buf * kBN);
-                    const int kend = min(nk, kc + C::CK);
+                    const int kend = min(nk, kc + ck);
                     for (int kb = kc; kb < kend; ++kb) {
                         if (!wait_bar(&full_bar[stage], phase, &abort_flag, a.status)) {
                             ok = false;
@@ -579,9 +582,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             float acc[kEpiCols];
 #pragma unroll
             for (int i = 0; i < kEpiCols; ++i) acc[i] = 0.f;
-            const int kpre = max(0, nk - 2 * C::CK);      // prefetch the state one chunk ahead of the end
-            for (int kc = 0; kc < nk; kc += C::CK) {
-                if (kc <= kpre && kpre < kc + C::CK) prefetch_state(a, e, r, C0);
+            const int kpre = max(0, nk - 2 * ck);         // prefetch the state one chunk ahead of the end
+            for (int kc = 0; kc < nk; kc += ck) {
+                if (kc <= kpre && kpre < kc + ck) prefetch_state(a, e, r, C0);
                 if (!wait_bar(&tfull_bar[buf], aphase, &abort_flag, a.status)) {
                     ok = false;
                     break;

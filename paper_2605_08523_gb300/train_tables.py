@@ -9,7 +9,10 @@ Two groups of tables:
   alpha = 0.842704;
 * the training sweep of L in {16, 24, 32} layers at scaled temperatures
   kT0 in [0.005, 0.05] (beta0 in {20, 50, 100, 200}, mu0 = 1/3): a Fermi table
-  from the SP2 initial guess, then an entropy table started from it.
+  from the SP2 initial guess, then an entropy table started from it;
+* ``--high``: tables at beta0 in {3000, 6000, 12000, 24000} with
+  L = ceil(layer count (Eq. layer count)) + 2 layers, which ragged batches of
+  rotated spectra need once the Gershgorin width inflates beta'.
 
 Every fit uses 1e5 fixed samples from p ~ 1 + |f'| (training.sample_points) and
 Levenberg-Marquardt with geodesic acceleration (ftsp2_train_coeffs).  The max
@@ -44,6 +47,30 @@ def fit(ft, target, beta0, L, init, iterations, alpha=1.0, nsamples=100_000):
     rep["seconds"] = time.time() - t0
     rep["max_err_grid"] = max_error(ft, target, beta0, MU0, th, alpha)
     return th, rep
+
+
+def main_high(outdir: str, iterations: int = 3000):
+    import math
+    import paper_2605_08523_gb300 as ft
+    from .build import build
+    build()
+    os.makedirs(outdir, exist_ok=True)
+    out = {}
+    for beta0 in (3000.0, 6000.0, 12000.0, 24000.0):
+        L = int(math.ceil(training.layer_count(beta0))) + 2
+        th, rep = fit(ft, ft.TARGET_FERMI, beta0, L, None, iterations)
+        ths, reps = fit(ft, ft.TARGET_ENTROPY, beta0, L, th, iterations, alpha=ALPHA)
+        name = "b%d_L%d" % (int(beta0), L)
+        out[name] = dict(beta0=beta0, mu0=MU0, alpha=ALPHA, L=L, theta=th.tolist(), theta_entropy=ths.tolist(),
+                         fit=dict(max_err_fermi=rep["max_err_grid"], max_err_entropy=reps["max_err_grid"],
+                                  max_err_sp2_init=max_error(ft, ft.TARGET_FERMI, beta0, MU0,
+                                                             training.sp2_init(L, beta0, MU0), 1.0),
+                                  layer_count=training.layer_count(beta0)),
+                         train=dict(fermi=rep, entropy=reps, samples=100_000, density="1+|f'|"))
+        print(name, out[name]["fit"], flush=True)
+        with open(os.path.join(outdir, name + ".json"), "w") as f:
+            json.dump(out[name], f, indent=1)
+    return out
 
 
 def main(outdir: str, iterations: int = 800, quick: bool = False):
@@ -84,6 +111,9 @@ def main(outdir: str, iterations: int = 800, quick: bool = False):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "tables_out",
-         iterations=int(sys.argv[2]) if len(sys.argv) > 2 else 800,
-         quick="--quick" in sys.argv)
+    args = [a for a in sys.argv[1:] if not a.startswith("--")]
+    outdir = args[0] if args else "tables_out"
+    if "--high" in sys.argv:
+        main_high(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)
+    else:
+        main(outdir, iterations=int(args[1]) if len(args) > 1 else 800, quick="--quick" in sys.argv)

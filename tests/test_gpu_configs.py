@@ -1,0 +1,146 @@
+"""The ragged batch (cfg2) and the large single matrix (cfg4) through the
+C ABI, against the CPU oracle.
+
+cfg2: 512 Hamiltonians, n ~ U{64..768}, eigenvalues U(-10, 10) eV rotated by
+Haar-random Q, mu ~ U(-5, 5), kT ~ U(0.02, 0.5): one grouped launch per layer
+for all instances and both chains.  Model choice and flip are checked for
+every instance; D and S on instances spread over the size range.
+cfg4: 16 x 16 x 32 lattice (n = 8192) with 5 % long-range couplings N(0, 0.05),
+kT = 0.1, FP16X2 layers with the last two layers in FP32, density + entropy.
+"""
+import glob
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import fermi, pipeline, rescale
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TABLES = os.path.join(ROOT, "paper_2605_08523_gb300", "tables")
+
+
+@pytest.fixture(scope="module")
+def ft():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2605_08523_gb300 as ft
+    return ft
+
+
+def table_meta(path):
+    # selection metadata only (beta0, mu0, L); coefficients trained by the
+    # library never enter an oracle computation in this file
+    import json
+    d = json.load(open(path))
+    L = len(d["theta"])
+    return rescale.Table(tuple((0.0, 0.0, 0.0, 0.0) for _ in range(L)), d["beta0"], d["mu0"], d["alpha"],
+                         name=os.path.basename(path))
+
+
+def model_set_paths():
+    # the printed table (with its trained entropy table), the 32-layer tables
+    # of the training sweep and the high-beta0 tables
+    paths = [os.path.join(TABLES, "entropy_b1500_L26.json")]
+    paths += sorted(glob.glob(os.path.join(TABLES, "b*_L32.json")))
+    paths += sorted(p for p in glob.glob(os.path.join(TABLES, "b*.json"))
+                    if int(os.path.basename(p)[1:].split("_")[0]) >= 3000)
+    return paths
+
+
+def test_cfg2_ragged_batch(ft):
+    paths = model_set_paths()
+    ms = ft.ModelSet.from_json(paths)
+    metas = [table_meta(p) for p in paths]
+    batch = wl.ragged_batch(512, 0)
+    Hs = [b["H"] for b in batch]
+    mus = [b["mu"] for b in batch]
+    kTs = [b["kT"] for b in batch]
+    s = ft.Solver([H.shape[0] for H in Hs], mus, kTs, ms, mode="fp16x2", want=3)
+    flat, _ = wl.pack_batch(Hs)
+    s.run(torch.from_numpy(flat).cuda(), sync=True)
+    rec = s.records()
+    # scalar decisions (bounds, flip, validity, smallest valid beta0) for every instance
+    n_valid = 0
+    for b, H in enumerate(Hs):
+        lo, hi = rescale.gershgorin(H)
+        mup, bp = rescale.normalise(lo, hi, mus[b], 1.0 / kTs[b])
+        flip = rescale.flip_needed(mup)
+        if flip:
+            mup = 1.0 - mup
+        m = rescale.select_model(metas, mup, bp)
+        assert rec["model"][b] == m, b
+        if m >= 0:
+            n_valid += 1
+            assert rec["status"][b] == 0 and bool(rec["flip"][b]) == flip
+        else:
+            assert rec["status"][b] == -4
+    assert n_valid >= 505
+    # D and S against the eigendecomposition on instances spread over the size
+    # range.  Rounding grows with the chosen table's slope beta0/4; the trained
+    # tables add their fit error (<= 1e-6 for these tables, 2.5e-6 entropy).
+    order = np.argsort([H.shape[0] for H in Hs])
+    picks = [int(order[i]) for i in np.linspace(0, 511, 12).astype(int)]
+    S = s.S.cpu().numpy()
+    for b in picks:
+        m = rec["model"][b]
+        if m < 0:
+            continue
+        H = Hs[b]
+        n = H.shape[0]
+        Dref, Sref, _, _ = fermi.eig_reference(H, mus[b], kTs[b])
+        D = s.matrix(b).double().cpu().numpy()
+        tol = 1.5e-6 * max(1.0, metas[m].beta0 / 1500.0) + 1.1e-6
+        assert np.max(np.abs(D - Dref)) < tol, (b, n, metas[m].name)
+        assert abs(S[b] - Sref) / n < tol + 2.5e-6, (b, n, metas[m].name)
+
+
+def test_cfg2_printed_table_method_exact(ft):
+    # Instances of the same batch family solved with the paper's printed table
+    # alone, against the oracle's method-exact result (rounding only).
+    from oracle import tables
+    printed = rescale.Table(tables.PRINTED_B1500, 1500.0, 1.0 / 3.0)
+    batch = wl.ragged_batch(40, 1)
+    Hs = [b["H"] for b in batch]
+    mus = [b["mu"] for b in batch]
+    kTs = [b["kT"] for b in batch]
+    ms = ft.ModelSet()
+    s = ft.Solver([H.shape[0] for H in Hs], mus, kTs, ms, mode="fp16x2", want=1)
+    flat, _ = wl.pack_batch(Hs)
+    s.run(torch.from_numpy(flat).cuda(), sync=True)
+    rec = s.records()
+    checked = 0
+    for b, H in enumerate(Hs):
+        ex = pipeline.method_exact(H, mus[b], kTs[b], [printed])
+        if ex["D"] is None:
+            assert rec["status"][b] == -4
+            continue
+        D = s.matrix(b).double().cpu().numpy()
+        assert np.max(np.abs(D - ex["D"])) < 1.5e-6, b
+        checked += 1
+    assert checked >= 20
+
+
+def test_cfg4_n8192_refine2(ft):
+    H = wl.lattice_3d((16, 16, 32), 0, longrange_frac=0.05, longrange_sigma=0.05)
+    n, kT = 8192, 0.1
+    eps, V = np.linalg.eigh(H)
+    mu = fermi.mu_at_filling(eps, kT, n / 2)
+    f = fermi.fermi(eps, mu, kT)
+    Dref = (V * f[None, :]) @ V.T
+    Sref = float(np.sum(fermi.entropy(eps, mu, kT)))
+    del V
+    ms = ft.ModelSet.from_json([os.path.join(TABLES, "entropy_b1500_L26.json")])
+    s = ft.Solver([n], [mu], [kT], ms, mode="fp16x2", want=3, flags=ft.REFINE2)
+    s.run(torch.from_numpy(H.ravel().copy()).cuda(), sync=True)
+    assert s.records()[0]["status"] == 0
+    D = s.matrix(0).double().cpu().numpy()
+    err = np.max(np.abs(D - Dref))
+    assert err <= 1.5e-6, err
+    assert abs(float(s.trace[0, 0]) - np.sum(f)) < 1e-3
+    assert abs(float(s.S[0]) - Sref) / n <= 1.5e-6
