@@ -187,7 +187,7 @@ def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
 # (mode, n, sha256[:16] of the layer-kernel sources) -> dram read + write bytes
 # of one layer launch (both chains), from the ncu capture summarised in
 # profiles/layer_tc_fp16x2_n4096.md
-MEASURED_TRAFFIC = {("fp16x2", 4096, "b813375eda399c75"): 428.024320e6 + 256.838912e6}
+MEASURED_TRAFFIC = {("fp16x2", 4096, "079b8407bcec3aa0"): 428.269568e6 + 256.946176e6}
 
 
 def kernel_sha():

@@ -135,12 +135,17 @@ def test_cfg4_n8192_refine2(ft):
     Dref = (V * f[None, :]) @ V.T
     Sref = float(np.sum(fermi.entropy(eps, mu, kT)))
     del V
-    ms = ft.ModelSet.from_json([os.path.join(TABLES, "entropy_b1500_L26.json")])
+    # The long-range couplings widen the Gershgorin interval to ~141 eV, so
+    # beta' ~ 1415 needs beta0 >= ~2100: the 34-layer beta0 = 3000 table is the
+    # smallest valid one; rounding then scales with 3000/1500.
+    ms = ft.ModelSet.from_json([os.path.join(TABLES, "entropy_b1500_L26.json"),
+                                os.path.join(TABLES, "b3000_L34.json")])
     s = ft.Solver([n], [mu], [kT], ms, mode="fp16x2", want=3, flags=ft.REFINE2)
     s.run(torch.from_numpy(H.ravel().copy()).cuda(), sync=True)
-    assert s.records()[0]["status"] == 0
+    rec = s.records()[0]
+    assert rec["status"] == 0 and rec["model"] == 1
     D = s.matrix(0).double().cpu().numpy()
     err = np.max(np.abs(D - Dref))
-    assert err <= 1.5e-6, err
+    assert err <= 3e-6, err
     assert abs(float(s.trace[0, 0]) - np.sum(f)) < 1e-3
-    assert abs(float(s.S[0]) - Sref) / n <= 1.5e-6
+    assert abs(float(s.S[0]) - Sref) / n <= 3e-6
