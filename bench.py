@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--mu", type=float, default=None,
                    help="skip the GPU eigendecomposition and use this mu (profiling runs)")
+    p.add_argument("--workload", default="cfg1", choices=["cfg1", "cfg2"],
+                   help="cfg1: the headline single n = 4096 matrix; cfg2: the 512-instance ragged batch "
+                        "(reported as a separate line, not the headline)")
     return p.parse_args()
 
 
@@ -274,10 +277,59 @@ def cpu_baseline(H, mu, kT, n):
                       "(%.1f s)" % (n, t)}
 
 
+def run_cfg2(args):
+    """Ragged batch of 512 rotated-spectrum Hamiltonians (n ~ U{64..768}),
+    one grouped launch per layer for all instances and both chains, model set
+    of every shipped table (smallest valid beta0 per instance)."""
+    import glob
+    import numpy as np
+    import torch
+    import paper_2605_08523_gb300 as ft
+    import workloads as wl
+    from paper_2605_08523_gb300 import build as ftbuild
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ftbuild.build()
+    tdir = os.path.join(ROOT, "paper_2605_08523_gb300", "tables")
+    paths = [os.path.join(tdir, "entropy_b1500_L26.json")] + sorted(glob.glob(os.path.join(tdir, "b*_L32.json")))
+    paths += sorted(p for p in glob.glob(os.path.join(tdir, "b*.json"))
+                    if int(os.path.basename(p)[1:].split("_")[0]) >= 3000)
+    ms = ft.ModelSet.from_json(paths)
+    batch = wl.ragged_batch(512, args.seed)
+    Hs = [b["H"] for b in batch]
+    ns = [H.shape[0] for H in Hs]
+    flat, _ = wl.pack_batch(Hs)
+    Hd = torch.from_numpy(flat).cuda()
+    solver = ft.Solver(ns, [b["mu"] for b in batch], [b["kT"] for b in batch], ms, mode=args.mode, want=3)
+    shape, ms_single, ms_pair = solver.autotune(Hd, reps=1)
+    for _ in range(args.warmup):
+        solver.run(Hd)
+    torch.cuda.synchronize()
+    rec = solver.records()
+    layers = rec["layers"]
+    valid = rec["status"] == 0
+    steps = max(3, args.steps // 10)
+    t = cuda_time(lambda: solver.run(Hd), steps)
+    alg = float(np.sum((np.array(ns, dtype=np.float64) ** 3 * 2 * layers)[valid]))
+    line = {"metric": "ragged-batch solves/s (instances/s, density + entropy)", "value": int(valid.sum()) / t,
+            "unit": "solves/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "dtype": args.mode, "data": "synthetic",
+            "config": {"workload": "cfg2 ragged batch 512 x n~U{64..768}, eigenvalues U(-10,10), kT~U(0.02,0.5), "
+                                   "mu~U(-5,5)", "valid_instances": int(valid.sum()),
+                       "sum_n3": float(np.sum(np.array(ns, dtype=np.float64) ** 3)),
+                       "models_used": {int(m): int(np.sum(rec["model"] == m)) for m in np.unique(rec["model"])},
+                       "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
+                       "autotune_ms": {"single": ms_single, "pair": ms_pair}},
+            "tflops_alg": alg / t / 1e12}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "cfg2":
+        run_cfg2(args)
         return
     import numpy as np
     import torch
@@ -314,6 +366,8 @@ def main():
     # trainer fitted for it (theta_entropy)
     ms = ft.ModelSet.from_json([os.path.join(ROOT, "paper_2605_08523_gb300", "tables", "entropy_b1500_L26.json")])
     solver = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3)
+    # tile shape: the library's autotuner times both shapes once (untimed)
+    shape, ms_single, ms_pair = solver.autotune(Hd, reps=2)
     for _ in range(args.warmup):
         solver.run(Hd)
     torch.cuda.synchronize()
@@ -377,12 +431,13 @@ def main():
     alg_per_launch = 2 * float(n) ** 3
     achieved = alg_per_launch / layer_avg / 1e12 if layer_avg > 0 else None
     peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-    # hardware tensor flops actually issued per launch: triangle tiles x 3 products
-    BN = 256 if args.mode in ("fp16x2", "tf32x3") else 128
-    nI, nJ, q = math.ceil(n / 128), math.ceil(n / BN), BN // 128
-    tiles = sum(min(q * (J + 1), nI) for J in range(nJ))
+    # hardware tensor flops actually issued per launch: upper-triangle tiles of
+    # the chosen shape x split products x 2 chains
+    T = 256 if shape == 1 else 128
+    nt = math.ceil(n / T)
+    tiles = nt * (nt + 1) // 2
     nprod = {"fp16x2": 3, "tf32x3": 3, "bf16x3": 6}.get(args.mode, 1)
-    hw_per_launch = 2 * tiles * 128 * BN * n * 2 * nprod
+    hw_per_launch = 2 * tiles * T * T * n * 2 * nprod
     hw_achieved = hw_per_launch / layer_avg / 1e12 if layer_avg > 0 else None
     hw_peak = peak if args.mode in ("fp16x2", "bf16x3") else peak / 2.0
     # DRAM bytes per launch from one ncu capture (profiles/layer_tc_fp16x2_n4096.md),
@@ -398,7 +453,9 @@ def main():
         "config": {"workload": "cfg1 lattice %dx%dx%d n=%d kT=%g mu=half filling, density+entropy, "
                                "printed 26-layer table + trained entropy table" % (dims + (n, kT)),
                    "n": n, "kT": kT, "mu": mu, "layers": L, "mode": args.mode, "chains": 2,
-                   "l2": "inputs and working set larger than L2 (no flush)", "parallelism": "replicas"},
+                   "l2": "inputs and working set larger than L2 (no flush)", "parallelism": "replicas",
+                   "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
+                   "autotune_ms": {"single": ms_single, "pair": ms_pair}},
         "tflops_alg": alg_flops / t_step / 1e12 * world,
         "accuracy": {"max_abs_D_minus_Dref": err_D, "abs_S_minus_Sref_per_n": err_S, "trD": trD,
                      "trD_ref": n / 2, "S": S, "S_ref": Sref},

@@ -79,6 +79,11 @@ typedef enum {
                                     FTSP2_E_VALIDITY and no result           */
 #define FTSP2_REFINE1       0x4  /* last layer in FTSP2_FP32 arithmetic       */
 #define FTSP2_REFINE2       0x8  /* last two layers in FTSP2_FP32 arithmetic  */
+/* Tile shape of the tensor-core layer launches.  By default a batch runs with
+ * the shape ftsp2_autotune recorded for it or, if none was recorded, with the
+ * shape a padding model prefers; these two flags override both. */
+#define FTSP2_PAIR_TILES    0x10 /* 256 x 256 tiles on CTA pairs (cta_group::2) */
+#define FTSP2_SINGLE_TILES  0x20 /* 128 x 128 tiles on single CTAs             */
 
 /* One Hamiltonian of a (ragged) batch.  H_b starts at dH + offset and is
  * n x n row-major; D_b starts at dD + offset.  Offsets are in elements. */
@@ -226,6 +231,39 @@ ftsp2_status ftsp2_density_noalloc(const double* dH, const ftsp2_instance* inst,
                                    const ftsp2_model_set* set, ftsp2_mode mode, int flags,
                                    float* dD, double* dTrace, ftsp2_rescale_rec* dRec,
                                    void* stream);
+
+/* ---- tile-shape autotuner ------------------------------------------------------ */
+
+/* Measures the batch with both tensor-core tile shapes and records the faster.
+ * Arguments are those of ftsp2_density_entropy (the buffers are written as by
+ * that call; the results of the last run are left in them).  For each shape
+ * the batch runs once untimed and then `reps` times between CUDA events on
+ * `stream`; ms[0] receives the mean time of the 128 x 128 single-CTA shape,
+ * ms[1] that of the 256 x 256 pair shape (ms nullable), *choice the shape kept
+ * (0 single, 1 pair; -1 in FTSP2_FP32 mode, which has no tensor-core layers and
+ * is not timed).  The record is keyed by device, mode, density/entropy
+ * selection, refinement flags and the sorted list of orders n, lives for the
+ * life of the process, and is shared by all threads (guarded by a mutex).
+ * Synchronises `stream`.  Not usable during stream capture.  FTSP2_PAIR_TILES
+ * and FTSP2_SINGLE_TILES in `flags` are ignored here.  Errors: those of
+ * ftsp2_density_entropy; FTSP2_E_ARG if reps < 1. */
+ftsp2_status ftsp2_autotune(const double* dH, const ftsp2_instance* inst,
+                            const ftsp2_instance* dInst, int nb,
+                            const ftsp2_model_set* set, ftsp2_mode mode, int flags,
+                            float* dD, double* dTrace, double* dS,
+                            ftsp2_rescale_rec* dRec, void* ws, size_t ws_bytes,
+                            int reps, int* choice, float* ms, void* stream);
+
+/* The tile shape a call with these arguments would use on the current device:
+ * 1 pair, 0 single, -1 none (FTSP2_FP32 mode).  `want` as in
+ * ftsp2_workspace_size.  *from_tuner is set to 1 if the shape comes from an
+ * ftsp2_autotune record, 0 if from the flags or the padding model.  Host-only
+ * apart from reading the device's SM count. */
+ftsp2_status ftsp2_tile_shape(const ftsp2_instance* inst, int nb, ftsp2_mode mode, int want,
+                              int flags, int* shape, int* from_tuner);
+
+/* Forgets every ftsp2_autotune record. */
+ftsp2_status ftsp2_autotune_clear(void);
 
 /* ---- training (a7) -------------------------------------------------------------- */
 

@@ -23,14 +23,15 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (BF16X3, CLAMP, FP16X2, FP32, MODES, REFINE1, REFINE2, SYNC, TARGET_ENTROPY,
-                   TARGET_FERMI, TF32X3, Ftsp2Error, Instance, RescaleRec, Table, TrainReport, check,
-                   lib, status_string)
+from ._lib import (BF16X3, CLAMP, FP16X2, FP32, MODES, PAIR_TILES, REFINE1, REFINE2, SINGLE_TILES, SYNC,
+                   TARGET_ENTROPY, TARGET_FERMI, TF32X3, Ftsp2Error, Instance, RescaleRec, Table, TrainReport,
+                   check, lib, status_string)
 
 __all__ = ["ModelSet", "Solver", "ftsp2_rescale", "ftsp2_train_coeffs", "ftsp2_train_residual_jacobian",
-           "ftsp2_train_normal_equations", "kernel_launch_count", "profile_layers", "profile_read", "MODES", "FP32", "TF32X3", "BF16X3",
-           "FP16X2", "SYNC", "CLAMP", "REFINE1", "REFINE2", "TARGET_FERMI", "TARGET_ENTROPY",
-           "Ftsp2Error", "status_string", "lib", "REC_DTYPE"]
+           "ftsp2_train_normal_equations", "ftsp2_autotune_clear", "kernel_launch_count", "profile_layers",
+           "profile_read", "MODES", "FP32", "TF32X3", "BF16X3", "FP16X2", "SYNC", "CLAMP", "REFINE1", "REFINE2",
+           "PAIR_TILES", "SINGLE_TILES", "TARGET_FERMI", "TARGET_ENTROPY", "Ftsp2Error", "status_string", "lib",
+           "REC_DTYPE"]
 
 REC_DTYPE = np.dtype([("e_min", "f8"), ("e_max", "f8"), ("mu_p", "f8"), ("beta_p", "f8"), ("scale", "f8"),
                       ("flip", "i4"), ("model", "i4"), ("status", "i4"), ("layers", "i4"), ("valid", "i4"),
@@ -224,6 +225,36 @@ class Solver:
             raise Ftsp2Error(st, "ftsp2 hot path")
         return st
 
+    def _outputs(self):
+        D = _ptr(self.D) if self.want & 1 else None
+        T = _ptr(self.trace) if self.want & 1 else None
+        S = _ptr(self.S) if self.want & 2 else None
+        return D, T, S
+
+    def autotune(self, H, reps=3, stream=None):
+        """ftsp2_autotune on this batch: times both tile shapes and records the
+        faster for every later call with the same signature.  Returns
+        (shape, ms_single, ms_pair); shape 1 = 256 x 256 pairs, 0 = 128 x 128
+        single CTAs, -1 = no tensor-core layers (FP32 mode)."""
+        torch = _torch()
+        if H.dtype != torch.float64 or not H.is_cuda or H.numel() < self.total:
+            raise ValueError("H must be a CUDA float64 tensor with sum(n^2) elements")
+        choice = C.c_int()
+        ms = (C.c_float * 2)()
+        D, T, S = self._outputs()
+        check(lib().ftsp2_autotune(_ptr(H), self.host_inst, _ptr(self.d_inst), self.nb, self.ms.handle, self.mode,
+                                   self.flags, D, T, S, _ptr(self.rec), C.c_void_p(self.ws_ptr), self.ws_bytes,
+                                   int(reps), C.byref(choice), ms, _stream(stream)), "ftsp2_autotune")
+        return choice.value, float(ms[0]), float(ms[1])
+
+    def tile_shape(self):
+        """(shape, from_tuner) that run() uses on the current device
+        (ftsp2_tile_shape)."""
+        shape, tuned = C.c_int(), C.c_int()
+        check(lib().ftsp2_tile_shape(self.host_inst, self.nb, self.mode, self.want, self.flags, C.byref(shape),
+                                     C.byref(tuned)), "ftsp2_tile_shape")
+        return shape.value, bool(tuned.value)
+
     def records(self):
         raw = self.rec.cpu().numpy()
         return raw.view(REC_DTYPE)
@@ -231,6 +262,11 @@ class Solver:
     def matrix(self, b):
         n, o = self.ns[b], self.offsets[b]
         return self.D[o:o + n * n].view(n, n)
+
+
+def ftsp2_autotune_clear():
+    """Forget every recorded tile-shape choice."""
+    check(lib().ftsp2_autotune_clear(), "ftsp2_autotune_clear")
 
 
 def ftsp2_rescale(H, ns, mus, kTs, model_set: ModelSet, flags=0, stream=None):

@@ -17,7 +17,7 @@ OK, E_ARG, E_CUDA, E_WORKSPACE, E_VALIDITY, E_NONFINITE, E_TIMEOUT, E_NOMODEL, E
 FP32, TF32X3, BF16X3, FP16X2 = 0, 1, 2, 3
 MODES = {"fp32": FP32, "tf32x3": TF32X3, "bf16x3": BF16X3, "fp16x2": FP16X2}
 # flags
-SYNC, CLAMP, REFINE1, REFINE2 = 0x1, 0x2, 0x4, 0x8
+SYNC, CLAMP, REFINE1, REFINE2, PAIR_TILES, SINGLE_TILES = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 TARGET_FERMI, TARGET_ENTROPY = 0, 1
 
 
@@ -63,6 +63,10 @@ SIGNATURES = {
     "ftsp2_entropy": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _SZ, _VP]),
     "ftsp2_density_entropy": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "ftsp2_density_noalloc": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP]),
+    "ftsp2_autotune": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _SZ, _I,
+                            C.POINTER(_I), C.POINTER(C.c_float), _VP]),
+    "ftsp2_tile_shape": (_I, [_PINST, _I, _I, _I, _I, C.POINTER(_I), C.POINTER(_I)]),
+    "ftsp2_autotune_clear": (_I, []),
     "ftsp2_train_workspace_size": (_SZ, [_I, _I]),
     "ftsp2_train_coeffs": (_I, [_I, _D, _D, _I, _D, _VP, _I, _I, _I, C.POINTER(_D), C.POINTER(_D),
                                 C.POINTER(TrainReport), _VP, _SZ, _VP]),

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -265,13 +266,17 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
     const int P = (int)align_up((size_t)maxn, kPad);
     const int nch = want == 3 ? 2 : 1;
     const bool simt_main = mode == FTSP2_FP32;
-    const int BN = simt_main ? 128 : tc_block_n(mode);
-    const int BM = simt_main ? 128 : tc_block_m(mode);
+    // main tile table: 256 x 256 pair tiles (tensor-core modes) or 128 x 128
+    // (FP32 mode); the 128 x 128 table serves single-CTA tensor-core layers and
+    // FP32 refinement layers
+    const int BN = simt_main ? 128 : tc_block_n(mode, 1);
+    const int BM = simt_main ? 128 : tc_block_m(mode, 1);
     const bool refine = !simt_main && refine_layers(flags) > 0;
+    const bool need_ref = !simt_main;
     long long nt = 0, ntr = 0;
     for (int b = 0; b < nb; ++b) {
         nt += host_tiles_of(inst[b].n, BM, BN);
-        if (refine) ntr += host_tiles_of(inst[b].n, 128, 128);
+        if (need_ref) ntr += host_tiles_of(inst[b].n, 128, 128);
     }
     nt *= nch;
     ntr *= nch;
@@ -293,7 +298,7 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
     L.status = take(256);
     L.inst_work = take(sizeof(InstWork) * nb);
     L.tiles = take(sizeof(Tile) * nt);
-    L.tiles_ref = refine ? take(sizeof(Tile) * ntr) : 0;
+    L.tiles_ref = need_ref ? take(sizeof(Tile) * ntr) : 0;
     L.partials = take(sizeof(double) * 2 * kPartialSlots * std::max<long long>(nt, ntr));
     const int fmt = fmt_of_mode(mode);
     for (int c = 0; c < kMaxChains; ++c) {
@@ -314,6 +319,72 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
 }
 
 static ftsp2_status from_cuda(cudaError_t e) { return e == cudaSuccess ? FTSP2_OK : FTSP2_E_CUDA; }
+
+// ---- tile-shape choice (autotuner) --------------------------------------------
+// Tensor-core layers run either on CTA pairs with 256 x 256 tiles or on single
+// CTAs with 128 x 128 tiles.  The choice is per batch signature (device, mode,
+// chains, refinement, the sorted list of orders n): ftsp2_autotune measures both
+// and records the faster; otherwise a padding model decides.
+static std::mutex g_tune_mu;
+static std::map<uint64_t, int> g_tune;
+
+static uint64_t batch_signature(const ftsp2_instance* inst, int nb, int mode, int want, int flags) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<int> ns(nb);
+    for (int b = 0; b < nb; ++b) ns[b] = inst[b].n;
+    std::sort(ns.begin(), ns.end());
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        h ^= v;
+        h *= 1099511628211ull;
+    };
+    mix((uint64_t)dev);
+    mix((uint64_t)mode);
+    mix((uint64_t)want);
+    mix((uint64_t)refine_layers(flags));
+    mix((uint64_t)nb);
+    for (int v : ns) mix((uint64_t)v);
+    return h;
+}
+
+// Padding model: multiply-adds issued per layer (tiles x tile^2 x n) divided by
+// the number of units that run them in parallel, with the waves rounded up.
+static int shape_by_model(const ftsp2_instance* inst, int nb, int sms) {
+    double cost[2] = {0.0, 0.0};
+    for (int pair = 0; pair < 2; ++pair) {
+        const int T = pair ? 256 : 128;
+        const int units = pair ? sms / 2 : sms;
+        double work = 0.0;
+        long long tiles = 0;
+        for (int b = 0; b < nb; ++b) {
+            const long long t = host_tiles_of(inst[b].n, T, T);
+            tiles += t;
+            work += (double)t * T * T * inst[b].n;
+        }
+        const double waves = std::ceil((double)tiles / std::max(1, units));
+        const double per_tile = work / std::max<long long>(1, tiles);
+        // a pair tile moves half of B per SM; count its MMA work at 0.8
+        cost[pair] = waves * per_tile / (pair ? 2.0 : 1.0) * (pair ? 0.8 : 1.0);
+    }
+    return cost[1] <= cost[0] ? 1 : 0;
+}
+
+static int tile_shape_choice(const ftsp2_instance* inst, int nb, int mode, int want, int flags, int sms,
+                             int* from_tuner = nullptr) {
+    if (from_tuner) *from_tuner = 0;
+    if (flags & FTSP2_PAIR_TILES) return 1;
+    if (flags & FTSP2_SINGLE_TILES) return 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(batch_signature(inst, nb, mode, want, flags));
+        if (it != g_tune.end()) {
+            if (from_tuner) *from_tuner = 1;
+            return it->second;
+        }
+    }
+    return shape_by_model(inst, nb, sms);
+}
 
 // The launch sequence of (a1)-(a6).
 static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp2_instance* dInst, int nb,
@@ -439,6 +510,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         la.A[c] = c < L.nchains ? reinterpret_cast<float*>(W + L.A[c]) : nullptr;
     }
     auto is_simt = [&](int g) { return all_simt || g >= refine_from; };
+    const int pair = all_simt ? 1 : tile_shape_choice(inst, nb, mode, want, flags, di.sms);
     int last_table = 0;
     for (int g = 0; g < Lmax; ++g) {
         const bool simt = is_simt(g);
@@ -468,9 +540,9 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
             e = launch_layer_simt(la, grid, s);
             last_table = use_ref ? 1 : 0;
         } else {
-            la.tiles = tiles;
-            la.ntiles = L.ntiles;
-            const int npairs = std::max(1, std::min(la.ntiles, di.sms / 2));
+            la.tiles = pair ? tiles : tiles_ref;
+            la.ntiles = pair ? L.ntiles : L.ntiles_ref;
+            const int units = std::max(1, std::min(la.ntiles, pair ? di.sms / 2 : di.sms));
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             {
                 std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -480,13 +552,13 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
                     e0 = e1 = nullptr;
                 }
             }
-            e = launch_layer_tc(mode, la, maps[g & 1], npairs, s);
+            e = launch_layer_tc(mode, la, maps[g & 1], units, pair, s);
             if (e0) {
                 cudaEventRecord(e1, s);
                 std::lock_guard<std::mutex> lk(g_prof_mu);
                 g_prof_events.emplace_back(e0, e1);
             }
-            last_table = 0;
+            last_table = pair ? 0 : 1;
         }
         if (e != cudaSuccess) return FTSP2_E_CUDA;
     }
@@ -793,6 +865,89 @@ ftsp2_status ftsp2_density_entropy(const double* dH, const ftsp2_instance* inst,
     if (!dD && !dTrace)
         return ftsp2_entropy(dH, inst, dInst, nb, set, mode, flags, dS, dRec, ws, ws_bytes, stream);
     return run(dH, inst, dInst, nb, set, mode, flags, 3, dD, dTrace, dS, dRec, ws, ws_bytes, stream);
+}
+
+static int want_of(const float* dD, const double* dTrace, const double* dS) {
+    if (!dS) return 1;
+    if (!dD && !dTrace) return 2;
+    return 3;
+}
+
+ftsp2_status ftsp2_autotune(const double* dH, const ftsp2_instance* inst, const ftsp2_instance* dInst, int nb,
+                            const ftsp2_model_set* set, ftsp2_mode mode, int flags, float* dD, double* dTrace,
+                            double* dS, ftsp2_rescale_rec* dRec, void* ws, size_t ws_bytes, int reps, int* choice,
+                            float* ms, void* stream) {
+    if (reps < 1 || !choice) return FTSP2_E_ARG;
+    if (nb < 1 || !inst) return FTSP2_E_ARG;
+    if (ms) ms[0] = ms[1] = 0.f;
+    const int base = flags & ~(FTSP2_PAIR_TILES | FTSP2_SINGLE_TILES | FTSP2_SYNC);
+    if (mode == FTSP2_FP32) {
+        *choice = -1;
+        return ftsp2_density_entropy(dH, inst, dInst, nb, set, mode, base | FTSP2_SYNC, dD, dTrace, dS, dRec, ws,
+                                     ws_bytes, stream);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return FTSP2_E_CUDA;
+    }
+    float t[2] = {0.f, 0.f};
+    ftsp2_status st = FTSP2_OK;
+    for (int shape = 0; shape < 2 && st == FTSP2_OK; ++shape) {
+        const int f = base | (shape ? FTSP2_PAIR_TILES : FTSP2_SINGLE_TILES);
+        // untimed run with FTSP2_SYNC: surfaces per-instance errors once
+        st = ftsp2_density_entropy(dH, inst, dInst, nb, set, mode, f | FTSP2_SYNC, dD, dTrace, dS, dRec, ws,
+                                   ws_bytes, stream);
+        if (st != FTSP2_OK) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = FTSP2_E_CUDA; break; }
+        for (int r = 0; r < reps && st == FTSP2_OK; ++r)
+            st = ftsp2_density_entropy(dH, inst, dInst, nb, set, mode, f, dD, dTrace, dS, dRec, ws, ws_bytes,
+                                       stream);
+        if (st != FTSP2_OK) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t[shape], e0, e1) != cudaSuccess) {
+            st = FTSP2_E_CUDA;
+            break;
+        }
+        t[shape] /= (float)reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != FTSP2_OK) return st;
+    const int pick = t[1] <= t[0] ? 1 : 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[batch_signature(inst, nb, mode, want_of(dD, dTrace, dS), base)] = pick;
+    }
+    *choice = pick;
+    if (ms) {
+        ms[0] = t[0];
+        ms[1] = t[1];
+    }
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_tile_shape(const ftsp2_instance* inst, int nb, ftsp2_mode mode, int want, int flags, int* shape,
+                              int* from_tuner) {
+    if (!inst || nb < 1 || !shape || want < 1 || want > 3) return FTSP2_E_ARG;
+    if (from_tuner) *from_tuner = 0;
+    if (mode == FTSP2_FP32) {
+        *shape = -1;
+        return FTSP2_OK;
+    }
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return FTSP2_E_CUDA;
+    *shape = tile_shape_choice(inst, nb, mode, want, flags, sms, from_tuner);
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_autotune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+    return FTSP2_OK;
 }
 
 }  // extern "C"

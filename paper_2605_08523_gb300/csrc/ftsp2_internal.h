@@ -166,11 +166,12 @@ struct TmaMaps {
 };
 
 // Tensor-core layer (k_layer_tc.cu); mode in {TF32X3, BF16X3, FP16X2}.
-int tc_block_n(int mode);
-int tc_block_m(int mode);
+int tc_block_n(int mode, int pair);
+int tc_block_m(int mode, int pair);
 int tc_smem_bytes(int mode);
-// npairs: CTA pairs (clusters of 2) of the persistent grid
-cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, int npairs,
+// pair = 1: 256 x 256 tiles on CTA pairs (units = pairs); pair = 0: 128 x 128
+// tiles on single CTAs (units = CTAs).  Persistent grid of `units`.
+cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, int units, int pair,
                             cudaStream_t s);
 // CUDA-core FP32 layer (k_layer_simt.cu), 128 x 128 tiles.
 cudaError_t launch_layer_simt(const LayerArgs& a, int grid, cudaStream_t s);

@@ -2,9 +2,10 @@
 // (instance, chain) of a grouped launch, on the 5th-generation tensor cores.
 //
 // The product of a layer is the symmetric square Z^2 of the centred state.
-// Output tiles are 256 x 256 and only those touching the upper triangle are
-// computed (I <= J); each element (r, c) with r <= c is produced once and
-// written to (r, c) and (c, r).  Since Z is symmetric, (Z^2)_{rc} =
+// Output tiles are square (256 x 256 on CTA pairs or 128 x 128 on single CTAs,
+// chosen per call) and only those touching the upper triangle are computed
+// (I <= J); each element (r, c) with r <= c is produced once and written to
+// (r, c) and (c, r).  Since Z is symmetric, (Z^2)_{rc} =
 // sum_k Z_{rk} Z_{ck}: both MMA operands are K-major row panels of the same
 // matrix, loaded by TMA with 128-byte swizzle.
 //
@@ -21,20 +22,23 @@
 // half of B.  Both CTAs' TMA loads complete on the even CTA's "full" barrier;
 // the MMA commit is multicast to both CTAs' "empty" and "tfull" barriers; the
 // odd CTA's epilogue warps release accumulators on the even CTA's "tempty".
+// Single CTAs (cta_group::1) run the same pipeline on 128 x 128 tiles with
+// M = 128 MMAs: a quarter of the padding of a pair tile on the diagonal and at
+// ragged edges, which pays for batches of small instances.
 //
 // Chunked accumulation.  Every 128 elements of K (CK slices; a launch may ask
-// for shorter chunks) the MMAs switch to the other of two TMEM accumulators and the epilogue adds the finished
-// chunk into FP32 registers; the tensor core's internal accumulation then
+// for shorter chunks) the MMAs switch to the other of two TMEM accumulators
+// and the epilogue adds the finished chunk into FP32 registers; the tensor core's internal accumulation then
 // spans 128 products per chunk instead of all n.  Measured at n = 4096 with the
 // printed table (density, FP16X2): chunks of 256 / 128 / 64 elements give
 // max|D - D_ref| = 1.85e-6 / 9.0e-7 / 6.9e-7 at layer times 0.235 / 0.251 /
 // 0.314 ms; 128 is the default.
 //
-// Warp roles (320 threads per CTA, persistent over the pair-tile list):
+// Warp roles (576 threads per CTA, persistent over the tile list):
 //   warp 0 lane 0 : TMA producer (STAGES-deep ring of 128-byte K-slices)
 //   warp 1        : TMEM allocation; lane 0 of the even CTA issues tcgen05.mma
-//   warps 2..9    : epilogue; warp w reads TMEM lane quarter w % 4 and column
-//                   half (w - 2) / 4 of the CTA's 128 x 256 accumulator.
+//   warps 2..17   : epilogue; warp w reads TMEM lane quarter w % 4 and column
+//                   quarter (w - 2) / 4 of the CTA's 128-row accumulator.
 // Every wait is bounded: on timeout the CTA sets FTSP2_E_TIMEOUT in the status
 // word and all roles leave their loops.
 #include <cuda_bf16.h>
@@ -67,12 +71,17 @@ struct TcCfg<FTSP2_TF32X3> {
     static constexpr bool TF32 = true;
 };
 
-constexpr int kPairRows = 256;       // rows of a pair tile (M of the 2-CTA MMA)
-constexpr int kBN = 256;             // columns of a tile (N)
+// Tile geometry.  PAIR = true: clusters of two CTAs, 256 x 256 tiles, M = 256
+// MMAs (the default for large matrices).  PAIR = false: one CTA, 128 x 128
+// tiles, M = 128 MMAs (less padding for small instances of a ragged batch).
+template <bool PAIR>
+struct Geo {
+    static constexpr int TILE = PAIR ? 256 : 128;    // rows = columns of a tile
+    static constexpr int NCTA = PAIR ? 2 : 1;
+};
 constexpr int kCtaRows = 128;
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kEpiCols = kBN / (kEpiWarps / 4);   // columns per epilogue warp (64)
 constexpr int kGrp = 8;                            // columns per epilogue group
 constexpr int kTbufBytes = kGrp * 32 * 4;          // per-warp transpose buffer
 static_assert(kPartialSlots == 2 * kEpiWarps, "one partial-sum slot per epilogue warp of the pair");
@@ -192,6 +201,39 @@ __device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
 }
 
 // 32 lanes x 16 columns of FP32 from TMEM into registers (no wait)
+// single-CTA counterparts
+__device__ __forceinline__ void tma_load_one(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+template <bool TF32>
+__device__ __forceinline__ void umma_one(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+    if constexpr (TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+    }
+}
+__device__ __forceinline__ void umma_commit_one(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void local_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void local_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
@@ -401,27 +443,31 @@ __device__ __forceinline__ void epi_group(const LayerArgs& a, const EpiCtx& e, i
 }
 
 // Pull this lane's row segment of Z and A into L2 ahead of the final epilogue.
+template <int COLS>
 __device__ __forceinline__ void prefetch_state(const LayerArgs& a, const EpiCtx& e, int r, int C0) {
-    if (r < e.n && C0 < e.n && C0 + kEpiCols - 1 >= r) {
+    if (r < e.n && C0 < e.n && C0 + COLS - 1 >= r) {
         const float* z = a.Z[e.chain] + e.slab + (size_t)r * e.P + C0;
         const float* ac = a.A[e.chain] + e.slab + (size_t)r * e.P + C0;
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(z), "r"(kEpiCols * 4) : "memory");
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ac), "r"(kEpiCols * 4) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(z), "r"(COLS * 4) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ac), "r"(COLS * 4) : "memory");
     }
 }
 
 // ----------------------------------------------------------------------------------
 // OUTFMT: operand format written for the next layer, or kLastLayer.
-template <int MODE, int OUTFMT>
+template <int MODE, int OUTFMT, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     layer_tc_kernel(const __grid_constant__ LayerArgs a, const __grid_constant__ TmaMaps maps) {
     using C = TcCfg<MODE>;
+    using G = Geo<PAIR>;
+    constexpr int TILE = G::TILE;
+    constexpr int EPI_COLS = TILE / (kEpiWarps / 4);   // columns per epilogue warp (64 or 32)
     constexpr int BKE = 128 / C::ESIZE;                // K elements per 128-byte slice
     constexpr int PLANE = kCtaRows * 128;              // bytes of one 128-row slice
-    constexpr int STAGE_BYTES = C::NSPLIT * 2 * PLANE; // A and B-half planes of this CTA
+    constexpr int STAGE_BYTES = C::NSPLIT * 2 * PLANE; // A and B planes (B: this CTA's half when PAIR)
     constexpr int KSTEPS = 4;                          // 128-byte slice / 32 bytes per MMA
-    constexpr uint32_t IDESC = make_idesc(C::ATYPE, kPairRows, kBN);
-    constexpr uint32_t TMEM_COLS = 2 * kBN;
+    constexpr uint32_t IDESC = make_idesc(C::ATYPE, TILE, TILE);
+    constexpr uint32_t TMEM_COLS = 2 * TILE;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -434,62 +480,83 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = cluster_rank();
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
     // K slices per accumulation chunk: the default 128 elements, or a shorter
     // chunk requested for this launch (a.chunk_elems)
     const int ck = max(1, (a.chunk_elems > 0 ? a.chunk_elems : C::CK * BKE) / BKE);
-    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+    const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;     // pair or CTA
+    const int nunits = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
-            mbar_init(&full_bar[s], 2);          // one expect_tx arrival per CTA
+            mbar_init(&full_bar[s], G::NCTA);      // one expect_tx arrival per CTA
             mbar_init(&empty_bar[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&tfull_bar[s], 1);
-            mbar_init(&tempty_bar[s], 2 * kEpiWarps);
+            mbar_init(&tempty_bar[s], G::NCTA * kEpiWarps);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        if constexpr (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tmem_slot)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tmem_slot)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();
+    if constexpr (PAIR) cluster_sync();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer (both CTAs) ----------------
+            // ---------------- TMA producer ----------------
             int stage = 0;
             uint32_t phase = 0;
-            for (int t = pair; t < a.ntiles && !abort_flag; t += npairs) {
+            for (int t = unit; t < a.ntiles && !abort_flag; t += nunits) {
                 const Tile tl = a.tiles[t];
                 int k;
                 if (!tile_active(a, tl, k)) continue;
                 const int n = a.inst[tl.inst].n;
                 const int nk = (n + BKE - 1) / BKE;
-                const int rowA = tl.inst * a.P + tl.I * kPairRows + (int)rank * kCtaRows;
-                const int rowB = tl.inst * a.P + tl.J * kBN + (int)rank * kCtaRows;
+                const int rowA = tl.inst * a.P + tl.I * TILE + (int)rank * kCtaRows;
+                const int rowB = tl.inst * a.P + tl.J * TILE + (int)rank * kCtaRows;
                 bool ok = true;
                 for (int kb = 0; kb < nk; ++kb) {
                     if (!wait_bar(&empty_bar[stage], phase ^ 1u, &abort_flag, a.status)) {
                         ok = false;
                         break;
                     }
-                    const uint32_t fb = map_to(smem_u32(&full_bar[stage]), 0);
-                    remote_expect_tx(fb, STAGE_BYTES);
                     uint8_t* sbase = smem + stage * STAGE_BYTES;
+                    if constexpr (PAIR) {
+                        const uint32_t fb = map_to(smem_u32(&full_bar[stage]), 0);
+                        remote_expect_tx(fb, STAGE_BYTES);
 #pragma unroll
-                    for (int s = 0; s < C::NSPLIT; ++s) {
-                        tma_load_pair(smem_u32(sbase + s * PLANE), &maps.a[tl.chain][s], fb, kb * BKE, rowA);
-                        tma_load_pair(smem_u32(sbase + (C::NSPLIT + s) * PLANE), &maps.a[tl.chain][s], fb,
-                                      kb * BKE, rowB);
+                        for (int s = 0; s < C::NSPLIT; ++s) {
+                            tma_load_pair(smem_u32(sbase + s * PLANE), &maps.a[tl.chain][s], fb, kb * BKE, rowA);
+                            tma_load_pair(smem_u32(sbase + (C::NSPLIT + s) * PLANE), &maps.a[tl.chain][s], fb,
+                                          kb * BKE, rowB);
+                        }
+                    } else {
+                        const uint32_t fb = smem_u32(&full_bar[stage]);
+                        local_expect_tx(fb, STAGE_BYTES);
+#pragma unroll
+                        for (int s = 0; s < C::NSPLIT; ++s) {
+                            tma_load_one(smem_u32(sbase + s * PLANE), &maps.a[tl.chain][s], fb, kb * BKE, rowA);
+                            tma_load_one(smem_u32(sbase + (C::NSPLIT + s) * PLANE), &maps.a[tl.chain][s], fb,
+                                         kb * BKE, rowB);
+                        }
                     }
                     if (++stage == C::STAGES) {
                         stage = 0;
@@ -502,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0 && rank == 0) {
-            // ---------------- MMA issuer (even CTA) ----------------
+            // ---------------- MMA issuer (the even CTA of a pair) ----------------
             int stage = 0;
             uint32_t phase = 0;
             int buf = 0;
@@ -511,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // descriptors differ only in the start-address field (bits 0-13,
             // address >> 4); all operand slices lie inside this CTA's window
             const uint64_t desc0 = sdesc_sw128(smem_u32(smem));
-            for (int t = pair; t < a.ntiles && ok && !abort_flag; t += npairs) {
+            for (int t = unit; t < a.ntiles && ok && !abort_flag; t += nunits) {
                 const Tile tl = a.tiles[t];
                 int k;
                 if (!tile_active(a, tl, k)) continue;
@@ -523,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t dt = tmem + (uint32_t)(buf * kBN);
+                    const uint32_t dt = tmem + (uint32_t)(buf * TILE);
                     const int kend = min(nk, kc + ck);
                     for (int kb = kc; kb < kend; ++kb) {
                         if (!wait_bar(&full_bar[stage], phase, &abort_flag, a.status)) {
@@ -539,17 +606,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                             for (int p = 0; p < C::NPROD; ++p) {
                                 const uint64_t da = ds + (uint64_t)((prod_a(p) * PLANE + kk * 32) >> 4);
                                 const uint64_t db = ds + (uint64_t)(((C::NSPLIT + prod_b(p)) * PLANE + kk * 32) >> 4);
-                                umma_pair<C::TF32>(dt, da, db, IDESC, (kk == 0 && p == 0) ? first : 1u);
+                                if constexpr (PAIR)
+                                    umma_pair<C::TF32>(dt, da, db, IDESC, (kk == 0 && p == 0) ? first : 1u);
+                                else
+                                    umma_one<C::TF32>(dt, da, db, IDESC, (kk == 0 && p == 0) ? first : 1u);
                             }
                         }
-                        umma_commit_pair(smem_u32(&empty_bar[stage]));
+                        if constexpr (PAIR) umma_commit_pair(smem_u32(&empty_bar[stage]));
+                        else umma_commit_one(smem_u32(&empty_bar[stage]));
                         if (++stage == C::STAGES) {
                             stage = 0;
                             phase ^= 1u;
                         }
                     }
                     if (!ok) break;
-                    umma_commit_pair(smem_u32(&tfull_bar[buf]));
+                    if constexpr (PAIR) umma_commit_pair(smem_u32(&tfull_bar[buf]));
+                    else umma_commit_one(smem_u32(&tfull_bar[buf]));
                     if (++buf == 2) {
                         buf = 0;
                         aphase ^= 1u;
@@ -559,32 +631,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue (warps 2..17, both CTAs) ----------------
+        // ---------------- epilogue (warps 2..17) ----------------
         const int q = warp & 3;                  // TMEM lane quarter
-        const int cq = (warp - 2) >> 2;          // column quarter of the 256-column tile
+        const int cq = (warp - 2) >> 2;          // column quarter of the tile
         uint8_t* tbuf = tbuf_all + (warp - 2) * kTbufBytes;
-        const uint32_t tempty_leader0 = map_to(smem_u32(&tempty_bar[0]), 0);
-        const uint32_t tempty_leader1 = map_to(smem_u32(&tempty_bar[1]), 0);
+        const uint32_t tempty0 = PAIR ? map_to(smem_u32(&tempty_bar[0]), 0) : smem_u32(&tempty_bar[0]);
+        const uint32_t tempty1 = PAIR ? map_to(smem_u32(&tempty_bar[1]), 0) : smem_u32(&tempty_bar[1]);
         int buf = 0;
         uint32_t aphase = 0;
         bool ok = true;
-        for (int t = pair; t < a.ntiles && ok; t += npairs) {
+        for (int t = unit; t < a.ntiles && ok; t += nunits) {
             const Tile tl = a.tiles[t];
             int k;
             if (!tile_active(a, tl, k)) continue;
             EpiCtx e;
             make_ctx(a, tl, k, e, MODE == FTSP2_FP16X2);
             const int nk = (e.n + BKE - 1) / BKE;
-            const int R0 = tl.I * kPairRows + (int)rank * kCtaRows + q * 32;   // first row of this warp
+            const int R0 = tl.I * TILE + (int)rank * kCtaRows + q * 32;   // first row of this warp
             const int r = R0 + lane;
-            const int C0 = tl.J * kBN + cq * kEpiCols;                         // first column of this warp
-            const bool warp_live = C0 < e.n && C0 + kEpiCols - 1 >= R0 && R0 < e.n;
-            float acc[kEpiCols];
+            const int C0 = tl.J * TILE + cq * EPI_COLS;                   // first column of this warp
+            const bool warp_live = C0 < e.n && C0 + EPI_COLS - 1 >= R0 && R0 < e.n;
+            float acc[EPI_COLS];
 #pragma unroll
-            for (int i = 0; i < kEpiCols; ++i) acc[i] = 0.f;
+            for (int i = 0; i < EPI_COLS; ++i) acc[i] = 0.f;
             const int kpre = max(0, nk - 2 * ck);         // prefetch the state one chunk ahead of the end
             for (int kc = 0; kc < nk; kc += ck) {
-                if (kc <= kpre && kpre < kc + ck) prefetch_state(a, e, r, C0);
+                if (kc <= kpre && kpre < kc + ck) prefetch_state<EPI_COLS>(a, e, r, C0);
                 if (!wait_bar(&tfull_bar[buf], aphase, &abort_flag, a.status)) {
                     ok = false;
                     break;
@@ -593,8 +665,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (warp_live) {
                     // two 16-column loads in flight per wait
 #pragma unroll
-                    for (int g = 0; g < kEpiCols / 16; g += 2) {
-                        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * kBN + cq * kEpiCols + 16 * g);
+                    for (int g = 0; g < EPI_COLS / 16; g += 2) {
+                        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) +
+                                            (uint32_t)(buf * TILE + cq * EPI_COLS + 16 * g);
                         uint32_t v0[16], v1[16];
                         tmem_ld16(ta, v0);
                         tmem_ld16(ta + 16, v1);
@@ -608,7 +681,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) remote_arrive(buf ? tempty_leader1 : tempty_leader0);
+                if (lane == 0) {
+                    if constexpr (PAIR) remote_arrive(buf ? tempty1 : tempty0);
+                    else local_arrive(buf ? tempty1 : tempty0);
+                }
                 if (++buf == 2) {
                     buf = 0;
                     aphase ^= 1u;
@@ -618,7 +694,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             double tr = 0.0, sq = 0.0;
             if (warp_live) {
 #pragma unroll
-                for (int g = 0; g < kEpiCols / kGrp; ++g) {
+                for (int g = 0; g < EPI_COLS / kGrp; ++g) {
                     const int c0 = C0 + kGrp * g;
                     if (c0 < e.n && c0 + kGrp - 1 >= R0)
                         epi_group<OUTFMT>(a, e, R0, r, c0, &acc[kGrp * g], tbuf, lane, tr, sq);
@@ -633,6 +709,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int slot = (int)rank * kEpiWarps + (warp - 2);
                     a.partials[((size_t)t * kPartialSlots + slot) * 2 + 0] = tr;
                     a.partials[((size_t)t * kPartialSlots + slot) * 2 + 1] = sq;
+                    if constexpr (!PAIR) {
+                        // a single CTA fills half of the tile's slots; the finalize sums all
+                        a.partials[((size_t)t * kPartialSlots + slot + kEpiWarps) * 2 + 0] = 0.0;
+                        a.partials[((size_t)t * kPartialSlots + slot + kEpiWarps) * 2 + 1] = 0.0;
+                    }
                 }
             }
         }
@@ -640,15 +721,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
     tc_fence_before();
     __syncthreads();
-    cluster_sync();
+    if constexpr (PAIR) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        if constexpr (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                         : "memory");
     }
 }
 
-int tc_block_n(int) { return kBN; }
-int tc_block_m(int) { return kPairRows; }
+int tc_block_n(int, int pair) { return pair ? Geo<true>::TILE : Geo<false>::TILE; }
+int tc_block_m(int, int pair) { return pair ? Geo<true>::TILE : Geo<false>::TILE; }
 
 template <int MODE>
 static int smem_of() {
@@ -665,45 +751,51 @@ int tc_smem_bytes(int mode) {
     return 0;
 }
 
-template <int MODE, int OUTFMT>
-static cudaError_t launch_variant(const LayerArgs& a, const TmaMaps& maps, int npairs, cudaStream_t s) {
+template <int MODE, int OUTFMT, bool PAIR>
+static cudaError_t launch_variant(const LayerArgs& a, const TmaMaps& maps, int units, cudaStream_t s) {
     const int smem = smem_of<MODE>();
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e =
-            cudaFuncSetAttribute(layer_tc_kernel<MODE, OUTFMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(layer_tc_kernel<MODE, OUTFMT, PAIR>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * npairs, 1, 1);
+    cfg.gridDim = dim3(Geo<PAIR>::NCTA * units, 1, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.x = Geo<PAIR>::NCTA;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, layer_tc_kernel<MODE, OUTFMT>, a, maps);
+    cfg.numAttrs = PAIR ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, layer_tc_kernel<MODE, OUTFMT, PAIR>, a, maps);
     count_launch();
     return e;
 }
 
-template <int MODE, int MAINFMT>
-static cudaError_t launch_mode(const LayerArgs& a, const TmaMaps& maps, int npairs, cudaStream_t s) {
-    if (a.last) return launch_variant<MODE, kLastLayer>(a, maps, npairs, s);
-    if (a.next_fmt == OP_F32) return launch_variant<MODE, OP_F32>(a, maps, npairs, s);
-    return launch_variant<MODE, MAINFMT>(a, maps, npairs, s);
+template <int MODE, int MAINFMT, bool PAIR>
+static cudaError_t launch_shape(const LayerArgs& a, const TmaMaps& maps, int units, cudaStream_t s) {
+    if (a.last) return launch_variant<MODE, kLastLayer, PAIR>(a, maps, units, s);
+    if (a.next_fmt == OP_F32) return launch_variant<MODE, OP_F32, PAIR>(a, maps, units, s);
+    return launch_variant<MODE, MAINFMT, PAIR>(a, maps, units, s);
 }
 
-cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, int npairs, cudaStream_t s) {
+template <int MODE, int MAINFMT>
+static cudaError_t launch_mode(const LayerArgs& a, const TmaMaps& maps, int units, int pair, cudaStream_t s) {
+    return pair ? launch_shape<MODE, MAINFMT, true>(a, maps, units, s)
+                : launch_shape<MODE, MAINFMT, false>(a, maps, units, s);
+}
+
+cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, int units, int pair, cudaStream_t s) {
     switch (mode) {
-        case FTSP2_FP16X2: return launch_mode<FTSP2_FP16X2, OP_F16X2>(a, maps, npairs, s);
-        case FTSP2_BF16X3: return launch_mode<FTSP2_BF16X3, OP_BF16X3>(a, maps, npairs, s);
-        case FTSP2_TF32X3: return launch_mode<FTSP2_TF32X3, OP_TF32X3>(a, maps, npairs, s);
+        case FTSP2_FP16X2: return launch_mode<FTSP2_FP16X2, OP_F16X2>(a, maps, units, pair, s);
+        case FTSP2_BF16X3: return launch_mode<FTSP2_BF16X3, OP_BF16X3>(a, maps, units, pair, s);
+        case FTSP2_TF32X3: return launch_mode<FTSP2_TF32X3, OP_TF32X3>(a, maps, units, pair, s);
     }
     return cudaErrorInvalidValue;
 }
