@@ -69,20 +69,21 @@ struct EpiCtx {
     double cdiag;         // f0 (or 1 - f0 when flipped) added on the diagonal of D
 };
 
-// Process row r, columns c0 .. c0 + W - 1 (c0 % 4 == 0, c0 + W <= P) with
+// Process row r, columns c0 .. c0 + W - 1 (c0 % 8 == 0, W % 4 == 0, c0 + W <= P) with
 // accumulator values v[W].  Accumulates (diagonal sum, weighted square sum) of the
 // centred output G into tr / sq at the last layer.
 template <int W>
 __device__ __forceinline__ void epi_segment(const LayerArgs& a, const EpiCtx& e, int r, int c0,
                                             const float* v, double& tr, double& sq) {
     if (r >= e.n) return;
-    float* Zr = a.Z[e.chain] + e.slab + (size_t)r * e.P + c0;
-    float* Ar = a.A[e.chain] + e.slab + (size_t)r * e.P + c0;
+    float* Zs = a.Z[e.chain] + e.slab;
+    float* As = a.A[e.chain] + e.slab;
     float z[W], ac[W];
 #pragma unroll
     for (int i = 0; i < W / 4; ++i) {
-        const float4 zz = reinterpret_cast<const float4*>(Zr)[i];
-        const float4 aa = reinterpret_cast<const float4*>(Ar)[i];
+        const size_t o = state_off(e.P, r, c0 + 4 * i);
+        const float4 zz = *reinterpret_cast<const float4*>(Zs + o);
+        const float4 aa = *reinterpret_cast<const float4*>(As + o);
         z[4 * i + 0] = zz.x; z[4 * i + 1] = zz.y; z[4 * i + 2] = zz.z; z[4 * i + 3] = zz.w;
         ac[4 * i + 0] = aa.x; ac[4 * i + 1] = aa.y; ac[4 * i + 2] = aa.z; ac[4 * i + 3] = aa.w;
     }
@@ -95,8 +96,9 @@ __device__ __forceinline__ void epi_segment(const LayerArgs& a, const EpiCtx& e,
     if (!e.last) {
 #pragma unroll
         for (int i = 0; i < W / 4; ++i) {
-            reinterpret_cast<float4*>(Zr)[i] = make_float4(zn[4 * i], zn[4 * i + 1], zn[4 * i + 2], zn[4 * i + 3]);
-            reinterpret_cast<float4*>(Ar)[i] = make_float4(an[4 * i], an[4 * i + 1], an[4 * i + 2], an[4 * i + 3]);
+            const size_t o = state_off(e.P, r, c0 + 4 * i);
+            *reinterpret_cast<float4*>(Zs + o) = make_float4(zn[4 * i], zn[4 * i + 1], zn[4 * i + 2], zn[4 * i + 3]);
+            *reinterpret_cast<float4*>(As + o) = make_float4(an[4 * i], an[4 * i + 1], an[4 * i + 2], an[4 * i + 3]);
         }
         uint8_t* ob = a.opw[e.chain];
         const float os = e.next_fmt == OP_F16X2 ? e.L.out_scale : 1.f;

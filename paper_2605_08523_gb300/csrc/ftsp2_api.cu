@@ -314,6 +314,9 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
             L.OPR[c][1] = take(4 * L.plane_elems);
         }
     }
+    // the layer epilogues address A_c as Z_c + plane_elems
+    for (int c = 0; c < nch; ++c)
+        if (L.A[c] != L.Z[c] + 4 * L.plane_elems) return FTSP2_E_WORKSPACE;
     L.total = off;
     return FTSP2_OK;
 }

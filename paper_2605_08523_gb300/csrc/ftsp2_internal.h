@@ -151,7 +151,7 @@ struct LayerArgs {
     int chain_kind[kMaxChains];
     int next_fmt;
     int chunk_elems;                  // K elements per TMEM accumulation chunk (0: kernel default)
-    float* Z[kMaxChains];
+    float* Z[kMaxChains];             // state (blocked layout); A[c] == Z[c] + plane_elems
     float* A[kMaxChains];
     const uint8_t* opr[kMaxChains];   // read operands (plane 0 base) - SIMT path
     uint8_t* opw[kMaxChains];         // write operands (plane 0 base)
@@ -194,6 +194,19 @@ cudaError_t launch_train_absmax(const double* dR, int ns, double* dPart, double*
                                 cudaStream_t s);
 
 void count_launch(int n = 1);
+
+// Element offset of (r, c) inside one P x P slab of the FP32 state Z, A (P a
+// multiple of 128).  The slab is cut into blocks of 32 rows x 8 columns (1 KB),
+// stored block row by block row; a block holds two 32 x 4 halves, each with the
+// 4 columns of a row contiguous.  An epilogue warp whose lane i owns row
+// r0 + i (r0 % 32 == 0) reads 4 consecutive columns (c % 4 == 0) of its 32 rows
+// as one contiguous 512-byte run, and the 32 x W region of a warp is W / 8
+// consecutive blocks.  Only the layer epilogues and the initialisation touch
+// the state, so its layout is free of the operands' row-major constraint.
+__host__ __device__ __forceinline__ size_t state_off(int P, int r, int c) {
+    return ((size_t)(r >> 5) * (size_t)(P >> 3) + (size_t)(c >> 3)) * 256 + (size_t)(((c >> 2) & 1) * 128) +
+           (size_t)((r & 31) * 4 + (c & 3));
+}
 
 }  // namespace ftsp2
 

@@ -83,7 +83,6 @@ constexpr int kCtaRows = 128;
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kGrp = 8;                            // columns per epilogue group
-constexpr int kTbufBytes = kGrp * 32 * 4;          // per-warp transpose buffer
 static_assert(kPartialSlots == 2 * kEpiWarps, "one partial-sum slot per epilogue warp of the pair");
 
 // split planes (s, t) of the products Z_s Z_t, in issue order
@@ -243,6 +242,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* x) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(__float_as_uint(x[0])), "r"(__float_as_uint(x[1])), "r"(__float_as_uint(x[2])),
+                 "r"(__float_as_uint(x[3])), "r"(__float_as_uint(x[4])), "r"(__float_as_uint(x[5])),
+                 "r"(__float_as_uint(x[6])), "r"(__float_as_uint(x[7]))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -296,161 +308,162 @@ struct OpFmtT<OP_F32> {
 };
 
 template <int ESZ>
-__device__ __forceinline__ void store8(uint8_t* dst, const uint32_t* v) {
-    if constexpr (ESZ == 2) {
-        uint4 a;
-        a.x = v[0] | (v[1] << 16); a.y = v[2] | (v[3] << 16); a.z = v[4] | (v[5] << 16); a.w = v[6] | (v[7] << 16);
-        *reinterpret_cast<uint4*>(dst) = a;
-    } else {
-        reinterpret_cast<uint4*>(dst)[0] = make_uint4(v[0], v[1], v[2], v[3]);
-        reinterpret_cast<uint4*>(dst)[1] = make_uint4(v[4], v[5], v[6], v[7]);
-    }
-}
-template <int ESZ>
 __device__ __forceinline__ void store1(uint8_t* dst, uint32_t v) {
     if constexpr (ESZ == 2) *reinterpret_cast<uint16_t*>(dst) = (uint16_t)v;
     else *reinterpret_cast<uint32_t*>(dst) = v;
 }
-template <int ESZ>
-__device__ __forceinline__ uint32_t load1(const uint8_t* src) {
-    if constexpr (ESZ == 2) return (uint32_t)*reinterpret_cast<const uint16_t*>(src);
-    else return *reinterpret_cast<const uint32_t*>(src);
-}
-
-// Operand stores of one 32-row x 8-column block held by a warp (lane = row r,
-// columns c0 .. c0 + 7): direct stores at (r, c) as one 8-element vector per
-// plane; the mirror (c, r) goes through a per-warp shared transpose buffer so
-// that lane l stores 8 consecutive elements of mirrored row c0 + l / 4.
-template <int FMT>
-__device__ __forceinline__ void store_block(const LayerArgs& a, const EpiCtx& e, int R0, int r, int c0,
-                                            const float* zs, uint8_t* tbuf, int lane) {
-    using F = OpFmtT<FMT>;
-    constexpr int ESZ = F::ESZ;
-    uint8_t* const base = a.opw[e.chain];
-    const size_t plane_bytes = a.plane_elems * ESZ;
-    uint32_t sp[F::NPL][kGrp];
-#pragma unroll
-    for (int jj = 0; jj < kGrp; ++jj) {
-        uint32_t o[F::NPL];
-        F::split(zs[jj], o);
-#pragma unroll
-        for (int p = 0; p < F::NPL; ++p) sp[p][jj] = o[p];
-    }
-    const bool row_ok = r < e.n;
-    const bool full_direct = row_ok && r <= c0 && c0 + kGrp - 1 < e.n;
-    const int jm = lane >> 2, qm = lane & 3;
-    const int cm = c0 + jm;                 // mirrored row handled by this lane
-    const int rr0 = R0 + 8 * qm;            // its first column
-    const bool full_mirror = cm < e.n && rr0 + 7 < cm && rr0 + 7 < e.n;
-#pragma unroll
-    for (int p = 0; p < F::NPL; ++p) {
-        uint8_t* pb = base + p * plane_bytes + (e.slab + (size_t)r * e.P + c0) * ESZ;
-        if (full_direct) {
-            store8<ESZ>(pb, sp[p]);
-        } else if (row_ok) {
-#pragma unroll
-            for (int jj = 0; jj < kGrp; ++jj)
-                if (c0 + jj < e.n && r <= c0 + jj) store1<ESZ>(pb + jj * ESZ, sp[p][jj]);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int jj = 0; jj < kGrp; ++jj) store1<ESZ>(tbuf + (jj * 32 + lane) * ESZ, sp[p][jj]);
-        __syncwarp();
-        uint8_t* mb = base + p * plane_bytes + (e.slab + (size_t)cm * e.P + rr0) * ESZ;
-        const uint8_t* src = tbuf + (jm * 32 + 8 * qm) * ESZ;
-        if (full_mirror) {
-            uint32_t v[kGrp];
-#pragma unroll
-            for (int i = 0; i < kGrp; ++i) v[i] = load1<ESZ>(src + i * ESZ);
-            store8<ESZ>(mb, v);
-        } else if (cm < e.n) {
-#pragma unroll
-            for (int i = 0; i < kGrp; ++i) {
-                const int rr = rr0 + i;
-                if (rr < e.n && rr < cm) store1<ESZ>(mb + i * ESZ, load1<ESZ>(src + i * ESZ));
-            }
-        }
-    }
-    __syncwarp();
-}
-
-// Centred update of an 8-column group for this lane's row, then operand stores
-// in format OUTFMT, or, for OUTFMT == kLastLayer, the output D and the partial
-// sums.  v holds the 8 accumulated products.
 constexpr int kLastLayer = -1;
 
-template <int OUTFMT>
-__device__ __forceinline__ void epi_group(const LayerArgs& a, const EpiCtx& e, int R0, int r, int c0, const float* v,
-                                          uint8_t* tbuf, int lane, double& tr, double& sq) {
-    constexpr bool LAST = OUTFMT == kLastLayer;
-    const bool row_ok = r < e.n;
-    float zn[kGrp];
-    if (row_ok) {
-        float* Zr = a.Z[e.chain] + e.slab + (size_t)r * e.P + c0;
-        float* Ar = a.A[e.chain] + e.slab + (size_t)r * e.P + c0;
-        const float4 z0 = reinterpret_cast<const float4*>(Zr)[0], z1 = reinterpret_cast<const float4*>(Zr)[1];
-        const float4 a0 = reinterpret_cast<const float4*>(Ar)[0], a1 = reinterpret_cast<const float4*>(Ar)[1];
-        const float z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
-        const float ac[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        float an[8];
+// What the final epilogue of a non-last layer needs beyond the kernel
+// parameters, with the instance's slab offset folded into the pointers (kept
+// small).  The accumulator A of a chain sits plane_elems floats after its Z
+// (the workspace places them back to back).
+struct EpiLite {
+    float* Z;          // state slab of Z (blocked layout); A = Z + plane_elems
+    uint8_t* op;       // next layer's operand plane 0, slab start (bytes)
+    float mul, bp, d, os;
+};
+
+// FMT: operand format written; scaled_in: the products were formed from
+// power-of-two scaled FP16 operands (FP16X2 layers).
+template <int FMT>
+__device__ __forceinline__ void make_lite(const LayerArgs& a, const Tile& t, int k, bool scaled_in, EpiLite& e) {
+    const ftsp2_rescale_rec& rec = a.rec[t.inst];
+    const DevModel& M = a.models[rec.model];
+    const DevLayer L = a.layers[(a.chain_kind[t.chain] == CHAIN_ENTROPY ? M.offS : M.off) + k];
+    const size_t slab = (size_t)t.inst * a.P * a.P;
+    e.Z = a.Z[t.chain] + slab;
+    e.op = a.opw[t.chain] + slab * OpFmtT<FMT>::ESZ;
+    e.mul = scaled_in ? L.acc_mul : L.a;
+    e.bp = L.bp;
+    e.d = L.d;
+    e.os = FMT == OP_F16X2 ? L.out_scale : 1.f;
+}
+
+// Load the 8 state values of row r, columns c0 .. c0 + 7 (two float4 runs 128
+// floats apart in the blocked layout).
+__device__ __forceinline__ void load_state8(const float* S, float* x) {
+    const float4 u = reinterpret_cast<const float4*>(S)[0], w = reinterpret_cast<const float4*>(S + 128)[0];
+    x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w; x[4] = w.x; x[5] = w.y; x[6] = w.z; x[7] = w.w;
+}
+__device__ __forceinline__ void store_state8(float* S, const float* x) {
+    reinterpret_cast<float4*>(S)[0] = make_float4(x[0], x[1], x[2], x[3]);
+    reinterpret_cast<float4*>(S + 128)[0] = make_float4(x[4], x[5], x[6], x[7]);
+}
+
+// Final epilogue of a non-last layer on one 8-column group of row r (columns
+// c0 .. c0 + 7), v = the accumulated products:
+//   Z_{k+1} = a_k v + (b_k + 2 a_k tau_k) Z_k,  A_{k+1} = A_k + d_k Z_k,
+// then the operands of Z_{k+1} (times the FP16 scale 2^e_{k+1}) for the next
+// layer: direct (r, c), r <= c, as one 16-byte vector per plane and lane;
+// mirror (c, r), r < c, one element per lane, so that for each column the
+// warp's 32 stores are one contiguous run of row c.
+template <int FMT>
+__device__ __forceinline__ void epi_group_next(const LayerArgs& a, const EpiLite& e, int n, int r, int c0,
+                                               const float* v) {
+    using F = OpFmtT<FMT>;
+    constexpr int ESZ = F::ESZ;
+    constexpr int CH = 16 / ESZ;                     // elements per 16-byte vector
+    if (r >= n) return;
+    const int P = a.P;
+    const size_t so = state_off(P, r, c0);
+    float* const Zg = e.Z + so;
+    float* const Ag = Zg + a.plane_elems;
+    float z[8], zn[8];
+    load_state8(Zg, z);
+    load_state8(Ag, zn);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) zn[u] = fmaf(e.d, z[u], zn[u]);
+    store_state8(Ag, zn);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) zn[u] = fmaf(e.mul, v[u], e.bp * z[u]);
+    store_state8(Zg, zn);
+    const bool full = r <= c0 && c0 + kGrp - 1 < n;
+#pragma unroll
+    for (int p = 0; p < F::NPL; ++p) {
+        uint8_t* const plane = e.op + p * a.plane_elems * ESZ;
+        uint32_t w[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            zn[u] = fmaf(e.mul, v[u], e.L.bp * z[u]);
-            an[u] = fmaf(e.L.d, z[u], ac[u]);
+            uint32_t o[F::NPL];
+            F::split(zn[u] * e.os, o);
+            w[u] = o[p];
         }
-        if constexpr (!LAST) {
-            reinterpret_cast<float4*>(Zr)[0] = make_float4(zn[0], zn[1], zn[2], zn[3]);
-            reinterpret_cast<float4*>(Zr)[1] = make_float4(zn[4], zn[5], zn[6], zn[7]);
-            reinterpret_cast<float4*>(Ar)[0] = make_float4(an[0], an[1], an[2], an[3]);
-            reinterpret_cast<float4*>(Ar)[1] = make_float4(an[4], an[5], an[6], an[7]);
+        uint8_t* const dst = plane + ((size_t)r * P + c0) * ESZ;
+        if (full) {
+#pragma unroll
+            for (int h = 0; h < 8 / CH; ++h) {
+                uint4 q4;
+                if constexpr (ESZ == 2)
+                    q4 = make_uint4(w[0] | (w[1] << 16), w[2] | (w[3] << 16), w[4] | (w[5] << 16), w[6] | (w[7] << 16));
+                else
+                    q4 = make_uint4(w[4 * h], w[4 * h + 1], w[4 * h + 2], w[4 * h + 3]);
+                reinterpret_cast<uint4*>(dst)[h] = q4;
+            }
         } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) zn[u] += an[u];     // G = A_L + Z_L
+            for (int u = 0; u < 8; ++u)
+                if (c0 + u < n && r <= c0 + u) store1<ESZ>(dst + u * ESZ, w[u]);
         }
-    } else {
 #pragma unroll
-        for (int jj = 0; jj < kGrp; ++jj) zn[jj] = 0.f;
+        for (int u = 0; u < 8; ++u) {
+            const int c = c0 + u;
+            if (r < c && c < n) store1<ESZ>(plane + ((size_t)c * P + r) * ESZ, w[u]);
+        }
     }
-    if constexpr (!LAST) {
-        if constexpr (OUTFMT == OP_F16X2) {
+}
+
+// Last layer: G = A_L + Z_L with A_L = A_{L-1} + d Z_{L-1}, Z_L = a v + b' Z_{L-1}
+// (v overwritten with G); rows r >= n give 0.
+__device__ __forceinline__ void epi_update_last(const LayerArgs& a, const EpiCtx& e, int r, int c0, float* v) {
+    if (r >= e.n) {
 #pragma unroll
-            for (int jj = 0; jj < kGrp; ++jj) zn[jj] *= e.L.out_scale;
-        }
-        store_block<(OUTFMT < 0 ? OP_F32 : OUTFMT)>(a, e, R0, r, c0, zn, tbuf, lane);
-    } else if (row_ok) {
+        for (int u = 0; u < kGrp; ++u) v[u] = 0.f;
+        return;
+    }
+    const size_t so = e.slab + state_off(e.P, r, c0);
+    float z[8], x[8];
+    load_state8(a.Z[e.chain] + so, z);
+    load_state8(a.A[e.chain] + so, x);
 #pragma unroll
-        for (int jj = 0; jj < kGrp; ++jj) {
-            const int c = c0 + jj;
-            if (c < e.n && r <= c) {
-                const float g = zn[jj];
-                if (e.kind == CHAIN_FERMI && a.D) {
-                    float dv;
-                    if (e.flip) dv = (r == c ? (float)e.cdiag : 0.f) - g;
-                    else dv = g + (r == c ? (float)e.cdiag : 0.f);
-                    a.D[e.doff + (int64_t)r * e.n + c] = dv;
-                    if (c != r) a.D[e.doff + (int64_t)c * e.n + r] = dv;
-                }
-                const double gd = (double)g;
-                if (r == c) {
-                    tr += gd;
-                    sq += gd * gd;
-                } else {
-                    sq += 2.0 * gd * gd;
-                }
+    for (int u = 0; u < 8; ++u) v[u] = fmaf(e.mul, v[u], e.L.bp * z[u]) + fmaf(e.L.d, z[u], x[u]);
+}
+
+// Last layer: D = G + f0 I (or (1 - f0) I - G when flipped) at (r, c) and
+// (c, r), and the FP64 sums of the diagonal and of the squares of G.
+__device__ __forceinline__ void epi_last(const LayerArgs& a, const EpiCtx& e, int r, int c0, const float* v,
+                                         double& tr, double& sq) {
+    if (r >= e.n) return;
+#pragma unroll
+    for (int jj = 0; jj < kGrp; ++jj) {
+        const int c = c0 + jj;
+        if (c < e.n && r <= c) {
+            const float g = v[jj];
+            if (e.kind == CHAIN_FERMI && a.D) {
+                float dv;
+                if (e.flip) dv = (r == c ? (float)e.cdiag : 0.f) - g;
+                else dv = g + (r == c ? (float)e.cdiag : 0.f);
+                a.D[e.doff + (int64_t)r * e.n + c] = dv;
+                if (c != r) a.D[e.doff + (int64_t)c * e.n + r] = dv;
+            }
+            const double gd = (double)g;
+            if (r == c) {
+                tr += gd;
+                sq += gd * gd;
+            } else {
+                sq += 2.0 * gd * gd;
             }
         }
     }
 }
 
-// Pull this lane's row segment of Z and A into L2 ahead of the final epilogue.
+// Pull the warp's 32 x COLS state region of Z and A into L2 ahead of the
+// final epilogue (COLS / 8 consecutive 1 KB blocks in each, blocked layout).
 template <int COLS>
-__device__ __forceinline__ void prefetch_state(const LayerArgs& a, const EpiCtx& e, int r, int C0) {
-    if (r < e.n && C0 < e.n && C0 + COLS - 1 >= r) {
-        const float* z = a.Z[e.chain] + e.slab + (size_t)r * e.P + C0;
-        const float* ac = a.A[e.chain] + e.slab + (size_t)r * e.P + C0;
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(z), "r"(COLS * 4) : "memory");
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ac), "r"(COLS * 4) : "memory");
-    }
+__device__ __forceinline__ void prefetch_state(const LayerArgs& a, const Tile& tl, int R0, int C0) {
+    const size_t off = (size_t)tl.inst * a.P * a.P + state_off(a.P, R0, C0);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.Z[tl.chain] + off), "r"(COLS * 128) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.A[tl.chain] + off), "r"(COLS * 128) : "memory");
 }
 
 // ----------------------------------------------------------------------------------
@@ -471,7 +484,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* tbuf_all = smem + C::STAGES * STAGE_BYTES;
     __shared__ __align__(8) uint64_t full_bar[C::STAGES];
     __shared__ __align__(8) uint64_t empty_bar[C::STAGES];
     __shared__ __align__(8) uint64_t tfull_bar[2];
@@ -634,7 +646,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- epilogue (warps 2..17) ----------------
         const int q = warp & 3;                  // TMEM lane quarter
         const int cq = (warp - 2) >> 2;          // column quarter of the tile
-        uint8_t* tbuf = tbuf_all + (warp - 2) * kTbufBytes;
         const uint32_t tempty0 = PAIR ? map_to(smem_u32(&tempty_bar[0]), 0) : smem_u32(&tempty_bar[0]);
         const uint32_t tempty1 = PAIR ? map_to(smem_u32(&tempty_bar[1]), 0) : smem_u32(&tempty_bar[1]);
         int buf = 0;
@@ -644,40 +655,53 @@ __global__ void __launch_bounds__(kThreads, 1)
             const Tile tl = a.tiles[t];
             int k;
             if (!tile_active(a, tl, k)) continue;
-            EpiCtx e;
-            make_ctx(a, tl, k, e, MODE == FTSP2_FP16X2);
-            const int nk = (e.n + BKE - 1) / BKE;
+            // only the order n is needed while the chunks drain; the rest of the
+            // epilogue context is formed afterwards (keeps the drain loop within
+            // the register budget)
+            const int n = a.inst[tl.inst].n;
+            const int nk = (n + BKE - 1) / BKE;
             const int R0 = tl.I * TILE + (int)rank * kCtaRows + q * 32;   // first row of this warp
             const int r = R0 + lane;
             const int C0 = tl.J * TILE + cq * EPI_COLS;                   // first column of this warp
-            const bool warp_live = C0 < e.n && C0 + EPI_COLS - 1 >= R0 && R0 < e.n;
+            const bool warp_live = C0 < n && C0 + EPI_COLS - 1 >= R0 && R0 < n;
             float acc[EPI_COLS];
 #pragma unroll
             for (int i = 0; i < EPI_COLS; ++i) acc[i] = 0.f;
-            const int kpre = max(0, nk - 2 * ck);         // prefetch the state one chunk ahead of the end
-            for (int kc = 0; kc < nk; kc += ck) {
-                if (kc <= kpre && kpre < kc + ck) prefetch_state<EPI_COLS>(a, e, r, C0);
+            // Chunk drain.  Chunks 0 .. nch - 2 are added into acc and their
+            // buffer released at once.  The last chunk is added too, and the
+            // finished sum is written back into that chunk's TMEM buffer, which
+            // stays held through the final epilogue: the epilogue then reads
+            // its 8-column groups from TMEM, so the 64 accumulator registers of
+            // a pair tile are free for the memory work.  The MMAs of the next
+            // tile meanwhile fill the other buffer.
+            const int nch = (nk + ck - 1) / ck;
+            const int jpre = max(0, nch - 2);       // prefetch the state one chunk ahead of the end
+            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cq * EPI_COLS);
+            for (int j = 0; j < nch; ++j) {
+                if (j == jpre && warp_live && lane == 0) prefetch_state<EPI_COLS>(a, tl, R0, C0);
                 if (!wait_bar(&tfull_bar[buf], aphase, &abort_flag, a.status)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
+                const uint32_t ta = tbase + (uint32_t)(buf * TILE);
                 if (warp_live) {
-                    // two 16-column loads in flight per wait
 #pragma unroll
-                    for (int g = 0; g < EPI_COLS / 16; g += 2) {
-                        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) +
-                                            (uint32_t)(buf * TILE + cq * EPI_COLS + 16 * g);
-                        uint32_t v0[16], v1[16];
-                        tmem_ld16(ta, v0);
-                        tmem_ld16(ta + 16, v1);
+                    for (int g = 0; g < EPI_COLS / 8; ++g) {
+                        uint32_t v[8];
+                        tmem_ld8(ta + 8 * g, v);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int jj = 0; jj < 16; ++jj) {
-                            acc[16 * g + jj] += __uint_as_float(v0[jj]);
-                            acc[16 * g + 16 + jj] += __uint_as_float(v1[jj]);
-                        }
+                        for (int jj = 0; jj < 8; ++jj) acc[8 * g + jj] += __uint_as_float(v[jj]);
                     }
+                }
+                if (j == nch - 1) {
+                    if (warp_live) {
+#pragma unroll
+                        for (int g = 0; g < EPI_COLS / 8; ++g) tmem_st8(ta + 8 * g, &acc[8 * g]);
+                        tmem_wait_st();
+                    }
+                    break;                            // buffer released after the final epilogue
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -691,14 +715,48 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             if (!ok) break;
+            const uint32_t tfin = tbase + (uint32_t)(buf * TILE);   // the held buffer
             double tr = 0.0, sq = 0.0;
             if (warp_live) {
-#pragma unroll
-                for (int g = 0; g < EPI_COLS / kGrp; ++g) {
-                    const int c0 = C0 + kGrp * g;
-                    if (c0 < e.n && c0 + kGrp - 1 >= R0)
-                        epi_group<OUTFMT>(a, e, R0, r, c0, &acc[kGrp * g], tbuf, lane, tr, sq);
+                if constexpr (OUTFMT == kLastLayer) {
+                    EpiCtx e;
+                    make_ctx(a, tl, k, e, MODE == FTSP2_FP16X2);
+#pragma unroll 1
+                    for (int g = 0; g < EPI_COLS / kGrp; ++g) {
+                        const int c0 = C0 + kGrp * g;
+                        if (c0 < e.n && c0 + kGrp - 1 >= R0) {
+                            float v[8];
+                            tmem_ld8(tfin + 8 * g, reinterpret_cast<uint32_t*>(v));
+                            tmem_wait_ld();
+                            epi_update_last(a, e, r, c0, v);
+                            epi_last(a, e, r, c0, v, tr, sq);
+                        }
+                    }
+                } else {
+                    EpiLite e;
+                    make_lite<OUTFMT>(a, tl, k, MODE == FTSP2_FP16X2, e);
+                    // the groups that touch the triangle and the order form one range
+                    const int g_lo = R0 > C0 ? min(EPI_COLS / kGrp, (R0 - C0) / kGrp) : 0;
+                    const int g_hi = min(EPI_COLS / kGrp, (n - C0 + kGrp - 1) / kGrp);
+#pragma unroll 1
+                    for (int g = g_lo; g < g_hi; ++g) {
+                        float v[8];
+                        tmem_ld8(tfin + 8 * g, reinterpret_cast<uint32_t*>(v));
+                        tmem_wait_ld();
+                        epi_group_next<OUTFMT>(a, e, n, r, C0 + kGrp * g, v);
+                    }
                 }
+            }
+            // release the held accumulator buffer
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if constexpr (PAIR) remote_arrive(buf ? tempty1 : tempty0);
+                else local_arrive(buf ? tempty1 : tempty0);
+            }
+            if (++buf == 2) {
+                buf = 0;
+                aphase ^= 1u;
             }
             if constexpr (OUTFMT == kLastLayer) {
                 for (int o = 16; o > 0; o >>= 1) {
@@ -739,7 +797,7 @@ int tc_block_m(int, int pair) { return pair ? Geo<true>::TILE : Geo<false>::TILE
 template <int MODE>
 static int smem_of() {
     using C = TcCfg<MODE>;
-    return C::STAGES * C::NSPLIT * 2 * kCtaRows * 128 + kEpiWarps * kTbufBytes + 1024;
+    return C::STAGES * C::NSPLIT * 2 * kCtaRows * 128 + 1024;
 }
 
 int tc_smem_bytes(int mode) {

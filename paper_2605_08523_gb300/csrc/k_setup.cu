@@ -335,14 +335,15 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
         const double* Hr = a.H + in.offset + (size_t)r * n;
         for (int c = threadIdx.x; c < P; c += blockDim.x) {
             const size_t e = base + (size_t)r * P + c;
+            const size_t es = base + state_off(P, r, c);
             const bool inside = r < n && c < n;
             float z = 0.f;
             if (ok && inside) z = (float)(rec.scale * ((r == c ? in.mu : 0.0) - __ldg(Hr + c)));
             for (int ch = 0; ch < a.nchains; ++ch) {
                 const bool ent = a.chain_kind[ch] == CHAIN_ENTROPY;
                 const float zc = ent ? alpha * z : z;
-                a.Z[ch][e] = zc;
-                a.A[ch][e] = 0.f;
+                a.Z[ch][es] = zc;
+                a.A[ch][es] = 0.f;
                 if (inside) {
                     const int start = (sl_packed >> (16 * ch)) & 0xffff;
                     if (a.main_fmt != OP_F32 && start >= a.refine_from) a.OPR[ch][start & 1][e] = zc;
