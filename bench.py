@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--mu", type=float, default=None,
                    help="skip the GPU eigendecomposition and use this mu (profiling runs)")
+    p.add_argument("--shape", default="auto", choices=["auto", "pair", "single"],
+                   help="tensor-core tile shape: auto = the library's autotuner (untimed), or forced")
     p.add_argument("--workload", default="cfg1", choices=["cfg1", "cfg2"],
                    help="cfg1: the headline single n = 4096 matrix; cfg2: the 512-instance ragged batch "
                         "(reported as a separate line, not the headline)")
@@ -190,7 +192,7 @@ def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
 # (mode, n, sha256[:16] of the layer-kernel sources) -> dram read + write bytes
 # of one layer launch (both chains), from the ncu capture summarised in
 # profiles/layer_tc_fp16x2_n4096.md
-MEASURED_TRAFFIC = {("fp16x2", 4096, "079b8407bcec3aa0"): 428.269568e6 + 256.946176e6}
+MEASURED_TRAFFIC = {("fp16x2", 4096, "02369ec7e046f451"): 424.213248e6 + 238.845696e6}
 
 
 def kernel_sha():
@@ -299,8 +301,13 @@ def run_cfg2(args):
     ns = [H.shape[0] for H in Hs]
     flat, _ = wl.pack_batch(Hs)
     Hd = torch.from_numpy(flat).cuda()
-    solver = ft.Solver(ns, [b["mu"] for b in batch], [b["kT"] for b in batch], ms, mode=args.mode, want=3)
-    shape, ms_single, ms_pair = solver.autotune(Hd, reps=1)
+    shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
+    solver = ft.Solver(ns, [b["mu"] for b in batch], [b["kT"] for b in batch], ms, mode=args.mode, want=3,
+                       flags=shape_flag)
+    if args.shape == "auto":
+        shape, ms_single, ms_pair = solver.autotune(Hd, reps=1)
+    else:
+        shape, ms_single, ms_pair = solver.tile_shape()[0], None, None
     for _ in range(args.warmup):
         solver.run(Hd)
     torch.cuda.synchronize()
@@ -365,9 +372,13 @@ def main():
     # the paper's printed Fermi table with the entropy table the library's
     # trainer fitted for it (theta_entropy)
     ms = ft.ModelSet.from_json([os.path.join(ROOT, "paper_2605_08523_gb300", "tables", "entropy_b1500_L26.json")])
-    solver = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3)
-    # tile shape: the library's autotuner times both shapes once (untimed)
-    shape, ms_single, ms_pair = solver.autotune(Hd, reps=2)
+    shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
+    solver = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3, flags=shape_flag)
+    if args.shape == "auto":
+        # tile shape: the library's autotuner times both shapes once (untimed)
+        shape, ms_single, ms_pair = solver.autotune(Hd, reps=2)
+    else:
+        shape, ms_single, ms_pair = solver.tile_shape()[0], None, None
     for _ in range(args.warmup):
         solver.run(Hd)
     torch.cuda.synchronize()

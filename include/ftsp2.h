@@ -193,6 +193,17 @@ ftsp2_status ftsp2_entropy(const double* dH, const ftsp2_instance* inst,
                            double* dS, ftsp2_rescale_rec* dRec,
                            void* ws, size_t ws_bytes, void* stream);
 
+/* CUDA graphs.  ftsp2_density, ftsp2_entropy and ftsp2_density_entropy only
+ * launch kernels on `stream` (planning is host-side arithmetic; the workspace
+ * is the caller's), so a call may be recorded by stream capture and the graph
+ * replayed: each replay recomputes the batch from the current contents of dH
+ * and the device copy dInst, into the same output buffers.  The pointers,
+ * instance sizes, model set and flags are fixed at capture; mu and kT may be
+ * changed between replays through dInst.  Make one uncaptured call with the
+ * same arguments first (it sets per-kernel attributes), and do not pass
+ * FTSP2_SYNC while capturing (FTSP2_E_ARG).  Layer profiling
+ * (ftsp2_profile_layers) skips captured launches. */
+
 /* (a1)-(a6) in one pass: both recursions share the bounds and the rescale and
  * run as two problems of the same grouped launch per layer (Alg. 2 runs them
  * in one loop).  Any of dD, dTrace, dS may be NULL (dD and dS not both). */

@@ -225,6 +225,20 @@ class Solver:
             raise Ftsp2Error(st, "ftsp2 hot path")
         return st
 
+    def graph(self, H):
+        """Record one ``run(H)`` into a CUDA graph and return it
+        (``torch.cuda.CUDAGraph``; ``g.replay()`` reruns the whole hot path on
+        the current contents of H and of the device instance table, writing
+        the same output tensors).  An eager run with the same arguments comes
+        first, as the C ABI asks."""
+        torch = _torch()
+        self.run(H)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(H)
+        return g
+
     def _outputs(self):
         D = _ptr(self.D) if self.want & 1 else None
         T = _ptr(self.trace) if self.want & 1 else None

@@ -406,6 +406,12 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     if (st != FTSP2_OK) return st;
     if (ws_bytes < L.total) return FTSP2_E_WORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // launches on a stream being captured into a CUDA graph are recorded, not
+    // run: no synchronising, and the layer profiling events stay off
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return FTSP2_E_CUDA;
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    if (capturing && (flags & FTSP2_SYNC)) return FTSP2_E_ARG;
     uint8_t* W = static_cast<uint8_t*>(ws);
     const bool scaled = mode == FTSP2_FP16X2;
     const DevModel* models = set->d_models[scaled ? 1 : 0];
@@ -549,7 +555,8 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             {
                 std::lock_guard<std::mutex> lk(g_prof_mu);
-                if (g_prof_on && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+                if (g_prof_on && !capturing && cudaEventCreate(&e0) == cudaSuccess &&
+                    cudaEventCreate(&e1) == cudaSuccess) {
                     cudaEventRecord(e0, s);
                 } else {
                     e0 = e1 = nullptr;
