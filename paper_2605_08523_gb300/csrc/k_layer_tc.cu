@@ -351,64 +351,91 @@ __device__ __forceinline__ void store_state8(float* S, const float* x) {
     reinterpret_cast<float4*>(S + 128)[0] = make_float4(x[4], x[5], x[6], x[7]);
 }
 
-// Final epilogue of a non-last layer on one 8-column group of row r (columns
-// c0 .. c0 + 7), v = the accumulated products:
-//   Z_{k+1} = a_k v + (b_k + 2 a_k tau_k) Z_k,  A_{k+1} = A_k + d_k Z_k,
+// 256-bit store (sm_100+): dst must be 32-byte aligned.
+__device__ __forceinline__ void st_global_v8(void* dst, const uint32_t* w) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
+// Final epilogue of a non-last layer on 16 columns c0 .. c0 + 15 (c0 % 16 == 0)
+// of row r, the sums S read from TMEM at tcol (8-column halves that do not
+// touch the triangle or the order are skipped):
+//   A_{k+1} = A_k + d_k Z_k,  Z_{k+1} = a_k S + (b_k + 2 a_k tau_k) Z_k,
 // then the operands of Z_{k+1} (times the FP16 scale 2^e_{k+1}) for the next
-// layer: direct (r, c), r <= c, as one 16-byte vector per plane and lane;
-// mirror (c, r), r < c, one element per lane, so that for each column the
-// warp's 32 stores are one contiguous run of row c.
+// layer: direct (r, c), r <= c, as one 32-byte vector per plane and lane (full
+// sectors; 4-byte formats store two), and mirror (c, r), r < c, one element per
+// lane, so that for each column the warp's 32 stores are one contiguous run of
+// row c.
 template <int FMT>
-__device__ __forceinline__ void epi_group_next(const LayerArgs& a, const EpiLite& e, int n, int r, int c0,
-                                               const float* v) {
+__device__ __forceinline__ void epi_dgroup_next(const LayerArgs& a, const EpiLite& e, int n, int R0, int r, int c0,
+                                                uint32_t tcol) {
     using F = OpFmtT<FMT>;
     constexpr int ESZ = F::ESZ;
-    constexpr int CH = 16 / ESZ;                     // elements per 16-byte vector
-    if (r >= n) return;
+    constexpr int NPL = F::NPL;
+    constexpr int WPH = 8 * ESZ / 4;                 // 32-bit words per plane per 8-column half
     const int P = a.P;
-    const size_t so = state_off(P, r, c0);
-    float* const Zg = e.Z + so;
-    float* const Ag = Zg + a.plane_elems;
-    float z[8], zn[8];
-    load_state8(Zg, z);
-    load_state8(Ag, zn);
+    uint32_t wd[NPL][2 * WPH];                       // packed operand words of both halves
 #pragma unroll
-    for (int u = 0; u < 8; ++u) zn[u] = fmaf(e.d, z[u], zn[u]);
-    store_state8(Ag, zn);
+    for (int hh = 0; hh < 2; ++hh) {
+        const int cg = c0 + 8 * hh;
+        if (!(cg < n && cg + kGrp - 1 >= R0)) continue;          // warp-uniform
+        float v[8];
+        tmem_ld8(tcol + 8 * hh, reinterpret_cast<uint32_t*>(v));
+        tmem_wait_ld();
+        if (r >= n) continue;
+        const size_t so = state_off(P, r, cg);
+        float* const Zg = e.Z + so;
+        float* const Ag = Zg + a.plane_elems;
+        float z[8], zn[8];
+        load_state8(Zg, z);
+        load_state8(Ag, zn);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) zn[u] = fmaf(e.mul, v[u], e.bp * z[u]);
-    store_state8(Zg, zn);
-    const bool full = r <= c0 && c0 + kGrp - 1 < n;
+        for (int u = 0; u < 8; ++u) zn[u] = fmaf(e.d, z[u], zn[u]);
+        store_state8(Ag, zn);
 #pragma unroll
-    for (int p = 0; p < F::NPL; ++p) {
-        uint8_t* const plane = e.op + p * a.plane_elems * ESZ;
-        uint32_t w[8];
+        for (int u = 0; u < 8; ++u) zn[u] = fmaf(e.mul, v[u], e.bp * z[u]);
+        store_state8(Zg, zn);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            uint32_t o[F::NPL];
+            uint32_t o[NPL];
             F::split(zn[u] * e.os, o);
-            w[u] = o[p];
-        }
-        uint8_t* const dst = plane + ((size_t)r * P + c0) * ESZ;
-        if (full) {
 #pragma unroll
-            for (int h = 0; h < 8 / CH; ++h) {
-                uint4 q4;
-                if constexpr (ESZ == 2)
-                    q4 = make_uint4(w[0] | (w[1] << 16), w[2] | (w[3] << 16), w[4] | (w[5] << 16), w[6] | (w[7] << 16));
-                else
-                    q4 = make_uint4(w[4 * h], w[4 * h + 1], w[4 * h + 2], w[4 * h + 3]);
-                reinterpret_cast<uint4*>(dst)[h] = q4;
+            for (int p = 0; p < NPL; ++p) {
+                if constexpr (ESZ == 2) {
+                    if (u & 1) wd[p][hh * WPH + u / 2] |= o[p] << 16;
+                    else wd[p][hh * WPH + u / 2] = o[p];
+                } else {
+                    wd[p][hh * WPH + u] = o[p];
+                }
+                // mirror (c, r), r < c: one contiguous run of row c per column
+                const int c = cg + u;
+                if (r < c && c < n)
+                    store1<ESZ>(e.op + (size_t)p * a.plane_elems * ESZ + ((size_t)c * P + r) * ESZ, o[p]);
+            }
+        }
+    }
+    if (r >= n) return;
+    const bool full = r <= c0 && c0 + 15 < n;
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+        uint8_t* const dst = e.op + (size_t)p * a.plane_elems * ESZ + ((size_t)r * P + c0) * ESZ;
+        if (full) {
+            if constexpr (ESZ == 2) {
+                st_global_v8(dst, wd[p]);
+            } else {
+                st_global_v8(dst, wd[p]);
+                st_global_v8(dst + 32, wd[p] + 8);
             }
         } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (c0 + u < n && r <= c0 + u) store1<ESZ>(dst + u * ESZ, w[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int c = c0 + u;
-            if (r < c && c < n) store1<ESZ>(plane + ((size_t)c * P + r) * ESZ, w[u]);
+            for (int u = 0; u < 16; ++u) {
+                const int c = c0 + u;
+                if (c < n && r <= c) {
+                    const uint32_t val = ESZ == 2 ? ((wd[p][u / 2] >> (16 * (u & 1))) & 0xffffu) : wd[p][u];
+                    store1<ESZ>(dst + u * ESZ, val);
+                }
+            }
         }
     }
 }
@@ -457,13 +484,27 @@ __device__ __forceinline__ void epi_last(const LayerArgs& a, const EpiCtx& e, in
     }
 }
 
-// Pull the warp's 32 x COLS state region of Z and A into L2 ahead of the
-// final epilogue (COLS / 8 consecutive 1 KB blocks in each, blocked layout).
-template <int COLS>
-__device__ __forceinline__ void prefetch_state(const LayerArgs& a, const Tile& tl, int R0, int C0) {
-    const size_t off = (size_t)tl.inst * a.P * a.P + state_off(a.P, R0, C0);
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.Z[tl.chain] + off), "r"(COLS * 128) : "memory");
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.A[tl.chain] + off), "r"(COLS * 128) : "memory");
+// L2 prefetch of the Z and A state that the CTA's epilogue warps read at the
+// end of tile tl: rows I*TILE + row0 .. + 127, columns from the diagonal (or the
+// tile's first column) to the order n; each 32-row block row of the blocked
+// layout is one contiguous run.  Issued by the TMA producer a few K-slices
+// before the tile ends.
+template <int TILE>
+__device__ __forceinline__ void prefetch_tile_state(const LayerArgs& a, const Tile& tl, int row0, int n) {
+    const size_t slab = (size_t)tl.inst * a.P * a.P;
+    const int cend = min(n, tl.J * TILE + TILE);
+#pragma unroll 1
+    for (int rb = 0; rb < kCtaRows; rb += 32) {
+        const int R = tl.I * TILE + row0 + rb;
+        if (R >= n) break;
+        const int cs = max(tl.J * TILE, R) & ~7;
+        if (cs >= cend) continue;
+        const uint32_t bytes = (uint32_t)((cend - cs + 7) / 8) * 1024u;
+        const size_t off = slab + state_off(a.P, R, cs);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.Z[tl.chain] + off), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.Z[tl.chain] + a.plane_elems + off), "r"(bytes)
+                     : "memory");
+    }
 }
 
 // ----------------------------------------------------------------------------------
@@ -550,6 +591,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
+                    if (kb == max(0, nk - 3)) prefetch_tile_state<TILE>(a, tl, (int)rank * kCtaRows, n);
                     uint8_t* sbase = smem + stage * STAGE_BYTES;
                     if constexpr (PAIR) {
                         const uint32_t fb = map_to(smem_u32(&full_bar[stage]), 0);
@@ -652,18 +694,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t aphase = 0;
         bool ok = true;
         for (int t = unit; t < a.ntiles && ok; t += nunits) {
-            const Tile tl = a.tiles[t];
-            int k;
-            if (!tile_active(a, tl, k)) continue;
-            // only the order n is needed while the chunks drain; the rest of the
-            // epilogue context is formed afterwards (keeps the drain loop within
-            // the register budget)
-            const int n = a.inst[tl.inst].n;
-            const int nk = (n + BKE - 1) / BKE;
-            const int R0 = tl.I * TILE + (int)rank * kCtaRows + q * 32;   // first row of this warp
-            const int r = R0 + lane;
-            const int C0 = tl.J * TILE + cq * EPI_COLS;                   // first column of this warp
-            const bool warp_live = C0 < n && C0 + EPI_COLS - 1 >= R0 && R0 < n;
+            // Only the chunk count and the liveness of the warp's block are
+            // carried through the drain loop; the tile's descriptor and the
+            // rest of the context are fetched again for the final epilogue
+            // (keeps the drain loop of a pair tile, with its 64 accumulator
+            // registers, free of spills).
+            int nch;
+            bool warp_live;
+            {
+                const Tile tl = a.tiles[t];
+                int k;
+                if (!tile_active(a, tl, k)) continue;
+                const int n = a.inst[tl.inst].n;
+                const int R0 = tl.I * TILE + (int)rank * kCtaRows + q * 32;
+                const int C0 = tl.J * TILE + cq * EPI_COLS;
+                warp_live = C0 < n && C0 + EPI_COLS - 1 >= R0 && R0 < n;
+                nch = ((n + BKE - 1) / BKE + ck - 1) / ck;
+            }
             float acc[EPI_COLS];
 #pragma unroll
             for (int i = 0; i < EPI_COLS; ++i) acc[i] = 0.f;
@@ -674,11 +721,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             // its 8-column groups from TMEM, so the 64 accumulator registers of
             // a pair tile are free for the memory work.  The MMAs of the next
             // tile meanwhile fill the other buffer.
-            const int nch = (nk + ck - 1) / ck;
-            const int jpre = max(0, nch - 2);       // prefetch the state one chunk ahead of the end
             const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cq * EPI_COLS);
             for (int j = 0; j < nch; ++j) {
-                if (j == jpre && warp_live && lane == 0) prefetch_state<EPI_COLS>(a, tl, R0, C0);
                 if (!wait_bar(&tfull_bar[buf], aphase, &abort_flag, a.status)) {
                     ok = false;
                     break;
@@ -716,6 +760,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok) break;
             const uint32_t tfin = tbase + (uint32_t)(buf * TILE);   // the held buffer
+            const Tile tl = a.tiles[t];
+            int k;
+            tile_active(a, tl, k);
+            const int n = a.inst[tl.inst].n;
+            const int R0 = tl.I * TILE + (int)rank * kCtaRows + q * 32;   // first row of this warp
+            const int r = R0 + lane;
+            const int C0 = tl.J * TILE + cq * EPI_COLS;                   // first column of this warp
             double tr = 0.0, sq = 0.0;
             if (warp_live) {
                 if constexpr (OUTFMT == kLastLayer) {
@@ -739,12 +790,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int g_lo = R0 > C0 ? min(EPI_COLS / kGrp, (R0 - C0) / kGrp) : 0;
                     const int g_hi = min(EPI_COLS / kGrp, (n - C0 + kGrp - 1) / kGrp);
 #pragma unroll 1
-                    for (int g = g_lo; g < g_hi; ++g) {
-                        float v[8];
-                        tmem_ld8(tfin + 8 * g, reinterpret_cast<uint32_t*>(v));
-                        tmem_wait_ld();
-                        epi_group_next<OUTFMT>(a, e, n, r, C0 + kGrp * g, v);
-                    }
+                    for (int g = g_lo & ~1; g < g_hi; g += 2)
+                        epi_dgroup_next<OUTFMT>(a, e, n, R0, r, C0 + kGrp * g, tfin + 8 * g);
                 }
             }
             // release the held accumulator buffer

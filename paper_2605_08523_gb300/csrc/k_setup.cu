@@ -331,9 +331,13 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
         sc0 = M.scale0;
         sc0S = M.scale0S;
     }
-    for (int r = blockIdx.x; r < P; r += gridDim.x) {
+    // The layers of this instance read rows and columns below n rounded up to
+    // the largest tile (256), never the rest of the P x P slab: only that
+    // square is initialised (padding zeroed).
+    const int R = min(P, (n + 255) & ~255);
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
         const double* Hr = a.H + in.offset + (size_t)r * n;
-        for (int c = threadIdx.x; c < P; c += blockDim.x) {
+        for (int c = threadIdx.x; c < R; c += blockDim.x) {
             const size_t e = base + (size_t)r * P + c;
             const size_t es = base + state_off(P, r, c);
             const bool inside = r < n && c < n;
