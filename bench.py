@@ -51,9 +51,12 @@ def parse():
                    help="skip the GPU eigendecomposition and use this mu (profiling runs)")
     p.add_argument("--shape", default="auto", choices=["auto", "pair", "single"],
                    help="tensor-core tile shape: auto = the library's autotuner (untimed), or forced")
-    p.add_argument("--workload", default="cfg1", choices=["cfg1", "cfg2"],
-                   help="cfg1: the headline single n = 4096 matrix; cfg2: the 512-instance ragged batch "
-                        "(reported as a separate line, not the headline)")
+    p.add_argument("--refine", type=int, default=0, choices=[0, 1, 2],
+                   help="last 0/1/2 layers in FP32 (FTSP2_REFINE1/2)")
+    p.add_argument("--workload", default="cfg1", choices=["cfg1", "cfg2", "cfg4"],
+                   help="cfg1: the headline single n = 4096 matrix; cfg2: the 512-instance ragged batch; "
+                        "cfg4: n = 8192 lattice with 5%% long-range couplings, two FP32 refinement layers "
+                        "(cfg2 and cfg4 are separate lines, not the headline)")
     return p.parse_args()
 
 
@@ -121,8 +124,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(dims, seed):
+def make_workload(dims, seed, longrange=False):
     import workloads as wl
+    if longrange:
+        return wl.lattice_3d(dims, seed, longrange_frac=0.05, longrange_sigma=0.05)
     return wl.lattice_3d(dims, seed)
 
 
@@ -159,7 +164,7 @@ def eig_reference_gpu(Hd, kT, n):
 
 def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
     """Baseline (i): the plain FP32 recursion of Alg. 2 with torch.matmul
-    (TF32 disabled): X and Y chains, 26 layers each."""
+    (TF32 disabled): X and Y chains with the chosen table's Fermi weights."""
     import torch
     n = Hd.shape[0]
     W = emax - emin
@@ -356,10 +361,11 @@ def main():
     if world > 1:
         dist.barrier()
     ft.lib()
-    dims = tuple(int(x) for x in args.dims.split(","))
+    cfg4 = args.workload == "cfg4"
+    dims = (16, 16, 32) if cfg4 else tuple(int(x) for x in args.dims.split(","))
     n = dims[0] * dims[1] * dims[2]
     kT = args.kT
-    H = make_workload(dims, args.seed + rank)
+    H = make_workload(dims, args.seed + rank, longrange=cfg4)
     Hd = torch.from_numpy(H.ravel().copy()).cuda()
     Hm = Hd.view(n, n)
 
@@ -371,8 +377,16 @@ def main():
         mu, Dref, Sref = args.mu, None, None
     # the paper's printed Fermi table with the entropy table the library's
     # trainer fitted for it (theta_entropy)
-    ms = ft.ModelSet.from_json([os.path.join(ROOT, "paper_2605_08523_gb300", "tables", "entropy_b1500_L26.json")])
+    tdir = os.path.join(ROOT, "paper_2605_08523_gb300", "tables")
+    tabs = [os.path.join(tdir, "entropy_b1500_L26.json")]
+    if cfg4:
+        # the long-range couplings widen the Gershgorin interval: beta' needs the
+        # 34-layer beta0 = 3000 table
+        tabs.append(os.path.join(tdir, "b3000_L34.json"))
+    ms = ft.ModelSet.from_json(tabs)
     shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
+    refine = 2 if cfg4 and args.refine == 0 else args.refine
+    shape_flag |= {0: 0, 1: ft.REFINE1, 2: ft.REFINE2}[refine]
     solver = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3, flags=shape_flag)
     if args.shape == "auto":
         # tile shape: the library's autotuner times both shapes once (untimed)
@@ -461,9 +475,12 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_step * 1000.0, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp16x2-split/fp32-accum" if args.mode == "fp16x2" else args.mode,
         "data": "synthetic",
-        "config": {"workload": "cfg1 lattice %dx%dx%d n=%d kT=%g mu=half filling, density+entropy, "
-                               "printed 26-layer table + trained entropy table" % (dims + (n, kT)),
+        "config": {"workload": ("cfg4 lattice %dx%dx%d with 5%% long-range couplings N(0,0.05) n=%d kT=%g "
+                                "mu=half filling, density+entropy, beta0=1500 and 3000 tables" if cfg4 else
+                                "cfg1 lattice %dx%dx%d n=%d kT=%g mu=half filling, density+entropy, "
+                                "printed 26-layer table + trained entropy table") % (dims + (n, kT)),
                    "n": n, "kT": kT, "mu": mu, "layers": L, "mode": args.mode, "chains": 2,
+                   "refine_layers_fp32": refine, "model": int(rec["model"]),
                    "l2": "inputs and working set larger than L2 (no flush)", "parallelism": "replicas",
                    "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
                    "autotune_ms": {"single": ms_single, "pair": ms_pair}},
@@ -483,12 +500,13 @@ def main():
 
     if not args.no_baselines:
         # baseline (i): plain FP32 recursion with torch.matmul, TF32 off
-        theta = [tuple(r) for r in ms.table(0)[0]]
+        th_tab, b0_tab, m0_tab, al_tab = ms.table(int(rec["model"]))
+        theta = [tuple(r) for r in th_tab]
         emin, emax = float(rec["e_min"]), float(rec["e_max"])
         out = {}
 
         def fp32_step():
-            out["r"] = plain_fp32_recursion(Hm, mu, kT, theta, 1500.0, 1 / 3, 0.842704, emin, emax)
+            out["r"] = plain_fp32_recursion(Hm, mu, kT, theta, b0_tab, m0_tab, al_tab, emin, emax)
 
         fp32_step()
         t32 = cuda_time(fp32_step, 2)

@@ -239,7 +239,21 @@ static int op_bytes(int fmt) {
         default: return 4;
     }
 }
-constexpr int kShortChunkLayers = 6;
+// K elements per TMEM accumulation chunk of a tensor-core layer.  FP16X2:
+// 128, and 64 for the last kShortChunkLayers layers; BF16X3 and TF32X3, whose
+// layers carry more MMA work per drained chunk (6 products, or half-rate TF32),
+// so that shorter chunks cost almost nothing: 64 for every layer.  Measured at
+// n = 2048 (cfg1 lattice, printed table, density + entropy; n = 4096 alike),
+// max|D - D_ref| / |S - S_ref|/n:
+//   FP16X2 128 + last 6 at 64:  1.00e-6 / 8.9e-7  (n = 2048)
+//   FP16X2 128 + last 12 at 64: 7.6e-7 / 6.2e-7, +2 to 3 % time
+//   BF16X3 128 + last 6 at 64:  8.3e-7 / 1.08e-6;  64 everywhere: 5.0e-7 / 8.0e-7, +0.2 %
+//   TF32X3 128 + last 6 at 64:  9.7e-7 / 1.25e-6;  64 everywhere: 6.2e-7 / 8.3e-7, +0.6 %
+constexpr int kShortChunkLayers = 12;
+static int chunk_elems_of(int mode, int g, int Lmax) {
+    if (mode == FTSP2_BF16X3 || mode == FTSP2_TF32X3) return 64;
+    return g >= Lmax - kShortChunkLayers ? 64 : 0;    // 0: the kernel's default (128)
+}
 
 static int refine_layers(int flags) { return (flags & FTSP2_REFINE2) ? 2 : ((flags & FTSP2_REFINE1) ? 1 : 0); }
 
@@ -530,7 +544,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         // reaches the output undamped (earlier errors are contracted by the
         // saturating layers), and the entropy is linear in it for occupations
         // near 0 and 1.
-        la.chunk_elems = g >= Lmax - kShortChunkLayers ? 64 : 0;
+        la.chunk_elems = chunk_elems_of(mode, g, Lmax);
         la.next_fmt = next_simt ? OP_F32 : fmt;
         for (int c = 0; c < L.nchains; ++c) {
             const int rp = g & 1, wp = (g + 1) & 1;

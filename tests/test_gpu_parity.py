@@ -5,7 +5,8 @@ Every case compares the library's D (FP32) and S with
     (isolates the implementation's rounding), and
   * D_ref / S_ref: the Fermi function and entropy by eigendecomposition
     (total error = model fit error + rounding).
-Tolerances are per precision mode; their derivation is in the design doc.
+The tolerance is the 1e-6 bound of the FP32-class paths, for every mode; the
+few cases with a larger bound say why next to it.
 """
 import math
 
@@ -21,11 +22,13 @@ torch = pytest.importorskip("torch")
 
 PRINTED = rescale.Table(tables.PRINTED_B1500, 1500.0, 1.0 / 3.0, name="printed")
 MODES = ["fp32", "tf32x3", "bf16x3", "fp16x2"]
-# max |D - D_rec| allowed for the printed beta0 = 1500 table: FP32-class rounding
-# of 128-element K chunks amplified by the slope beta0/4;
-# measured 0.8-1.03e-6 for the split modes at n <= 1024
-TOL_D = {"fp32": 2.5e-6, "tf32x3": 1.5e-6, "bf16x3": 1.5e-6, "fp16x2": 1.5e-6}
-TOL_S = 2e-6          # |S - S_rec| / n
+# max |D - D_rec| and |S - S_rec| / n allowed for the printed beta0 = 1500
+# table: 1e-6.  A layer's rounding is amplified by up to the slope beta0 / 4 of
+# the table; the accumulation-chunk setting of each mode (64-element chunks for
+# the last 12 FP16X2 layers, for every BF16X3 and TF32X3 layer) keeps the split
+# modes inside the bound (measured 5e-7 to 9e-7 at n = 1024 .. 4096).
+TOL_D = {"fp32": 1e-6, "tf32x3": 1e-6, "bf16x3": 1e-6, "fp16x2": 1e-6}
+TOL_S = 1e-6          # |S - S_rec| / n
 
 
 @pytest.fixture(scope="module")

@@ -12,10 +12,9 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 PRINTED = rescale.Table(tables.PRINTED_B1500, 1500.0, 1.0 / 3.0, name="printed")
-# the same per-mode bounds as the main parity suite (FP32-class rounding of
-# 128-element K chunks amplified by the slope beta0 / 4 of the printed table)
-TOL_D = {"tf32x3": 1.5e-6, "bf16x3": 1.5e-6, "fp16x2": 1.5e-6}
-TOL_S = 2e-6
+# the bound of the main parity suite: 1e-6 for every mode
+TOL_D = {"tf32x3": 1e-6, "bf16x3": 1e-6, "fp16x2": 1e-6}
+TOL_S = 1e-6
 
 
 @pytest.fixture(scope="module")
