@@ -29,6 +29,9 @@ Modules and the passages they follow (arXiv 2605.08523):
 * ``sp2``      -- SP2 with known mu (Eq. sp2-mu), its MLSP2 embedding
                   (Appendix C), the layer-count estimate (Eq. layer count) and
                   the golden-ratio fixed point (Sec. IV B).
+* ``newton``   -- the chemical potential for a prescribed electron count by
+                  Newton-Raphson (Sec. III A 4, Eqs. g, dg, delta_mu; sign of
+                  Eq. drho taken from the definition of D).
 * ``train``    -- training: eigenvalue sampling (Sec. II C 1), residuals,
                   reverse-mode Jacobian, Levenberg-Marquardt with optional
                   geodesic acceleration (Sec. II C 2).
