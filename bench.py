@@ -162,6 +162,53 @@ def eig_reference_gpu(Hd, kT, n):
     return mu, D, S, eps, V
 
 
+def method_exact_gpu(eps, V, rec, table, mu):
+    """The method's exact result in FP64 (isolates the library's rounding): the
+    scalar recursion of the chosen table on the eigenvalues, with the library's
+    own rescale decisions (rec: scale, flip), D_rec = V P(x0) V^T and
+    S_rec = sum 4 ln2 F (1 - F) over the entropy chain (Eq. entropy expansion)."""
+    import torch
+    mu0, alpha = table["mu0"], table["alpha"]
+    # X0 = mu0 I + scale (mu I - H): on the eigenvalues x0 = mu0 + scale (mu - eps)
+    x = mu0 + float(rec["scale"]) * (mu - eps)
+    def chain(x0, th):
+        A = torch.zeros_like(x0)
+        xx = x0.clone()
+        for a, b, c, d in th:
+            A = A + d * xx
+            xx = a * xx * xx + b * xx + c
+        return A + xx
+    P = chain(x, table["theta"])
+    if int(rec["flip"]):
+        P = 1.0 - P
+    Drec = (V * P[None, :]) @ V.T
+    F = chain(alpha * (x - mu0) + mu0, table.get("theta_entropy") or table["theta"])
+    Srec = float((4.0 * LN2 * F * (1.0 - F)).sum())
+    return Drec, Srec
+
+
+def probe_dtype_peaks():
+    """Dense-GEMM rates of the dtypes the split modes use (torch.matmul, 8192^3,
+    best of 3 after a warm-up, TF32 through allow_tf32), for the hardware
+    fractions of FP16X2 and TF32X3: their peak is the measured sustained BF16
+    figure times the measured ratio to BF16."""
+    import torch
+    n = 8192
+    out = {}
+    old = torch.backends.cuda.matmul.allow_tf32
+    for name, dt in (("bf16", torch.bfloat16), ("fp16", torch.float16), ("tf32", torch.float32)):
+        torch.backends.cuda.matmul.allow_tf32 = name == "tf32"
+        a = torch.randn(n, n, device="cuda").to(dt)
+        b = torch.randn(n, n, device="cuda").to(dt)
+        torch.matmul(a, b)
+        t = min(cuda_time(lambda: torch.matmul(a, b), 1) for _ in range(3))
+        out[name] = 2.0 * n ** 3 / t / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = old
+    torch.cuda.empty_cache()
+    return out
+
+
 def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
     """Baseline (i): the plain FP32 recursion of Alg. 2 with torch.matmul
     (TF32 disabled): X and Y chains with the chosen table's Fermi weights."""
@@ -374,7 +421,7 @@ def main():
     if args.mu is None:
         mu, Dref, Sref, eps, V = eig_reference_gpu(Hm, kT, n)
     else:
-        mu, Dref, Sref = args.mu, None, None
+        mu, Dref, Sref, eps, V = args.mu, None, None, None, None
     # the paper's printed Fermi table with the entropy table the library's
     # trainer fitted for it (theta_entropy)
     tdir = os.path.join(ROOT, "paper_2605_08523_gb300", "tables")
@@ -428,6 +475,21 @@ def main():
     err_D = float((D - Dref).abs().max()) if Dref is not None else None
     err_S = abs(S - Sref) / n if Sref is not None else None
     trD = float(solver.trace[0, 0])
+    err_Drec = err_Srec = None
+    if Dref is not None:
+        with open(tabs[int(rec["model"])]) as fh:
+            tab_json = json.load(fh)
+        Drec, Srec = method_exact_gpu(eps, V, rec, tab_json, mu)
+        err_Drec = float((D - Drec).abs().max())
+        err_Srec = abs(S - Srec) / n
+        del Drec
+
+    # density only (no entropy chain): solves/s of the same call with want = 1
+    solver_d = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=1, flags=shape_flag)
+    solver_d.run(Hd)
+    torch.cuda.synchronize()
+    t_density = cuda_time(lambda: solver_d.run(Hd), max(3, args.steps // 4))
+    del solver_d
 
     # ---- end to end through the public API with host buffers ----
     Hh = torch.from_numpy(H.ravel().copy()).pin_memory()
@@ -464,7 +526,16 @@ def main():
     nprod = {"fp16x2": 3, "tf32x3": 3, "bf16x3": 6}.get(args.mode, 1)
     hw_per_launch = 2 * tiles * T * T * n * 2 * nprod
     hw_achieved = hw_per_launch / layer_avg / 1e12 if layer_avg > 0 else None
-    hw_peak = peak if args.mode in ("fp16x2", "bf16x3") else peak / 2.0
+    # the split modes' own dtypes: fp16 (FP16X2), bf16 (BF16X3), tf32 (TF32X3);
+    # their peak is the measured sustained bf16 figure x the dtype's measured
+    # (else nominal) rate ratio to bf16
+    dt_of_mode = {"fp16x2": "fp16", "bf16x3": "bf16", "tf32x3": "tf32"}.get(args.mode)
+    dtype_rates = probe_dtype_peaks() if (not args.no_baselines and dt_of_mode) else None
+    if dtype_rates:
+        ratio, ratio_kind = dtype_rates[dt_of_mode] / dtype_rates["bf16"], "measured (torch.matmul 8192^3 probe)"
+    else:
+        ratio, ratio_kind = {"fp16": 1.0, "bf16": 1.0, "tf32": 1.1 / 2.25}.get(dt_of_mode, 1.0), "nominal"
+    hw_peak = peak * ratio
     # DRAM bytes per launch from one ncu capture (profiles/layer_tc_fp16x2_n4096.md),
     # valid only while the kernel sources are the ones that were profiled
     ksha = kernel_sha()
@@ -485,14 +556,18 @@ def main():
                    "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
                    "autotune_ms": {"single": ms_single, "pair": ms_pair}},
         "tflops_alg": alg_flops / t_step / 1e12 * world,
-        "accuracy": {"max_abs_D_minus_Dref": err_D, "abs_S_minus_Sref_per_n": err_S, "trD": trD,
+        "density_only": {"value": world / t_density, "unit": "solves/s", "ms_per_step": t_density * 1e3},
+        "accuracy": {"max_abs_D_minus_Dref": err_D, "abs_S_minus_Sref_per_n": err_S,
+                     "max_abs_D_minus_Drec": err_Drec, "abs_S_minus_Srec_per_n": err_Srec, "trD": trD,
                      "trD_ref": n / 2, "S": S, "S_ref": Sref},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": "layer_tc_kernel<%s>" % args.mode.upper(), "kernel_sha": ksha,
                      "per_launch_alg_flops": alg_per_launch, "avg_launch_ms": layer_avg * 1000,
                      "peak_kind": "bf16_tflops_sustained (%s)" % pk_kind,
-                     "hw_tensor_tflops": hw_achieved, "hw_frac": (hw_achieved / hw_peak) if hw_achieved else None},
+                     "hw_tensor_tflops": hw_achieved, "hw_frac": (hw_achieved / hw_peak) if hw_achieved else None,
+                     "hw_peak": hw_peak, "hw_peak_dtype": dt_of_mode, "hw_peak_ratio_to_bf16": ratio,
+                     "hw_peak_ratio_kind": ratio_kind, "dtype_probe_tflops": dtype_rates},
         "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk.summary(),

@@ -243,6 +243,37 @@ ftsp2_status ftsp2_density_noalloc(const double* dH, const ftsp2_instance* inst,
                                    float* dD, double* dTrace, ftsp2_rescale_rec* dRec,
                                    void* stream);
 
+/* ---- chemical potential for a prescribed electron count -------------------------- */
+
+/* Newton-Raphson on g(mu) = N_occ - Tr D(mu) (Sec. III A 4, Eqs. g, dg,
+ * delta_mu), entirely on the device.  Differentiating the Fermi operator
+ * (Eq. FD_Func) gives dD/dmu = +beta D (I - D) (the printed Eq. drho has the
+ * opposite sign), so one update is
+ *     Delta mu = (N_occ - Tr D) / (beta (Tr D - ||D||_F^2)),
+ * from the traces the density call already returns (Eq. tr(D^2)), limited to
+ * |Delta mu| <= (e_max - e_min) / 16.  An instance takes no step once
+ * |N_occ - Tr D| <= tol, when Tr D - ||D||_F^2 <= 0, or while it has no valid
+ * model.
+ *   - The starting mu is dInst[b].mu; every update is written there (device
+ *     memory, the caller's table; inst on the host is not changed and is used
+ *     for planning only).
+ *   - The call runs `iterations` + 1 evaluations of the hot path (bounds,
+ *     rescale and model choice are redone for every mu) and `iterations`
+ *     updates in between; dD, dTrace, dS (nullable: then no entropy chain) and
+ *     dRec hold the result at the final mu.  dSteps[b] receives the number of
+ *     updates instance b took.  dNocc: nb doubles (device), the electron counts
+ *     per spin channel (0 <= N_occ <= n).
+ *   - Workspace as for ftsp2_density_entropy (want = 3 when dS is given, else 1).
+ *   - Launches only; no host synchronisation unless FTSP2_SYNC (then the worst
+ *     final per-instance status is returned).  Capturable into a CUDA graph.
+ *   - Errors: FTSP2_E_ARG for iterations outside [0, 64], tol < 0 or NULL
+ *     dNocc / dTrace / dSteps; otherwise those of ftsp2_density_entropy. */
+ftsp2_status ftsp2_density_mu(const double* dH, const ftsp2_instance* inst, ftsp2_instance* dInst, int nb,
+                              const double* dNocc, const ftsp2_model_set* set, ftsp2_mode mode, int flags,
+                              int iterations, double tol, float* dD, double* dTrace, double* dS,
+                              ftsp2_rescale_rec* dRec, int32_t* dSteps, void* ws, size_t ws_bytes,
+                              void* stream);
+
 /* ---- tile-shape autotuner ------------------------------------------------------ */
 
 /* Measures the batch with both tensor-core tile shapes and records the faster.

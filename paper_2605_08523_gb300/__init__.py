@@ -225,6 +225,35 @@ class Solver:
             raise Ftsp2Error(st, "ftsp2 hot path")
         return st
 
+    def run_mu(self, H, n_occ, iterations=3, tol=1e-6, stream=None, sync=False):
+        """Chemical potentials for prescribed electron counts (ftsp2_density_mu):
+        ``iterations`` Newton updates of mu from the current device values,
+        then D (and S when the solver has the entropy chain) at the final mu.
+        n_occ: per-instance electron counts.  Returns the per-instance number of
+        updates taken (int32 tensor); the final mu are in ``mus()``."""
+        torch = _torch()
+        if self.want == 2:
+            raise ValueError("run_mu needs the density chain (want = 1 or 3)")
+        if H.dtype != torch.float64 or not H.is_cuda or H.numel() < self.total:
+            raise ValueError("H must be a CUDA float64 tensor with sum(n^2) elements")
+        nocc = torch.as_tensor(n_occ, dtype=torch.float64, device=self.device).reshape(self.nb).contiguous()
+        steps = torch.zeros(self.nb, dtype=torch.int32, device=self.device)
+        flags = self.flags | (SYNC if sync else 0)
+        S = _ptr(self.S) if self.want == 3 else None
+        st = lib().ftsp2_density_mu(_ptr(H), self.host_inst, _ptr(self.d_inst), self.nb, _ptr(nocc), self.ms.handle,
+                                    self.mode, flags, int(iterations), float(tol), _ptr(self.D), _ptr(self.trace), S,
+                                    _ptr(self.rec), _ptr(steps), C.c_void_p(self.ws_ptr), self.ws_bytes,
+                                    _stream(stream))
+        if st in (_lib.E_ARG, _lib.E_CUDA, _lib.E_WORKSPACE, _lib.E_NOMODEL, _lib.E_UNSUPPORTED):
+            raise Ftsp2Error(st, "ftsp2_density_mu")
+        self._nocc_keepalive = nocc
+        return steps
+
+    def mus(self):
+        """The per-instance mu of the device instance table (after run_mu)."""
+        raw = self.d_inst.cpu().numpy().view(INST_DTYPE)
+        return raw["mu"].copy()
+
     def graph(self, H):
         """Record one ``run(H)`` into a CUDA graph and return it
         (``torch.cuda.CUDAGraph``; ``g.replay()`` reruns the whole hot path on

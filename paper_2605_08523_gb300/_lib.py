@@ -63,6 +63,8 @@ SIGNATURES = {
     "ftsp2_entropy": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _SZ, _VP]),
     "ftsp2_density_entropy": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "ftsp2_density_noalloc": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP]),
+    "ftsp2_density_mu": (_I, [_VP, _PINST, _VP, _I, _VP, _VP, _I, _I, _I, _D, _VP, _VP, _VP, _VP, _VP, _VP, _SZ,
+                              _VP]),
     "ftsp2_autotune": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _SZ, _I,
                             C.POINTER(_I), C.POINTER(C.c_float), _VP]),
     "ftsp2_tile_shape": (_I, [_PINST, _I, _I, _I, _I, C.POINTER(_I), C.POINTER(_I)]),

@@ -891,6 +891,37 @@ ftsp2_status ftsp2_density_entropy(const double* dH, const ftsp2_instance* inst,
     return run(dH, inst, dInst, nb, set, mode, flags, 3, dD, dTrace, dS, dRec, ws, ws_bytes, stream);
 }
 
+ftsp2_status ftsp2_density_mu(const double* dH, const ftsp2_instance* inst, ftsp2_instance* dInst, int nb,
+                              const double* dNocc, const ftsp2_model_set* set, ftsp2_mode mode, int flags,
+                              int iterations, double tol, float* dD, double* dTrace, double* dS,
+                              ftsp2_rescale_rec* dRec, int32_t* dSteps, void* ws, size_t ws_bytes, void* stream) {
+    if (iterations < 0 || iterations > 64 || !(tol >= 0.0) || nb < 1 || !inst) return FTSP2_E_ARG;
+    if (!dNocc || !dTrace || !dSteps || !dInst) return FTSP2_E_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(dSteps, 0, sizeof(int32_t) * (size_t)nb, s) != cudaSuccess) return FTSP2_E_CUDA;
+    const int quiet = flags & ~FTSP2_SYNC;
+    for (int it = 0;; ++it) {
+        const bool last = it == iterations;
+        // evaluations before the last need only the density and its traces
+        const ftsp2_status st = last && dS
+                                    ? run(dH, inst, dInst, nb, set, mode, flags, 3, dD, dTrace, dS, dRec, ws, ws_bytes,
+                                          stream)
+                                    : run(dH, inst, dInst, nb, set, mode, last ? flags : quiet, 1, dD, dTrace,
+                                          nullptr, dRec, ws, ws_bytes, stream);
+        if (last || st != FTSP2_OK) return st;
+        MuArgs ma;
+        ma.inst = dInst;
+        ma.rec = dRec;
+        ma.trace = dTrace;
+        ma.nocc = dNocc;
+        ma.steps = dSteps;
+        ma.tol = tol;
+        ma.nb = nb;
+        launch_mu_update(ma, s);
+        if (cudaGetLastError() != cudaSuccess) return FTSP2_E_CUDA;
+    }
+}
+
 static int want_of(const float* dD, const double* dTrace, const double* dS) {
     if (!dS) return 1;
     if (!dD && !dTrace) return 2;

@@ -128,7 +128,7 @@ struct FinalArgs {
     ftsp2_rescale_rec* rec;
     const DevModel* models;
     const InstWork* iw;
-    const double* partials;   // [tile][4 quarters][2]
+    const double* partials;   // [tile][kPartialSlots][2]
     int table;                // tile table used by the last layer (0 main, 1 128x128)
     int nb, nchains;
     int chain_kind[kMaxChains];
@@ -137,6 +137,18 @@ struct FinalArgs {
     const int* status;
 };
 void launch_finalize(const FinalArgs& a, cudaStream_t s);
+
+// --- chemical potential for a prescribed electron count (f1) ---------------------
+struct MuArgs {
+    ftsp2_instance* inst;            // device instance table; mu is updated in place
+    const ftsp2_rescale_rec* rec;
+    const double* trace;             // [nb][2]: Tr D, ||D||_F^2 at the current mu
+    const double* nocc;              // [nb] prescribed electron counts
+    int32_t* steps;                  // [nb] updates applied so far
+    double tol;
+    int nb;
+};
+void launch_mu_update(const MuArgs& a, cudaStream_t s);
 
 // --- layer kernels -------------------------------------------------------------
 struct LayerArgs {

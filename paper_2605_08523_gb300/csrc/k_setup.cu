@@ -450,6 +450,37 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a) {
     }
 }
 
+// ------------------------------------------------------------------------------
+// One Newton-Raphson update of the chemical potential per instance (Sec. III A 4,
+// Eqs. g, dg, delta_mu).  dD/dmu = +beta D (I - D) follows from the definition
+// of D (the printed Eq. drho has the opposite sign), so
+//   Delta mu = (N_occ - Tr D) / (beta (Tr D - ||D||_F^2)),
+// limited to |Delta mu| <= W / 16 (W the Gershgorin width).  No step when
+// |N_occ - Tr D| <= tol, when Tr D - ||D||_F^2 <= 0, or when the instance has no
+// valid model.  One thread per instance.
+// ------------------------------------------------------------------------------
+__global__ void mu_update_kernel(MuArgs a) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= a.nb) return;
+    const ftsp2_rescale_rec rec = a.rec[b];
+    if (rec.status != FTSP2_OK || rec.model < 0) return;
+    const double trD = a.trace[2 * b], trD2 = a.trace[2 * b + 1];
+    const double g = a.nocc[b] - trD;
+    if (!(fabs(g) > a.tol)) return;
+    const double kT = a.inst[b].kT;
+    const double gp = (trD - trD2) / kT;
+    if (!(gp > 0.0)) return;
+    const double cap = (rec.e_max - rec.e_min) * (1.0 / 16.0);
+    const double d = fmin(fmax(g / gp, -cap), cap);
+    a.inst[b].mu += d;
+    a.steps[b] += 1;
+}
+
+void launch_mu_update(const MuArgs& a, cudaStream_t s) {
+    mu_update_kernel<<<(a.nb + 127) / 128, 128, 0, s>>>(a);
+    count_launch();
+}
+
 void launch_finalize(const FinalArgs& a, cudaStream_t s) {
     finalize_kernel<<<a.nb, 256, 0, s>>>(a);
     count_launch();
