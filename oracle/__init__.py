@@ -29,6 +29,8 @@ Modules and the passages they follow (arXiv 2605.08523):
 * ``sp2``      -- SP2 with known mu (Eq. sp2-mu), its MLSP2 embedding
                   (Appendix C), the layer-count estimate (Eq. layer count) and
                   the golden-ratio fixed point (Sec. IV B).
+* ``lanczos``  -- spectral bounds tightened by a few Lanczos steps (counter-
+                  based start vector, splitmix64), intersected with Gershgorin.
 * ``newton``   -- the chemical potential for a prescribed electron count by
                   Newton-Raphson (Sec. III A 4, Eqs. g, dg, delta_mu; sign of
                   Eq. drho taken from the definition of D).

@@ -109,7 +109,7 @@ class RescaleRecord:
     valid: bool
 
 
-def rescale(H: np.ndarray, mu: float, kT: float, tables, clamp: bool = False):
+def rescale(H: np.ndarray, mu: float, kT: float, tables, clamp: bool = False, lanczos: bool = False):
     """Bounds -> (H', mu', beta') -> flip -> model -> H0 (Sec. III A, Appendix A).
 
     Returns (H0, record).  With ``clamp`` the paper's behaviour outside the
@@ -117,12 +117,18 @@ def rescale(H: np.ndarray, mu: float, kT: float, tables, clamp: bool = False):
     the largest-beta0 model); otherwise the record says ``valid=False`` and H0 is
     None.  Degenerate spectrum (e_max == e_min, only H = cI): the normalisation
     divides by zero, so the equivalent form H0 = mu0 I + (beta/beta0)(mu I - H)
-    is used with no flip (reading; the two agree whenever both are defined)."""
+    is used with no flip (reading; the two agree whenever both are defined).
+    With ``lanczos`` the bounds are those of ``oracle.lanczos.bounds`` (the
+    Gershgorin interval tightened by a few Lanczos steps) instead."""
     beta = 1.0 / kT
     H = np.asarray(H, dtype=np.float64)
     n = H.shape[0]
     I = np.eye(n)
-    e_min, e_max = gershgorin(H)
+    if lanczos:
+        from . import lanczos as lz
+        e_min, e_max = lz.bounds(H)
+    else:
+        e_min, e_max = gershgorin(H)
     if e_max == e_min:
         best = -1
         for k, t in enumerate(tables):
