@@ -51,6 +51,10 @@ def parse():
                    help="skip the GPU eigendecomposition and use this mu (profiling runs)")
     p.add_argument("--shape", default="auto", choices=["auto", "pair", "single"],
                    help="tensor-core tile shape: auto = the library's autotuner (untimed), or forced")
+    p.add_argument("--bounds", default="gershgorin", choices=["gershgorin", "lanczos"],
+                   help="spectral bounds: Gershgorin (Appendix A) or tightened by Lanczos (FTSP2_LANCZOS)")
+    p.add_argument("--policy", default="beta0", choices=["beta0", "layers"],
+                   help="model choice: smallest beta0 (default) or fewest layers (FTSP2_MIN_LAYERS)")
     p.add_argument("--refine", type=int, default=0, choices=[0, 1, 2],
                    help="last 0/1/2 layers in FP32 (FTSP2_REFINE1/2)")
     p.add_argument("--workload", default="cfg1", choices=["cfg1", "cfg2", "cfg4"],
@@ -354,6 +358,10 @@ def run_cfg2(args):
     flat, _ = wl.pack_batch(Hs)
     Hd = torch.from_numpy(flat).cuda()
     shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
+    if args.bounds == "lanczos":
+        shape_flag |= ft.LANCZOS
+    if args.policy == "layers":
+        shape_flag |= ft.MIN_LAYERS
     solver = ft.Solver(ns, [b["mu"] for b in batch], [b["kT"] for b in batch], ms, mode=args.mode, want=3,
                        flags=shape_flag)
     if args.shape == "auto":
@@ -369,6 +377,16 @@ def run_cfg2(args):
     steps = max(3, args.steps // 10)
     t = cuda_time(lambda: solver.run(Hd), steps)
     alg = float(np.sum((np.array(ns, dtype=np.float64) ** 3 * 2 * layers)[valid]))
+    # accuracy on a sample of 32 instances (FP64 eigendecomposition on the GPU)
+    errD, errS = 0.0, 0.0
+    for b in range(0, len(ns), max(1, len(ns) // 32)):
+        n_b = ns[b]
+        Hb = torch.from_numpy(Hs[b]).cuda()
+        eps, V = torch.linalg.eigh(Hb)
+        tt = (eps - batch[b]["mu"]) / batch[b]["kT"]
+        Dref = (V * fermi_t(tt)[None, :]) @ V.T
+        errD = max(errD, float((solver.matrix(b).double() - Dref).abs().max()))
+        errS = max(errS, abs(float(solver.S[b]) - float(entropy_t(tt).sum())) / n_b)
     line = {"metric": "ragged-batch solves/s (instances/s, density + entropy)", "value": int(valid.sum()) / t,
             "unit": "solves/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "dtype": args.mode, "data": "synthetic",
@@ -376,9 +394,12 @@ def run_cfg2(args):
                                    "mu~U(-5,5)", "valid_instances": int(valid.sum()),
                        "sum_n3": float(np.sum(np.array(ns, dtype=np.float64) ** 3)),
                        "models_used": {int(m): int(np.sum(rec["model"] == m)) for m in np.unique(rec["model"])},
+                       "bounds": args.bounds, "policy": args.policy, "global_layers": int(rec["layers"].max()),
                        "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
                        "autotune_ms": {"single": ms_single, "pair": ms_pair}},
-            "tflops_alg": alg / t / 1e12}
+            "tflops_alg": alg / t / 1e12,
+            "accuracy_sampled": {"instances": len(range(0, len(ns), max(1, len(ns) // 32))),
+                                 "max_abs_D_minus_Dref": errD, "max_abs_S_minus_Sref_per_n": errS}}
     print(json.dumps(line), flush=True)
 
 
@@ -434,6 +455,8 @@ def main():
     shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
     refine = 2 if cfg4 and args.refine == 0 else args.refine
     shape_flag |= {0: 0, 1: ft.REFINE1, 2: ft.REFINE2}[refine]
+    if args.bounds == "lanczos":
+        shape_flag |= ft.LANCZOS
     solver = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3, flags=shape_flag)
     if args.shape == "auto":
         # tile shape: the library's autotuner times both shapes once (untimed)
@@ -551,7 +574,8 @@ def main():
                                 "cfg1 lattice %dx%dx%d n=%d kT=%g mu=half filling, density+entropy, "
                                 "printed 26-layer table + trained entropy table") % (dims + (n, kT)),
                    "n": n, "kT": kT, "mu": mu, "layers": L, "mode": args.mode, "chains": 2,
-                   "refine_layers_fp32": refine, "model": int(rec["model"]),
+                   "refine_layers_fp32": refine, "model": int(rec["model"]), "bounds": args.bounds,
+                   "e_min": float(rec["e_min"]), "e_max": float(rec["e_max"]),
                    "l2": "inputs and working set larger than L2 (no flush)", "parallelism": "replicas",
                    "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
                    "autotune_ms": {"single": ms_single, "pair": ms_pair}},

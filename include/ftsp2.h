@@ -84,6 +84,24 @@ typedef enum {
  * shape a padding model prefers; these two flags override both. */
 #define FTSP2_PAIR_TILES    0x10 /* 256 x 256 tiles on CTA pairs (cta_group::2) */
 #define FTSP2_SINGLE_TILES  0x20 /* 128 x 128 tiles on single CTAs             */
+/* Spectral bounds: by default the Gershgorin interval of Appendix A.  With this
+ * flag it is tightened by 24 Lanczos steps in FP64 (start vector from
+ * splitmix64 of the row index, no re-orthogonalisation): the extreme Ritz
+ * values of the tridiagonal, widened by their residual bounds, by 1 % of their
+ * spread and by 1e-6 of their magnitude (the products H v are formed in FP32),
+ * intersected with the Gershgorin interval.  A narrower interval
+ * lowers beta' = W beta, so a model of smaller beta0 (fewer layers, less
+ * amplified rounding) may be chosen.  Cost: 24 matrix-vector products in FP64
+ * per instance.  The interval is not a rigorous enclosure (the residual bound
+ * and the margin are safety terms, checked on the workload families of the
+ * tests); a few eigenvalues slightly outside it map just outside [0, 1], where
+ * the shipped tables stay within their fit error for excursions up to 0.02. */
+#define FTSP2_LANCZOS       0x40
+/* Model choice (workflow step 4) among the models whose region of validity
+ * contains (beta', mu'): by default the smallest beta0 (least amplified
+ * rounding), ties to fewer layers; with this flag the fewest Fermi-chain layers
+ * (the fastest), ties to the smaller beta0. */
+#define FTSP2_MIN_LAYERS    0x80
 
 /* One Hamiltonian of a (ragged) batch.  H_b starts at dH + offset and is
  * n x n row-major; D_b starts at dD + offset.  Offsets are in elements. */
@@ -166,7 +184,9 @@ ftsp2_status ftsp2_rescale_workspace_size(int nb, size_t* bytes);
 /* (a1)+(a2) only: Gershgorin bounds, normalisation, flip, validity and model
  * choice for every instance; writes dRec[nb].  dInst is a device copy of inst
  * (same contents; the kernels read it, the host plans from inst).  ws must be
- * 1024-byte aligned and hold ftsp2_rescale_workspace_size(nb) bytes. */
+ * 1024-byte aligned and hold ftsp2_rescale_workspace_size(nb) bytes, or, with
+ * FTSP2_LANCZOS, ftsp2_workspace_size(inst, nb, any mode, 1) bytes
+ * (FTSP2_E_WORKSPACE otherwise). */
 ftsp2_status ftsp2_rescale(const double* dH, const ftsp2_instance* inst,
                            const ftsp2_instance* dInst, int nb,
                            const ftsp2_model_set* set, int flags,

@@ -40,11 +40,13 @@ def density_entropy(H: np.ndarray, mu: float, kT: float, tables, clamp: bool = F
     return dict(D=D, S=S, trD=float(np.trace(D)), frobD=float(np.sum(D * D)), rec=rec)
 
 
-def method_exact(H: np.ndarray, mu: float, kT: float, tables, clamp: bool = False, lanczos: bool = False):
+def method_exact(H: np.ndarray, mu: float, kT: float, tables, clamp: bool = False, lanczos: bool = False,
+                 min_layers: bool = False):
     """D_rec = V diag(P(x0(eps))) V^T (flipped if needed) and
     S_rec = sum_i s~(x0(eps_i)), with P the FP64 scalar recursion.  ``lanczos``
-    selects the Lanczos-tightened spectral bounds (oracle.lanczos)."""
-    H0, rec = rescale.rescale(H, mu, kT, tables, clamp=clamp, lanczos=lanczos)
+    selects the Lanczos-tightened spectral bounds (oracle.lanczos),
+    ``min_layers`` the fewest-layers model policy (rescale.select_model)."""
+    H0, rec = rescale.rescale(H, mu, kT, tables, clamp=clamp, lanczos=lanczos, min_layers=min_layers)
     if H0 is None:
         return dict(D=None, S=None, rec=rec)
     t = tables[rec.model]

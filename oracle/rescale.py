@@ -84,16 +84,21 @@ class Table:
         return len(self.theta)
 
 
-def select_model(tables, mu_p: float, beta_p: float):
+def select_model(tables, mu_p: float, beta_p: float, min_layers: bool = False):
     """Workflow step 4: a model whose region of validity contains (beta', mu').
-    Reading (the paper only asks for one that contains it, and prefers the
-    minimum layer count): the valid model with the smallest beta0, ties broken
-    by fewer layers, then by position in the set.  Returns the index or -1."""
+    Reading (the paper only asks for one that contains it, and names the
+    minimum layer count as one favourable property): by default the valid
+    model with the smallest beta0 (least amplified rounding), ties broken by
+    fewer layers; with ``min_layers`` the valid model with the fewest layers,
+    ties broken by the smaller beta0.  Then by position in the set.  Returns the
+    index or -1."""
+    def key(t):
+        return (t.L, t.beta0) if min_layers else (t.beta0, t.L)
     best = -1
     for k, t in enumerate(tables):
         if not is_valid(mu_p, beta_p, t.beta0, t.mu0):
             continue
-        if best < 0 or (t.beta0, t.L) < (tables[best].beta0, tables[best].L):
+        if best < 0 or key(t) < key(tables[best]):
             best = k
     return best
 
@@ -109,7 +114,8 @@ class RescaleRecord:
     valid: bool
 
 
-def rescale(H: np.ndarray, mu: float, kT: float, tables, clamp: bool = False, lanczos: bool = False):
+def rescale(H: np.ndarray, mu: float, kT: float, tables, clamp: bool = False, lanczos: bool = False,
+            min_layers: bool = False):
     """Bounds -> (H', mu', beta') -> flip -> model -> H0 (Sec. III A, Appendix A).
 
     Returns (H0, record).  With ``clamp`` the paper's behaviour outside the
@@ -119,7 +125,8 @@ def rescale(H: np.ndarray, mu: float, kT: float, tables, clamp: bool = False, la
     divides by zero, so the equivalent form H0 = mu0 I + (beta/beta0)(mu I - H)
     is used with no flip (reading; the two agree whenever both are defined).
     With ``lanczos`` the bounds are those of ``oracle.lanczos.bounds`` (the
-    Gershgorin interval tightened by a few Lanczos steps) instead."""
+    Gershgorin interval tightened by a few Lanczos steps) instead; ``min_layers``
+    selects the model policy of ``select_model``."""
     beta = 1.0 / kT
     H = np.asarray(H, dtype=np.float64)
     n = H.shape[0]
@@ -131,9 +138,11 @@ def rescale(H: np.ndarray, mu: float, kT: float, tables, clamp: bool = False, la
         e_min, e_max = gershgorin(H)
     if e_max == e_min:
         best = -1
+        def key(t):
+            return (t.L, t.beta0) if min_layers else (t.beta0, t.L)
         for k, t in enumerate(tables):
             x = t.mu0 + (beta / t.beta0) * (mu - e_min)
-            if 0.0 <= x <= 1.0 and (best < 0 or (t.beta0, t.L) < (tables[best].beta0, tables[best].L)):
+            if 0.0 <= x <= 1.0 and (best < 0 or key(t) < key(tables[best])):
                 best = k
         rec = RescaleRecord(e_min, e_max, math.nan, 0.0, False, best, best >= 0)
         if best < 0:
@@ -147,7 +156,7 @@ def rescale(H: np.ndarray, mu: float, kT: float, tables, clamp: bool = False, la
     if flip:                                          # Eq. flip
         H_p = I - H_p
         mu_p = 1.0 - mu_p
-    k = select_model(tables, mu_p, beta_p)
+    k = select_model(tables, mu_p, beta_p, min_layers=min_layers)
     valid = k >= 0
     if not valid:
         if not clamp:

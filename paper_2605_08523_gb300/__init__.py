@@ -23,14 +23,15 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (BF16X3, CLAMP, FP16X2, FP32, MODES, PAIR_TILES, REFINE1, REFINE2, SINGLE_TILES, SYNC,
+from ._lib import (BF16X3, CLAMP, FP16X2, FP32, LANCZOS, MIN_LAYERS, MODES, PAIR_TILES, REFINE1, REFINE2,
+                   SINGLE_TILES, SYNC,
                    TARGET_ENTROPY, TARGET_FERMI, TF32X3, Ftsp2Error, Instance, RescaleRec, Table, TrainReport,
                    check, lib, status_string)
 
 __all__ = ["ModelSet", "Solver", "ftsp2_rescale", "ftsp2_train_coeffs", "ftsp2_train_residual_jacobian",
            "ftsp2_train_normal_equations", "ftsp2_autotune_clear", "kernel_launch_count", "profile_layers",
            "profile_read", "MODES", "FP32", "TF32X3", "BF16X3", "FP16X2", "SYNC", "CLAMP", "REFINE1", "REFINE2",
-           "PAIR_TILES", "SINGLE_TILES", "TARGET_FERMI", "TARGET_ENTROPY", "Ftsp2Error", "status_string", "lib",
+           "PAIR_TILES", "SINGLE_TILES", "LANCZOS", "MIN_LAYERS", "TARGET_FERMI", "TARGET_ENTROPY", "Ftsp2Error", "status_string", "lib",
            "REC_DTYPE"]
 
 REC_DTYPE = np.dtype([("e_min", "f8"), ("e_max", "f8"), ("mu_p", "f8"), ("beta_p", "f8"), ("scale", "f8"),
@@ -321,7 +322,11 @@ def ftsp2_rescale(H, ns, mus, kTs, model_set: ModelSet, flags=0, stream=None):
     d_inst = torch.from_numpy(raw).to(H.device)
     rec = torch.empty(nb * 64, dtype=torch.uint8, device=H.device)
     wsz = C.c_size_t()
-    check(lib().ftsp2_rescale_workspace_size(nb, C.byref(wsz)), "ftsp2_rescale_workspace_size")
+    if int(flags) & LANCZOS:
+        # the Lanczos buffers are part of the hot path's workspace
+        check(lib().ftsp2_workspace_size(host, nb, FP16X2, 1, C.byref(wsz)), "ftsp2_workspace_size")
+    else:
+        check(lib().ftsp2_rescale_workspace_size(nb, C.byref(wsz)), "ftsp2_rescale_workspace_size")
     ws = torch.empty(wsz.value + 1024, dtype=torch.uint8, device=H.device)
     wp = (ws.data_ptr() + 1023) // 1024 * 1024
     st = lib().ftsp2_rescale(_ptr(H), host, _ptr(d_inst), nb, model_set.handle, int(flags) | SYNC, _ptr(rec),

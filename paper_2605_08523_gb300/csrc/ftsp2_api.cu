@@ -314,6 +314,7 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
     L.tiles = take(sizeof(Tile) * nt);
     L.tiles_ref = need_ref ? take(sizeof(Tile) * ntr) : 0;
     L.partials = take(sizeof(double) * 2 * kPartialSlots * std::max<long long>(nt, ntr));
+    L.lanczos = take(lanczos_ws_bytes(nb, P));   // used with FTSP2_LANCZOS only
     const int fmt = fmt_of_mode(mode);
     for (int c = 0; c < kMaxChains; ++c) {
         L.Z[c] = L.A[c] = L.OP[c][0] = L.OP[c][1] = L.OPR[c][0] = L.OPR[c][1] = 0;
@@ -468,8 +469,19 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     sa.tiles_ref = tiles_ref;
     sa.rec = dRec;
     sa.status = dstatus;
+    // FTSP2_LANCZOS: the FP32 copy of H lives in chain 0's Z plane, which the
+    // initialisation overwrites only after the bounds are final
+    sa.h32 = (flags & FTSP2_LANCZOS) ? reinterpret_cast<float*>(W + L.Z[0]) : nullptr;
     launch_prep(sa, s);
     launch_gershgorin(sa, maxn, s);
+    if (flags & FTSP2_LANCZOS) {
+        LanczosArgs lz;
+        lz.H32 = sa.h32;
+        lz.inst = dInst;
+        lz.iw = iw;
+        lanczos_bind(lz, W + L.lanczos, nb, L.P);
+        launch_lanczos(lz, maxn, s);
+    }
     launch_decide(sa, s);
 
     InitArgs ia;
@@ -832,6 +844,12 @@ ftsp2_status ftsp2_rescale(const double* dH, const ftsp2_instance* inst, const f
         if (inst[b].n < 1 || inst[b].offset < 0) return FTSP2_E_ARG;
         maxn = std::max(maxn, inst[b].n);
     }
+    const int P = (int)align_up((size_t)maxn, kPad);
+    // FTSP2_LANCZOS: Lanczos buffers, then the FP32 copy of H (same element offsets)
+    size_t h32_elems = 0;
+    for (int b = 0; b < nb; ++b) h32_elems = std::max(h32_elems, (size_t)inst[b].offset + (size_t)inst[b].n * inst[b].n);
+    const size_t lz_off = rescale_ws_bytes(nb), h32_off = lz_off + lanczos_ws_bytes(nb, P);
+    if ((flags & FTSP2_LANCZOS) && ws_bytes < h32_off + sizeof(float) * h32_elems) return FTSP2_E_WORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint8_t* W = static_cast<uint8_t*>(ws);
     SetupArgs sa;
@@ -852,8 +870,17 @@ ftsp2_status ftsp2_rescale(const double* dH, const ftsp2_instance* inst, const f
     sa.tiles_ref = nullptr;
     sa.rec = dRec;
     sa.status = reinterpret_cast<int*>(W);
+    sa.h32 = (flags & FTSP2_LANCZOS) ? reinterpret_cast<float*>(W + h32_off) : nullptr;
     launch_prep(sa, s);
     launch_gershgorin(sa, maxn, s);
+    if (flags & FTSP2_LANCZOS) {
+        LanczosArgs lz;
+        lz.H32 = sa.h32;
+        lz.inst = dInst;
+        lz.iw = sa.iw;
+        lanczos_bind(lz, W + lz_off, nb, P);
+        launch_lanczos(lz, maxn, s);
+    }
     launch_decide(sa, s);
     if (cudaGetLastError() != cudaSuccess) return FTSP2_E_CUDA;
     if (flags & FTSP2_SYNC) {

@@ -78,7 +78,7 @@ struct InstWork {
 
 struct Layout {
     // all offsets in bytes from the workspace base
-    size_t inst_work, tiles, tiles_ref, partials, status;
+    size_t inst_work, tiles, tiles_ref, partials, status, lanczos;
     size_t Z[kMaxChains], A[kMaxChains], OP[kMaxChains][2], OPR[kMaxChains][2];
     size_t total;
     size_t plane_elems;   // nb * P * P
@@ -99,6 +99,7 @@ struct SetupArgs {
     Tile* tiles_ref;
     ftsp2_rescale_rec* rec;
     int* status;
+    float* h32;                       // nullable: FP32 copy of H (same element offsets), for FTSP2_LANCZOS
 };
 
 void launch_prep(const SetupArgs& a, cudaStream_t s);
@@ -137,6 +138,29 @@ struct FinalArgs {
     const int* status;
 };
 void launch_finalize(const FinalArgs& a, cudaStream_t s);
+
+// --- spectral bounds tightened by Lanczos (FTSP2_LANCZOS; k_lanczos.cu) ------------
+constexpr int kLzSteps = 24;          // Lanczos steps (fewer when n is smaller)
+constexpr int kLzRows = 8;            // matrix rows per block of the matvec (one warp each)
+constexpr int kLzStopped = 0x10000;   // state flag: invariant subspace reached
+struct LanczosArgs {
+    const float* H32;                 // FP32 copy of H written by the Gershgorin pass
+    const ftsp2_instance* inst;
+    InstWork* iw;                     // Gershgorin keys in, tightened keys out
+    int nb, P, RB;                    // RB = ceil(P / kLzRows) partial sums per instance
+    double* V0;                       // [nb][P] Lanczos vectors (ping-pong on the step parity)
+    double* V1;
+    double* W;                        // [nb][P] the next vector before normalisation
+    float* V32;                       // [nb][P] FP32 copy of the current vector (matvec operand)
+    double* ab;                       // [nb][kLzSteps][2] alpha_j, beta_j
+    double* part;                     // [nb][RB]
+    int* state;                       // [nb] steps done | kLzStopped
+};
+void launch_lanczos(const LanczosArgs& a, int max_n, cudaStream_t s);
+// bytes of the Lanczos buffers for nb instances of pitch P (1024-aligned pieces)
+size_t lanczos_ws_bytes(int nb, int P);
+// carve the buffers out of ws (at least lanczos_ws_bytes(nb, P) bytes)
+void lanczos_bind(LanczosArgs& a, uint8_t* ws, int nb, int P);
 
 // --- chemical potential for a prescribed electron count (f1) ---------------------
 struct MuArgs {

@@ -106,6 +106,15 @@ __global__ void __launch_bounds__(kGWarps * 32) gershgorin_kernel(SetupArgs a) {
         const double* Hr = a.H + a.inst[b].offset + (size_t)row * n;
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int j = lane;
+        if (a.h32) {
+            // same pass, plus the FP32 copy the Lanczos matrix-vector products read
+            float* hr = a.h32 + a.inst[b].offset + (size_t)row * n;
+            for (; j < n; j += 32) {
+                const double h = __ldg(Hr + j);
+                s0 += fabs(h);
+                hr[j] = (float)h;
+            }
+        }
         for (; j + 96 < n; j += 128) {
             s0 += fabs(__ldg(Hr + j));
             s1 += fabs(__ldg(Hr + j + 32));
@@ -156,7 +165,10 @@ __device__ __forceinline__ bool valid_region(double mup, double betap, double be
     return (s * (0.0 - mup) + mu0 >= 0.0) && (s * (1.0 - mup) + mu0 <= 1.0);
 }
 
-__device__ __forceinline__ bool better(const DevModel& m, const DevModel& cur) {
+// model preference (workflow step 4): smallest beta0 then fewest layers, or,
+// with FTSP2_MIN_LAYERS, fewest (Fermi-chain) layers then smallest beta0
+__device__ __forceinline__ bool better(const DevModel& m, const DevModel& cur, bool min_layers) {
+    if (min_layers) return (m.L < cur.L) || (m.L == cur.L && m.beta0 < cur.beta0);
     return (m.beta0 < cur.beta0) || (m.beta0 == cur.beta0 && m.L < cur.L);
 }
 
@@ -164,6 +176,7 @@ __global__ void decide_kernel(SetupArgs a) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.nb) return;
     const ftsp2_instance in = a.inst[b];
+    const bool min_layers = (a.flags & FTSP2_MIN_LAYERS) != 0;
     ftsp2_rescale_rec r;
     r.e_min = dunkey(a.iw[b].kmin);
     r.e_max = dunkey(a.iw[b].kmax);
@@ -187,7 +200,7 @@ __global__ void decide_kernel(SetupArgs a) {
             // H = cI: X0 = mu0 + (beta/beta0)(mu - c), no flip
             for (int m = 0; m < a.nmodels; ++m) {
                 const double x = a.models[m].mu0 + (beta / a.models[m].beta0) * (in.mu - r.e_min);
-                if (x >= 0.0 && x <= 1.0 && (best < 0 || better(a.models[m], a.models[best]))) best = m;
+                if (x >= 0.0 && x <= 1.0 && (best < 0 || better(a.models[m], a.models[best], min_layers))) best = m;
             }
             if (best >= 0) {
                 r.model = best;
@@ -206,7 +219,7 @@ __global__ void decide_kernel(SetupArgs a) {
             if (flip) mup = 1.0 - mup;
             for (int m = 0; m < a.nmodels; ++m)
                 if (valid_region(mup, betap, a.models[m].beta0, a.models[m].mu0) &&
-                    (best < 0 || better(a.models[m], a.models[best])))
+                    (best < 0 || better(a.models[m], a.models[best], min_layers)))
                     best = m;
             r.valid = best >= 0;
             if (best < 0 && (a.flags & FTSP2_CLAMP)) {

@@ -1,0 +1,147 @@
+"""Lanczos-tightened spectral bounds on the GPU (FTSP2_LANCZOS) against the
+oracle's bounds, and the hot path with them against the oracle's method-exact
+result under the same bounds."""
+import glob
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import lanczos, pipeline, rescale, tables
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TABLES = os.path.join(ROOT, "paper_2605_08523_gb300", "tables")
+PRINTED = rescale.Table(tables.PRINTED_B1500, 1500.0, 1.0 / 3.0, name="printed")
+
+
+@pytest.fixture(scope="module")
+def ft():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2605_08523_gb300 as ft
+    return ft
+
+
+def _cases():
+    out = [wl.chain_1d(256, 0), np.array([[0.3]]), 0.5 * np.eye(70),
+           wl.lattice_3d((8, 8, 8), 0), wl.lattice_3d((8, 8, 16), 2, longrange_frac=0.05, longrange_sigma=0.05)]
+    out += [b["H"] for b in wl.ragged_batch(5, 7)]
+    return out
+
+
+def test_bounds_match_oracle(ft):
+    Hs = _cases()
+    ns = [H.shape[0] for H in Hs]
+    flat, _ = wl.pack_batch(Hs)
+    ms = ft.ModelSet()
+    rec = ft.ftsp2_rescale(torch.from_numpy(flat).cuda(), ns, [0.0] * len(ns), [0.1] * len(ns), ms,
+                           flags=ft.LANCZOS)
+    for b, H in enumerate(Hs):
+        # the oracle's recurrence is FP64 throughout; the GPU's products H v read
+        # FP32 copies (FP32 row sums), which moves the Ritz values by ~1e-7 of W
+        lo, hi = lanczos.bounds(H)
+        W = max(hi - lo, 1e-30)
+        assert abs(rec["e_min"][b] - lo) <= 2e-6 * max(1.0, W), (b, rec["e_min"][b], lo)
+        assert abs(rec["e_max"][b] - hi) <= 2e-6 * max(1.0, W), (b, rec["e_max"][b], hi)
+        ev = np.linalg.eigvalsh(H)
+        assert rec["e_min"][b] <= ev[0] and rec["e_max"][b] >= ev[-1]
+
+
+@pytest.mark.parametrize("mode", ["fp16x2", "bf16x3"])
+def test_hot_path_with_lanczos_bounds(ft, mode):
+    Hs = [wl.lattice_3d((8, 8, 8), 4), wl.chain_1d(300, 3)] + [b["H"] for b in wl.ragged_batch(3, 11)]
+    ns = [H.shape[0] for H in Hs]
+    mus = [0.0, 0.2, 1.0, -2.0, 0.5]
+    kTs = [0.1, 0.05, 0.1, 0.2, 0.05]
+    flat, _ = wl.pack_batch(Hs)
+    s = ft.Solver(ns, mus, kTs, ft.ModelSet(), mode=mode, want=3, flags=ft.LANCZOS)
+    s.run(torch.from_numpy(flat).cuda(), sync=True)
+    torch.cuda.synchronize()
+    recs = s.records()
+    for b, H in enumerate(Hs):
+        ex = pipeline.method_exact(H, mus[b], kTs[b], [PRINTED], lanczos=True)
+        assert recs[b]["status"] == 0
+        assert recs[b]["model"] == ex["rec"].model and bool(recs[b]["flip"]) == ex["rec"].flip
+        D = s.matrix(b).double().cpu().numpy()
+        assert np.max(np.abs(D - ex["D"])) < 1e-6, b
+        assert abs(float(s.S.cpu()[b]) - ex["S"]) / ns[b] < 1e-6, b
+
+
+def test_ragged_rotated_batch_needs_smaller_beta0(ft):
+    # Gershgorin over-estimates a rotated spectrum U(-10, 10) ~10x: with the
+    # tightened bounds every instance fits the printed beta0 = 1500 table,
+    # without them the colder ones need the beta0 >= 3000 tables
+    paths = [os.path.join(TABLES, "entropy_b1500_L26.json")]
+    paths += sorted(p for p in glob.glob(os.path.join(TABLES, "b*.json"))
+                    if int(os.path.basename(p)[1:].split("_")[0]) >= 3000)
+    ms = ft.ModelSet.from_json(paths)
+    batch = wl.ragged_batch(12, 21)
+    Hs = [b["H"] for b in batch]
+    ns = [H.shape[0] for H in Hs]
+    mus = [b["mu"] for b in batch]
+    kTs = [max(b["kT"], 0.05) for b in batch]
+    flat, _ = wl.pack_batch(Hs)
+    Hd = torch.from_numpy(flat).cuda()
+    g = ft.Solver(ns, mus, kTs, ms, mode="fp16x2", want=1)
+    g.run(Hd, sync=True)
+    lz = ft.Solver(ns, mus, kTs, ms, mode="fp16x2", want=1, flags=ft.LANCZOS)
+    lz.run(Hd, sync=True)
+    torch.cuda.synchronize()
+    rg, rl = g.records(), lz.records()
+    assert np.all(rl["model"] == 0), rl["model"]
+    assert np.sum(rg["model"] > 0) >= 3, rg["model"]
+    assert np.all(rl["beta_p"] < 0.2 * rg["beta_p"])
+    for b in range(0, len(ns), 3):
+        ex = pipeline.method_exact(Hs[b], mus[b], kTs[b], [PRINTED], lanczos=True)
+        D = lz.matrix(b).double().cpu().numpy()
+        assert np.max(np.abs(D - ex["D"])) < 1e-6, b
+
+
+def _oracle_table(path):
+    import json
+    with open(path) as f:
+        d = json.load(f)
+    th = tuple(tuple(r) for r in d["theta"])
+    te = tuple(tuple(r) for r in d["theta_entropy"]) if d.get("theta_entropy") else None
+    return rescale.Table(th, d["beta0"], d["mu0"], d["alpha"], te, name=os.path.basename(path))
+
+
+def test_fewest_layers_policy_with_lanczos_bounds(ft):
+    # the ragged-batch model set (printed 26-layer table, the 32-layer
+    # beta0 = 20 .. 200 tables, the 34 .. 44-layer beta0 >= 3000 tables): with
+    # tightened bounds the default policy takes the small-beta0 32-layer tables,
+    # the fewest-layers policy the 26-layer table, matching the oracle
+    paths = [os.path.join(TABLES, "entropy_b1500_L26.json")] + sorted(glob.glob(os.path.join(TABLES, "b*_L32.json")))
+    paths += sorted(p for p in glob.glob(os.path.join(TABLES, "b*.json"))
+                    if int(os.path.basename(p)[1:].split("_")[0]) >= 3000)
+    ms = ft.ModelSet.from_json(paths)
+    otabs = [_oracle_table(p) for p in paths]
+    batch = wl.ragged_batch(8, 33)
+    Hs = [b["H"] for b in batch]
+    ns = [H.shape[0] for H in Hs]
+    mus = [b["mu"] for b in batch]
+    kTs = [b["kT"] for b in batch]
+    flat, _ = wl.pack_batch(Hs)
+    Hd = torch.from_numpy(flat).cuda()
+    d = ft.Solver(ns, mus, kTs, ms, mode="fp16x2", want=3, flags=ft.LANCZOS)
+    d.run(Hd, sync=True)
+    f = ft.Solver(ns, mus, kTs, ms, mode="fp16x2", want=3, flags=ft.LANCZOS | ft.MIN_LAYERS)
+    f.run(Hd, sync=True)
+    torch.cuda.synchronize()
+    rd, rf = d.records(), f.records()
+    assert np.all(rf["layers"] <= rd["layers"])
+    assert int(rf["layers"].max()) == 26
+    for b, H in enumerate(Hs):
+        exd = pipeline.method_exact(H, mus[b], kTs[b], otabs, lanczos=True)
+        exf = pipeline.method_exact(H, mus[b], kTs[b], otabs, lanczos=True, min_layers=True)
+        assert rd[b]["model"] == exd["rec"].model and rf[b]["model"] == exf["rec"].model, b
+        D = f.matrix(b).double().cpu().numpy()
+        assert np.max(np.abs(D - exf["D"])) < 1e-6, b
+        assert abs(float(f.S.cpu()[b]) - exf["S"]) / ns[b] < 1e-6, b

@@ -74,6 +74,21 @@ def test_model_choice_smallest_valid_beta0():
     assert rescale.select_model([t_big, t_small], 0.4, 1400.0) == -1
 
 
+def test_model_choice_fewest_layers_policy():
+    # with the fewest-layers policy a longer low-beta0 table loses to a shorter
+    # valid one; ties in the layer count go to the smaller beta0
+    th26 = np.asarray(TH)
+    th32 = np.vstack([th26, th26[:6]])
+    t_low_long = rescale.Table(th32, 200.0, 1 / 3, name="b200_L32")
+    t_mid = rescale.Table(th26, 1500.0, 1 / 3, name="b1500_L26")
+    t_mid2 = rescale.Table(th26, 3000.0, 1 / 3, name="b3000_L26")
+    ts = [t_low_long, t_mid2, t_mid]
+    assert rescale.select_model(ts, 0.4, 100.0) == 0                    # default: smallest beta0
+    assert rescale.select_model(ts, 0.4, 100.0, min_layers=True) == 2   # fewest layers, then beta0
+    assert rescale.select_model(ts, 0.4, 1400.0, min_layers=True) == 1  # only b3000 is valid
+    assert rescale.select_model(ts, 0.4, 9000.0, min_layers=True) == -1
+
+
 def test_appendix_harness():
     # Appendix A test cases: 10 seeds, N = 100, beta ~ U(1, (2/3 beta0)/W),
     # mu ~ U(e_min, e_max); the 2-norm error against diagonalisation is at the
