@@ -149,3 +149,28 @@ def test_cfg4_n8192_refine2(ft):
     assert err <= 3e-6, err
     assert abs(float(s.trace[0, 0]) - np.sum(f)) < 1e-3
     assert abs(float(s.S[0]) - Sref) / n <= 3e-6
+
+
+def test_cfg2_with_lanczos_bounds_within_north_star_bound(ft):
+    # with the Lanczos-tightened bounds and the fewest-layers policy every
+    # instance of the ragged batch runs the printed 26-layer table, and D and S
+    # meet the 1e-6 bound against the eigendecomposition
+    paths = model_set_paths()
+    ms = ft.ModelSet.from_json(paths)
+    batch = wl.ragged_batch(512, 0)
+    Hs = [b["H"] for b in batch]
+    ns = [H.shape[0] for H in Hs]
+    flat, _ = wl.pack_batch(Hs)
+    s = ft.Solver(ns, [b["mu"] for b in batch], [b["kT"] for b in batch], ms, mode="fp16x2", want=3,
+                  flags=ft.LANCZOS | ft.MIN_LAYERS)
+    s.run(torch.from_numpy(flat).cuda(), sync=True)
+    torch.cuda.synchronize()
+    rec = s.records()
+    assert np.all(rec["status"] == 0) and np.all(rec["model"] == 0)
+    S = s.S.cpu().numpy()
+    for b in range(0, 512, 23):
+        H = Hs[b]
+        Dref, Sref, _, _ = fermi.eig_reference(H, batch[b]["mu"], batch[b]["kT"])
+        D = s.matrix(b).double().cpu().numpy()
+        assert np.max(np.abs(D - Dref)) < 1e-6, b
+        assert abs(S[b] - Sref) / ns[b] < 1e-6, b
