@@ -27,9 +27,10 @@
 // ragged edges, which pays for batches of small instances.
 //
 // Chunked accumulation.  Every 128 elements of K (CK slices; a launch may ask
-// for shorter chunks) the MMAs switch to the other of two TMEM accumulators
-// and the epilogue adds the finished chunk into FP32 registers; the tensor core's internal accumulation then
-// spans 128 products per chunk instead of all n.  Measured at n = 4096 with the
+// for shorter chunks) the MMAs switch to the next of the TMEM chunk
+// accumulators (two on a CTA pair, four on a single CTA) and the epilogue adds
+// the finished chunk into FP32 registers; the tensor core's internal
+// accumulation then spans 128 products per chunk instead of all n.  Measured at n = 4096 with the
 // printed table (density, FP16X2): chunks of 256 / 128 / 64 elements give
 // max|D - D_ref| = 1.85e-6 / 9.0e-7 / 6.9e-7 at layer times 0.235 / 0.251 /
 // 0.314 ms; 128 is the default.
@@ -78,6 +79,10 @@ template <bool PAIR>
 struct Geo {
     static constexpr int TILE = PAIR ? 256 : 128;    // rows = columns of a tile
     static constexpr int NCTA = PAIR ? 2 : 1;
+    // TMEM chunk accumulators (512 columns): two of 256 columns on a pair,
+    // four of 128 on a single CTA, so that the MMAs of the next tile can run
+    // three chunks ahead of a single CTA's final epilogue
+    static constexpr int NBUF = PAIR ? 2 : 4;
 };
 constexpr int kCtaRows = 128;
 constexpr int kEpiWarps = 16;
@@ -521,14 +526,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int STAGE_BYTES = C::NSPLIT * 2 * PLANE; // A and B planes (B: this CTA's half when PAIR)
     constexpr int KSTEPS = 4;                          // 128-byte slice / 32 bytes per MMA
     constexpr uint32_t IDESC = make_idesc(C::ATYPE, TILE, TILE);
-    constexpr uint32_t TMEM_COLS = 2 * TILE;
+    constexpr int NBUF = G::NBUF;
+    constexpr uint32_t TMEM_COLS = NBUF * TILE;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t full_bar[C::STAGES];
     __shared__ __align__(8) uint64_t empty_bar[C::STAGES];
-    __shared__ __align__(8) uint64_t tfull_bar[2];
-    __shared__ __align__(8) uint64_t tempty_bar[2];
+    __shared__ __align__(8) uint64_t tfull_bar[NBUF];
+    __shared__ __align__(8) uint64_t tempty_bar[NBUF];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -544,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&full_bar[s], G::NCTA);      // one expect_tx arrival per CTA
             mbar_init(&empty_bar[s], 1);
         }
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < NBUF; ++s) {
             mbar_init(&tfull_bar[s], 1);
             mbar_init(&tempty_bar[s], G::NCTA * kEpiWarps);
         }
@@ -676,7 +682,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!ok) break;
                     if constexpr (PAIR) umma_commit_pair(smem_u32(&tfull_bar[buf]));
                     else umma_commit_one(smem_u32(&tfull_bar[buf]));
-                    if (++buf == 2) {
+                    if (++buf == NBUF) {
                         buf = 0;
                         aphase ^= 1u;
                     }
@@ -688,8 +694,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- epilogue (warps 2..17) ----------------
         const int q = warp & 3;                  // TMEM lane quarter
         const int cq = (warp - 2) >> 2;          // column quarter of the tile
+        // "tempty" barriers of the even CTA (consecutive 8-byte words)
         const uint32_t tempty0 = PAIR ? map_to(smem_u32(&tempty_bar[0]), 0) : smem_u32(&tempty_bar[0]);
-        const uint32_t tempty1 = PAIR ? map_to(smem_u32(&tempty_bar[1]), 0) : smem_u32(&tempty_bar[1]);
         int buf = 0;
         uint32_t aphase = 0;
         bool ok = true;
@@ -720,7 +726,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // stays held through the final epilogue: the epilogue then reads
             // its 8-column groups from TMEM, so the 64 accumulator registers of
             // a pair tile are free for the memory work.  The MMAs of the next
-            // tile meanwhile fill the other buffer.
+            // tile meanwhile fill the other buffers.
             const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cq * EPI_COLS);
             for (int j = 0; j < nch; ++j) {
                 if (!wait_bar(&tfull_bar[buf], aphase, &abort_flag, a.status)) {
@@ -750,10 +756,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
-                    if constexpr (PAIR) remote_arrive(buf ? tempty1 : tempty0);
-                    else local_arrive(buf ? tempty1 : tempty0);
+                    if constexpr (PAIR) remote_arrive(tempty0 + 8u * (uint32_t)buf);
+                    else local_arrive(tempty0 + 8u * (uint32_t)buf);
                 }
-                if (++buf == 2) {
+                if (++buf == NBUF) {
                     buf = 0;
                     aphase ^= 1u;
                 }
@@ -798,10 +804,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
-                if constexpr (PAIR) remote_arrive(buf ? tempty1 : tempty0);
-                else local_arrive(buf ? tempty1 : tempty0);
+                if constexpr (PAIR) remote_arrive(tempty0 + 8u * (uint32_t)buf);
+                else local_arrive(tempty0 + 8u * (uint32_t)buf);
             }
-            if (++buf == 2) {
+            if (++buf == NBUF) {
                 buf = 0;
                 aphase ^= 1u;
             }
