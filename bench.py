@@ -56,7 +56,9 @@ def parse():
     p.add_argument("--policy", default="beta0", choices=["beta0", "layers"],
                    help="model choice: smallest beta0 (default) or fewest layers (FTSP2_MIN_LAYERS)")
     p.add_argument("--refine", type=int, default=0, choices=[0, 1, 2],
-                   help="last 0/1/2 layers in FP32 (FTSP2_REFINE1/2)")
+                   help="last 0/1/2 layers in FP32 (FTSP2_REFINE1/2); cfg4 defaults to 2")
+    p.add_argument("--refine-tc", action="store_true",
+                   help="refinement layers as BF16X3 tensor-core layers (FTSP2_REFINE_TC)")
     p.add_argument("--workload", default="cfg1", choices=["cfg1", "cfg2", "cfg4"],
                    help="cfg1: the headline single n = 4096 matrix; cfg2: the 512-instance ragged batch; "
                         "cfg4: n = 8192 lattice with 5%% long-range couplings, two FP32 refinement layers "
@@ -455,6 +457,8 @@ def main():
     shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
     refine = 2 if cfg4 and args.refine == 0 else args.refine
     shape_flag |= {0: 0, 1: ft.REFINE1, 2: ft.REFINE2}[refine]
+    if args.refine_tc:
+        shape_flag |= ft.REFINE_TC
     if args.bounds == "lanczos":
         shape_flag |= ft.LANCZOS
     solver = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3, flags=shape_flag)
@@ -574,7 +578,8 @@ def main():
                                 "cfg1 lattice %dx%dx%d n=%d kT=%g mu=half filling, density+entropy, "
                                 "printed 26-layer table + trained entropy table") % (dims + (n, kT)),
                    "n": n, "kT": kT, "mu": mu, "layers": L, "mode": args.mode, "chains": 2,
-                   "refine_layers_fp32": refine, "model": int(rec["model"]), "bounds": args.bounds,
+                   "refine_layers_fp32": refine, "refine_on_tensor_cores": bool(args.refine_tc),
+                   "model": int(rec["model"]), "bounds": args.bounds,
                    "e_min": float(rec["e_min"]), "e_max": float(rec["e_max"]),
                    "l2": "inputs and working set larger than L2 (no flush)", "parallelism": "replicas",
                    "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],

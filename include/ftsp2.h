@@ -102,6 +102,12 @@ typedef enum {
  * rounding), ties to fewer layers; with this flag the fewest Fermi-chain layers
  * (the fastest), ties to the smaller beta0. */
 #define FTSP2_MIN_LAYERS    0x80
+/* With FTSP2_REFINE1/2: the refinement layers run on the tensor cores as
+ * BF16X3 layers (6 products of 3-way BF16 splits, FP32 accumulation in
+ * 64-element chunks: FP32-class products) instead of FP32 FMA on the CUDA
+ * cores, which on this GPU cost ten times a tensor-core layer.  No effect in
+ * FTSP2_BF16X3 mode (its layers are BF16X3 already). */
+#define FTSP2_REFINE_TC     0x100
 
 /* One Hamiltonian of a (ragged) batch.  H_b starts at dH + offset and is
  * n x n row-major; D_b starts at dD + offset.  Offsets are in elements. */
@@ -247,7 +253,8 @@ ftsp2_status ftsp2_density_entropy(const double* dH, const ftsp2_instance* inst,
  *     nb * P^2 * (8 + 2 b) bytes plus a few KiB of bookkeeping, where P is the
  *     largest n rounded up to 128 and b the operand bytes per element (4 for
  *     FTSP2_FP16X2 and FTSP2_FP32, 6 for FTSP2_BF16X3, 8 for FTSP2_TF32X3;
- *     FTSP2_REFINE1/2 add 8).  A single FP16X2 instance fits up to n = 640.
+ *     FTSP2_REFINE1/2 add 8, or 12 with FTSP2_REFINE_TC).  A single FP16X2
+ *     instance fits up to n = 640.
  *     Larger batches are rejected with FTSP2_E_WORKSPACE before any launch.
  *     FTSP2_SYNC is refused (FTSP2_E_ARG); read dRec instead.
  *   - The first call on each device looks up the array's device address

@@ -17,8 +17,8 @@ OK, E_ARG, E_CUDA, E_WORKSPACE, E_VALIDITY, E_NONFINITE, E_TIMEOUT, E_NOMODEL, E
 FP32, TF32X3, BF16X3, FP16X2 = 0, 1, 2, 3
 MODES = {"fp32": FP32, "tf32x3": TF32X3, "bf16x3": BF16X3, "fp16x2": FP16X2}
 # flags
-SYNC, CLAMP, REFINE1, REFINE2, PAIR_TILES, SINGLE_TILES, LANCZOS, MIN_LAYERS = \
-    0x1, 0x2, 0x4, 0x8, 0x10, 0x20, 0x40, 0x80
+SYNC, CLAMP, REFINE1, REFINE2, PAIR_TILES, SINGLE_TILES, LANCZOS, MIN_LAYERS, REFINE_TC = \
+    0x1, 0x2, 0x4, 0x8, 0x10, 0x20, 0x40, 0x80, 0x100
 TARGET_FERMI, TARGET_ENTROPY = 0, 1
 
 

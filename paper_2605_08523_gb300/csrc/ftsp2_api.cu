@@ -325,8 +325,9 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
         L.OP[c][0] = take((size_t)op_bytes(fmt) * L.plane_elems);
         L.OP[c][1] = take((size_t)op_bytes(fmt) * L.plane_elems);
         if (refine) {
-            L.OPR[c][0] = take(4 * L.plane_elems);
-            L.OPR[c][1] = take(4 * L.plane_elems);
+            const size_t rb = (flags & FTSP2_REFINE_TC) ? (size_t)op_bytes(OP_BF16X3) : 4;
+            L.OPR[c][0] = take(rb * L.plane_elems);
+            L.OPR[c][1] = take(rb * L.plane_elems);
         }
     }
     // the layer epilogues address A_c as Z_c + plane_elems
@@ -432,10 +433,15 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     const DevModel* models = set->d_models[scaled ? 1 : 0];
     const DevLayer* layers = set->d_layers[scaled ? 1 : 0];
     const int Lmax = set->Lmax;
-    const int R = mode == FTSP2_FP32 ? 0 : refine_layers(flags);
-    const int refine_from = Lmax - R;       // global layers >= this run in FP32
+    // refinement layers: the last R global layers, in FP32 on the CUDA cores, or
+    // with FTSP2_REFINE_TC as BF16X3 tensor-core layers (nothing to refine when
+    // the main layers are BF16X3 already)
+    const bool refine_tc = (flags & FTSP2_REFINE_TC) && mode != FTSP2_FP32;
+    const int R = (mode == FTSP2_FP32 || (refine_tc && mode == FTSP2_BF16X3)) ? 0 : refine_layers(flags);
+    const int refine_from = Lmax - R;       // global layers >= this are refinement layers
     const bool all_simt = mode == FTSP2_FP32;
     const int fmt = fmt_of_mode(mode);
+    const int rfmt = refine_tc ? OP_BF16X3 : OP_F32;
     int maxn = 0;
     for (int b = 0; b < nb; ++b) maxn = std::max(maxn, inst[b].n);
 
@@ -495,6 +501,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     ia.nchains = L.nchains;
     ia.plane_elems = L.plane_elems;
     ia.main_fmt = fmt;
+    ia.refine_fmt = rfmt;
     ia.refine_from = all_simt ? 0 : refine_from;
     for (int c = 0; c < kMaxChains; ++c) {
         ia.chain_kind[c] = kinds[c];
@@ -502,7 +509,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         ia.A[c] = c < L.nchains ? reinterpret_cast<float*>(W + L.A[c]) : nullptr;
         for (int p = 0; p < 2; ++p) {
             ia.OP[c][p] = c < L.nchains ? W + L.OP[c][p] : nullptr;
-            ia.OPR[c][p] = (c < L.nchains && L.OPR[c][p]) ? reinterpret_cast<float*>(W + L.OPR[c][p]) : nullptr;
+            ia.OPR[c][p] = (c < L.nchains && L.OPR[c][p]) ? W + L.OPR[c][p] : nullptr;
         }
     }
     launch_init(ia, maxn, s);
@@ -522,6 +529,18 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
                 for (int sp = 0; sp < nsplit; ++sp) {
                     void* base = W + L.OP[c][p] + (size_t)sp * es * L.plane_elems;
                     if (!encode_map(&maps[p].a[c][sp], base, dt, es, L.P, nb, bke, kTileM)) return FTSP2_E_CUDA;
+                }
+    }
+    // tensor maps of the BF16X3 refinement operands (FTSP2_REFINE_TC)
+    TmaMaps mapsR[2];
+    if (refine_tc && R > 0) {
+        std::memset(mapsR, 0, sizeof(mapsR));
+        for (int p = 0; p < 2; ++p)
+            for (int c = 0; c < L.nchains; ++c)
+                for (int sp = 0; sp < 3; ++sp) {
+                    void* base = W + L.OPR[c][p] + (size_t)sp * 2 * L.plane_elems;
+                    if (!encode_map(&mapsR[p].a[c][sp], base, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, L.P, nb, 64, kTileM))
+                        return FTSP2_E_CUDA;
                 }
     }
 
@@ -544,25 +563,29 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         la.Z[c] = c < L.nchains ? reinterpret_cast<float*>(W + L.Z[c]) : nullptr;
         la.A[c] = c < L.nchains ? reinterpret_cast<float*>(W + L.A[c]) : nullptr;
     }
-    auto is_simt = [&](int g) { return all_simt || g >= refine_from; };
+    auto is_simt = [&](int g) { return all_simt || (g >= refine_from && !refine_tc); };
+    auto is_rtc = [&](int g) { return refine_tc && g >= refine_from; };
     const int pair = all_simt ? 1 : tile_shape_choice(inst, nb, mode, want, flags, di.sms);
     int last_table = 0;
     for (int g = 0; g < Lmax; ++g) {
         const bool simt = is_simt(g);
         const bool next_simt = g + 1 < Lmax && is_simt(g + 1);
+        const bool rtc = is_rtc(g);
+        const bool next_rtc = g + 1 < Lmax && is_rtc(g + 1);
+        const int lmode = rtc ? (int)FTSP2_BF16X3 : mode;   // arithmetic of this layer
         la.gl = g;
         la.last = g == Lmax - 1;
         // The last layers run with 64-element accumulation chunks: their rounding
         // reaches the output undamped (earlier errors are contracted by the
         // saturating layers), and the entropy is linear in it for occupations
         // near 0 and 1.
-        la.chunk_elems = chunk_elems_of(mode, g, Lmax);
-        la.next_fmt = next_simt ? OP_F32 : fmt;
+        la.chunk_elems = chunk_elems_of(lmode, g, Lmax);
+        la.next_fmt = next_simt ? OP_F32 : (next_rtc ? OP_BF16X3 : fmt);
         for (int c = 0; c < L.nchains; ++c) {
             const int rp = g & 1, wp = (g + 1) & 1;
-            if (simt) la.opr[c] = all_simt ? W + L.OP[c][rp] : W + L.OPR[c][rp];
+            if (simt || rtc) la.opr[c] = all_simt ? W + L.OP[c][rp] : W + L.OPR[c][rp];
             else la.opr[c] = W + L.OP[c][rp];
-            if (next_simt) la.opw[c] = all_simt ? W + L.OP[c][wp] : W + L.OPR[c][wp];
+            if (next_simt || next_rtc) la.opw[c] = all_simt ? W + L.OP[c][wp] : W + L.OPR[c][wp];
             else la.opw[c] = W + L.OP[c][wp];
         }
         if (dD == nullptr && la.last) la.D = nullptr;
@@ -588,7 +611,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
                     e0 = e1 = nullptr;
                 }
             }
-            e = launch_layer_tc(mode, la, maps[g & 1], units, pair, s);
+            e = launch_layer_tc(lmode, la, rtc ? mapsR[g & 1] : maps[g & 1], units, pair, s);
             if (e0) {
                 cudaEventRecord(e1, s);
                 std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -816,7 +839,7 @@ ftsp2_status ftsp2_workspace_size(const ftsp2_instance* inst, int nb, ftsp2_mode
     if (!bytes) return FTSP2_E_ARG;
     Layout L;
     // sized for the largest refinement setting so one workspace serves every flag
-    const ftsp2_status st = plan(inst, nb, mode, want, FTSP2_REFINE2, L);
+    const ftsp2_status st = plan(inst, nb, mode, want, FTSP2_REFINE2 | FTSP2_REFINE_TC, L);
     if (st != FTSP2_OK) return st;
     *bytes = L.total;
     return FTSP2_OK;

@@ -117,9 +117,10 @@ struct InitArgs {
     float* Z[kMaxChains];
     float* A[kMaxChains];
     uint8_t* OP[kMaxChains][2];    // operands in the main format
-    float* OPR[kMaxChains][2];     // FP32 operands of refinement layers (nullable)
+    uint8_t* OPR[kMaxChains][2];   // operands of refinement layers (nullable), format refine_fmt
     int main_fmt;                  // format of the main layers (OP_F32 in FTSP2_FP32 mode)
-    int refine_from;               // global layers >= refine_from run in FP32 on OPR
+    int refine_fmt;                // OP_F32 (CUDA-core refinement) or OP_BF16X3 (FTSP2_REFINE_TC)
+    int refine_from;               // global layers >= refine_from are refinement layers on OPR
     size_t plane_elems;
 };
 void launch_init(const InitArgs& a, int max_n, cudaStream_t s);

@@ -893,6 +893,10 @@ template <int MODE, int MAINFMT, bool PAIR>
 static cudaError_t launch_shape(const LayerArgs& a, const TmaMaps& maps, int units, cudaStream_t s) {
     if (a.last) return launch_variant<MODE, kLastLayer, PAIR>(a, maps, units, s);
     if (a.next_fmt == OP_F32) return launch_variant<MODE, OP_F32, PAIR>(a, maps, units, s);
+    if constexpr (MAINFMT != OP_BF16X3) {
+        // the layer before BF16X3 refinement layers (FTSP2_REFINE_TC)
+        if (a.next_fmt == OP_BF16X3) return launch_variant<MODE, OP_BF16X3, PAIR>(a, maps, units, s);
+    }
     return launch_variant<MODE, MAINFMT, PAIR>(a, maps, units, s);
 }
 

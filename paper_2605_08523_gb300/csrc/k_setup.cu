@@ -363,7 +363,8 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
                 a.A[ch][es] = 0.f;
                 if (inside) {
                     const int start = (sl_packed >> (16 * ch)) & 0xffff;
-                    if (a.main_fmt != OP_F32 && start >= a.refine_from) a.OPR[ch][start & 1][e] = zc;
+                    if (a.main_fmt != OP_F32 && start >= a.refine_from)
+                        write_operand(a.refine_fmt, a.OPR[ch][start & 1], a.plane_elems, e, zc, 1.f);
                     else write_operand(a.main_fmt, a.OP[ch][start & 1], a.plane_elems, e, zc,
                                        ent ? sc0S : sc0);
                 } else {
@@ -371,8 +372,8 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
                     zero_operand(a.main_fmt, a.OP[ch][0], a.plane_elems, e);
                     zero_operand(a.main_fmt, a.OP[ch][1], a.plane_elems, e);
                     if (a.OPR[ch][0]) {
-                        a.OPR[ch][0][e] = 0.f;
-                        a.OPR[ch][1][e] = 0.f;
+                        zero_operand(a.refine_fmt, a.OPR[ch][0], a.plane_elems, e);
+                        zero_operand(a.refine_fmt, a.OPR[ch][1], a.plane_elems, e);
                     }
                 }
             }

@@ -185,6 +185,18 @@ def test_refinement_layers(ft, printed_set, flags):
     check_instance(s, 0, H, 0.1, 0.1, [PRINTED], "fp16x2")
 
 
+@pytest.mark.parametrize("mode", ["fp16x2", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("refine", ["REFINE1", "REFINE2"])
+def test_refinement_layers_on_tensor_cores(ft, printed_set, mode, refine):
+    # FTSP2_REFINE_TC: the refinement layers run as BF16X3 tensor-core layers;
+    # a ragged pair of instances (different start layers) and a lattice
+    Hs = [wl.chain_1d(260, 4), wl.lattice_3d((8, 8, 8), 6)]
+    mus, kTs = [0.1, 0.0], [0.1, 0.3]
+    s = solve(ft, printed_set, Hs, mus, kTs, mode, flags=getattr(ft, refine) | ft.REFINE_TC)
+    for b, H in enumerate(Hs):
+        check_instance(s, b, H, mus[b], kTs[b], [PRINTED], mode)
+
+
 def test_deterministic(ft, printed_set):
     H = wl.chain_1d(384, 12)
     a = solve(ft, printed_set, [H], [0.0], [0.1], "fp16x2")
