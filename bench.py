@@ -250,7 +250,8 @@ def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
 # (mode, n, sha256[:16] of the layer-kernel sources) -> dram read + write bytes
 # of one layer launch (both chains), from the ncu capture summarised in
 # profiles/layer_tc_fp16x2_n4096.md
-MEASURED_TRAFFIC = {("fp16x2", 4096, "52ae88a99f185e28"): 420.6208e6 + 233.582592e6}
+MEASURED_TRAFFIC = {("fp16x2", 4096, "52ae88a99f185e28"): 420.6208e6 + 233.582592e6,
+                    ("fp16x2", 4096, "acc91d76912da5c8"): 422.81472e6 + 233.330176e6}
 
 
 def kernel_sha():
