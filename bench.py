@@ -57,6 +57,9 @@ def parse():
                    help="model choice: smallest beta0 (default) or fewest layers (FTSP2_MIN_LAYERS)")
     p.add_argument("--refine", type=int, default=0, choices=[0, 1, 2],
                    help="last 0/1/2 layers in FP32 (FTSP2_REFINE1/2); cfg4 defaults to 2")
+    p.add_argument("--epilogue", default="auto", choices=["auto", "deferred", "inline"],
+                   help="final epilogue of the pair tiles: the library's default, or forced "
+                        "(FTSP2_EPI_DEFERRED / FTSP2_EPI_INLINE)")
     p.add_argument("--refine-tc", action="store_true",
                    help="refinement layers as BF16X3 tensor-core layers (FTSP2_REFINE_TC)")
     p.add_argument("--workload", default="cfg1", choices=["cfg1", "cfg2", "cfg4"],
@@ -361,6 +364,7 @@ def run_cfg2(args):
     flat, _ = wl.pack_batch(Hs)
     Hd = torch.from_numpy(flat).cuda()
     shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
+    shape_flag |= {"auto": 0, "deferred": ft.EPI_DEFERRED, "inline": ft.EPI_INLINE}[args.epilogue]
     if args.bounds == "lanczos":
         shape_flag |= ft.LANCZOS
     if args.policy == "layers":
@@ -399,6 +403,7 @@ def run_cfg2(args):
                        "models_used": {int(m): int(np.sum(rec["model"] == m)) for m in np.unique(rec["model"])},
                        "bounds": args.bounds, "policy": args.policy, "global_layers": int(rec["layers"].max()),
                        "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
+                   "epilogue": args.epilogue,
                        "autotune_ms": {"single": ms_single, "pair": ms_pair}},
             "tflops_alg": alg / t / 1e12,
             "accuracy_sampled": {"instances": len(range(0, len(ns), max(1, len(ns) // 32))),
@@ -456,6 +461,7 @@ def main():
         tabs.append(os.path.join(tdir, "b3000_L34.json"))
     ms = ft.ModelSet.from_json(tabs)
     shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
+    shape_flag |= {"auto": 0, "deferred": ft.EPI_DEFERRED, "inline": ft.EPI_INLINE}[args.epilogue]
     refine = 2 if cfg4 and args.refine == 0 else args.refine
     shape_flag |= {0: 0, 1: ft.REFINE1, 2: ft.REFINE2}[refine]
     if args.refine_tc:
@@ -584,6 +590,7 @@ def main():
                    "e_min": float(rec["e_min"]), "e_max": float(rec["e_max"]),
                    "l2": "inputs and working set larger than L2 (no flush)", "parallelism": "replicas",
                    "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
+                   "epilogue": args.epilogue,
                    "autotune_ms": {"single": ms_single, "pair": ms_pair}},
         "tflops_alg": alg_flops / t_step / 1e12 * world,
         "density_only": {"value": world / t_density, "unit": "solves/s", "ms_per_step": t_density * 1e3},

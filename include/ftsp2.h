@@ -108,6 +108,17 @@ typedef enum {
  * cores, which on this GPU cost ten times a tensor-core layer.  No effect in
  * FTSP2_BF16X3 mode (its layers are BF16X3 already). */
 #define FTSP2_REFINE_TC     0x100
+/* Final epilogue of the 256 x 256 pair tiles in the layers of the main format
+ * (Z_{k+1}, A_{k+1} and the next layer's operands from a finished tile).  By
+ * default it is deferred when the tiles are long (mean order n over the pair
+ * tiles >= 2048): the accumulating warps pass a finished tile's sums to two
+ * store warps per CTA through a scratch in the workspace (128 KB per CTA, at
+ * most 192 CTAs) and go on with the next tile, so that the epilogue's memory
+ * traffic overlaps the next tile's MMAs; for shorter tiles the accumulating
+ * warps run it inline.  These two flags force one or the other (results are
+ * identical). */
+#define FTSP2_EPI_DEFERRED  0x200
+#define FTSP2_EPI_INLINE    0x400
 
 /* One Hamiltonian of a (ragged) batch.  H_b starts at dH + offset and is
  * n x n row-major; D_b starts at dD + offset.  Offsets are in elements. */
@@ -177,7 +188,9 @@ ftsp2_status ftsp2_model_set_table(const ftsp2_model_set* set, int idx, int* L, 
 /* ---- workspace ------------------------------------------------------------ */
 
 /* Bytes of device workspace needed by a density/entropy call with these
- * instances and mode.  `want` = 1 density, 2 entropy, 3 both. */
+ * instances and mode.  `want` = 1 density, 2 entropy, 3 both.  The size covers
+ * every flag (refinement layers, Lanczos bounds, the deferred epilogue's
+ * scratch). */
 ftsp2_status ftsp2_workspace_size(const ftsp2_instance* inst, int nb, ftsp2_mode mode,
                                   int want, size_t* bytes);
 

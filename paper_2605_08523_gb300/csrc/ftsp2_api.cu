@@ -288,10 +288,17 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
     const bool refine = !simt_main && refine_layers(flags) > 0;
     const bool need_ref = !simt_main;
     long long nt = 0, ntr = 0;
+    double tile_k = 0.0;                       // sum of the orders n over the pair tiles
     for (int b = 0; b < nb; ++b) {
-        nt += host_tiles_of(inst[b].n, BM, BN);
+        const long long t = host_tiles_of(inst[b].n, BM, BN);
+        nt += t;
+        tile_k += (double)t * inst[b].n;
         if (need_ref) ntr += host_tiles_of(inst[b].n, 128, 128);
     }
+    // deferred final epilogue of the pair tiles: by default when their mean
+    // K is long enough for two store warps to keep up with the MMAs
+    const bool defer = !simt_main && !(flags & FTSP2_EPI_INLINE) &&
+                       ((flags & FTSP2_EPI_DEFERRED) || tile_k >= (double)kDeferMinK * (double)nt);
     nt *= nch;
     ntr *= nch;
     if (nt > (1ll << 30)) return FTSP2_E_ARG;
@@ -315,6 +322,8 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
     L.tiles_ref = need_ref ? take(sizeof(Tile) * ntr) : 0;
     L.partials = take(sizeof(double) * 2 * kPartialSlots * std::max<long long>(nt, ntr));
     L.lanczos = take(lanczos_ws_bytes(nb, P));   // used with FTSP2_LANCZOS only
+    L.escr_ctas = defer ? (int)std::min<long long>(kMaxDeferCtas, 2 * nt) : 0;
+    L.escr = L.escr_ctas ? take((size_t)L.escr_ctas * kEpiScratchFloats * sizeof(float)) : 0;
     const int fmt = fmt_of_mode(mode);
     for (int c = 0; c < kMaxChains; ++c) {
         L.Z[c] = L.A[c] = L.OP[c][0] = L.OP[c][1] = L.OPR[c][0] = L.OPR[c][1] = 0;
@@ -601,6 +610,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
             la.tiles = pair ? tiles : tiles_ref;
             la.ntiles = pair ? L.ntiles : L.ntiles_ref;
             const int units = std::max(1, std::min(la.ntiles, pair ? di.sms / 2 : di.sms));
+            la.escr = pair && L.escr_ctas >= 2 * units ? reinterpret_cast<float*>(W + L.escr) : nullptr;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             {
                 std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -839,7 +849,7 @@ ftsp2_status ftsp2_workspace_size(const ftsp2_instance* inst, int nb, ftsp2_mode
     if (!bytes) return FTSP2_E_ARG;
     Layout L;
     // sized for the largest refinement setting so one workspace serves every flag
-    const ftsp2_status st = plan(inst, nb, mode, want, FTSP2_REFINE2 | FTSP2_REFINE_TC, L);
+    const ftsp2_status st = plan(inst, nb, mode, want, FTSP2_REFINE2 | FTSP2_REFINE_TC | FTSP2_EPI_DEFERRED, L);
     if (st != FTSP2_OK) return st;
     *bytes = L.total;
     return FTSP2_OK;

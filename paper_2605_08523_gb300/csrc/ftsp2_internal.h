@@ -29,6 +29,9 @@ constexpr int kMaxChains = 2;
 constexpr int kTileM = 128;                  // tensor-core tile rows (UMMA M)
 constexpr int kPad = 128;                    // matrix pitch granularity (elements)
 constexpr int kPartialSlots = 32;            // FP64 partial-sum slots per tile (last layer)
+constexpr int kEpiScratchFloats = 32768;     // deferred epilogue: finished sums of one CTA's tile
+constexpr int kMaxDeferCtas = 192;           // CTAs with a scratch slot in the workspace
+constexpr int kDeferMinK = 2048;             // default: deferred epilogue from this mean tile K
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;   // 4 s
 
 enum ChainKind : int { CHAIN_FERMI = 0, CHAIN_ENTROPY = 1 };
@@ -79,6 +82,8 @@ struct InstWork {
 struct Layout {
     // all offsets in bytes from the workspace base
     size_t inst_work, tiles, tiles_ref, partials, status, lanczos;
+    size_t escr;          // deferred-epilogue scratch (escr_ctas x kEpiScratchFloats floats)
+    int escr_ctas;        // 0: the pair tiles run their final epilogue inline
     size_t Z[kMaxChains], A[kMaxChains], OP[kMaxChains][2], OPR[kMaxChains][2];
     size_t total;
     size_t plane_elems;   // nb * P * P
@@ -196,6 +201,7 @@ struct LayerArgs {
     float* D;
     double* partials;
     int* status;
+    float* escr;                      // deferred final epilogue: kEpiScratchFloats per CTA, or null (inline)
 };
 
 struct TmaMaps {

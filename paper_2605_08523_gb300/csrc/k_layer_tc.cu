@@ -35,11 +35,23 @@
 // max|D - D_ref| = 1.85e-6 / 9.0e-7 / 6.9e-7 at layer times 0.235 / 0.251 /
 // 0.314 ms; 128 is the default.
 //
-// Warp roles (576 threads per CTA, persistent over the tile list):
+// Warp roles (576 threads per CTA, 640 with the deferred epilogue; persistent
+// over the tile list):
 //   warp 0 lane 0 : TMA producer (STAGES-deep ring of 128-byte K-slices)
 //   warp 1        : TMEM allocation; lane 0 of the even CTA issues tcgen05.mma
-//   warps 2..17   : epilogue; warp w reads TMEM lane quarter w % 4 and column
-//                   quarter (w - 2) / 4 of the CTA's 128-row accumulator.
+//   warps 2..17   : accumulating warps; warp w reads TMEM lane quarter w % 4
+//                   and column quarter (w - 2) / 4 of the CTA's 128-row
+//                   accumulator and adds the chunks in FP32 registers
+//   warps 18..19  : (deferred epilogue only) store warps.
+// Final epilogue of a tile (Z_{k+1}, A_{k+1}, next operands).  Inline: the
+// accumulating warps write the finished sum back into the last chunk's TMEM
+// buffer and run the epilogue from there while the MMAs of the next tile fill
+// the other buffer (one chunk ahead).  Deferred (pair tiles, long K): they
+// store the sum to a per-CTA scratch in global memory and go on with the next
+// tile at once; the two store warps stream scratch, Z_k and A_k through a small
+// shared ring (cp.async) and write the results while the next tile's MMAs run.
+// A unit's last tile always runs inline, so no store-warp tail follows the
+// last MMAs.
 // Every wait is bounded: on timeout the CTA sets FTSP2_E_TIMEOUT in the status
 // word and all roles leave their loops.
 #include <cuda_bf16.h>
@@ -86,8 +98,19 @@ struct Geo {
 };
 constexpr int kCtaRows = 128;
 constexpr int kEpiWarps = 16;
-constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kGrp = 8;                            // columns per epilogue group
+// Deferred final epilogue: store warps, their shared-memory staging ring
+// (entries of 16 columns x 32 rows: sums, Z_k, A_k) and the per-CTA scratch
+// of finished tile sums in global memory (one 32-row x 64-column block per
+// accumulating warp, in the blocked layout of the state).
+constexpr int kStoreWarps = 2;
+constexpr int kRing = 2;
+constexpr int kEntryBytes = 3 * 2048;
+constexpr int kItemFloats = 2048;
+static_assert(kEpiWarps * kItemFloats == kEpiScratchFloats, "scratch of one CTA");
+__host__ __device__ constexpr int threads_of(bool deferred) {
+    return 64 + 32 * (kEpiWarps + (deferred ? kStoreWarps : 0));
+}
 static_assert(kPartialSlots == 2 * kEpiWarps, "one partial-sum slot per epilogue warp of the pair");
 
 // split planes (s, t) of the products Z_s Z_t, in issue order
@@ -363,18 +386,42 @@ __device__ __forceinline__ void st_global_v8(void* dst, const uint32_t* w) {
                  : "memory");
 }
 
+// Where the final epilogue reads a group's sums S and state Z_k, A_k: the
+// sums from TMEM and the state from global memory (inline epilogue of the
+// accumulating warps), or all three from a shared-memory staging entry in
+// the blocked [half][lane][4] layout of the state (deferred epilogue).
+struct SrcTmem {
+    uint32_t tcol;
+    __device__ __forceinline__ void sums(int hh, float* v) const {
+        tmem_ld8(tcol + 8 * hh, reinterpret_cast<uint32_t*>(v));
+        tmem_wait_ld();
+    }
+    __device__ __forceinline__ void state(int, const float* Zg, const float* Ag, float* z, float* x) const {
+        load_state8(Zg, z);
+        load_state8(Ag, x);
+    }
+};
+struct SrcSmem {
+    const float* s;    // entry + lane * 4: sums, then Z_k, then A_k (512 floats each)
+    __device__ __forceinline__ void sums(int hh, float* v) const { load_state8(s + 256 * hh, v); }
+    __device__ __forceinline__ void state(int hh, const float*, const float*, float* z, float* x) const {
+        load_state8(s + 512 + 256 * hh, z);
+        load_state8(s + 1024 + 256 * hh, x);
+    }
+};
+
 // Final epilogue of a non-last layer on 16 columns c0 .. c0 + 15 (c0 % 16 == 0)
-// of row r, the sums S read from TMEM at tcol (8-column halves that do not
-// touch the triangle or the order are skipped):
+// of row r, the sums and the state read through src (8-column halves that do
+// not touch the triangle or the order are skipped):
 //   A_{k+1} = A_k + d_k Z_k,  Z_{k+1} = a_k S + (b_k + 2 a_k tau_k) Z_k,
 // then the operands of Z_{k+1} (times the FP16 scale 2^e_{k+1}) for the next
 // layer: direct (r, c), r <= c, as one 32-byte vector per plane and lane (full
 // sectors; 4-byte formats store two), and mirror (c, r), r < c, one element per
 // lane, so that for each column the warp's 32 stores are one contiguous run of
 // row c.
-template <int FMT>
+template <int FMT, class Src>
 __device__ __forceinline__ void epi_dgroup_next(const LayerArgs& a, const EpiLite& e, int n, int R0, int r, int c0,
-                                                uint32_t tcol) {
+                                                const Src& src) {
     using F = OpFmtT<FMT>;
     constexpr int ESZ = F::ESZ;
     constexpr int NPL = F::NPL;
@@ -386,15 +433,13 @@ __device__ __forceinline__ void epi_dgroup_next(const LayerArgs& a, const EpiLit
         const int cg = c0 + 8 * hh;
         if (!(cg < n && cg + kGrp - 1 >= R0)) continue;          // warp-uniform
         float v[8];
-        tmem_ld8(tcol + 8 * hh, reinterpret_cast<uint32_t*>(v));
-        tmem_wait_ld();
+        src.sums(hh, v);
         if (r >= n) continue;
         const size_t so = state_off(P, r, cg);
         float* const Zg = e.Z + so;
         float* const Ag = Zg + a.plane_elems;
         float z[8], zn[8];
-        load_state8(Zg, z);
-        load_state8(Ag, zn);
+        src.state(hh, Zg, Ag, z, zn);
 #pragma unroll
         for (int u = 0; u < 8; ++u) zn[u] = fmaf(e.d, z[u], zn[u]);
         store_state8(Ag, zn);
@@ -514,11 +559,67 @@ __device__ __forceinline__ void prefetch_tile_state(const LayerArgs& a, const Ti
 
 // ----------------------------------------------------------------------------------
 // OUTFMT: operand format written for the next layer, or kLastLayer.
-template <int MODE, int OUTFMT, bool PAIR>
-__global__ void __launch_bounds__(kThreads, 1)
+// 16-byte asynchronous global -> shared copies through the load/store path
+// (cp.async, L2 only): the store warps' loads do not queue behind the operand
+// tiles in the TMA unit.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// The persistent loop of a unit visits tiles t, t + nunits, ...: is there an
+// active tile after t?  (The last tile of a unit runs its final epilogue inline,
+// so that no store-warp tail follows the last MMAs.)
+__device__ __forceinline__ bool has_next_tile(const LayerArgs& a, int t, int nunits) {
+    for (int u = t + nunits; u < a.ntiles; u += nunits) {
+        int k;
+        if (tile_active(a, a.tiles[u], k)) return true;
+    }
+    return false;
+}
+
+// Work items of the deferred epilogue: item i (the block of accumulating warp
+// 2 + i) of a tile is 32 rows x EPI_COLS columns; its entries are the 16-column
+// groups that touch the triangle and the order.  A cursor (i, g) steps through
+// the items i = sw, sw + kStoreWarps, ... of store warp sw.
+struct ItemGeo {
+    int R0, C0, g_lo, g_hi;
+};
+template <int TILE, int EPI_COLS>
+__device__ __forceinline__ bool item_geo(const Tile& tl, int rank, int n, int i, ItemGeo& ig) {
+    const int q = (i + 2) & 3, cq = i >> 2;
+    ig.R0 = tl.I * TILE + rank * kCtaRows + q * 32;
+    ig.C0 = tl.J * TILE + cq * EPI_COLS;
+    if (!(ig.C0 < n && ig.C0 + EPI_COLS - 1 >= ig.R0 && ig.R0 < n)) return false;
+    ig.g_lo = ig.R0 > ig.C0 ? min(EPI_COLS / kGrp, (ig.R0 - ig.C0) / kGrp) : 0;
+    ig.g_hi = min(EPI_COLS / kGrp, (n - ig.C0 + kGrp - 1) / kGrp);
+    return true;
+}
+template <int TILE, int EPI_COLS>
+__device__ __forceinline__ bool next_entry(const Tile& tl, int rank, int n, int& i, int& g) {
+    while (i < kEpiWarps) {
+        ItemGeo ig;
+        if (item_geo<TILE, EPI_COLS>(tl, rank, n, i, ig)) {
+            const int gn = g < 0 ? (ig.g_lo & ~1) : g + 2;
+            if (gn < ig.g_hi) {
+                g = gn;
+                return true;
+            }
+        }
+        i += kStoreWarps;
+        g = -1;
+    }
+    return false;
+}
+
+template <int MODE, int OUTFMT, bool PAIR, bool DEFER>
+__global__ void __launch_bounds__(threads_of(DEFER), 1)
     layer_tc_kernel(const __grid_constant__ LayerArgs a, const __grid_constant__ TmaMaps maps) {
     using C = TcCfg<MODE>;
     using G = Geo<PAIR>;
+    static_assert(!(DEFER && OUTFMT == kLastLayer), "the last layer runs its epilogue inline");
     constexpr int TILE = G::TILE;
     constexpr int EPI_COLS = TILE / (kEpiWarps / 4);   // columns per epilogue warp (64 or 32)
     constexpr int BKE = 128 / C::ESIZE;                // K elements per 128-byte slice
@@ -535,6 +636,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ __align__(8) uint64_t empty_bar[C::STAGES];
     __shared__ __align__(8) uint64_t tfull_bar[NBUF];
     __shared__ __align__(8) uint64_t tempty_bar[NBUF];
+    // deferred epilogue: scratch full / empty
+    __shared__ __align__(8) uint64_t sfull_bar, sempty_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -553,6 +656,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = 0; s < NBUF; ++s) {
             mbar_init(&tfull_bar[s], 1);
             mbar_init(&tempty_bar[s], G::NCTA * kEpiWarps);
+        }
+        if constexpr (DEFER) {
+            mbar_init(&sfull_bar, kEpiWarps);
+            mbar_init(&sempty_bar, kStoreWarps);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -690,6 +797,84 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         __syncwarp();
+    } else if (DEFER && warp >= 2 + kEpiWarps) {
+        // ---------------- deferred final epilogue (store warps) ----------------
+        // Tile t's finished sums arrive in the CTA's scratch while the MMAs and
+        // the accumulating warps already work on tile t + 1.  Each lane streams
+        // its rows of the entries (sums, Z_k, A_k of 16 columns) into a
+        // two-deep shared ring with cp.async; the warp computes Z_{k+1},
+        // A_{k+1} and the next operands one entry at a time.
+        if constexpr (DEFER) {
+        const int sw = warp - 2 - kEpiWarps;
+        uint8_t* const ring = smem + C::STAGES * STAGE_BYTES + sw * (kRing * kEntryBytes);
+        const float* const scr = a.escr + (size_t)blockIdx.x * kEpiScratchFloats;
+        uint32_t sp = 0;
+        uint32_t used = 0;                       // entries consumed (ring slot)
+        bool ok = true;
+        for (int t = unit; t < a.ntiles && ok; t += nunits) {
+            const Tile tl = a.tiles[t];
+            int k;
+            if (!tile_active(a, tl, k)) continue;
+            if (!has_next_tile(a, t, nunits)) continue;     // inline in the accumulating warps
+            if (!wait_bar(&sfull_bar, sp, &abort_flag, a.status)) {
+                ok = false;
+                break;
+            }
+            sp ^= 1u;
+            const int n = a.inst[tl.inst].n;
+            EpiLite e;
+            make_lite<OUTFMT>(a, tl, k, MODE == FTSP2_FP16X2, e);
+            // each lane copies exactly the 16-byte runs it reads later (its row
+            // of the 8-column halves), so its own cp.async.wait_group suffices
+            auto issue = [&](int i, int g, uint32_t slot) {
+                ItemGeo ig;
+                item_geo<TILE, EPI_COLS>(tl, (int)rank, n, i, ig);
+                const int c0 = ig.C0 + kGrp * g;
+                const bool two = c0 + kGrp < n;          // second 8-column block inside the order
+                const uint32_t dst = smem_u32(ring + slot * kEntryBytes) + 16u * lane;
+                const float* ssrc = scr + i * kItemFloats + g * 256 + lane * 4;
+                const float* zsrc = e.Z + state_off(a.P, ig.R0, c0) + lane * 4;
+#pragma unroll
+                for (int o = 0; o < 512; o += 128) {
+                    cp_async16(dst + 4u * o, ssrc + o);
+                    if (o < 256 || two) {
+                        cp_async16(dst + 4u * (512 + o), zsrc + o);
+                        cp_async16(dst + 4u * (1024 + o), zsrc + a.plane_elems + o);
+                    }
+                }
+                cp_async_commit();
+            };
+            int ii = sw, gi = -1, iu = sw, gu = -1;
+            uint32_t pending = 0;                // copy groups in flight
+            bool more = next_entry<TILE, EPI_COLS>(tl, (int)rank, n, ii, gi);
+            for (uint32_t s = 0; s < (uint32_t)kRing && more; ++s) {
+                issue(ii, gi, (used + s) % kRing);
+                ++pending;
+                more = next_entry<TILE, EPI_COLS>(tl, (int)rank, n, ii, gi);
+            }
+            while (next_entry<TILE, EPI_COLS>(tl, (int)rank, n, iu, gu)) {
+                const uint32_t slot = used % kRing;
+                if (pending > 1) cp_async_wait<1>();
+                else cp_async_wait<0>();
+                --pending;
+                ItemGeo ig;
+                item_geo<TILE, EPI_COLS>(tl, (int)rank, n, iu, ig);
+                const SrcSmem src{reinterpret_cast<const float*>(ring + slot * kEntryBytes) + lane * 4};
+                epi_dgroup_next<OUTFMT>(a, e, n, ig.R0, ig.R0 + lane, ig.C0 + kGrp * gu, src);
+                __syncwarp();                    // every lane is done with the slot
+                ++used;
+                if (more) {
+                    issue(ii, gi, (used + kRing - 1) % kRing);
+                    ++pending;
+                    more = next_entry<TILE, EPI_COLS>(tl, (int)rank, n, ii, gi);
+                }
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) local_arrive(smem_u32(&sempty_bar));
+        }
+        }
+        __syncwarp();
     } else {
         // ---------------- epilogue (warps 2..17) ----------------
         const int q = warp & 3;                  // TMEM lane quarter
@@ -698,6 +883,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t tempty0 = PAIR ? map_to(smem_u32(&tempty_bar[0]), 0) : smem_u32(&tempty_bar[0]);
         int buf = 0;
         uint32_t aphase = 0;
+        uint32_t sp = 0;                         // scratch parity (deferred epilogue)
         bool ok = true;
         for (int t = unit; t < a.ntiles && ok; t += nunits) {
             // Only the chunk count and the liveness of the warp's block are
@@ -706,7 +892,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // (keeps the drain loop of a pair tile, with its 64 accumulator
             // registers, free of spills).
             int nch;
-            bool warp_live;
+            bool warp_live, defer_tile;
             {
                 const Tile tl = a.tiles[t];
                 int k;
@@ -716,6 +902,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int C0 = tl.J * TILE + cq * EPI_COLS;
                 warp_live = C0 < n && C0 + EPI_COLS - 1 >= R0 && R0 < n;
                 nch = ((n + BKE - 1) / BKE + ck - 1) / ck;
+                defer_tile = DEFER && has_next_tile(a, t, nunits);
             }
             float acc[EPI_COLS];
 #pragma unroll
@@ -737,15 +924,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t ta = tbase + (uint32_t)(buf * TILE);
                 if (warp_live) {
 #pragma unroll
-                    for (int g = 0; g < EPI_COLS / 8; ++g) {
-                        uint32_t v[8];
-                        tmem_ld8(ta + 8 * g, v);
+                    for (int g = 0; g < EPI_COLS / 16; ++g) {
+                        uint32_t v[16];
+                        tmem_ld16(ta + 16 * g, v);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) acc[8 * g + jj] += __uint_as_float(v[jj]);
+                        for (int jj = 0; jj < 16; ++jj) acc[16 * g + jj] += __uint_as_float(v[jj]);
                     }
                 }
-                if (j == nch - 1) {
+                if (j == nch - 1 && !defer_tile) {
                     if (warp_live) {
 #pragma unroll
                         for (int g = 0; g < EPI_COLS / 8; ++g) tmem_st8(ta + 8 * g, &acc[8 * g]);
@@ -765,6 +952,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             if (!ok) break;
+            if (defer_tile) {
+                // hand the finished sums to the store warps through the scratch
+                // (its previous tile must have been read), then go on to the next tile
+                if (!wait_bar(&sempty_bar, sp ^ 1u, &abort_flag, a.status)) break;
+                sp ^= 1u;
+                if (warp_live) {
+                    float* const dst = a.escr + (size_t)blockIdx.x * kEpiScratchFloats + (warp - 2) * kItemFloats + lane * 4;
+#pragma unroll
+                    for (int g = 0; g < EPI_COLS / 8; ++g) store_state8(dst + 256 * g, &acc[8 * g]);
+                }
+                __syncwarp();
+                if (lane == 0) local_arrive(smem_u32(&sfull_bar));
+                continue;
+            }
             const uint32_t tfin = tbase + (uint32_t)(buf * TILE);   // the held buffer
             const Tile tl = a.tiles[t];
             int k;
@@ -797,7 +998,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int g_hi = min(EPI_COLS / kGrp, (n - C0 + kGrp - 1) / kGrp);
 #pragma unroll 1
                     for (int g = g_lo & ~1; g < g_hi; g += 2)
-                        epi_dgroup_next<OUTFMT>(a, e, n, R0, r, C0 + kGrp * g, tfin + 8 * g);
+                        epi_dgroup_next<OUTFMT>(a, e, n, R0, r, C0 + kGrp * g, SrcTmem{tfin + 8 * g});
                 }
             }
             // release the held accumulator buffer
@@ -848,9 +1049,9 @@ int tc_block_n(int, int pair) { return pair ? Geo<true>::TILE : Geo<false>::TILE
 int tc_block_m(int, int pair) { return pair ? Geo<true>::TILE : Geo<false>::TILE; }
 
 template <int MODE>
-static int smem_of() {
+static int smem_of(bool deferred = false) {
     using C = TcCfg<MODE>;
-    return C::STAGES * C::NSPLIT * 2 * kCtaRows * 128 + 1024;
+    return C::STAGES * C::NSPLIT * 2 * kCtaRows * 128 + 1024 + (deferred ? kStoreWarps * kRing * kEntryBytes : 0);
 }
 
 int tc_smem_bytes(int mode) {
@@ -862,19 +1063,19 @@ int tc_smem_bytes(int mode) {
     return 0;
 }
 
-template <int MODE, int OUTFMT, bool PAIR>
+template <int MODE, int OUTFMT, bool PAIR, bool DEFER>
 static cudaError_t launch_variant(const LayerArgs& a, const TmaMaps& maps, int units, cudaStream_t s) {
-    const int smem = smem_of<MODE>();
+    const int smem = smem_of<MODE>(DEFER);
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(layer_tc_kernel<MODE, OUTFMT, PAIR>,
+        cudaError_t e = cudaFuncSetAttribute(layer_tc_kernel<MODE, OUTFMT, PAIR, DEFER>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(Geo<PAIR>::NCTA * units, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3(threads_of(DEFER), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -884,20 +1085,25 @@ static cudaError_t launch_variant(const LayerArgs& a, const TmaMaps& maps, int u
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = PAIR ? 1 : 0;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, layer_tc_kernel<MODE, OUTFMT, PAIR>, a, maps);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, layer_tc_kernel<MODE, OUTFMT, PAIR, DEFER>, a, maps);
     count_launch();
     return e;
 }
 
 template <int MODE, int MAINFMT, bool PAIR>
 static cudaError_t launch_shape(const LayerArgs& a, const TmaMaps& maps, int units, cudaStream_t s) {
-    if (a.last) return launch_variant<MODE, kLastLayer, PAIR>(a, maps, units, s);
-    if (a.next_fmt == OP_F32) return launch_variant<MODE, OP_F32, PAIR>(a, maps, units, s);
+    if (a.last) return launch_variant<MODE, kLastLayer, PAIR, false>(a, maps, units, s);
+    if (a.next_fmt == OP_F32) return launch_variant<MODE, OP_F32, PAIR, false>(a, maps, units, s);
     if constexpr (MAINFMT != OP_BF16X3) {
         // the layer before BF16X3 refinement layers (FTSP2_REFINE_TC)
-        if (a.next_fmt == OP_BF16X3) return launch_variant<MODE, OP_BF16X3, PAIR>(a, maps, units, s);
+        if (a.next_fmt == OP_BF16X3) return launch_variant<MODE, OP_BF16X3, PAIR, false>(a, maps, units, s);
     }
-    return launch_variant<MODE, MAINFMT, PAIR>(a, maps, units, s);
+    // the layers of the main format: the final epilogue inline or deferred to
+    // store warps (a.escr set: a scratch slot for each CTA of the grid)
+    if constexpr (PAIR) {
+        if (a.escr) return launch_variant<MODE, MAINFMT, PAIR, true>(a, maps, units, s);
+    }
+    return launch_variant<MODE, MAINFMT, PAIR, false>(a, maps, units, s);
 }
 
 template <int MODE, int MAINFMT>
