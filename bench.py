@@ -60,6 +60,10 @@ def parse():
     p.add_argument("--epilogue", default="auto", choices=["auto", "deferred", "inline"],
                    help="final epilogue of the pair tiles: the library's default, or forced "
                         "(FTSP2_EPI_DEFERRED / FTSP2_EPI_INLINE)")
+    p.add_argument("--table", default="printed", choices=["printed", "alt"],
+                   help="cfg1/cfg4 Fermi table: the paper's printed 26-layer table (with the trained entropy "
+                        "table), or the 26-layer beta0 = 1500 table of the one-term form (Eq. mlsp2_alt) "
+                        "trained by the library")
     p.add_argument("--refine-tc", action="store_true",
                    help="refinement layers as BF16X3 tensor-core layers (FTSP2_REFINE_TC)")
     p.add_argument("--workload", default="cfg1", choices=["cfg1", "cfg2", "cfg4"],
@@ -454,7 +458,7 @@ def main():
     # the paper's printed Fermi table with the entropy table the library's
     # trainer fitted for it (theta_entropy)
     tdir = os.path.join(ROOT, "paper_2605_08523_gb300", "tables")
-    tabs = [os.path.join(tdir, "entropy_b1500_L26.json")]
+    tabs = [os.path.join(tdir, "alt_b1500_L26.json" if args.table == "alt" else "entropy_b1500_L26.json")]
     if cfg4:
         # the long-range couplings widen the Gershgorin interval: beta' needs the
         # 34-layer beta0 = 3000 table
@@ -511,9 +515,8 @@ def main():
     trD = float(solver.trace[0, 0])
     err_Drec = err_Srec = None
     if Dref is not None:
-        with open(tabs[int(rec["model"])]) as fh:
-            tab_json = json.load(fh)
-        Drec, Srec = method_exact_gpu(eps, V, rec, tab_json, mu)
+        # the model set's table (one-term tables as their converted rows)
+        Drec, Srec = method_exact_gpu(eps, V, rec, ms.tables[int(rec["model"])], mu)
         err_Drec = float((D - Drec).abs().max())
         err_Srec = abs(S - Srec) / n
         del Drec
@@ -583,14 +586,16 @@ def main():
         "config": {"workload": ("cfg4 lattice %dx%dx%d with 5%% long-range couplings N(0,0.05) n=%d kT=%g "
                                 "mu=half filling, density+entropy, beta0=1500 and 3000 tables" if cfg4 else
                                 "cfg1 lattice %dx%dx%d n=%d kT=%g mu=half filling, density+entropy, "
-                                "printed 26-layer table + trained entropy table") % (dims + (n, kT)),
+                                + ("26-layer beta0=1500 table of the one-term form (Eq. mlsp2_alt)"
+                                   if args.table == "alt" else "printed 26-layer table + trained entropy table"))
+                                % (dims + (n, kT)),
                    "n": n, "kT": kT, "mu": mu, "layers": L, "mode": args.mode, "chains": 2,
                    "refine_layers_fp32": refine, "refine_on_tensor_cores": bool(args.refine_tc),
                    "model": int(rec["model"]), "bounds": args.bounds,
                    "e_min": float(rec["e_min"]), "e_max": float(rec["e_max"]),
                    "l2": "inputs and working set larger than L2 (no flush)", "parallelism": "replicas",
                    "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
-                   "epilogue": args.epilogue,
+                   "epilogue": args.epilogue, "table": args.table,
                    "autotune_ms": {"single": ms_single, "pair": ms_pair}},
         "tflops_alg": alg_flops / t_step / 1e12 * world,
         "density_only": {"value": world / t_density, "unit": "solves/s", "ms_per_step": t_density * 1e3},

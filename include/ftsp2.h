@@ -376,6 +376,30 @@ ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, dou
                                 ftsp2_train_report* rep, void* dWork, size_t work_bytes,
                                 void* stream);
 
+/* The one-term form of the recursion (Eq. mlsp2_alt).  A table of this form
+ * holds L + 1 rows (t_i1, t_i2), (L + 1) * 2 doubles: layers
+ * x_{i+1} = (t_i1 + x_i)^2, A_{i+1} = A_i + t_i2 x_i for i < L, and the output
+ * row (t_L1, t_L2) with f = A_L + t_L1 + t_L2 x_L (Eq. mlsp2_alt-output).
+ * ftsp2_alt_to_mlsp2 writes the L rows (a, b, c, d) of Eq. mlsp2 that compute
+ * the same function (the embedding of the Appendix on model embeddings):
+ * (1, 2 t_i1, t_i1^2, t_i2), with the last layer's (a, b, c) multiplied by
+ * t_L2 and t_L1 added to its c.  Such rows go into an ftsp2_table like any
+ * other; the layer kernels run them unchanged (their centred epilogue folds
+ * every term of a layer into one pass whichever form the table has).
+ * FTSP2_E_ARG for L outside 1..64 or non-finite entries. */
+ftsp2_status ftsp2_alt_to_mlsp2(int L, const double* alt, double* theta_out);
+
+/* Levenberg-Marquardt training in the one-term form: as ftsp2_train_coeffs,
+ * with alt_init / alt_out (host) of (L + 1) * 2 doubles.  The GPU computes the
+ * Eq. mlsp2 Jacobian of the mapped table and its reductions J^T J, J^T r; the
+ * host applies the chain rule of ftsp2_alt_to_mlsp2 (P^T J^T J P, P^T J^T r,
+ * P = d theta / d t) and solves for the 2L + 2 parameters.  Same workspace
+ * (ftsp2_train_workspace_size(nsamples, L)). */
+ftsp2_status ftsp2_train_coeffs_alt(int target, double beta0, double mu0, int L, double alpha,
+                                    const double* dX, int nsamples, int iterations, int accel,
+                                    const double* alt_init, double* alt_out, ftsp2_train_report* rep,
+                                    void* dWork, size_t work_bytes, void* stream);
+
 /* Building blocks of one LM iteration, exposed for parity tests.
  * ftsp2_train_residual_jacobian: residuals dR[nsamples] = model(theta) - target
  * and (if dM != NULL) the augmented Jacobian dM[(4L+1) * nsamples],

@@ -28,7 +28,8 @@ from ._lib import (BF16X3, CLAMP, EPI_DEFERRED, EPI_INLINE, FP16X2, FP32, LANCZO
                    TARGET_ENTROPY, TARGET_FERMI, TF32X3, Ftsp2Error, Instance, RescaleRec, Table, TrainReport,
                    check, lib, status_string)
 
-__all__ = ["ModelSet", "Solver", "ftsp2_rescale", "ftsp2_train_coeffs", "ftsp2_train_residual_jacobian",
+__all__ = ["ModelSet", "Solver", "ftsp2_rescale", "ftsp2_train_coeffs", "ftsp2_train_coeffs_alt", "ftsp2_alt_to_mlsp2",
+           "ftsp2_train_residual_jacobian",
            "ftsp2_train_normal_equations", "ftsp2_autotune_clear", "kernel_launch_count", "profile_layers",
            "profile_read", "MODES", "FP32", "TF32X3", "BF16X3", "FP16X2", "SYNC", "CLAMP", "REFINE1", "REFINE2",
            "PAIR_TILES", "SINGLE_TILES", "LANCZOS", "MIN_LAYERS", "REFINE_TC", "EPI_DEFERRED", "EPI_INLINE", "TARGET_FERMI", "TARGET_ENTROPY", "Ftsp2Error", "status_string", "lib",
@@ -74,7 +75,10 @@ def profile_read():
 class ModelSet:
     """A set of trained tables (Sec. III A 2).  ``tables`` is a list of dicts
     with keys theta ((L, 4) rows a, b, c, d), beta0, mu0, alpha and optionally
-    theta_entropy; ``None`` gives the paper's printed 26-layer table."""
+    theta_entropy; ``None`` gives the paper's printed 26-layer table.  A table
+    of the one-term form (Eq. mlsp2_alt) gives ``alt`` ((L + 1, 2) rows) instead
+    of theta (and ``alt_entropy`` instead of theta_entropy); it is converted by
+    ftsp2_alt_to_mlsp2."""
 
     def __init__(self, tables=None):
         self._h = C.c_void_p()
@@ -84,7 +88,13 @@ class ModelSet:
             self.tables = None
             return
         arr = (Table * len(tables))()
+        conv = []
         for i, t in enumerate(tables):
+            if t.get("theta") is None and t.get("alt") is not None:
+                t = dict(t, theta=ftsp2_alt_to_mlsp2(t["alt"]).tolist())
+            if t.get("theta_entropy") is None and t.get("alt_entropy") is not None:
+                t = dict(t, theta_entropy=ftsp2_alt_to_mlsp2(t["alt_entropy"]).tolist())
+            conv.append(t)
             th = np.ascontiguousarray(np.asarray(t["theta"], dtype=np.float64).reshape(-1, 4))
             self._keep.append(th)
             arr[i].L = th.shape[0]
@@ -102,7 +112,7 @@ class ModelSet:
                 arr[i].L_entropy = 0
                 arr[i].theta_entropy = None
         check(lib().ftsp2_model_set_create(arr, len(tables), C.byref(self._h)), "ftsp2_model_set_create")
-        self.tables = tables
+        self.tables = conv
 
     @classmethod
     def from_json(cls, paths):
@@ -113,8 +123,9 @@ class ModelSet:
         for p in paths:
             with open(p) as f:
                 d = json.load(f)
-            tabs.append(dict(theta=d["theta"], beta0=d["beta0"], mu0=d["mu0"], alpha=d.get("alpha", 0.842704),
-                             theta_entropy=d.get("theta_entropy")))
+            tabs.append(dict(theta=d.get("theta"), alt=d.get("alt"), beta0=d["beta0"], mu0=d["mu0"],
+                             alpha=d.get("alpha", 0.842704), theta_entropy=d.get("theta_entropy"),
+                             alt_entropy=d.get("alt_entropy")))
         return cls(tabs)
 
     @property
@@ -361,6 +372,37 @@ def ftsp2_train_normal_equations(M, L, stream=None):
     check(lib().ftsp2_train_normal_equations(_ptr(M), ns, L, _ptr(G), _ptr(ws), wb, _stream(stream)),
           "ftsp2_train_normal_equations")
     return G
+
+
+def ftsp2_alt_to_mlsp2(alt):
+    """Rows (a, b, c, d) (numpy (L, 4)) of Eq. mlsp2 computing the same function
+    as the one-term table alt ((L + 1, 2) rows, Eq. mlsp2_alt)."""
+    a = np.ascontiguousarray(np.asarray(alt, dtype=np.float64).reshape(-1, 2))
+    L = a.shape[0] - 1
+    out = np.zeros((max(L, 1), 4))
+    check(lib().ftsp2_alt_to_mlsp2(L, a.ctypes.data_as(C.POINTER(C.c_double)),
+                                   out.ctypes.data_as(C.POINTER(C.c_double))), "ftsp2_alt_to_mlsp2")
+    return out
+
+
+def ftsp2_train_coeffs_alt(target, beta0, mu0, alt_init, x, iterations=100, accel=True, alpha=1.0, stream=None):
+    """Levenberg-Marquardt fit of a one-term table (Eq. mlsp2_alt) on the GPU.
+    x: CUDA float64 samples.  Returns (alt (L + 1, 2) numpy, report dict)."""
+    torch = _torch()
+    a0 = np.ascontiguousarray(np.asarray(alt_init, dtype=np.float64).reshape(-1, 2))
+    L = a0.shape[0] - 1
+    ns = x.numel()
+    out = np.zeros_like(a0)
+    wb = lib().ftsp2_train_workspace_size(ns, L)
+    ws = torch.empty(wb, dtype=torch.uint8, device=x.device)
+    rep = TrainReport()
+    check(lib().ftsp2_train_coeffs_alt(int(target), float(beta0), float(mu0), L, float(alpha), _ptr(x), ns,
+                                       int(iterations), int(bool(accel)),
+                                       a0.ctypes.data_as(C.POINTER(C.c_double)),
+                                       out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep), _ptr(ws), wb,
+                                       _stream(stream)), "ftsp2_train_coeffs_alt")
+    return out, dict(iterations=rep.iterations, accepted=rep.accepted, cost0=rep.cost0, cost=rep.cost,
+                     max_err=rep.max_err, lam=rep.lam)
 
 
 def ftsp2_train_coeffs(target, beta0, mu0, theta_init, x, iterations=100, accel=True, alpha=1.0, stream=None):

@@ -1167,15 +1167,76 @@ ftsp2_status ftsp2_train_normal_equations(const double* dM, int nsamples, int L,
     return from_cuda(launch_train_gram(dM, nsamples, 4 * L, dG, dPart, tl.nchunks, static_cast<cudaStream_t>(stream)));
 }
 
-ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, double alpha, const double* dX,
-                                int nsamples, int iterations, int accel, const double* theta_init,
-                                double* theta_out, ftsp2_train_report* rep, void* dWork, size_t work_bytes,
-                                void* stream) {
-    if ((target != FTSP2_TARGET_FERMI && target != FTSP2_TARGET_ENTROPY) || !dX || nsamples < 1 || !theta_out ||
-        !dWork || iterations < 0)
+// ---- parameterisations of the trained table ---------------------------------
+// The LM loop runs on a parameter vector p.  Eq. mlsp2 tables: p = theta (4L).
+// One-term form (Eq. mlsp2_alt): p = (t_01, t_02, ..., t_L1, t_L2) (2L + 2),
+// theta(p) by ftsp2_alt_to_mlsp2 and the Jacobian P = d theta / d p, so that
+// J_p = J P and the reductions transform as P^T (J^T J) P and P^T (J^T r).
+enum { FORM_MLSP2 = 0, FORM_ALT = 1 };
+
+static int form_params(int form, int L) { return form == FORM_ALT ? 2 * L + 2 : 4 * L; }
+
+static void alt_rows(int L, const double* alt, double* th) {
+    for (int i = 0; i < L; ++i) {
+        const double t1 = alt[2 * i], t2 = alt[2 * i + 1];
+        th[4 * i + 0] = 1.0;
+        th[4 * i + 1] = 2.0 * t1;
+        th[4 * i + 2] = t1 * t1;
+        th[4 * i + 3] = t2;
+    }
+    const double u = alt[2 * L], w = alt[2 * L + 1];
+    double* last = th + 4 * (L - 1);
+    last[0] *= w;
+    last[1] *= w;
+    last[2] = last[2] * w + u;
+}
+
+// P (4L x np, row-major) at p
+static void form_jacobian(int form, int L, const double* p, std::vector<double>& P) {
+    const int np = form_params(form, L), nt = 4 * L;
+    P.assign((size_t)nt * np, 0.0);
+    if (form == FORM_MLSP2) {
+        for (int i = 0; i < nt; ++i) P[(size_t)i * np + i] = 1.0;
+        return;
+    }
+    const double w = p[2 * L + 1];
+    for (int i = 0; i < L; ++i) {
+        const double t1 = p[2 * i];
+        const double sc = i == L - 1 ? w : 1.0;
+        P[(size_t)(4 * i + 1) * np + 2 * i] = 2.0 * sc;
+        P[(size_t)(4 * i + 2) * np + 2 * i] = 2.0 * t1 * sc;
+        P[(size_t)(4 * i + 3) * np + 2 * i + 1] = 1.0;
+    }
+    const double t1 = p[2 * (L - 1)];
+    const int r = 4 * (L - 1);
+    P[(size_t)(r + 0) * np + 2 * L + 1] = 1.0;
+    P[(size_t)(r + 1) * np + 2 * L + 1] = 2.0 * t1;
+    P[(size_t)(r + 2) * np + 2 * L + 1] = t1 * t1;
+    P[(size_t)(r + 2) * np + 2 * L] = 1.0;
+}
+
+static ftsp2_status form_theta(int form, int L, const double* p, ThetaParam& tp) {
+    if (form == FORM_MLSP2) return load_theta(L, p, tp);
+    if (!p || L < 1 || L > kMaxLayers) return FTSP2_E_ARG;
+    for (int i = 0; i < 2 * L + 2; ++i)
+        if (!std::isfinite(p[i])) return FTSP2_E_ARG;
+    std::memset(&tp, 0, sizeof(tp));
+    alt_rows(L, p, tp.v);
+    return FTSP2_OK;
+}
+
+// Levenberg-Marquardt (optionally geodesic-accelerated) on p; residuals, the
+// Jacobian of theta and J^T J, J^T r run on the GPU, the rest on the host.
+static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int L, double alpha, const double* dX,
+                             int nsamples, int iterations, int accel, const double* p_init, double* p_out,
+                             ftsp2_train_report* rep, void* dWork, size_t work_bytes, void* stream) {
+    if ((target != FTSP2_TARGET_FERMI && target != FTSP2_TARGET_ENTROPY) || !dX || nsamples < 1 || !p_out ||
+        !dWork || iterations < 0 || !p_init)
         return FTSP2_E_ARG;
+    const int np = form_params(form, L), nt = 4 * L;
+    std::vector<double> p(p_init, p_init + np);
     ThetaParam tp;
-    ftsp2_status st = load_theta(L, theta_init, tp);
+    ftsp2_status st = form_theta(form, L, p.data(), tp);
     if (st != FTSP2_OK) return st;
     const TrainLayout tl = train_layout(nsamples, L);
     if (work_bytes < tl.total) return FTSP2_E_WORKSPACE;
@@ -1190,32 +1251,49 @@ ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, dou
     double* dV = reinterpret_cast<double*>(W + tl.v);
     double* dOut = reinterpret_cast<double*>(W + tl.out);
     double* dAm = reinterpret_cast<double*>(W + tl.amax);
-    const int np = 4 * L, m = np + 1;
-    std::vector<double> G((size_t)m * m), Gc((size_t)m * m);
+    const int mt = nt + 1;
+    std::vector<double> Gt((size_t)mt * mt);
 
-    auto eval = [&](const ThetaParam& t, std::vector<double>& g) -> ftsp2_status {
+    // JTJ (np x np), g = J^T r (np) and the cost at p; P at p in Pj
+    std::vector<double> JTJ((size_t)np * np), g(np), Pj;
+    auto eval = [&](const ThetaParam& t, const double* pp, std::vector<double>& jtj, std::vector<double>& gg,
+                    std::vector<double>& Pm, double& cst) -> ftsp2_status {
         if (launch_train_fwd_jac(target, beta0, mu0, L, alpha, t, dX, nsamples, dRr, dM, s) != cudaSuccess)
             return FTSP2_E_CUDA;
-        if (launch_train_gram(dM, nsamples, np, dG, dPart, tl.nchunks, s) != cudaSuccess) return FTSP2_E_CUDA;
-        if (cudaMemcpyAsync(g.data(), dG, sizeof(double) * m * m, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        if (launch_train_gram(dM, nsamples, nt, dG, dPart, tl.nchunks, s) != cudaSuccess) return FTSP2_E_CUDA;
+        if (cudaMemcpyAsync(Gt.data(), dG, sizeof(double) * mt * mt, cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return FTSP2_E_CUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return FTSP2_E_CUDA;
+        form_jacobian(form, L, pp, Pm);
+        cst = 0.5 * Gt[(size_t)nt * mt + nt];
+        std::vector<double> GP((size_t)nt * np, 0.0);   // (J^T J) P
+        for (int i = 0; i < nt; ++i)
+            for (int k = 0; k < nt; ++k) {
+                const double v = Gt[(size_t)i * mt + k];
+                if (v == 0.0) continue;
+                for (int j = 0; j < np; ++j) GP[(size_t)i * np + j] += v * Pm[(size_t)k * np + j];
+            }
+        jtj.assign((size_t)np * np, 0.0);
+        gg.assign(np, 0.0);
+        for (int k = 0; k < nt; ++k)
+            for (int i = 0; i < np; ++i) {
+                const double pk = Pm[(size_t)k * np + i];
+                if (pk == 0.0) continue;
+                for (int j = 0; j < np; ++j) jtj[(size_t)i * np + j] += pk * GP[(size_t)k * np + j];
+                gg[i] += pk * Gt[(size_t)k * mt + nt];
+            }
         return FTSP2_OK;
     };
 
-    st = eval(tp, G);
+    double cost = 0.0;
+    st = eval(tp, p.data(), JTJ, g, Pj, cost);
     if (st != FTSP2_OK) return st;
-    double cost = 0.5 * G[(size_t)np * m + np];
     const double cost0 = cost;
     double lam = 1e-3;
     int accepted = 0, it = 0;
     const double h = 0.1;
-    std::vector<double> JTJ((size_t)np * np), g(np), Md((size_t)np * np), v, a, rhs(np);
+    std::vector<double> Md((size_t)np * np), v, a, rhs(np), JTJc, gc, Pc, vt(nt);
     for (it = 0; it < iterations; ++it) {
-        for (int i = 0; i < np; ++i) {
-            for (int j = 0; j < np; ++j) JTJ[(size_t)i * np + j] = G[(size_t)i * m + j];
-            g[i] = G[(size_t)i * m + np];
-        }
         Md = JTJ;
         for (int i = 0; i < np; ++i) Md[(size_t)i * np + i] += lam * JTJ[(size_t)i * np + i];
         for (int i = 0; i < np; ++i) rhs[i] = -g[i];
@@ -1223,18 +1301,31 @@ ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, dou
             lam = std::min(lam * 10.0, 1e12);
             continue;
         }
-        ThetaParam cand = tp;
         std::vector<double> step = v;
         if (accel) {
-            ThetaParam th_h = tp;
-            for (int i = 0; i < np; ++i) th_h.v[i] += h * v[i];
+            // second directional derivative of r along p + tau v, by finite
+            // differences at tau = h, with J v = J (P v) from the stored Jacobian
+            std::vector<double> ph(p);
+            for (int i = 0; i < np; ++i) ph[i] += h * v[i];
+            ThetaParam th_h;
+            if (form_theta(form, L, ph.data(), th_h) != FTSP2_OK) return FTSP2_E_ARG;
+            for (int k = 0; k < nt; ++k) {
+                double acc = 0.0;
+                for (int j = 0; j < np; ++j) acc += Pj[(size_t)k * np + j] * v[j];
+                vt[k] = acc;
+            }
+            std::vector<double> rt(nt);
             if (launch_train_residual(target, beta0, mu0, L, alpha, th_h, dX, nsamples, dRh, s) != cudaSuccess ||
-                cudaMemcpyAsync(dV, v.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-                launch_train_accel(dM, dV, dRh, h, nsamples, np, dAp, dOut, s) != cudaSuccess ||
-                cudaMemcpyAsync(rhs.data(), dOut, sizeof(double) * np, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaMemcpyAsync(dV, vt.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                launch_train_accel(dM, dV, dRh, h, nsamples, nt, dAp, dOut, s) != cudaSuccess ||
+                cudaMemcpyAsync(rt.data(), dOut, sizeof(double) * nt, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                 cudaStreamSynchronize(s) != cudaSuccess)
                 return FTSP2_E_CUDA;
-            for (int i = 0; i < np; ++i) rhs[i] = -rhs[i];
+            for (int i = 0; i < np; ++i) {
+                double acc = 0.0;
+                for (int k = 0; k < nt; ++k) acc += Pj[(size_t)k * np + i] * rt[k];
+                rhs[i] = -acc;
+            }
             if (chol_solve(Md, np, rhs, a)) {
                 double na = 0, nv = 0;
                 for (int i = 0; i < np; ++i) {
@@ -1245,13 +1336,20 @@ ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, dou
                     for (int i = 0; i < np; ++i) step[i] = v[i] + 0.5 * a[i];
             }
         }
-        for (int i = 0; i < np; ++i) cand.v[i] += step[i];
-        st = eval(cand, Gc);
-        if (st != FTSP2_OK) return st;
-        const double cc = 0.5 * Gc[(size_t)np * m + np];
+        std::vector<double> pc(p);
+        for (int i = 0; i < np; ++i) pc[i] += step[i];
+        ThetaParam cand;
+        double cc = INFINITY;
+        if (form_theta(form, L, pc.data(), cand) == FTSP2_OK) {
+            st = eval(cand, pc.data(), JTJc, gc, Pc, cc);
+            if (st != FTSP2_OK) return st;
+        }
         if (std::isfinite(cc) && cc < cost) {
+            p.swap(pc);
             tp = cand;
-            G.swap(Gc);
+            JTJ.swap(JTJc);
+            g.swap(gc);
+            Pj.swap(Pc);
             cost = cc;
             lam = std::max(lam / 10.0, 1e-12);
             ++accepted;
@@ -1267,7 +1365,7 @@ ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, dou
     if (cudaMemcpyAsync(&mx, dAm, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return FTSP2_E_CUDA;
-    for (int i = 0; i < np; ++i) theta_out[i] = tp.v[i];
+    for (int i = 0; i < np; ++i) p_out[i] = p[i];
     if (rep) {
         rep->iterations = it;
         rep->accepted = accepted;
@@ -1276,6 +1374,29 @@ ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, dou
         rep->max_err = mx;
         rep->lambda = lam;
     }
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, double alpha, const double* dX,
+                                int nsamples, int iterations, int accel, const double* theta_init,
+                                double* theta_out, ftsp2_train_report* rep, void* dWork, size_t work_bytes,
+                                void* stream) {
+    return lm_train(FORM_MLSP2, target, beta0, mu0, L, alpha, dX, nsamples, iterations, accel, theta_init, theta_out,
+                    rep, dWork, work_bytes, stream);
+}
+
+ftsp2_status ftsp2_train_coeffs_alt(int target, double beta0, double mu0, int L, double alpha, const double* dX,
+                                    int nsamples, int iterations, int accel, const double* alt_init, double* alt_out,
+                                    ftsp2_train_report* rep, void* dWork, size_t work_bytes, void* stream) {
+    return lm_train(FORM_ALT, target, beta0, mu0, L, alpha, dX, nsamples, iterations, accel, alt_init, alt_out, rep,
+                    dWork, work_bytes, stream);
+}
+
+ftsp2_status ftsp2_alt_to_mlsp2(int L, const double* alt, double* theta_out) {
+    if (!alt || !theta_out || L < 1 || L > kMaxLayers) return FTSP2_E_ARG;
+    for (int i = 0; i < 2 * L + 2; ++i)
+        if (!std::isfinite(alt[i])) return FTSP2_E_ARG;
+    alt_rows(L, alt, theta_out);
     return FTSP2_OK;
 }
 

@@ -10,6 +10,9 @@ Two groups of tables:
 * the training sweep of L in {16, 24, 32} layers at scaled temperatures
   kT0 in [0.005, 0.05] (beta0 in {20, 50, 100, 200}, mu0 = 1/3): a Fermi table
   from the SP2 initial guess, then an entropy table started from it;
+* ``--alt``: tables of the one-term form (Eq. mlsp2_alt) at (beta0, L) =
+  (1500, 26) and (100, 16), from the SP2 sequence in that form
+  (ftsp2_train_coeffs_alt), with entropy tables started from them;
 * ``--high``: tables at beta0 in {3000, 6000, 12000, 24000} with
   L = ceil(layer count (Eq. layer count)) + 2 layers, which ragged batches of
   rotated spectra need once the Gershgorin width inflates beta'.
@@ -73,6 +76,34 @@ def main_high(outdir: str, iterations: int = 3000):
     return out
 
 
+def main_alt(outdir: str, iterations: int = 3000):
+    import paper_2605_08523_gb300 as ft
+    from .build import build
+    build()
+    os.makedirs(outdir, exist_ok=True)
+    out = {}
+    for beta0, L in ((1500.0, 26), (100.0, 16)):
+        t0 = time.time()
+        alt, rep = training.train_alt_table(ft, ft.TARGET_FERMI, beta0, MU0, L, iterations=iterations)
+        rep["seconds"] = time.time() - t0
+        th = ft.ftsp2_alt_to_mlsp2(alt)
+        rep["max_err_grid"] = max_error(ft, ft.TARGET_FERMI, beta0, MU0, th, 1.0)
+        t0 = time.time()
+        alts, reps = training.train_alt_table(ft, ft.TARGET_ENTROPY, beta0, MU0, L, alpha=ALPHA,
+                                              iterations=iterations, alt_init=alt)
+        reps["seconds"] = time.time() - t0
+        reps["max_err_grid"] = max_error(ft, ft.TARGET_ENTROPY, beta0, MU0, ft.ftsp2_alt_to_mlsp2(alts), ALPHA)
+        name = "alt_b%d_L%d" % (int(beta0), L)
+        out[name] = dict(beta0=beta0, mu0=MU0, alpha=ALPHA, L=L, form="one-term (Eq. mlsp2_alt)",
+                         alt=alt.tolist(), alt_entropy=alts.tolist(),
+                         fit=dict(max_err_fermi=rep["max_err_grid"], max_err_entropy=reps["max_err_grid"]),
+                         train=dict(fermi=rep, entropy=reps, samples=100_000, density="1+|f'|"))
+        print(name, out[name]["fit"], flush=True)
+        with open(os.path.join(outdir, name + ".json"), "w") as f:
+            json.dump(out[name], f, indent=1)
+    return out
+
+
 def main(outdir: str, iterations: int = 800, quick: bool = False):
     import paper_2605_08523_gb300 as ft
     from .build import build
@@ -113,7 +144,9 @@ def main(outdir: str, iterations: int = 800, quick: bool = False):
 if __name__ == "__main__":
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
     outdir = args[0] if args else "tables_out"
-    if "--high" in sys.argv:
+    if "--alt" in sys.argv:
+        main_alt(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)
+    elif "--high" in sys.argv:
         main_high(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)
     else:
         main(outdir, iterations=int(args[1]) if len(args) > 1 else 800, quick="--quick" in sys.argv)

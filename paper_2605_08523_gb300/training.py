@@ -79,6 +79,34 @@ def sp2_init(L: int, beta0: float, mu0: float):
     return th
 
 
+def sp2_alt_init(L: int, mu0: float):
+    """(L + 1, 2) table of the one-term form (Eq. mlsp2_alt) computing the SP2
+    sequence at mu0 exactly: the state y is x or 1 - x, and both branches are
+    squares, X^2 = (0 + y)^2 and 1 - (2X - X^2) = (-1 + y)^2 (or the same with
+    the roles of the offsets swapped when y = 1 - x); the output row undoes a
+    final y = 1 - x."""
+    alt = np.zeros((L + 1, 2))
+    flipped = False
+    for i, s in enumerate(sp2_sequence(mu0, L)):
+        if s > 0:
+            alt[i, 0] = -1.0 if flipped else 0.0
+            flipped = False
+        else:
+            alt[i, 0] = 0.0 if flipped else -1.0
+            flipped = True
+    alt[L] = (1.0, -1.0) if flipped else (0.0, 1.0)
+    return alt
+
+
+def train_alt_table(ft, target: int, beta0: float, mu0: float, L: int, alpha: float = 1.0, iterations: int = 500,
+                    nsamples: int = 100_000, alt_init=None, accel: bool = True, device="cuda"):
+    """Fit a table of the one-term form on the GPU (ftsp2_train_coeffs_alt)."""
+    import torch
+    x = torch.from_numpy(sample_points(nsamples, beta0, mu0)).to(device)
+    a0 = sp2_alt_init(L, mu0) if alt_init is None else np.asarray(alt_init, dtype=np.float64)
+    return ft.ftsp2_train_coeffs_alt(target, beta0, mu0, a0, x, iterations=iterations, accel=accel, alpha=alpha)
+
+
 def train_table(ft, target: int, beta0: float, mu0: float, L: int, alpha: float = 1.0, iterations: int = 500,
                 nsamples: int = 100_000, theta_init=None, accel: bool = True, device="cuda"):
     """Fit a table on the GPU (ftsp2_train_coeffs).  Returns (theta, report)."""

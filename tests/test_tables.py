@@ -10,7 +10,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import tables, train
+from oracle import altform, tables, train
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 FILES = sorted(glob.glob(os.path.join(ROOT, "paper_2605_08523_gb300", "tables", "*.json")))
@@ -32,12 +32,19 @@ def test_tables_present():
 @pytest.mark.parametrize("path", FILES, ids=[os.path.basename(f) for f in FILES])
 def test_table_fit_errors(path):
     d = json.load(open(path))
-    th = np.array(d["theta"])
-    ths = np.array(d["theta_entropy"])
-    assert th.shape == (d["L"], 4) and ths.shape == (d["L"], 4)
     b0, m0, al = d["beta0"], d["mu0"], d["alpha"]
-    ef = train.max_error(th, "fermi", b0, m0, 1.0, grid=400001)
-    es = train.max_error(ths, "entropy", b0, m0, al, grid=400001)
+    if "alt" in d:
+        # one-term form (Eq. mlsp2_alt): evaluated with the oracle's own recursion of that form
+        a, ae = np.array(d["alt"]), np.array(d["alt_entropy"])
+        assert a.shape == (d["L"] + 1, 2) and ae.shape == (d["L"] + 1, 2)
+        ef = altform.max_error(a, "fermi", b0, m0, 1.0, grid=400001)
+        es = altform.max_error(ae, "entropy", b0, m0, al, grid=400001)
+    else:
+        th = np.array(d["theta"])
+        ths = np.array(d["theta_entropy"])
+        assert th.shape == (d["L"], 4) and ths.shape == (d["L"], 4)
+        ef = train.max_error(th, "fermi", b0, m0, 1.0, grid=400001)
+        es = train.max_error(ths, "entropy", b0, m0, al, grid=400001)
     # the recorded GPU figures agree with the oracle's evaluation
     assert ef == pytest.approx(d["fit"]["max_err_fermi"], rel=0.05, abs=1e-9)
     assert es == pytest.approx(d["fit"]["max_err_entropy"], rel=0.05, abs=1e-9)
@@ -51,6 +58,13 @@ def test_entropy_table_for_printed_weights():
     # Table entropy: theta_fermi 1.24e-3; training theta_entropy improves it by orders of magnitude
     assert abs(e_fermi - 1.24e-3) < 1e-5
     assert es < 1e-6
+
+
+def test_one_term_tables():
+    # trained in the one-term form from the SP2 sequence; the fit reaches ~1e-5
+    for name in ("alt_b1500_L26", "alt_b100_L16"):
+        d = load(name)
+        assert d["fit"]["max_err_fermi"] < 3e-5 and d["fit"]["max_err_entropy"] < 3e-5, name
 
 
 def test_training_sweep_layer_count():
