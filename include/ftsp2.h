@@ -130,13 +130,29 @@ typedef struct {
     double kT;          /* electronic temperature (eV), > 0                   */
 } ftsp2_instance;
 
-/* One trained model (Sec. III A 2, "a set of models").  theta holds L rows
- * (a, b, c, d) = (theta_i1, theta_i2, theta_i3, theta_i4) of Eq. mlsp2, acting
- * on the layer-0 input x0 = H0 without an inner flip and approximating
- * 1/(1 + exp(-beta0 (x - mu0))) on [0, 1].  theta_entropy holds L_entropy rows
- * of the entropy recursion (Eq. entropy expansion) or is NULL to reuse theta
- * (the theta_fermi strategy).  alpha is the entropy input scale of
- * Eq. entropy expansion.  All pointers are host pointers, copied at creation. */
+/* One trained model (Sec. III A 2, "a set of models").
+ *
+ * family FTSP2_FAMILY_MLSP2: theta holds L rows (a, b, c, d) = (theta_i1,
+ * theta_i2, theta_i3, theta_i4) of Eq. mlsp2, acting on the layer-0 input
+ * x0 = H0 without an inner flip and approximating 1/(1 + exp(-beta0 (x - mu0)))
+ * on [0, 1].
+ *
+ * family FTSP2_FAMILY_SKIP: Skip-SP2 (Sec. II A 3) with one stored layer and
+ * one accumulator; theta holds L + 1 rows of 4 doubles: layer rows
+ * (delta_i, alpha_i, beta_i, gamma_i) with u_i = delta_i + alpha_i x_i +
+ * beta_i A_i, A_{i+1} = A_i + gamma_i x_i, x_{i+1} = u_i^2, and the output row
+ * (A_0, gamma_L, 0, 0): the accumulator starts at A_0 and
+ * f = A_L + gamma_L x_L.  The accumulator feeding back into the squared
+ * combination (beta_i) is what the family adds; beta = 0 covers Eq. mlsp2
+ * through the embedding of the Appendix on model embeddings.
+ *
+ * theta_entropy holds the entropy recursion's rows (Eq. entropy expansion) in
+ * the same family (L_entropy layers) or is NULL to reuse theta (the
+ * theta_fermi strategy).  alpha is the entropy input scale of Eq. entropy
+ * expansion.  All pointers are host pointers, copied at creation.  A set may
+ * mix families. */
+#define FTSP2_FAMILY_MLSP2 0
+#define FTSP2_FAMILY_SKIP  1
 typedef struct {
     int32_t L;
     int32_t L_entropy;
@@ -145,6 +161,8 @@ typedef struct {
     double alpha;
     const double* theta;
     const double* theta_entropy;
+    int32_t family;          /* FTSP2_FAMILY_*                               */
+    int32_t reserved;
 } ftsp2_table;
 
 typedef struct ftsp2_model_set ftsp2_model_set;   /* opaque */
@@ -181,7 +199,9 @@ void ftsp2_model_set_destroy(ftsp2_model_set* set);
 ftsp2_status ftsp2_model_set_info(const ftsp2_model_set* set, int* ntab, int* max_layers);
 
 /* Copy of table `idx` of the set: *L layers, theta_out (host, room for 4*64
- * doubles) receives the rows (a, b, c, d); any output pointer may be NULL. */
+ * doubles) receives the table's rows as given at creation (Eq. mlsp2: L rows
+ * (a, b, c, d); Skip-SP2: L + 1 rows); any output pointer may be NULL.  A
+ * Skip-SP2 table has at most 63 layers. */
 ftsp2_status ftsp2_model_set_table(const ftsp2_model_set* set, int idx, int* L, double* theta_out,
                                    double* beta0, double* mu0, double* alpha);
 
@@ -399,6 +419,17 @@ ftsp2_status ftsp2_train_coeffs_alt(int target, double beta0, double mu0, int L,
                                     const double* dX, int nsamples, int iterations, int accel,
                                     const double* alt_init, double* alt_out, ftsp2_train_report* rep,
                                     void* dWork, size_t work_bytes, void* stream);
+
+/* Levenberg-Marquardt training of a Skip-SP2 table (FTSP2_FAMILY_SKIP, one
+ * stored layer and one accumulator): as ftsp2_train_coeffs, with skip_init /
+ * skip_out (host) of (L + 1) * 4 doubles (layer rows, then the output row
+ * (A_0, gamma_L, 0, 0)); the 4L + 2 parameters get their own forward and
+ * reverse sweep on the GPU.  dWork must hold
+ * ftsp2_train_workspace_size(nsamples, L + 1) bytes; L <= 63. */
+ftsp2_status ftsp2_train_coeffs_skip(int target, double beta0, double mu0, int L, double alpha,
+                                     const double* dX, int nsamples, int iterations, int accel,
+                                     const double* skip_init, double* skip_out, ftsp2_train_report* rep,
+                                     void* dWork, size_t work_bytes, void* stream);
 
 /* Building blocks of one LM iteration, exposed for parity tests.
  * ftsp2_train_residual_jacobian: residuals dR[nsamples] = model(theta) - target

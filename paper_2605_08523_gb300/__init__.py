@@ -29,6 +29,7 @@ from ._lib import (BF16X3, CLAMP, EPI_DEFERRED, EPI_INLINE, FP16X2, FP32, LANCZO
                    check, lib, status_string)
 
 __all__ = ["ModelSet", "Solver", "ftsp2_rescale", "ftsp2_train_coeffs", "ftsp2_train_coeffs_alt", "ftsp2_alt_to_mlsp2",
+           "ftsp2_train_coeffs_skip",
            "ftsp2_train_residual_jacobian",
            "ftsp2_train_normal_equations", "ftsp2_autotune_clear", "kernel_launch_count", "profile_layers",
            "profile_read", "MODES", "FP32", "TF32X3", "BF16X3", "FP16X2", "SYNC", "CLAMP", "REFINE1", "REFINE2",
@@ -78,7 +79,10 @@ class ModelSet:
     theta_entropy; ``None`` gives the paper's printed 26-layer table.  A table
     of the one-term form (Eq. mlsp2_alt) gives ``alt`` ((L + 1, 2) rows) instead
     of theta (and ``alt_entropy`` instead of theta_entropy); it is converted by
-    ftsp2_alt_to_mlsp2."""
+    ftsp2_alt_to_mlsp2.  A Skip-SP2 table (one stored layer, one accumulator;
+    FTSP2_FAMILY_SKIP) gives ``skip`` ((L + 1, 4) rows: (delta, alpha, beta,
+    gamma) per layer and the output row (A_0, gamma_L, 0, 0)) and optionally
+    ``skip_entropy``."""
 
     def __init__(self, tables=None):
         self._h = C.c_void_p()
@@ -95,18 +99,25 @@ class ModelSet:
             if t.get("theta_entropy") is None and t.get("alt_entropy") is not None:
                 t = dict(t, theta_entropy=ftsp2_alt_to_mlsp2(t["alt_entropy"]).tolist())
             conv.append(t)
-            th = np.ascontiguousarray(np.asarray(t["theta"], dtype=np.float64).reshape(-1, 4))
+            skip = t.get("skip") is not None
+            if skip:
+                th = np.ascontiguousarray(np.asarray(t["skip"], dtype=np.float64).reshape(-1, 4))
+                arr[i].family = 1
+                arr[i].L = th.shape[0] - 1
+            else:
+                th = np.ascontiguousarray(np.asarray(t["theta"], dtype=np.float64).reshape(-1, 4))
+                arr[i].family = 0
+                arr[i].L = th.shape[0]
             self._keep.append(th)
-            arr[i].L = th.shape[0]
             arr[i].beta0 = float(t["beta0"])
             arr[i].mu0 = float(t["mu0"])
             arr[i].alpha = float(t.get("alpha", 0.842704))
             arr[i].theta = th.ctypes.data_as(C.POINTER(C.c_double))
-            te = t.get("theta_entropy")
+            te = t.get("skip_entropy") if skip else t.get("theta_entropy")
             if te is not None:
                 te = np.ascontiguousarray(np.asarray(te, dtype=np.float64).reshape(-1, 4))
                 self._keep.append(te)
-                arr[i].L_entropy = te.shape[0]
+                arr[i].L_entropy = te.shape[0] - (1 if skip else 0)
                 arr[i].theta_entropy = te.ctypes.data_as(C.POINTER(C.c_double))
             else:
                 arr[i].L_entropy = 0
@@ -123,9 +134,9 @@ class ModelSet:
         for p in paths:
             with open(p) as f:
                 d = json.load(f)
-            tabs.append(dict(theta=d.get("theta"), alt=d.get("alt"), beta0=d["beta0"], mu0=d["mu0"],
-                             alpha=d.get("alpha", 0.842704), theta_entropy=d.get("theta_entropy"),
-                             alt_entropy=d.get("alt_entropy")))
+            tabs.append(dict(theta=d.get("theta"), alt=d.get("alt"), skip=d.get("skip"), beta0=d["beta0"],
+                             mu0=d["mu0"], alpha=d.get("alpha", 0.842704), theta_entropy=d.get("theta_entropy"),
+                             alt_entropy=d.get("alt_entropy"), skip_entropy=d.get("skip_entropy")))
         return cls(tabs)
 
     @property
@@ -401,6 +412,27 @@ def ftsp2_train_coeffs_alt(target, beta0, mu0, alt_init, x, iterations=100, acce
                                        a0.ctypes.data_as(C.POINTER(C.c_double)),
                                        out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep), _ptr(ws), wb,
                                        _stream(stream)), "ftsp2_train_coeffs_alt")
+    return out, dict(iterations=rep.iterations, accepted=rep.accepted, cost0=rep.cost0, cost=rep.cost,
+                     max_err=rep.max_err, lam=rep.lam)
+
+
+def ftsp2_train_coeffs_skip(target, beta0, mu0, skip_init, x, iterations=100, accel=True, alpha=1.0, stream=None):
+    """Levenberg-Marquardt fit of a Skip-SP2 table (one stored layer, one
+    accumulator) on the GPU.  x: CUDA float64 samples.  Returns (table
+    (L + 1, 4) numpy, report dict)."""
+    torch = _torch()
+    t0 = np.ascontiguousarray(np.asarray(skip_init, dtype=np.float64).reshape(-1, 4))
+    L = t0.shape[0] - 1
+    ns = x.numel()
+    out = np.zeros_like(t0)
+    wb = lib().ftsp2_train_workspace_size(ns, L + 1)
+    ws = torch.empty(wb, dtype=torch.uint8, device=x.device)
+    rep = TrainReport()
+    check(lib().ftsp2_train_coeffs_skip(int(target), float(beta0), float(mu0), L, float(alpha), _ptr(x), ns,
+                                        int(iterations), int(bool(accel)),
+                                        t0.ctypes.data_as(C.POINTER(C.c_double)),
+                                        out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep), _ptr(ws), wb,
+                                        _stream(stream)), "ftsp2_train_coeffs_skip")
     return out, dict(iterations=rep.iterations, accepted=rep.accepted, cost0=rep.cost0, cost=rep.cost,
                      max_err=rep.max_err, lam=rep.lam)
 

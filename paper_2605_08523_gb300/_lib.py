@@ -20,6 +20,7 @@ MODES = {"fp32": FP32, "tf32x3": TF32X3, "bf16x3": BF16X3, "fp16x2": FP16X2}
 SYNC, CLAMP, REFINE1, REFINE2, PAIR_TILES, SINGLE_TILES, LANCZOS, MIN_LAYERS, REFINE_TC = \
     0x1, 0x2, 0x4, 0x8, 0x10, 0x20, 0x40, 0x80, 0x100
 EPI_DEFERRED, EPI_INLINE = 0x200, 0x400
+FAMILY_MLSP2, FAMILY_SKIP = 0, 1
 TARGET_FERMI, TARGET_ENTROPY = 0, 1
 
 
@@ -31,7 +32,8 @@ class Instance(C.Structure):
 class Table(C.Structure):
     _fields_ = [("L", C.c_int32), ("L_entropy", C.c_int32), ("beta0", C.c_double),
                 ("mu0", C.c_double), ("alpha", C.c_double),
-                ("theta", C.POINTER(C.c_double)), ("theta_entropy", C.POINTER(C.c_double))]
+                ("theta", C.POINTER(C.c_double)), ("theta_entropy", C.POINTER(C.c_double)),
+                ("family", C.c_int32), ("reserved", C.c_int32)]
 
 
 class RescaleRec(C.Structure):
@@ -77,6 +79,8 @@ SIGNATURES = {
     "ftsp2_train_coeffs_alt": (_I, [_I, _D, _D, _I, _D, _VP, _I, _I, _I, C.POINTER(_D), C.POINTER(_D),
                                     C.POINTER(TrainReport), _VP, _SZ, _VP]),
     "ftsp2_alt_to_mlsp2": (_I, [_I, C.POINTER(_D), C.POINTER(_D)]),
+    "ftsp2_train_coeffs_skip": (_I, [_I, _D, _D, _I, _D, _VP, _I, _I, _I, C.POINTER(_D), C.POINTER(_D),
+                                     C.POINTER(TrainReport), _VP, _SZ, _VP]),
     "ftsp2_train_residual_jacobian": (_I, [_I, _D, _D, _I, _D, C.POINTER(_D), _VP, _I, _VP, _VP, _VP]),
     "ftsp2_train_normal_equations": (_I, [_VP, _I, _I, _VP, _VP, _SZ, _VP]),
     "ftsp2_profile_layers": (_I, [_I]),

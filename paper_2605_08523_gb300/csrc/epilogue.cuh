@@ -1,7 +1,11 @@
 // Epilogue of one layer of the centred recursion, shared by the tensor-core
-// and the CUDA-core layer kernels.  For an owned element (r, c), r <= c:
-//   Z_{k+1} = a_k (Z_k^2)_{rc} + (b_k + 2 a_k tau_k) (Z_k)_{rc}     (centred Eq. mlsp2)
-//   A_{k+1} = A_k + d_k (Z_k)_{rc}
+// and the CUDA-core layer kernels.  For an owned element (r, c), r <= c, with
+// the constants of DevLayer:
+//   xh = mul (Z_k^2)_{rc} + bp (Z_k)_{rc},   A' = A + d (Z_k)_{rc} + d2 xh,
+//   Z_{k+1} = p xh + q A
+// (centred Eq. mlsp2: Z_{k+1} = a_k Z_k^2 + (b_k + 2 a_k tau_k) Z_k,
+// A' = A + d_k Z_k; centred Skip-SP2 with one stored layer and one
+// accumulator: the square of the combination, then the next combination)
 // then either the next layer's operands are written at (r, c) and (c, r), or,
 // at the last layer, D = G + f0 I (Appendix A output, flipped as I - (A + X)
 // when Eq. flip was used) is written and the FP64 partial sums of G are formed.
@@ -90,8 +94,9 @@ __device__ __forceinline__ void epi_segment(const LayerArgs& a, const EpiCtx& e,
     float zn[W], an[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) {
-        zn[j] = fmaf(e.mul, v[j], e.L.bp * z[j]);
-        an[j] = fmaf(e.L.d, z[j], ac[j]);
+        const float xh = fmaf(e.mul, v[j], e.L.bp * z[j]);
+        an[j] = fmaf(e.L.d2, xh, fmaf(e.L.d, z[j], ac[j]));
+        zn[j] = e.last ? xh : fmaf(e.L.p, xh, e.L.q * ac[j]);
     }
     if (!e.last) {
 #pragma unroll
@@ -116,7 +121,7 @@ __device__ __forceinline__ void epi_segment(const LayerArgs& a, const EpiCtx& e,
         for (int j = 0; j < W; ++j) {
             const int c = c0 + j;
             if (c < e.n && r <= c) {
-                const float g = an[j] + zn[j];
+                const float g = fmaf(e.L.g, zn[j], an[j]);
                 if (e.kind == CHAIN_FERMI && a.D) {
                     float dv;
                     if (e.flip) dv = (r == c ? (float)e.cdiag : 0.f) - g;

@@ -84,8 +84,9 @@ static bool encode_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int e
 // ------------------------------------------------------------------------------
 struct HostModel {
     int L = 0, LS = 0;
+    int family = FTSP2_FAMILY_MLSP2;
     double beta0 = 0, mu0 = 0, alpha = 0;
-    std::vector<double> th, thS;
+    std::vector<double> th, thS;   // Eq. mlsp2: 4L; Skip-SP2: 4(L + 1) (output row last)
 };
 
 }  // namespace ftsp2
@@ -100,6 +101,73 @@ struct ftsp2_model_set {
 };
 
 namespace ftsp2 {
+
+// FP16 range control: 2^e with 1.25 max|Z| 2^e <= 2^14 (0 when unscaled).
+static int fp16_exponent(double m, bool scaled) {
+    if (!scaled || !(m > 0.0)) return 0;
+    const int ek = (int)std::floor(std::log2(16384.0 / (1.25 * m)));
+    return std::min(40, std::max(-20, ek));
+}
+
+// Skip-SP2 chain (one stored layer, one accumulator): the centre trajectory at
+// x0 = mu0 (sigma_k of the squared combination, chi_k of x_k, rho_k of A_k),
+// the FP16 exponents from max over the inputs of |u_k - sigma_k|, and the
+// epilogue constants of DevLayer.
+static void chain_constants_skip(const std::vector<double>& tb, int L, double mu0, double lo, double hi,
+                                 bool scaled, std::vector<DevLayer>& out, double& f0, float& scale0, float& z0,
+                                 float& a0) {
+    std::vector<double> sig(L), chi(L + 1), rho(L + 1);
+    chi[0] = mu0;
+    rho[0] = tb[4 * L];
+    for (int k = 0; k < L; ++k) {
+        const double dl = tb[4 * k], al = tb[4 * k + 1], be = tb[4 * k + 2], ga = tb[4 * k + 3];
+        sig[k] = dl + al * chi[k] + be * rho[k];
+        rho[k + 1] = rho[k] + ga * chi[k];
+        chi[k + 1] = sig[k] * sig[k];
+    }
+    const double gL = tb[4 * L + 1];
+    f0 = rho[L] + gL * chi[L];
+    const int G = 20001;
+    std::vector<double> x(G), A(G, tb[4 * L]);
+    for (int i = 0; i < G; ++i) x[i] = lo + (hi - lo) * (double)i / (G - 1);
+    std::vector<int> e(L + 1, 0);
+    for (int k = 0; k < L; ++k) {
+        const double dl = tb[4 * k], al = tb[4 * k + 1], be = tb[4 * k + 2], ga = tb[4 * k + 3];
+        double m = 0.0;
+        for (int i = 0; i < G; ++i) {
+            const double u = dl + al * x[i] + be * A[i];
+            m = std::max(m, std::fabs(u - sig[k]));
+            A[i] += ga * x[i];
+            x[i] = u * u;
+        }
+        e[k] = fp16_exponent(m, scaled);
+    }
+    out.resize(L);
+    for (int k = 0; k < L; ++k) {
+        DevLayer dl;
+        dl.a = 1.f;
+        dl.acc_mul = (float)std::ldexp(1.0, -2 * e[k]);
+        dl.bp = (float)(2.0 * sig[k]);
+        dl.d = 0.f;
+        dl.in_scale = (float)std::ldexp(1.0, e[k]);
+        if (k + 1 < L) {
+            dl.p = (float)tb[4 * (k + 1) + 1];
+            dl.q = (float)tb[4 * (k + 1) + 2];
+            dl.d2 = (float)tb[4 * (k + 1) + 3];
+            dl.g = 0.f;
+            dl.out_scale = (float)std::ldexp(1.0, e[k + 1]);
+        } else {
+            dl.p = dl.q = dl.d2 = 0.f;
+            dl.g = (float)gL;
+            dl.out_scale = 1.f;
+        }
+        dl.pad0 = dl.pad1 = 0.f;
+        out[k] = dl;
+    }
+    scale0 = (float)std::ldexp(1.0, e[0]);
+    z0 = (float)tb[1];
+    a0 = (float)tb[3];
+}
 
 // Trajectory of the centre and the per-layer constants of one chain.
 // x0range: interval of layer-0 inputs the chain sees (subset of [0, 1]).
@@ -140,6 +208,10 @@ static void chain_constants(const std::vector<double>& th, int L, double mu0, do
         dl.d = (float)d;
         dl.in_scale = (float)std::ldexp(1.0, e[k]);
         dl.out_scale = (float)std::ldexp(1.0, e[k + 1]);
+        dl.p = 1.f;
+        dl.q = 0.f;
+        dl.d2 = 0.f;
+        dl.g = 1.f;
         dl.pad0 = dl.pad1 = 0.f;
         out[k] = dl;
     }
@@ -161,10 +233,19 @@ static ftsp2_status upload_models(ftsp2_model_set* s) {
             M.L = h.L;
             M.LS = h.LS;
             std::vector<DevLayer> lf, ls;
-            chain_constants(h.th, h.L, h.mu0, 0.0, 1.0, scaled, lf, M.f0, M.scale0);
             const double ylo = h.mu0 + h.alpha * (0.0 - h.mu0), yhi = h.mu0 + h.alpha * (1.0 - h.mu0);
-            chain_constants(h.thS.empty() ? h.th : h.thS, h.LS, h.mu0, std::min(ylo, yhi), std::max(ylo, yhi),
-                            scaled, ls, M.g0, M.scale0S);
+            const std::vector<double>& thE = h.thS.empty() ? h.th : h.thS;
+            if (h.family == FTSP2_FAMILY_SKIP) {
+                chain_constants_skip(h.th, h.L, h.mu0, 0.0, 1.0, scaled, lf, M.f0, M.scale0, M.z0, M.a0);
+                chain_constants_skip(thE, h.LS, h.mu0, std::min(ylo, yhi), std::max(ylo, yhi), scaled, ls, M.g0,
+                                     M.scale0S, M.z0S, M.a0S);
+            } else {
+                chain_constants(h.th, h.L, h.mu0, 0.0, 1.0, scaled, lf, M.f0, M.scale0);
+                chain_constants(thE, h.LS, h.mu0, std::min(ylo, yhi), std::max(ylo, yhi), scaled, ls, M.g0,
+                                M.scale0S);
+                M.z0 = M.z0S = 1.f;
+                M.a0 = M.a0S = 0.f;
+            }
             M.off = (int)dl[v].size();
             dl[v].insert(dl[v].end(), lf.begin(), lf.end());
             M.offS = (int)dl[v].size();
@@ -779,19 +860,27 @@ ftsp2_status ftsp2_model_set_create(const ftsp2_table* tabs, int ntab, ftsp2_mod
     for (int i = 0; i < ntab; ++i) {
         const ftsp2_table& t = tabs[i];
         const int LS = t.theta_entropy ? t.L_entropy : t.L;
-        if (t.L < 1 || t.L > kMaxLayers || LS < 1 || LS > kMaxLayers || !t.theta || !(t.beta0 > 0) ||
+        // a Skip-SP2 table carries an output row: at most kMaxLayers rows in all
+        const int lmax = t.family == FTSP2_FAMILY_SKIP ? kMaxLayers - 1 : kMaxLayers;
+        if (t.L < 1 || t.L > lmax || LS < 1 || LS > lmax || !t.theta || !(t.beta0 > 0) ||
             !(t.mu0 > 0 && t.mu0 < 1) || !std::isfinite(t.alpha)) {
+            delete s;
+            return FTSP2_E_ARG;
+        }
+        if (t.family != FTSP2_FAMILY_MLSP2 && t.family != FTSP2_FAMILY_SKIP) {
             delete s;
             return FTSP2_E_ARG;
         }
         HostModel h;
         h.L = t.L;
         h.LS = LS;
+        h.family = t.family;
         h.beta0 = t.beta0;
         h.mu0 = t.mu0;
         h.alpha = t.alpha;
-        h.th.assign(t.theta, t.theta + 4 * t.L);
-        if (t.theta_entropy) h.thS.assign(t.theta_entropy, t.theta_entropy + 4 * LS);
+        const int rows = t.family == FTSP2_FAMILY_SKIP ? 1 : 0;   // the output row of Skip-SP2
+        h.th.assign(t.theta, t.theta + 4 * (t.L + rows));
+        if (t.theta_entropy) h.thS.assign(t.theta_entropy, t.theta_entropy + 4 * (LS + rows));
         for (double v : h.th)
             if (!std::isfinite(v)) { delete s; return FTSP2_E_ARG; }
         for (double v : h.thS)
@@ -810,6 +899,8 @@ ftsp2_status ftsp2_model_set_create(const ftsp2_table* tabs, int ntab, ftsp2_mod
 
 ftsp2_status ftsp2_model_set_builtin(ftsp2_model_set** out) {
     ftsp2_table t;
+    std::memset(&t, 0, sizeof(t));
+    t.family = FTSP2_FAMILY_MLSP2;
     t.L = 26;
     t.L_entropy = 0;
     t.beta0 = 1500.0;
@@ -1172,9 +1263,15 @@ ftsp2_status ftsp2_train_normal_equations(const double* dM, int nsamples, int L,
 // One-term form (Eq. mlsp2_alt): p = (t_01, t_02, ..., t_L1, t_L2) (2L + 2),
 // theta(p) by ftsp2_alt_to_mlsp2 and the Jacobian P = d theta / d p, so that
 // J_p = J P and the reductions transform as P^T (J^T J) P and P^T (J^T r).
-enum { FORM_MLSP2 = 0, FORM_ALT = 1 };
+// Skip-SP2 tables (FORM_SKIP): p = the table itself, 4L + 2 entries (layer
+// rows, then A_0 and gamma_L), with its own forward/Jacobian kernel.
+enum { FORM_MLSP2 = 0, FORM_ALT = 1, FORM_SKIP = 2 };
 
-static int form_params(int form, int L) { return form == FORM_ALT ? 2 * L + 2 : 4 * L; }
+static int form_params(int form, int L) {
+    return form == FORM_ALT ? 2 * L + 2 : (form == FORM_SKIP ? 4 * L + 2 : 4 * L);
+}
+static int form_theta_dim(int form, int L) { return form == FORM_SKIP ? 4 * L + 2 : 4 * L; }
+static int form_family(int form) { return form == FORM_SKIP ? FTSP2_FAMILY_SKIP : FTSP2_FAMILY_MLSP2; }
 
 static void alt_rows(int L, const double* alt, double* th) {
     for (int i = 0; i < L; ++i) {
@@ -1193,9 +1290,9 @@ static void alt_rows(int L, const double* alt, double* th) {
 
 // P (4L x np, row-major) at p
 static void form_jacobian(int form, int L, const double* p, std::vector<double>& P) {
-    const int np = form_params(form, L), nt = 4 * L;
+    const int np = form_params(form, L), nt = form_theta_dim(form, L);
     P.assign((size_t)nt * np, 0.0);
-    if (form == FORM_MLSP2) {
+    if (form != FORM_ALT) {
         for (int i = 0; i < nt; ++i) P[(size_t)i * np + i] = 1.0;
         return;
     }
@@ -1217,6 +1314,15 @@ static void form_jacobian(int form, int L, const double* p, std::vector<double>&
 
 static ftsp2_status form_theta(int form, int L, const double* p, ThetaParam& tp) {
     if (form == FORM_MLSP2) return load_theta(L, p, tp);
+    if (form == FORM_SKIP) {
+        if (!p || L < 1 || L > kMaxLayers - 1) return FTSP2_E_ARG;
+        std::memset(&tp, 0, sizeof(tp));
+        for (int i = 0; i < 4 * L + 2; ++i) {
+            if (!std::isfinite(p[i])) return FTSP2_E_ARG;
+            tp.v[i] = p[i];
+        }
+        return FTSP2_OK;
+    }
     if (!p || L < 1 || L > kMaxLayers) return FTSP2_E_ARG;
     for (int i = 0; i < 2 * L + 2; ++i)
         if (!std::isfinite(p[i])) return FTSP2_E_ARG;
@@ -1233,12 +1339,14 @@ static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int
     if ((target != FTSP2_TARGET_FERMI && target != FTSP2_TARGET_ENTROPY) || !dX || nsamples < 1 || !p_out ||
         !dWork || iterations < 0 || !p_init)
         return FTSP2_E_ARG;
-    const int np = form_params(form, L), nt = 4 * L;
+    const int np = form_params(form, L), nt = form_theta_dim(form, L);
+    const int fam = form_family(form);
     std::vector<double> p(p_init, p_init + np);
     ThetaParam tp;
     ftsp2_status st = form_theta(form, L, p.data(), tp);
     if (st != FTSP2_OK) return st;
-    const TrainLayout tl = train_layout(nsamples, L);
+    // room for nt + 1 columns (the Skip-SP2 form has 4L + 2 parameters)
+    const TrainLayout tl = train_layout(nsamples, form == FORM_SKIP ? L + 1 : L);
     if (work_bytes < tl.total) return FTSP2_E_WORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint8_t* W = static_cast<uint8_t*>(dWork);
@@ -1258,7 +1366,7 @@ static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int
     std::vector<double> JTJ((size_t)np * np), g(np), Pj;
     auto eval = [&](const ThetaParam& t, const double* pp, std::vector<double>& jtj, std::vector<double>& gg,
                     std::vector<double>& Pm, double& cst) -> ftsp2_status {
-        if (launch_train_fwd_jac(target, beta0, mu0, L, alpha, t, dX, nsamples, dRr, dM, s) != cudaSuccess)
+        if (launch_train_fwd_jac(target, beta0, mu0, L, alpha, t, dX, nsamples, dRr, dM, s, fam) != cudaSuccess)
             return FTSP2_E_CUDA;
         if (launch_train_gram(dM, nsamples, nt, dG, dPart, tl.nchunks, s) != cudaSuccess) return FTSP2_E_CUDA;
         if (cudaMemcpyAsync(Gt.data(), dG, sizeof(double) * mt * mt, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -1315,7 +1423,7 @@ static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int
                 vt[k] = acc;
             }
             std::vector<double> rt(nt);
-            if (launch_train_residual(target, beta0, mu0, L, alpha, th_h, dX, nsamples, dRh, s) != cudaSuccess ||
+            if (launch_train_residual(target, beta0, mu0, L, alpha, th_h, dX, nsamples, dRh, s, fam) != cudaSuccess ||
                 cudaMemcpyAsync(dV, vt.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, s) != cudaSuccess ||
                 launch_train_accel(dM, dV, dRh, h, nsamples, nt, dAp, dOut, s) != cudaSuccess ||
                 cudaMemcpyAsync(rt.data(), dOut, sizeof(double) * nt, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1358,7 +1466,7 @@ static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int
         }
     }
     // residuals at the final table and their max
-    if (launch_train_residual(target, beta0, mu0, L, alpha, tp, dX, nsamples, dRr, s) != cudaSuccess ||
+    if (launch_train_residual(target, beta0, mu0, L, alpha, tp, dX, nsamples, dRr, s, fam) != cudaSuccess ||
         launch_train_absmax(dRr, nsamples, dAm + 8, dAm, s) != cudaSuccess)
         return FTSP2_E_CUDA;
     double mx = 0;
@@ -1390,6 +1498,23 @@ ftsp2_status ftsp2_train_coeffs_alt(int target, double beta0, double mu0, int L,
                                     ftsp2_train_report* rep, void* dWork, size_t work_bytes, void* stream) {
     return lm_train(FORM_ALT, target, beta0, mu0, L, alpha, dX, nsamples, iterations, accel, alt_init, alt_out, rep,
                     dWork, work_bytes, stream);
+}
+
+ftsp2_status ftsp2_train_coeffs_skip(int target, double beta0, double mu0, int L, double alpha, const double* dX,
+                                     int nsamples, int iterations, int accel, const double* skip_init,
+                                     double* skip_out, ftsp2_train_report* rep, void* dWork, size_t work_bytes,
+                                     void* stream) {
+    if (L < 1 || L > kMaxLayers - 1) return FTSP2_E_ARG;
+    // the table's (L + 1) x 4 rows: the output row's last two entries are unused
+    std::vector<double> p(4 * L + 2), out(4 * L + 2);
+    if (!skip_init || !skip_out) return FTSP2_E_ARG;
+    std::copy(skip_init, skip_init + 4 * L + 2, p.begin());
+    const ftsp2_status st = lm_train(FORM_SKIP, target, beta0, mu0, L, alpha, dX, nsamples, iterations, accel,
+                                     p.data(), out.data(), rep, dWork, work_bytes, stream);
+    if (st != FTSP2_OK) return st;
+    std::copy(out.begin(), out.end(), skip_out);
+    skip_out[4 * L + 2] = skip_out[4 * L + 3] = 0.0;
+    return FTSP2_OK;
 }
 
 ftsp2_status ftsp2_alt_to_mlsp2(int L, const double* alt, double* theta_out) {

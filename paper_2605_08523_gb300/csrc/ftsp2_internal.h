@@ -40,13 +40,23 @@ enum ChainKind : int { CHAIN_FERMI = 0, CHAIN_ENTROPY = 1 };
 enum OpFmt : int { OP_F32 = 0, OP_TF32X3 = 1, OP_BF16X3 = 2, OP_F16X2 = 3 };
 
 // Per layer constants of the centred recursion (float: what the epilogue uses).
+// Per-layer constants of the centred epilogue.  From the product S = Z_k^2 and
+// the stored state (Z_k, A):
+//   xh = mul S + bp Z_k,   A' = A + d Z_k + d2 xh,   Z_{k+1} = p xh + q A,
+// and at the last layer G = A + d Z_k + g xh.
+// Eq. mlsp2: mul = a_k (times 2^(-2 e_k) for scaled FP16 products),
+// bp = b_k + 2 a_k tau_k, d = d_k, d2 = 0, p = 1, q = 0, g = 1.
+// Skip-SP2 (one stored layer, one accumulator; xh is the centred x_{k+1},
+// A holds the centred A_{k+1}): mul = 2^(-2 e_k), bp = 2 sigma_k, d = 0,
+// d2 = gamma_{k+1}, p = alpha_{k+1}, q = beta_{k+1}, and g = gamma_L.
 struct DevLayer {
-    float acc_mul;    // a_k * 2^(-2 e_k): undoes the operand scale of FP16 splits
-    float bp;         // b_k + 2 a_k tau_k
-    float d;          // d_k
+    float acc_mul;    // mul for scaled FP16 products (undoes 2^(2 e_k))
+    float bp;
+    float d;
     float out_scale;  // 2^(e_{k+1}): scale of the operands written for layer k+1
     float in_scale;   // 2^(e_k)
-    float a;          // a_k
+    float a;          // mul for unscaled products
+    float p, q, d2, g;
     float pad0, pad1;
 };
 
@@ -60,6 +70,9 @@ struct DevModel {
     int offS;         // first DevLayer of the entropy chain
     float scale0;     // 2^(e_0) of the Fermi chain (FP16 operands of Z_0)
     float scale0S;    // 2^(e_0) of the entropy chain
+    // layer-0 state from the centred input X0 - mu0 I of each chain:
+    // Z_0 = z0 (X0 - mu0 I), A = a0 (X0 - mu0 I) (Eq. mlsp2: 1, 0)
+    float z0, a0, z0S, a0S;
 };
 
 // One output tile of one grouped layer launch.
@@ -223,12 +236,15 @@ cudaError_t launch_layer_simt(const LayerArgs& a, int grid, cudaStream_t s);
 struct ThetaParam {
     double v[4 * kMaxLayers];
 };
+// family FTSP2_FAMILY_MLSP2: th = L rows (a, b, c, d), 4L Jacobian columns;
+// FTSP2_FAMILY_SKIP: th = L rows (delta, alpha, beta, gamma) + (A_0, gamma_L),
+// 4L + 2 columns.  The residual column follows the Jacobian's.
 cudaError_t launch_train_fwd_jac(int target, double beta0, double mu0, int L, double alpha,
                                  const ThetaParam& th, const double* dX, int ns,
-                                 double* dR, double* dM, cudaStream_t s);
+                                 double* dR, double* dM, cudaStream_t s, int family = FTSP2_FAMILY_MLSP2);
 cudaError_t launch_train_residual(int target, double beta0, double mu0, int L, double alpha,
                                   const ThetaParam& th, const double* dX, int ns,
-                                  double* dR, cudaStream_t s);
+                                  double* dR, cudaStream_t s, int family = FTSP2_FAMILY_MLSP2);
 cudaError_t launch_train_gram(const double* dM, int ns, int np, double* dG, double* dScratch,
                               int nchunks, cudaStream_t s);
 cudaError_t launch_train_accel(const double* dM, const double* dV, const double* dRh, double h,

@@ -350,6 +350,7 @@ struct EpiLite {
     float* Z;          // state slab of Z (blocked layout); A = Z + plane_elems
     uint8_t* op;       // next layer's operand plane 0, slab start (bytes)
     float mul, bp, d, os;
+    float p, q, d2;    // next state Z' = p xh + q A, A' = A + d Z + d2 xh (DevLayer)
 };
 
 // FMT: operand format written; scaled_in: the products were formed from
@@ -366,6 +367,9 @@ __device__ __forceinline__ void make_lite(const LayerArgs& a, const Tile& t, int
     e.bp = L.bp;
     e.d = L.d;
     e.os = FMT == OP_F16X2 ? L.out_scale : 1.f;
+    e.p = L.p;
+    e.q = L.q;
+    e.d2 = L.d2;
 }
 
 // Load the 8 state values of row r, columns c0 .. c0 + 7 (two float4 runs 128
@@ -440,11 +444,15 @@ __device__ __forceinline__ void epi_dgroup_next(const LayerArgs& a, const EpiLit
         float* const Ag = Zg + a.plane_elems;
         float z[8], zn[8];
         src.state(hh, Zg, Ag, z, zn);
+        // xh in v, A' in z, Z' in zn (A read before it is replaced)
 #pragma unroll
-        for (int u = 0; u < 8; ++u) zn[u] = fmaf(e.d, z[u], zn[u]);
-        store_state8(Ag, zn);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) zn[u] = fmaf(e.mul, v[u], e.bp * z[u]);
+        for (int u = 0; u < 8; ++u) {
+            const float xh = fmaf(e.mul, v[u], e.bp * z[u]);
+            const float an = fmaf(e.d2, xh, fmaf(e.d, z[u], zn[u]));
+            zn[u] = fmaf(e.p, xh, e.q * zn[u]);
+            z[u] = an;
+        }
+        store_state8(Ag, z);
         store_state8(Zg, zn);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -490,7 +498,8 @@ __device__ __forceinline__ void epi_dgroup_next(const LayerArgs& a, const EpiLit
     }
 }
 
-// Last layer: G = A_L + Z_L with A_L = A_{L-1} + d Z_{L-1}, Z_L = a v + b' Z_{L-1}
+// Last layer: G = A + d Z + g xh with xh = mul v + bp Z (Eq. mlsp2: A_L + Z_L,
+// A_L = A_{L-1} + d Z_{L-1}, Z_L = a v + b' Z_{L-1}; Skip-SP2: A_L + gamma_L x_L)
 // (v overwritten with G); rows r >= n give 0.
 __device__ __forceinline__ void epi_update_last(const LayerArgs& a, const EpiCtx& e, int r, int c0, float* v) {
     if (r >= e.n) {
@@ -503,7 +512,7 @@ __device__ __forceinline__ void epi_update_last(const LayerArgs& a, const EpiCtx
     load_state8(a.Z[e.chain] + so, z);
     load_state8(a.A[e.chain] + so, x);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = fmaf(e.mul, v[u], e.L.bp * z[u]) + fmaf(e.L.d, z[u], x[u]);
+    for (int u = 0; u < 8; ++u) v[u] = fmaf(e.L.g, fmaf(e.mul, v[u], e.L.bp * z[u]), fmaf(e.L.d, z[u], x[u]));
 }
 
 // Last layer: D = G + f0 I (or (1 - f0) I - G when flipped) at (r, c) and

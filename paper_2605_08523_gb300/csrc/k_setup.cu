@@ -337,12 +337,16 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
     const bool ok = rec.status == FTSP2_OK && rec.model >= 0;
     const size_t base = (size_t)b * P * P;
     const int sl_packed = a.iw[b].start_layer;
-    float alpha = 1.f, sc0 = 1.f, sc0S = 1.f;
+    float alpha = 1.f, sc0 = 1.f, sc0S = 1.f, z0 = 1.f, a0 = 0.f, z0S = 1.f, a0S = 0.f;
     if (ok) {
         const DevModel& M = a.models[rec.model];
         alpha = (float)M.alpha;
         sc0 = M.scale0;
         sc0S = M.scale0S;
+        z0 = M.z0;
+        a0 = M.a0;
+        z0S = M.z0S;
+        a0S = M.a0S;
     }
     // The layers of this instance read rows and columns below n rounded up to
     // the largest tile (256), never the rest of the P x P slab: only that
@@ -358,9 +362,11 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
             if (ok && inside) z = (float)(rec.scale * ((r == c ? in.mu : 0.0) - __ldg(Hr + c)));
             for (int ch = 0; ch < a.nchains; ++ch) {
                 const bool ent = a.chain_kind[ch] == CHAIN_ENTROPY;
-                const float zc = ent ? alpha * z : z;
+                // centred layer-0 input of the chain, then the family's layer-0 state
+                const float xc = ent ? alpha * z : z;
+                const float zc = (ent ? z0S : z0) * xc;
                 a.Z[ch][es] = zc;
-                a.A[ch][es] = 0.f;
+                a.A[ch][es] = (ent ? a0S : a0) * xc;
                 if (inside) {
                     const int start = (sl_packed >> (16 * ch)) & 0xffff;
                     if (a.main_fmt != OP_F32 && start >= a.refine_from)

@@ -70,16 +70,76 @@ __global__ void __launch_bounds__(128) fwd_kernel(int target, double beta0, doub
     }
 }
 
+// Skip-SP2 with one stored layer and one accumulator (Sec. II A 3): th holds
+// L rows (delta, alpha, beta, gamma) and the output row (A_0, gamma_L);
+// u_i = delta_i + alpha_i x_i + beta_i A_i, A_{i+1} = A_i + gamma_i x_i,
+// x_{i+1} = u_i^2, F = A_L + gamma_L x_L.  Reverse sweep with gx = dF/dx_i,
+// gA = dF/dA_i: w = 2 u_i gx_{i+1} gives dF/d(delta, alpha, beta)_i =
+// w (1, x_i, A_i), dF/dgamma_i = gA_{i+1} x_i, gx_i = w alpha_i + gA_{i+1}
+// gamma_i, gA_i = w beta_i + gA_{i+1}; dF/dA_0 = gA_0, dF/dgamma_L = x_L.
+// Columns j < 4L + 2 in that flattened order, the residual in column 4L + 2.
+template <bool WITH_J>
+__global__ void __launch_bounds__(128) fwd_skip_kernel(int target, double beta0, double mu0, int L, double alpha,
+                                                       const __grid_constant__ ThetaParam thp,
+                                                       const double* __restrict__ X, int ns,
+                                                       double* __restrict__ R, double* __restrict__ M) {
+    const double* th = thp.v;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    const double x = X[s];
+    double xs[kTrainMaxL], As[kTrainMaxL], us[kTrainMaxL];
+    double xi = target == FTSP2_TARGET_ENTROPY ? alpha * (x - mu0) + mu0 : x;
+    double A = th[4 * L];
+    for (int i = 0; i < L; ++i) {
+        xs[i] = xi;
+        As[i] = A;
+        const double u = fma(th[4 * i + 2], A, fma(th[4 * i + 1], xi, th[4 * i]));
+        us[i] = u;
+        A = fma(th[4 * i + 3], xi, A);
+        xi = u * u;
+    }
+    const double F = fma(th[4 * L + 1], xi, A);
+    double out = F, fac = 1.0;
+    if (target == FTSP2_TARGET_ENTROPY) {
+        const double k4 = 4.0 * 0.69314718055994530942;
+        out = k4 * F * (1.0 - F);
+        fac = k4 * (1.0 - 2.0 * F);
+    }
+    const double r = out - target_value(target, x, beta0, mu0);
+    R[s] = r;
+    if (!WITH_J) return;
+    const int np = 4 * L + 2;
+    M[(size_t)np * ns + s] = r;
+    M[(size_t)(4 * L + 1) * ns + s] = fac * xi;
+    double gx = th[4 * L + 1], gA = 1.0;
+    for (int i = L - 1; i >= 0; --i) {
+        const double w = 2.0 * us[i] * gx;
+        M[(size_t)(4 * i + 0) * ns + s] = fac * w;
+        M[(size_t)(4 * i + 1) * ns + s] = fac * w * xs[i];
+        M[(size_t)(4 * i + 2) * ns + s] = fac * w * As[i];
+        M[(size_t)(4 * i + 3) * ns + s] = fac * gA * xs[i];
+        const double gx_i = fma(w, th[4 * i + 1], gA * th[4 * i + 3]);
+        gA = fma(w, th[4 * i + 2], gA);
+        gx = gx_i;
+    }
+    M[(size_t)(4 * L) * ns + s] = fac * gA;
+}
+
 cudaError_t launch_train_fwd_jac(int target, double beta0, double mu0, int L, double alpha, const ThetaParam& th,
-                                 const double* dX, int ns, double* dR, double* dM, cudaStream_t s) {
-    fwd_kernel<true><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR, dM);
+                                 const double* dX, int ns, double* dR, double* dM, cudaStream_t s, int family) {
+    if (family == FTSP2_FAMILY_SKIP)
+        fwd_skip_kernel<true><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR, dM);
+    else fwd_kernel<true><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR, dM);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_train_residual(int target, double beta0, double mu0, int L, double alpha, const ThetaParam& th,
-                                  const double* dX, int ns, double* dR, cudaStream_t s) {
-    fwd_kernel<false><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR, nullptr);
+                                  const double* dX, int ns, double* dR, cudaStream_t s, int family) {
+    if (family == FTSP2_FAMILY_SKIP)
+        fwd_skip_kernel<false><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR,
+                                                                nullptr);
+    else fwd_kernel<false><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR, nullptr);
     count_launch();
     return cudaGetLastError();
 }

@@ -58,8 +58,8 @@ def test_struct_layouts_match_c(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(ftsp2_instance), offsetof(ftsp2_instance, offset),
          offsetof(ftsp2_instance, mu), offsetof(ftsp2_instance, kT));
-  printf("%zu %zu %zu %zu\\n", sizeof(ftsp2_table), offsetof(ftsp2_table, beta0),
-         offsetof(ftsp2_table, theta), offsetof(ftsp2_table, theta_entropy));
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(ftsp2_table), offsetof(ftsp2_table, beta0),
+         offsetof(ftsp2_table, theta), offsetof(ftsp2_table, theta_entropy), offsetof(ftsp2_table, family));
   printf("%zu %zu %zu %zu\\n", sizeof(ftsp2_rescale_rec), offsetof(ftsp2_rescale_rec, flip),
          offsetof(ftsp2_rescale_rec, status), offsetof(ftsp2_rescale_rec, valid));
   printf("%zu %zu %zu %zu\\n", sizeof(ftsp2_train_report), offsetof(ftsp2_train_report, cost0),
@@ -72,7 +72,8 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     I, T, R, P = _lib.Instance, _lib.Table, _lib.RescaleRec, _lib.TrainReport
     assert out[0].split() == [str(v) for v in (C.sizeof(I), I.offset.offset, I.mu.offset, I.kT.offset)]
-    assert out[1].split() == [str(v) for v in (C.sizeof(T), T.beta0.offset, T.theta.offset, T.theta_entropy.offset)]
+    assert out[1].split() == [str(v) for v in (C.sizeof(T), T.beta0.offset, T.theta.offset, T.theta_entropy.offset,
+                                                T.family.offset)]
     assert out[2].split() == [str(v) for v in (C.sizeof(R), R.flip.offset, R.status.offset, R.valid.offset)]
     assert out[3].split() == [str(v) for v in (C.sizeof(P), P.cost0.offset, P.max_err.offset, P.lam.offset)]
 
