@@ -60,10 +60,10 @@ def parse():
     p.add_argument("--epilogue", default="auto", choices=["auto", "deferred", "inline"],
                    help="final epilogue of the pair tiles: the library's default, or forced "
                         "(FTSP2_EPI_DEFERRED / FTSP2_EPI_INLINE)")
-    p.add_argument("--table", default="printed", choices=["printed", "alt"],
+    p.add_argument("--table", default="printed", choices=["printed", "alt", "skip"],
                    help="cfg1/cfg4 Fermi table: the paper's printed 26-layer table (with the trained entropy "
-                        "table), or the 26-layer beta0 = 1500 table of the one-term form (Eq. mlsp2_alt) "
-                        "trained by the library")
+                        "table), the 26-layer beta0 = 1500 table of the one-term form (Eq. mlsp2_alt), or the "
+                        "26-layer beta0 = 1500 Skip-SP2 table, both trained by the library")
     p.add_argument("--refine-tc", action="store_true",
                    help="refinement layers as BF16X3 tensor-core layers (FTSP2_REFINE_TC)")
     p.add_argument("--workload", default="cfg1", choices=["cfg1", "cfg2", "cfg4"],
@@ -191,11 +191,29 @@ def method_exact_gpu(eps, V, rec, table, mu):
             A = A + d * xx
             xx = a * xx * xx + b * xx + c
         return A + xx
-    P = chain(x, table["theta"])
+
+    def chain_skip(x0, tb):
+        # Skip-SP2, one stored layer and one accumulator: rows (delta, alpha,
+        # beta, gamma), output row (A_0, gamma_L)
+        A = torch.full_like(x0, tb[-1][0])
+        xx = x0.clone()
+        for dl, al, be, ga in tb[:-1]:
+            u = dl + al * xx + be * A
+            A = A + ga * xx
+            xx = u * u
+        return A + tb[-1][1] * xx
+
+    if table.get("skip") is not None:
+        fermi_f = lambda x0: chain_skip(x0, table["skip"])
+        ent_f = lambda x0: chain_skip(x0, table.get("skip_entropy") or table["skip"])
+    else:
+        fermi_f = lambda x0: chain(x0, table["theta"])
+        ent_f = lambda x0: chain(x0, table.get("theta_entropy") or table["theta"])
+    P = fermi_f(x)
     if int(rec["flip"]):
         P = 1.0 - P
     Drec = (V * P[None, :]) @ V.T
-    F = chain(alpha * (x - mu0) + mu0, table.get("theta_entropy") or table["theta"])
+    F = ent_f(alpha * (x - mu0) + mu0)
     Srec = float((4.0 * LN2 * F * (1.0 - F)).sum())
     return Drec, Srec
 
@@ -458,7 +476,8 @@ def main():
     # the paper's printed Fermi table with the entropy table the library's
     # trainer fitted for it (theta_entropy)
     tdir = os.path.join(ROOT, "paper_2605_08523_gb300", "tables")
-    tabs = [os.path.join(tdir, "alt_b1500_L26.json" if args.table == "alt" else "entropy_b1500_L26.json")]
+    tabs = [os.path.join(tdir, {"alt": "alt_b1500_L26.json", "skip": "skip_b1500_L26.json"}.get(
+        args.table, "entropy_b1500_L26.json"))]
     if cfg4:
         # the long-range couplings widen the Gershgorin interval: beta' needs the
         # 34-layer beta0 = 3000 table
@@ -586,8 +605,9 @@ def main():
         "config": {"workload": ("cfg4 lattice %dx%dx%d with 5%% long-range couplings N(0,0.05) n=%d kT=%g "
                                 "mu=half filling, density+entropy, beta0=1500 and 3000 tables" if cfg4 else
                                 "cfg1 lattice %dx%dx%d n=%d kT=%g mu=half filling, density+entropy, "
-                                + ("26-layer beta0=1500 table of the one-term form (Eq. mlsp2_alt)"
-                                   if args.table == "alt" else "printed 26-layer table + trained entropy table"))
+                                + {"alt": "26-layer beta0=1500 table of the one-term form (Eq. mlsp2_alt)",
+                                   "skip": "26-layer beta0=1500 Skip-SP2 table (one stored layer, one accumulator)"}
+                                .get(args.table, "printed 26-layer table + trained entropy table"))
                                 % (dims + (n, kT)),
                    "n": n, "kT": kT, "mu": mu, "layers": L, "mode": args.mode, "chains": 2,
                    "refine_layers_fp32": refine, "refine_on_tensor_cores": bool(args.refine_tc),

@@ -13,6 +13,9 @@ Two groups of tables:
 * ``--alt``: tables of the one-term form (Eq. mlsp2_alt) at (beta0, L) =
   (1500, 26) and (100, 16), from the SP2 sequence in that form
   (ftsp2_train_coeffs_alt), with entropy tables started from them;
+* ``--skip``: Skip-SP2 tables (one stored layer, one accumulator): (1500, 26)
+  from the embedding of the printed table, (100, 16) from the embedding of
+  the SP2 initial guess (ftsp2_train_coeffs_skip), with entropy tables;
 * ``--high``: tables at beta0 in {3000, 6000, 12000, 24000} with
   L = ceil(layer count (Eq. layer count)) + 2 layers, which ragged batches of
   rotated spectra need once the Gershgorin width inflates beta'.
@@ -104,6 +107,47 @@ def main_alt(outdir: str, iterations: int = 3000):
     return out
 
 
+def skip_max_error(target, beta0, mu0, tab, alpha, grid=400_001):
+    """max |model - target| of a Skip-SP2 table on a uniform grid, evaluated
+    with the library's own training kernel (residuals only)."""
+    import torch
+    import paper_2605_08523_gb300 as ft
+    x = torch.linspace(0.0, 1.0, grid, dtype=torch.float64, device="cuda")
+    _, rep = ft.ftsp2_train_coeffs_skip(target, beta0, mu0, tab, x, iterations=0, accel=False, alpha=alpha)
+    return rep["max_err"]
+
+
+def main_skip(outdir: str, iterations: int = 3000):
+    import paper_2605_08523_gb300 as ft
+    from .build import build
+    build()
+    os.makedirs(outdir, exist_ok=True)
+    out = {}
+    printed = ft.ModelSet().table(0)[0]
+    for beta0, L, init in ((1500.0, 26, training.skip_from_mlsp2(printed)), (100.0, 16, None)):
+        t0 = time.time()
+        tab, rep = training.train_skip_table(ft, ft.TARGET_FERMI, beta0, MU0, L, iterations=iterations,
+                                             skip_init=init)
+        rep["seconds"] = time.time() - t0
+        rep["max_err_grid"] = skip_max_error(ft.TARGET_FERMI, beta0, MU0, tab, 1.0)
+        t0 = time.time()
+        tabs, reps = training.train_skip_table(ft, ft.TARGET_ENTROPY, beta0, MU0, L, alpha=ALPHA,
+                                               iterations=iterations, skip_init=tab)
+        reps["seconds"] = time.time() - t0
+        reps["max_err_grid"] = skip_max_error(ft.TARGET_ENTROPY, beta0, MU0, tabs, ALPHA)
+        name = "skip_b%d_L%d" % (int(beta0), L)
+        fit = dict(max_err_fermi=rep["max_err_grid"], max_err_entropy=reps["max_err_grid"])
+        if init is not None:
+            fit["max_err_fermi_start"] = skip_max_error(ft.TARGET_FERMI, beta0, MU0, init, 1.0)
+        out[name] = dict(beta0=beta0, mu0=MU0, alpha=ALPHA, L=L, family="Skip-SP2, one stored layer, one accumulator",
+                         skip=tab.tolist(), skip_entropy=tabs.tolist(), fit=fit,
+                         train=dict(fermi=rep, entropy=reps, samples=100_000, density="1+|f'|"))
+        print(name, out[name]["fit"], flush=True)
+        with open(os.path.join(outdir, name + ".json"), "w") as f:
+            json.dump(out[name], f, indent=1)
+    return out
+
+
 def main(outdir: str, iterations: int = 800, quick: bool = False):
     import paper_2605_08523_gb300 as ft
     from .build import build
@@ -144,7 +188,9 @@ def main(outdir: str, iterations: int = 800, quick: bool = False):
 if __name__ == "__main__":
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
     outdir = args[0] if args else "tables_out"
-    if "--alt" in sys.argv:
+    if "--skip" in sys.argv:
+        main_skip(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)
+    elif "--alt" in sys.argv:
         main_alt(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)
     elif "--high" in sys.argv:
         main_high(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)

@@ -98,6 +98,36 @@ def sp2_alt_init(L: int, mu0: float):
     return alt
 
 
+def skip_from_mlsp2(theta):
+    """(L + 1, 4) Skip-SP2 table (one stored layer, one accumulator, no
+    accumulator feedback) computing the same function as Eq. mlsp2 rows theta
+    (the Appendix embedding): each quadratic is a_i (x + b_i / (2 a_i))^2 + e_i
+    with e_i = c_i - b_i^2 / (4 a_i); the square is the next layer's x~, whose
+    combination carries a_{i-1} and e_{i-1}; the accumulator weights pick up
+    a_{i-1}, and the constants e collect in A_0."""
+    th = np.asarray(theta, dtype=np.float64)
+    L = th.shape[0]
+    a, b, c, d = th[:, 0], th[:, 1], th[:, 2], th[:, 3]
+    e = c - b * b / (4.0 * a)
+    tab = np.zeros((L + 1, 4))
+    tab[0] = (b[0] / (2.0 * a[0]), 1.0, 0.0, d[0])
+    for i in range(1, L):
+        tab[i] = (e[i - 1] + b[i] / (2.0 * a[i]), a[i - 1], 0.0, d[i] * a[i - 1])
+    tab[L, 0] = e[L - 1] + float(np.dot(d[1:], e[:-1]))
+    tab[L, 1] = a[L - 1]
+    return tab
+
+
+def train_skip_table(ft, target: int, beta0: float, mu0: float, L: int, alpha: float = 1.0, iterations: int = 500,
+                     nsamples: int = 100_000, skip_init=None, accel: bool = True, device="cuda"):
+    """Fit a Skip-SP2 table on the GPU (ftsp2_train_coeffs_skip); the default
+    start is the embedding of the SP2 initial guess."""
+    import torch
+    x = torch.from_numpy(sample_points(nsamples, beta0, mu0)).to(device)
+    t0 = skip_from_mlsp2(sp2_init(L, beta0, mu0)) if skip_init is None else np.asarray(skip_init, dtype=np.float64)
+    return ft.ftsp2_train_coeffs_skip(target, beta0, mu0, t0, x, iterations=iterations, accel=accel, alpha=alpha)
+
+
 def train_alt_table(ft, target: int, beta0: float, mu0: float, L: int, alpha: float = 1.0, iterations: int = 500,
                     nsamples: int = 100_000, alt_init=None, accel: bool = True, device="cuda"):
     """Fit a table of the one-term form on the GPU (ftsp2_train_coeffs_alt)."""

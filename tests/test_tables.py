@@ -10,7 +10,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import altform, tables, train
+from oracle import altform, skipsp2, tables, train
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 FILES = sorted(glob.glob(os.path.join(ROOT, "paper_2605_08523_gb300", "tables", "*.json")))
@@ -33,7 +33,13 @@ def test_tables_present():
 def test_table_fit_errors(path):
     d = json.load(open(path))
     b0, m0, al = d["beta0"], d["mu0"], d["alpha"]
-    if "alt" in d:
+    if "skip" in d:
+        # Skip-SP2 (one stored layer, one accumulator): the oracle's recursion of that family
+        t, te = np.array(d["skip"]), np.array(d["skip_entropy"])
+        assert t.shape == (d["L"] + 1, 4) and te.shape == (d["L"] + 1, 4)
+        ef = skipsp2.max_error(t, "fermi", b0, m0, 1.0, grid=400001)
+        es = skipsp2.max_error(te, "entropy", b0, m0, al, grid=400001)
+    elif "alt" in d:
         # one-term form (Eq. mlsp2_alt): evaluated with the oracle's own recursion of that form
         a, ae = np.array(d["alt"]), np.array(d["alt_entropy"])
         assert a.shape == (d["L"] + 1, 2) and ae.shape == (d["L"] + 1, 2)
@@ -65,6 +71,15 @@ def test_one_term_tables():
     for name in ("alt_b1500_L26", "alt_b100_L16"):
         d = load(name)
         assert d["fit"]["max_err_fermi"] < 3e-5 and d["fit"]["max_err_entropy"] < 3e-5, name
+
+
+def test_skip_tables():
+    # the accumulator feedback improves the embedded printed table's fit
+    d = load("skip_b1500_L26")
+    assert d["fit"]["max_err_fermi"] < 0.5 * d["fit"]["max_err_fermi_start"]
+    assert d["fit"]["max_err_fermi"] < 1e-7 and d["fit"]["max_err_entropy"] < 1e-5
+    assert max(abs(r[2]) for r in d["skip"][:-1]) > 0.0
+    assert load("skip_b100_L16")["fit"]["max_err_fermi"] < 3e-5
 
 
 def test_training_sweep_layer_count():
