@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--epilogue", default="auto", choices=["auto", "deferred", "inline"],
                    help="final epilogue of the pair tiles: the library's default, or forced "
                         "(FTSP2_EPI_DEFERRED / FTSP2_EPI_INLINE)")
+    p.add_argument("--operands", default="upper", choices=["upper", "full"],
+                   help="operand storage of the 16-bit tensor-core layers: upper triangle with transposed "
+                        "panel loads (default), or full matrices (FTSP2_FULL_OPERANDS)")
     p.add_argument("--table", default="printed", choices=["printed", "alt", "skip"],
                    help="cfg1/cfg4 Fermi table: the paper's printed 26-layer table (with the trained entropy "
                         "table), the 26-layer beta0 = 1500 table of the one-term form (Eq. mlsp2_alt), or the "
@@ -387,6 +390,7 @@ def run_cfg2(args):
     Hd = torch.from_numpy(flat).cuda()
     shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
     shape_flag |= {"auto": 0, "deferred": ft.EPI_DEFERRED, "inline": ft.EPI_INLINE}[args.epilogue]
+    shape_flag |= ft.FULL_OPERANDS if args.operands == "full" else 0
     if args.bounds == "lanczos":
         shape_flag |= ft.LANCZOS
     if args.policy == "layers":
@@ -485,6 +489,7 @@ def main():
     ms = ft.ModelSet.from_json(tabs)
     shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
     shape_flag |= {"auto": 0, "deferred": ft.EPI_DEFERRED, "inline": ft.EPI_INLINE}[args.epilogue]
+    shape_flag |= ft.FULL_OPERANDS if args.operands == "full" else 0
     refine = 2 if cfg4 and args.refine == 0 else args.refine
     shape_flag |= {0: 0, 1: ft.REFINE1, 2: ft.REFINE2}[refine]
     if args.refine_tc:
@@ -615,7 +620,7 @@ def main():
                    "e_min": float(rec["e_min"]), "e_max": float(rec["e_max"]),
                    "l2": "inputs and working set larger than L2 (no flush)", "parallelism": "replicas",
                    "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
-                   "epilogue": args.epilogue, "table": args.table,
+                   "epilogue": args.epilogue, "table": args.table, "operands": args.operands,
                    "autotune_ms": {"single": ms_single, "pair": ms_pair}},
         "tflops_alg": alg_flops / t_step / 1e12 * world,
         "density_only": {"value": world / t_density, "unit": "solves/s", "ms_per_step": t_density * 1e3},

@@ -119,6 +119,14 @@ typedef enum {
  * identical). */
 #define FTSP2_EPI_DEFERRED  0x200
 #define FTSP2_EPI_INLINE    0x400
+/* Operand storage of the FP16X2 / BF16X3 tensor-core layers.  The square of a
+ * symmetric matrix needs its full row panels, but by default a layer stores
+ * the next operands only for the upper triangle (plus the diagonal tile
+ * blocks), and the next layer loads the K-slices left of a panel's diagonal
+ * block as transposed panels of the upper triangle (MN-major tcgen05
+ * operands).  This halves the operand stores of the epilogue.  With this flag
+ * every layer writes and reads full matrices (results are identical). */
+#define FTSP2_FULL_OPERANDS 0x800
 
 /* One Hamiltonian of a (ragged) batch.  H_b starts at dH + offset and is
  * n x n row-major; D_b starts at dD + offset.  Offsets are in elements. */

@@ -619,6 +619,9 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
                 for (int sp = 0; sp < nsplit; ++sp) {
                     void* base = W + L.OP[c][p] + (size_t)sp * es * L.plane_elems;
                     if (!encode_map(&maps[p].a[c][sp], base, dt, es, L.P, nb, bke, kTileM)) return FTSP2_E_CUDA;
+                    // transposed 64 x 64 panels of the upper triangle (16-bit planes)
+                    if (es == 2 && !encode_map(&maps[p].t[c][sp], base, dt, es, L.P, nb, 64, 64))
+                        return FTSP2_E_CUDA;
                 }
     }
     // tensor maps of the BF16X3 refinement operands (FTSP2_REFINE_TC)
@@ -630,6 +633,8 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
                 for (int sp = 0; sp < 3; ++sp) {
                     void* base = W + L.OPR[c][p] + (size_t)sp * 2 * L.plane_elems;
                     if (!encode_map(&mapsR[p].a[c][sp], base, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, L.P, nb, 64, kTileM))
+                        return FTSP2_E_CUDA;
+                    if (!encode_map(&mapsR[p].t[c][sp], base, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, L.P, nb, 64, 64))
                         return FTSP2_E_CUDA;
                 }
     }
@@ -657,6 +662,11 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     auto is_rtc = [&](int g) { return refine_tc && g >= refine_from; };
     const int pair = all_simt ? 1 : tile_shape_choice(inst, nb, mode, want, flags, di.sms);
     int last_table = 0;
+    // Operands of 16-bit tensor-core layers are stored as the upper triangle
+    // plus the diagonal tile blocks when the layer that reads them can load the
+    // rest transposed (FP16X2, BF16X3); the mirror is written everywhere before
+    // an FP32 or TF32X3 layer.  Layer 0 reads the full matrices of init.
+    int prev_skips_mirror = 0;
     for (int g = 0; g < Lmax; ++g) {
         const bool simt = is_simt(g);
         const bool next_simt = g + 1 < Lmax && is_simt(g + 1);
@@ -671,6 +681,10 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         // near 0 and 1.
         la.chunk_elems = chunk_elems_of(lmode, g, Lmax);
         la.next_fmt = next_simt ? OP_F32 : (next_rtc ? OP_BF16X3 : fmt);
+        const bool next_tc16 = !la.last && (la.next_fmt == OP_F16X2 || la.next_fmt == OP_BF16X3);
+        la.mirror_all = (next_tc16 && !(flags & FTSP2_FULL_OPERANDS)) ? 0 : 1;
+        la.lower_t = (!simt && prev_skips_mirror) ? 1 : 0;
+        prev_skips_mirror = la.mirror_all ? 0 : 1;
         for (int c = 0; c < L.nchains; ++c) {
             const int rp = g & 1, wp = (g + 1) & 1;
             if (simt || rtc) la.opr[c] = all_simt ? W + L.OP[c][rp] : W + L.OPR[c][rp];

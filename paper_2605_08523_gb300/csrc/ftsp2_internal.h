@@ -215,10 +215,17 @@ struct LayerArgs {
     double* partials;
     int* status;
     float* escr;                      // deferred final epilogue: kEpiScratchFloats per CTA, or null (inline)
+    // Symmetric operands stored as the upper triangle plus the diagonal tile
+    // blocks: lower_t = this layer's operands are stored so (K-slices left of
+    // a panel's diagonal block are loaded transposed from the upper triangle);
+    // mirror_all = this layer writes the mirror (c, r) everywhere (the next
+    // layer reads full matrices), else only inside diagonal tiles.
+    int lower_t, mirror_all;
 };
 
 struct TmaMaps {
     CUtensorMap a[kMaxChains][3];   // [chain][split plane], boxes of 128 rows x 128 bytes
+    CUtensorMap t[kMaxChains][3];   // 16-bit planes: boxes of 64 rows x 64 columns (transposed panels)
 };
 
 // Tensor-core layer (k_layer_tc.cu); mode in {TF32X3, BF16X3, FP16X2}.

@@ -138,6 +138,24 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
+// MN-major (transposed) operand panel, 128-byte swizzle: atoms of 8 K-rows x
+// 64 MN elements (1 KB), the K atoms of one 64-wide MN half consecutive, the
+// second MN half 8 KB further.
+#ifndef FTSP2_MN_LBO
+#define FTSP2_MN_LBO 8192
+#endif
+constexpr uint32_t kMnLbo = FTSP2_MN_LBO;
+constexpr uint32_t kMnSbo = FTSP2_MN_LBO == 8192 ? 1024 : 8192;
+__device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(kMnLbo >> 4) << 16;     // leading byte offset
+    d |= (uint64_t)(kMnSbo >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    return d;
+}
+
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -425,7 +443,7 @@ struct SrcSmem {
 // row c.
 template <int FMT, class Src>
 __device__ __forceinline__ void epi_dgroup_next(const LayerArgs& a, const EpiLite& e, int n, int R0, int r, int c0,
-                                                const Src& src) {
+                                                const Src& src, bool mirror) {
     using F = OpFmtT<FMT>;
     constexpr int ESZ = F::ESZ;
     constexpr int NPL = F::NPL;
@@ -468,7 +486,7 @@ __device__ __forceinline__ void epi_dgroup_next(const LayerArgs& a, const EpiLit
                 }
                 // mirror (c, r), r < c: one contiguous run of row c per column
                 const int c = cg + u;
-                if (r < c && c < n)
+                if (mirror && r < c && c < n)
                     store1<ESZ>(e.op + (size_t)p * a.plane_elems * ESZ + ((size_t)c * P + r) * ESZ, o[p]);
             }
         }
@@ -707,8 +725,15 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                 const int nk = (n + BKE - 1) / BKE;
                 const int rowA = tl.inst * a.P + tl.I * TILE + (int)rank * kCtaRows;
                 const int rowB = tl.inst * a.P + tl.J * TILE + (int)rank * kCtaRows;
+                // transposed panels: MN index (column of the stored upper block)
+                const int mnA = tl.I * TILE + (int)rank * kCtaRows, mnB = tl.J * TILE + (int)rank * kCtaRows;
                 bool ok = true;
                 for (int kb = 0; kb < nk; ++kb) {
+                    // K-slices left of a panel's diagonal block: not stored below
+                    // the diagonal, loaded from the transposed upper block
+                    const bool lowA = !C::TF32 && a.lower_t && kb * BKE + BKE <= tl.I * TILE;
+                    const bool lowB = !C::TF32 && a.lower_t && kb * BKE + BKE <= tl.J * TILE;
+                    const int krow = tl.inst * a.P + kb * BKE;
                     if (!wait_bar(&empty_bar[stage], phase ^ 1u, &abort_flag, a.status)) {
                         ok = false;
                         break;
@@ -720,18 +745,38 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                         remote_expect_tx(fb, STAGE_BYTES);
 #pragma unroll
                         for (int s = 0; s < C::NSPLIT; ++s) {
-                            tma_load_pair(smem_u32(sbase + s * PLANE), &maps.a[tl.chain][s], fb, kb * BKE, rowA);
-                            tma_load_pair(smem_u32(sbase + (C::NSPLIT + s) * PLANE), &maps.a[tl.chain][s], fb,
-                                          kb * BKE, rowB);
+                            const uint32_t dA = smem_u32(sbase + s * PLANE), dB = smem_u32(sbase + (C::NSPLIT + s) * PLANE);
+                            if (lowA) {
+                                tma_load_pair(dA, &maps.t[tl.chain][s], fb, mnA, krow);
+                                tma_load_pair(dA + PLANE / 2, &maps.t[tl.chain][s], fb, mnA + 64, krow);
+                            } else {
+                                tma_load_pair(dA, &maps.a[tl.chain][s], fb, kb * BKE, rowA);
+                            }
+                            if (lowB) {
+                                tma_load_pair(dB, &maps.t[tl.chain][s], fb, mnB, krow);
+                                tma_load_pair(dB + PLANE / 2, &maps.t[tl.chain][s], fb, mnB + 64, krow);
+                            } else {
+                                tma_load_pair(dB, &maps.a[tl.chain][s], fb, kb * BKE, rowB);
+                            }
                         }
                     } else {
                         const uint32_t fb = smem_u32(&full_bar[stage]);
                         local_expect_tx(fb, STAGE_BYTES);
 #pragma unroll
                         for (int s = 0; s < C::NSPLIT; ++s) {
-                            tma_load_one(smem_u32(sbase + s * PLANE), &maps.a[tl.chain][s], fb, kb * BKE, rowA);
-                            tma_load_one(smem_u32(sbase + (C::NSPLIT + s) * PLANE), &maps.a[tl.chain][s], fb,
-                                         kb * BKE, rowB);
+                            const uint32_t dA = smem_u32(sbase + s * PLANE), dB = smem_u32(sbase + (C::NSPLIT + s) * PLANE);
+                            if (lowA) {
+                                tma_load_one(dA, &maps.t[tl.chain][s], fb, mnA, krow);
+                                tma_load_one(dA + PLANE / 2, &maps.t[tl.chain][s], fb, mnA + 64, krow);
+                            } else {
+                                tma_load_one(dA, &maps.a[tl.chain][s], fb, kb * BKE, rowA);
+                            }
+                            if (lowB) {
+                                tma_load_one(dB, &maps.t[tl.chain][s], fb, mnB, krow);
+                                tma_load_one(dB + PLANE / 2, &maps.t[tl.chain][s], fb, mnB + 64, krow);
+                            } else {
+                                tma_load_one(dB, &maps.a[tl.chain][s], fb, kb * BKE, rowB);
+                            }
                         }
                     }
                     if (++stage == C::STAGES) {
@@ -754,6 +799,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             // descriptors differ only in the start-address field (bits 0-13,
             // address >> 4); all operand slices lie inside this CTA's window
             const uint64_t desc0 = sdesc_sw128(smem_u32(smem));
+            const uint64_t descT = sdesc_mn_sw128(smem_u32(smem));   // transposed panels
             for (int t = unit; t < a.ntiles && ok && !abort_flag; t += nunits) {
                 const Tile tl = a.tiles[t];
                 int k;
@@ -775,17 +821,25 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                         }
                         tc_fence_after();
                         const uint64_t ds = desc0 + (uint64_t)((stage * STAGE_BYTES) >> 4);
+                        const uint64_t dsT = descT + (uint64_t)((stage * STAGE_BYTES) >> 4);
                         const uint32_t first = kb == kc ? 0u : 1u;
+                        // the producer's classification of this K-slice (transposed
+                        // panels: MN-major operand, K steps of two 1 KB atoms)
+                        const bool lowA = !C::TF32 && a.lower_t && kb * BKE + BKE <= tl.I * TILE;
+                        const bool lowB = !C::TF32 && a.lower_t && kb * BKE + BKE <= tl.J * TILE;
+                        const uint32_t idesc = IDESC | (lowA ? 1u << 15 : 0u) | (lowB ? 1u << 16 : 0u);
+                        const uint64_t baseA = lowA ? dsT : ds, baseB = lowB ? dsT : ds;
+                        const uint32_t stepA = lowA ? 2048u : 32u, stepB = lowB ? 2048u : 32u;
 #pragma unroll
                         for (int kk = 0; kk < KSTEPS; ++kk) {
 #pragma unroll
                             for (int p = 0; p < C::NPROD; ++p) {
-                                const uint64_t da = ds + (uint64_t)((prod_a(p) * PLANE + kk * 32) >> 4);
-                                const uint64_t db = ds + (uint64_t)(((C::NSPLIT + prod_b(p)) * PLANE + kk * 32) >> 4);
+                                const uint64_t da = baseA + (uint64_t)((prod_a(p) * PLANE + kk * stepA) >> 4);
+                                const uint64_t db = baseB + (uint64_t)(((C::NSPLIT + prod_b(p)) * PLANE + kk * stepB) >> 4);
                                 if constexpr (PAIR)
-                                    umma_pair<C::TF32>(dt, da, db, IDESC, (kk == 0 && p == 0) ? first : 1u);
+                                    umma_pair<C::TF32>(dt, da, db, idesc, (kk == 0 && p == 0) ? first : 1u);
                                 else
-                                    umma_one<C::TF32>(dt, da, db, IDESC, (kk == 0 && p == 0) ? first : 1u);
+                                    umma_one<C::TF32>(dt, da, db, idesc, (kk == 0 && p == 0) ? first : 1u);
                             }
                         }
                         if constexpr (PAIR) umma_commit_pair(smem_u32(&empty_bar[stage]));
@@ -869,7 +923,8 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                 ItemGeo ig;
                 item_geo<TILE, EPI_COLS>(tl, (int)rank, n, iu, ig);
                 const SrcSmem src{reinterpret_cast<const float*>(ring + slot * kEntryBytes) + lane * 4};
-                epi_dgroup_next<OUTFMT>(a, e, n, ig.R0, ig.R0 + lane, ig.C0 + kGrp * gu, src);
+                epi_dgroup_next<OUTFMT>(a, e, n, ig.R0, ig.R0 + lane, ig.C0 + kGrp * gu, src,
+                                        a.mirror_all || tl.I == tl.J);
                 __syncwarp();                    // every lane is done with the slot
                 ++used;
                 if (more) {
@@ -1007,7 +1062,8 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                     const int g_hi = min(EPI_COLS / kGrp, (n - C0 + kGrp - 1) / kGrp);
 #pragma unroll 1
                     for (int g = g_lo & ~1; g < g_hi; g += 2)
-                        epi_dgroup_next<OUTFMT>(a, e, n, R0, r, C0 + kGrp * g, SrcTmem{tfin + 8 * g});
+                        epi_dgroup_next<OUTFMT>(a, e, n, R0, r, C0 + kGrp * g, SrcTmem{tfin + 8 * g},
+                                                a.mirror_all || tl.I == tl.J);
                 }
             }
             // release the held accumulator buffer
