@@ -554,23 +554,55 @@ def main():
     del solver_d
 
     # ---- end to end through the public API with host buffers ----
+    # Every step copies its H from pinned host memory and reads D, S and the
+    # traces back.  Two solvers alternate so that the copies of one step run on
+    # their own streams while the other step computes: H -> device of step i+1
+    # and D -> host of step i-1 overlap step i.
     Hh = torch.from_numpy(H.ravel().copy()).pin_memory()
-    Dh = torch.empty(n * n, dtype=torch.float32).pin_memory()
-    Sh = torch.empty(1, dtype=torch.float64).pin_memory()
-    Th = torch.empty(2, dtype=torch.float64).pin_memory()
-    Hdev = torch.empty_like(Hd)
+    Dh = [torch.empty(n * n, dtype=torch.float32).pin_memory() for _ in range(2)]
+    Sh = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
+    Th = [torch.empty(2, dtype=torch.float64).pin_memory() for _ in range(2)]
+    Hdev = [torch.empty_like(Hd) for _ in range(2)]
+    solvers = [solver, ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3, flags=shape_flag)]
+    comp = torch.cuda.current_stream()
+    s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
 
-    def e2e_step():
-        Hdev.copy_(Hh, non_blocking=True)
-        solver.run(Hdev)
-        Dh.copy_(solver.D, non_blocking=True)
-        Sh.copy_(solver.S, non_blocking=True)
-        Th.copy_(solver.trace[0], non_blocking=True)
+    def e2e_run(steps):
+        ev_h2d = [torch.cuda.Event() for _ in range(2)]
+        ev_done = [torch.cuda.Event() for _ in range(2)]
+        ev_d2h = [torch.cuda.Event() for _ in range(2)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(comp)
+        s_h2d.wait_event(e0)
+        for i in range(steps):
+            k = i % 2
+            if i >= 2:
+                s_h2d.wait_event(ev_done[k])        # step i-2 has consumed Hdev[k]
+            with torch.cuda.stream(s_h2d):
+                Hdev[k].copy_(Hh, non_blocking=True)
+                ev_h2d[k].record(s_h2d)
+            comp.wait_event(ev_h2d[k])
+            if i >= 2:
+                comp.wait_event(ev_d2h[k])          # step i-2's outputs are on the host
+            solvers[k].run(Hdev[k], stream=comp)
+            ev_done[k].record(comp)
+            s_d2h.wait_event(ev_done[k])
+            with torch.cuda.stream(s_d2h):
+                Dh[k].copy_(solvers[k].D, non_blocking=True)
+                Sh[k].copy_(solvers[k].S, non_blocking=True)
+                Th[k].copy_(solvers[k].trace[0], non_blocking=True)
+                ev_d2h[k].record(s_d2h)
+        comp.wait_event(ev_d2h[(steps - 1) % 2])
+        if steps >= 2:
+            comp.wait_event(ev_d2h[(steps - 2) % 2])
+        e1.record(comp)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0 / steps
 
-    e2e_step()
-    torch.cuda.synchronize()
+    e2e_run(2)
+    assert torch.equal(Dh[0], Dh[1]) and torch.equal(Dh[0], solver.D.cpu()), "end-to-end outputs differ"
     e2e_steps = max(3, args.steps // 2)
-    t_e2e = cuda_time(e2e_step, e2e_steps)
+    t_e2e = e2e_run(e2e_steps)
     h2d = n * n * 8
     d2h = n * n * 4 + 8 + 16
 
