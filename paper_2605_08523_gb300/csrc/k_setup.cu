@@ -268,71 +268,87 @@ void launch_decide(const SetupArgs& a, cudaStream_t s) {
 // parity buffer of its start layer; the other parity buffer is zeroed so that
 // padding rows and columns read as zeros in every layer.
 // ------------------------------------------------------------------------------
-__device__ __forceinline__ void write_operand(int fmt, uint8_t* base, size_t plane_elems, size_t idx,
-                                              float z, float scale) {
+// 32-byte store (sm_100+): dst 32-byte aligned.
+__device__ __forceinline__ void st32(void* dst, const uint32_t* w) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
+// The operands of 16 consecutive elements of one row (idx0 % 16 == 0) in
+// format fmt, as 32-byte vectors per plane; z == nullptr writes zeros.
+__device__ __forceinline__ void write_operand16(int fmt, uint8_t* base, size_t plane_elems, size_t idx0,
+                                                const float* z, float scale) {
+    uint32_t w[3][16];
+    int npl = 1, esz = 4;
     switch (fmt) {
-        case OP_F32:
-            reinterpret_cast<float*>(base)[idx] = z;
-            break;
-        case OP_TF32X3: {
-            uint32_t hb;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(z));
-            const float h = __uint_as_float(hb);
-            reinterpret_cast<float*>(base)[idx] = h;
-            reinterpret_cast<float*>(base)[plane_elems + idx] = z - h;
-            break;
+        case OP_F16X2: npl = 2; esz = 2; break;
+        case OP_BF16X3: npl = 3; esz = 2; break;
+        case OP_TF32X3: npl = 2; esz = 4; break;
+        default: npl = 1; esz = 4; break;
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        uint32_t o[3] = {0u, 0u, 0u};
+        if (z) {
+            const float v = z[u];
+            if (fmt == OP_F16X2) {
+                const float zs = v * scale;
+                const __half h = __float2half_rn(zs);
+                const __half l = __float2half_rn(zs - __half2float(h));
+                o[0] = __half_as_ushort(h);
+                o[1] = __half_as_ushort(l);
+            } else if (fmt == OP_BF16X3) {
+                const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
+                const float r1 = v - __bfloat162float(b0);
+                const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+                const __nv_bfloat16 b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
+                o[0] = __bfloat16_as_ushort(b0);
+                o[1] = __bfloat16_as_ushort(b1);
+                o[2] = __bfloat16_as_ushort(b2);
+            } else if (fmt == OP_TF32X3) {
+                uint32_t hb;
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
+                o[0] = hb;
+                o[1] = __float_as_uint(v - __uint_as_float(hb));
+            } else {
+                o[0] = __float_as_uint(v);
+            }
         }
-        case OP_BF16X3: {
-            const __nv_bfloat16 b0 = __float2bfloat16_rn(z);
-            const float r1 = z - __bfloat162float(b0);
-            const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
-            const float r2 = r1 - __bfloat162float(b1);
-            const __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
-            __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(base);
-            p[idx] = b0;
-            p[plane_elems + idx] = b1;
-            p[2 * plane_elems + idx] = b2;
-            break;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            if (esz == 2) {
+                if (u & 1) w[p][u / 2] |= o[p] << 16;
+                else w[p][u / 2] = o[p];
+            } else {
+                w[p][u] = o[p];
+            }
         }
-        case OP_F16X2: {
-            const float zs = z * scale;
-            const __half h = __float2half_rn(zs);
-            const __half l = __float2half_rn(zs - __half2float(h));
-            __half* p = reinterpret_cast<__half*>(base);
-            p[idx] = h;
-            p[plane_elems + idx] = l;
-            break;
-        }
+    }
+    for (int p = 0; p < npl; ++p) {
+        uint8_t* dst = base + ((size_t)p * plane_elems + idx0) * esz;
+        st32(dst, w[p]);
+        if (esz == 4) st32(dst + 32, w[p] + 8);
     }
 }
 
-__device__ __forceinline__ void zero_operand(int fmt, uint8_t* base, size_t plane_elems, size_t idx) {
-    switch (fmt) {
-        case OP_F32: reinterpret_cast<float*>(base)[idx] = 0.f; break;
-        case OP_TF32X3:
-            reinterpret_cast<float*>(base)[idx] = 0.f;
-            reinterpret_cast<float*>(base)[plane_elems + idx] = 0.f;
-            break;
-        case OP_BF16X3: {
-            uint16_t* p = reinterpret_cast<uint16_t*>(base);
-            p[idx] = 0;
-            p[plane_elems + idx] = 0;
-            p[2 * plane_elems + idx] = 0;
-            break;
-        }
-        case OP_F16X2: {
-            uint16_t* p = reinterpret_cast<uint16_t*>(base);
-            p[idx] = 0;
-            p[plane_elems + idx] = 0;
-            break;
-        }
-    }
-}
-
+// Layer-0 state and operands.  One CTA per (32-row band, instance); lane =
+// row of the band, each warp walks 16-column chunks of the instance's
+// R x R square (R = n rounded up to the largest tile, 256, at most P):
+// * Z_0 = z0 X, A = a0 X with X = H0 - mu0 I (times alpha for the entropy
+//   chain), in the blocked state layout, for the rows below n and the chunks
+//   that reach the upper triangle of the band's 32-row block (the only state
+//   the layer epilogues read): four 512-byte runs per warp and chunk;
+// * operands of Z_0 in the format of the instance's first layer (one parity),
+//   zeros outside n x n in every format and parity a layer may read, as one
+//   32-byte vector per lane and plane (row-major planes).
 __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
     const int b = blockIdx.y;
     const ftsp2_instance in = a.inst[b];
     const int n = in.n, P = a.P;
+    const int R = min(P, (n + 255) & ~255);
+    const int band = blockIdx.x * 32;
+    if (band >= R) return;
     const ftsp2_rescale_rec rec = a.rec[b];
     const bool ok = rec.status == FTSP2_OK && rec.model >= 0;
     const size_t base = (size_t)b * P * P;
@@ -348,39 +364,68 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
         z0S = M.z0S;
         a0S = M.a0S;
     }
-    // The layers of this instance read rows and columns below n rounded up to
-    // the largest tile (256), never the rest of the P x P slab: only that
-    // square is initialised (padding zeroed).
-    const int R = min(P, (n + 255) & ~255);
-    for (int r = blockIdx.x; r < R; r += gridDim.x) {
-        const double* Hr = a.H + in.offset + (size_t)r * n;
-        for (int c = threadIdx.x; c < R; c += blockDim.x) {
-            const size_t e = base + (size_t)r * P + c;
-            const size_t es = base + state_off(P, r, c);
-            const bool inside = r < n && c < n;
-            float z = 0.f;
-            if (ok && inside) z = (float)(rec.scale * ((r == c ? in.mu : 0.0) - __ldg(Hr + c)));
-            for (int ch = 0; ch < a.nchains; ++ch) {
-                const bool ent = a.chain_kind[ch] == CHAIN_ENTROPY;
-                // centred layer-0 input of the chain, then the family's layer-0 state
-                const float xc = ent ? alpha * z : z;
-                const float zc = (ent ? z0S : z0) * xc;
-                a.Z[ch][es] = zc;
-                a.A[ch][es] = (ent ? a0S : a0) * xc;
-                if (inside) {
-                    const int start = (sl_packed >> (16 * ch)) & 0xffff;
-                    if (a.main_fmt != OP_F32 && start >= a.refine_from)
-                        write_operand(a.refine_fmt, a.OPR[ch][start & 1], a.plane_elems, e, zc, 1.f);
-                    else write_operand(a.main_fmt, a.OP[ch][start & 1], a.plane_elems, e, zc,
-                                       ent ? sc0S : sc0);
-                } else {
-                    // padding: zero in every format and parity a layer may read
-                    zero_operand(a.main_fmt, a.OP[ch][0], a.plane_elems, e);
-                    zero_operand(a.main_fmt, a.OP[ch][1], a.plane_elems, e);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = band + lane;
+    const bool row_in = r < n;
+    const double* Hr = a.H + in.offset + (size_t)r * n;
+    for (int cc = warp * 16; cc < R; cc += 8 * 16) {
+        float z[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int c = cc + u;
+            z[u] = (ok && row_in && c < n) ? (float)(rec.scale * ((r == c ? in.mu : 0.0) - __ldg(Hr + c))) : 0.f;
+        }
+        const bool inside = row_in && cc < n;        // the chunk holds elements of the n x n matrix
+        const bool state = inside && cc + 15 >= band;
+        for (int ch = 0; ch < a.nchains; ++ch) {
+            const bool ent = a.chain_kind[ch] == CHAIN_ENTROPY;
+            const float xs = ent ? alpha : 1.f;
+            const float zf = (ent ? z0S : z0) * xs, af = (ent ? a0S : a0) * xs;
+            float zc[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) zc[u] = zf * z[u];
+            if (state) {
+#pragma unroll
+                for (int blk = 0; blk < 2; ++blk) {
+                    const size_t so = base + state_off(P, r, cc + 8 * blk);
+                    float* Zs = a.Z[ch] + so;
+                    float* As = a.A[ch] + so;
+                    reinterpret_cast<float4*>(Zs)[0] = make_float4(zc[8 * blk], zc[8 * blk + 1], zc[8 * blk + 2], zc[8 * blk + 3]);
+                    reinterpret_cast<float4*>(Zs + 128)[0] =
+                        make_float4(zc[8 * blk + 4], zc[8 * blk + 5], zc[8 * blk + 6], zc[8 * blk + 7]);
+                    reinterpret_cast<float4*>(As)[0] = make_float4(af * z[8 * blk], af * z[8 * blk + 1],
+                                                                   af * z[8 * blk + 2], af * z[8 * blk + 3]);
+                    reinterpret_cast<float4*>(As + 128)[0] = make_float4(af * z[8 * blk + 4], af * z[8 * blk + 5],
+                                                                         af * z[8 * blk + 6], af * z[8 * blk + 7]);
+                }
+            }
+            const size_t e0 = base + (size_t)r * P + cc;
+            if (inside) {
+                // the values (zeros beyond n within the chunk) in the first layer's format
+                const int start = (sl_packed >> (16 * ch)) & 0xffff;
+                const bool ref = a.main_fmt != OP_F32 && start >= a.refine_from;
+                if (ref) write_operand16(a.refine_fmt, a.OPR[ch][start & 1], a.plane_elems, e0, zc, 1.f);
+                else write_operand16(a.main_fmt, a.OP[ch][start & 1], a.plane_elems, e0, zc, ent ? sc0S : sc0);
+                if (cc + 15 >= n) {
+                    // a chunk across the order: its padding columns must read as zero in
+                    // every other format and parity too (its columns below n there are
+                    // written by a layer before any layer reads them)
+                    if (ref || (start & 1) != 0) write_operand16(a.main_fmt, a.OP[ch][0], a.plane_elems, e0, nullptr, 1.f);
+                    if (ref || (start & 1) != 1) write_operand16(a.main_fmt, a.OP[ch][1], a.plane_elems, e0, nullptr, 1.f);
                     if (a.OPR[ch][0]) {
-                        zero_operand(a.refine_fmt, a.OPR[ch][0], a.plane_elems, e);
-                        zero_operand(a.refine_fmt, a.OPR[ch][1], a.plane_elems, e);
+                        if (!ref || (start & 1) != 0)
+                            write_operand16(a.refine_fmt, a.OPR[ch][0], a.plane_elems, e0, nullptr, 1.f);
+                        if (!ref || (start & 1) != 1)
+                            write_operand16(a.refine_fmt, a.OPR[ch][1], a.plane_elems, e0, nullptr, 1.f);
                     }
+                }
+            } else {
+                // padding: zero in every format and parity a layer may read
+                write_operand16(a.main_fmt, a.OP[ch][0], a.plane_elems, e0, nullptr, 1.f);
+                write_operand16(a.main_fmt, a.OP[ch][1], a.plane_elems, e0, nullptr, 1.f);
+                if (a.OPR[ch][0]) {
+                    write_operand16(a.refine_fmt, a.OPR[ch][0], a.plane_elems, e0, nullptr, 1.f);
+                    write_operand16(a.refine_fmt, a.OPR[ch][1], a.plane_elems, e0, nullptr, 1.f);
                 }
             }
         }
@@ -388,8 +433,7 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
 }
 
 void launch_init(const InitArgs& a, int max_n, cudaStream_t s) {
-    int gx = a.P < 2048 ? a.P : 2048;
-    dim3 grid(gx, a.nb);
+    dim3 grid((a.P + 31) / 32, a.nb);
     init_kernel<<<grid, 256, 0, s>>>(a);
     count_launch();
 }
