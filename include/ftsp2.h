@@ -111,7 +111,7 @@ typedef enum {
 /* Final epilogue of the 256 x 256 pair tiles in the layers of the main format
  * (Z_{k+1}, A_{k+1} and the next layer's operands from a finished tile).  By
  * default it is deferred when the tiles are long (mean order n over the pair
- * tiles >= 2048): the accumulating warps pass a finished tile's sums to two
+ * tiles >= 3072): the accumulating warps pass a finished tile's sums to two
  * store warps per CTA through a scratch in the workspace (128 KB per CTA, at
  * most 192 CTAs) and go on with the next tile, so that the epilogue's memory
  * traffic overlaps the next tile's MMAs; for shorter tiles the accumulating

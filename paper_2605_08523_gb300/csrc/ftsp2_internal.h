@@ -31,7 +31,7 @@ constexpr int kPad = 128;                    // matrix pitch granularity (elemen
 constexpr int kPartialSlots = 32;            // FP64 partial-sum slots per tile (last layer)
 constexpr int kEpiScratchFloats = 32768;     // deferred epilogue: finished sums of one CTA's tile
 constexpr int kMaxDeferCtas = 192;           // CTAs with a scratch slot in the workspace
-constexpr int kDeferMinK = 2048;             // default: deferred epilogue from this mean tile K
+constexpr int kDeferMinK = 3072;             // default: deferred epilogue from this mean tile K
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;   // 4 s
 
 enum ChainKind : int { CHAIN_FERMI = 0, CHAIN_ENTROPY = 1 };
