@@ -132,3 +132,16 @@ def test_library_conversion_matches_oracle():
     bad[1, 0] = np.nan
     with pytest.raises(ft.Ftsp2Error):
         ft.ftsp2_alt_to_mlsp2(bad)
+
+
+def test_lm_fit_lowers_the_cost_from_the_sp2_start():
+    # property of the LM loop (Marquardt acceptance): the accepted cost never
+    # rises, and a few iterations from the exact SP2 sequence cut it by orders
+    beta0, mu0, L = 40.0, 1.0 / 3.0, 8
+    x = train.sample_grid(3000, beta0, mu0)
+    a0 = altform.sp2_alt(mu0, L)
+    a, hist = altform.lm_fit(a0, x, "fermi", beta0, mu0, iters=30, accel=True)
+    costs = [h[0] for h in hist]
+    assert all(b <= c for c, b in zip(costs, costs[1:]))
+    c0 = 0.5 * np.sum((altform.forward(a0, x) - train.target(x, "fermi", beta0, mu0)) ** 2)
+    assert costs[-1] < 1e-2 * c0
