@@ -37,13 +37,23 @@ Modules and the passages they follow (arXiv 2605.08523):
 * ``train``    -- training: eigenvalue sampling (Sec. II C 1), residuals,
                   reverse-mode Jacobian, Levenberg-Marquardt with optional
                   geodesic acceleration (Sec. II C 2).
+* ``altform``  -- the one-term form of the recursion (Eq. mlsp2_alt and its
+                  output), its embedding into Eq. mlsp2 (Appendix on model
+                  embeddings), the SP2 sequence in that form, the chain-rule
+                  Jacobian, LM fit and method-exact references.
+* ``skipsp2``  -- Skip-SP2 with one stored layer and one accumulator
+                  (Sec. II A 3), the Appendix embedding of Eq. mlsp2, the
+                  reverse-mode Jacobian, LM fit and method-exact references.
 
 Readings of passages that are silent, garbled or inconsistent are stated in
 the docstring of the function that takes them.
 
 Pins (checked by ``tests/test_oracle_*.py`` against values the paper prints,
 closed forms, invariants and brute force):  every function above is pinned;
-the one exception is the accuracy of tables trained by ``train`` beyond the
-paper's printed targets, which is "parity unpinned" (the paper prints no
-trained entropy table and no Fig. 2 weights).
+the one exception is the accuracy of tables trained by ``train``,
+``altform.lm_fit`` and ``skipsp2.lm_fit`` beyond the paper's printed targets,
+which is "parity unpinned" (the paper prints no trained entropy table, no
+Fig. 2 weights and no coefficients of the one-term form or of Skip-SP2); the
+LM loops themselves are pinned by their acceptance property and their
+Jacobians by central differences.
 """
