@@ -280,7 +280,8 @@ def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
 # profiles/layer_tc_fp16x2_n4096.md
 MEASURED_TRAFFIC = {("fp16x2", 4096, "52ae88a99f185e28"): 420.6208e6 + 233.582592e6,
                     ("fp16x2", 4096, "acc91d76912da5c8"): 422.81472e6 + 233.330176e6,
-                    ("fp16x2", 4096, "8ddc9beb5ccd7e9f"): 341.659136e6 + 217.101312e6}
+                    ("fp16x2", 4096, "8ddc9beb5ccd7e9f"): 341.659136e6 + 217.101312e6,
+                    ("fp16x2", 4096, "ac140164032fa295"): 344.602112e6 + 217.907712e6}
 
 
 def kernel_sha():
