@@ -275,21 +275,48 @@ def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
     return D, S
 
 
-# (mode, n, sha256[:16] of the layer-kernel sources) -> dram read + write bytes
+# (mode, n, kernel_sha(): code hash of the layer kernel) -> dram read + write bytes
 # of one layer launch (both chains), from the ncu capture summarised in
 # profiles/layer_tc_fp16x2_n4096.md
-MEASURED_TRAFFIC = {("fp16x2", 4096, "52ae88a99f185e28"): 420.6208e6 + 233.582592e6,
-                    ("fp16x2", 4096, "acc91d76912da5c8"): 422.81472e6 + 233.330176e6,
-                    ("fp16x2", 4096, "8ddc9beb5ccd7e9f"): 341.659136e6 + 217.101312e6,
-                    ("fp16x2", 4096, "ac140164032fa295"): 344.602112e6 + 217.907712e6}
+MEASURED_TRAFFIC = {("fp16x2", 4096, "5a532e9ee5962246"): 420.6208e6 + 233.582592e6,
+                    ("fp16x2", 4096, "f28e2970fe6099cb"): 422.81472e6 + 233.330176e6,
+                    ("fp16x2", 4096, "f2da72eea28cec7d"): 341.659136e6 + 217.101312e6,
+                    ("fp16x2", 4096, "35cc88bb61af8eea"): 344.602112e6 + 217.907712e6}
+
+
+def _code_only(src: str) -> str:
+    """C/C++ source without comments, blank lines and trailing blanks (string
+    and character literals kept), so that comment edits keep the hash."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            while i < n and src[i] != "\n":
+                i += 1
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = [ln.rstrip() for ln in "".join(out).split("\n")]
+    return "\n".join(ln for ln in lines if ln.strip())
 
 
 def kernel_sha():
+    """sha256[:16] of the layer kernel's code (k_layer_tc.cu, epilogue.cuh,
+    ftsp2_internal.h without comments): the key of MEASURED_TRAFFIC."""
     import hashlib
     h = hashlib.sha256()
     for f in ("k_layer_tc.cu", "epilogue.cuh", "ftsp2_internal.h"):
-        with open(os.path.join(ROOT, "paper_2605_08523_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2605_08523_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

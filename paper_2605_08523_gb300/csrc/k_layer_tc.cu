@@ -307,10 +307,8 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // ----------------------------------------------------------------------------------
-// Next-layer operand stores of one 32-row x 16-column block held by a warp
-// (lane = row).  Direct stores at (r, c) as 16-element vectors; the mirror
-// (c, r) goes through a per-warp shared transpose buffer so that each lane
-// stores 16 consecutive elements of one mirrored row.
+// Split formats of the next layer's operands (planes of 2- or 4-byte
+// elements); the stores themselves are in epi_dgroup_next.
 // ----------------------------------------------------------------------------------
 template <int FMT>
 struct OpFmtT;

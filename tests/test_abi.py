@@ -113,3 +113,15 @@ def test_flag_constants_match_header():
     bits = [defs[n] for n in ("SYNC", "CLAMP", "REFINE1", "REFINE2", "PAIR_TILES", "SINGLE_TILES", "LANCZOS", "MIN_LAYERS",
                               "REFINE_TC", "EPI_DEFERRED", "EPI_INLINE", "FULL_OPERANDS")]
     assert all(b & (b - 1) == 0 for b in bits) and len(set(bits)) == len(bits)
+
+
+def test_kernel_code_hash_ignores_comments():
+    # bench.kernel_sha keys the measured DRAM traffic of the layer kernel: it
+    # hashes code only, so comment edits keep a capture valid and code edits
+    # do not
+    import bench
+    src = 'int f() { // a comment\n  /* block\n comment */ return g("//x", \'/\'); }\n'
+    code = bench._code_only(src)
+    assert "comment" not in code and '"//x"' in code and "'/'" in code
+    assert bench._code_only(src.replace("a comment", "another remark")) == code
+    assert bench._code_only(src.replace("return", "return 1 +")) != code
