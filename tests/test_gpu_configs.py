@@ -155,7 +155,7 @@ def test_cfg4_n8192_refine2(ft, refine_tc):
     assert abs(float(s.S[0]) - Sref) / n <= 1e-6
 
 
-def test_cfg2_with_lanczos_bounds_within_north_star_bound(ft):
+def test_cfg2_with_lanczos_bounds_within_1e6(ft):
     # with the Lanczos-tightened bounds and the fewest-layers policy every
     # instance of the ragged batch runs the printed 26-layer table, and D and S
     # meet the 1e-6 bound against the eigendecomposition

@@ -236,7 +236,7 @@ def test_model_set_selection(ft):
 
 
 @pytest.mark.parametrize("mode", ["fp16x2", "bf16x3"])
-def test_cfg1_n4096_within_north_star_bound(ft, printed_set, mode):
+def test_cfg1_n4096_within_the_1e6_bound(ft, printed_set, mode):
     # The bench workload at full size (16 x 16 x 16 lattice, kT = 0.1, mu at
     # half filling): every element of D within 1e-6 of the eigendecomposition
     # reference, traces consistent, S within the model's own error.
