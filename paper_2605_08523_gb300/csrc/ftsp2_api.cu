@@ -22,7 +22,7 @@ static bool g_prof_on = false;
 static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_events;
 
 // ------------------------------------------------------------------------------
-// device checks and the driver's tensor-map encoder
+// device checks and the CUDA driver API's tensor-map encoder
 // ------------------------------------------------------------------------------
 struct DeviceInfo {
     int sms = 0;
