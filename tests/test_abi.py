@@ -125,3 +125,27 @@ def test_kernel_code_hash_ignores_comments():
     assert "comment" not in code and '"//x"' in code and "'/'" in code
     assert bench._code_only(src.replace("a comment", "another remark")) == code
     assert bench._code_only(src.replace("return", "return 1 +")) != code
+
+
+def test_model_set_arguments_checked_on_the_host(built):
+    # invalid tables are refused before any device call (works without a GPU)
+    from paper_2605_08523_gb300 import _lib
+    L = built.lib()
+    th = (C.c_double * (4 * 65))(*([0.5] * (4 * 65)))
+
+    def create(L_, family, beta0=100.0, mu0=1.0 / 3.0):
+        t = (_lib.Table * 1)()
+        t[0].L, t[0].L_entropy, t[0].beta0, t[0].mu0, t[0].alpha = L_, 0, beta0, mu0, 0.84
+        t[0].theta = C.cast(th, C.POINTER(C.c_double))
+        t[0].theta_entropy = None
+        t[0].family = family
+        h = C.c_void_p()
+        return L.ftsp2_model_set_create(t, 1, C.byref(h))
+
+    E_ARG = -1
+    assert create(16, 7) == E_ARG                  # unknown family
+    assert create(64, 1) == E_ARG                  # Skip-SP2 tables carry an output row: at most 63 layers
+    assert create(65, 0) == E_ARG                  # Eq. mlsp2: at most 64 layers
+    assert create(0, 0) == E_ARG
+    assert create(16, 1, beta0=-1.0) == E_ARG
+    assert create(16, 0, mu0=1.0) == E_ARG
