@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--operands", default="upper", choices=["upper", "full"],
                    help="operand storage of the 16-bit tensor-core layers: upper triangle with transposed "
                         "panel loads (default), or full matrices (FTSP2_FULL_OPERANDS)")
+    p.add_argument("--batch", type=int, default=512,
+                   help="cfg2: number of instances (512; smaller batches for profiling captures)")
     p.add_argument("--table", default="printed", choices=["printed", "alt", "skip"],
                    help="cfg1/cfg4 Fermi table: the paper's printed 26-layer table (with the trained entropy "
                         "table), the 26-layer beta0 = 1500 table of the one-term form (Eq. mlsp2_alt), or the "
@@ -396,7 +398,7 @@ def cpu_baseline(H, mu, kT, n):
 
 
 def run_cfg2(args):
-    """Ragged batch of 512 rotated-spectrum Hamiltonians (n ~ U{64..768}),
+    """Ragged batch of --batch (512) rotated-spectrum Hamiltonians (n ~ U{64..768}),
     one grouped launch per layer for all instances and both chains, model set
     of every shipped table (smallest valid beta0 per instance)."""
     import glob
@@ -412,7 +414,7 @@ def run_cfg2(args):
     paths += sorted(p for p in glob.glob(os.path.join(tdir, "b*.json"))
                     if int(os.path.basename(p)[1:].split("_")[0]) >= 3000)
     ms = ft.ModelSet.from_json(paths)
-    batch = wl.ragged_batch(512, args.seed)
+    batch = wl.ragged_batch(args.batch, args.seed)
     Hs = [b["H"] for b in batch]
     ns = [H.shape[0] for H in Hs]
     flat, _ = wl.pack_batch(Hs)
@@ -452,8 +454,8 @@ def run_cfg2(args):
     line = {"metric": "ragged-batch solves/s (instances/s, density + entropy)", "value": int(valid.sum()) / t,
             "unit": "solves/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "dtype": args.mode, "data": "synthetic",
-            "config": {"workload": "cfg2 ragged batch 512 x n~U{64..768}, eigenvalues U(-10,10), kT~U(0.02,0.5), "
-                                   "mu~U(-5,5)", "valid_instances": int(valid.sum()),
+            "config": {"workload": "cfg2 ragged batch %d x n~U{64..768}, eigenvalues U(-10,10), kT~U(0.02,0.5), "
+                                   "mu~U(-5,5)" % args.batch, "valid_instances": int(valid.sum()),
                        "sum_n3": float(np.sum(np.array(ns, dtype=np.float64) ** 3)),
                        "models_used": {int(m): int(np.sum(rec["model"] == m)) for m in np.unique(rec["model"])},
                        "bounds": args.bounds, "policy": args.policy, "global_layers": int(rec["layers"].max()),
