@@ -593,6 +593,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     ia.main_fmt = fmt;
     ia.refine_fmt = rfmt;
     ia.refine_from = all_simt ? 0 : refine_from;
+    ia.upper_only = (flags & FTSP2_FULL_OPERANDS) ? 0 : 1;
     for (int c = 0; c < kMaxChains; ++c) {
         ia.chain_kind[c] = kinds[c];
         ia.Z[c] = c < L.nchains ? reinterpret_cast<float*>(W + L.Z[c]) : nullptr;
@@ -665,8 +666,11 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     // Operands of 16-bit tensor-core layers are stored as the upper triangle
     // plus the diagonal tile blocks when the layer that reads them can load the
     // rest transposed (FP16X2, BF16X3); the mirror is written everywhere before
-    // an FP32 or TF32X3 layer.  Layer 0 reads the full matrices of init.
-    int prev_skips_mirror = 0;
+    // an FP32 or TF32X3 layer.  init writes the same form for an instance whose
+    // first layer is such a layer (ia.upper_only), so a layer's operands are
+    // all of one form, whichever layer wrote them.
+    const bool tc16_0 = !is_simt(0) && (is_rtc(0) || fmt == OP_F16X2 || fmt == OP_BF16X3);
+    int prev_skips_mirror = (tc16_0 && ia.upper_only) ? 1 : 0;
     for (int g = 0; g < Lmax; ++g) {
         const bool simt = is_simt(g);
         const bool next_simt = g + 1 < Lmax && is_simt(g + 1);

@@ -139,6 +139,7 @@ struct InitArgs {
     int main_fmt;                  // format of the main layers (OP_F32 in FTSP2_FP32 mode)
     int refine_fmt;                // OP_F32 (CUDA-core refinement) or OP_BF16X3 (FTSP2_REFINE_TC)
     int refine_from;               // global layers >= refine_from are refinement layers on OPR
+    int upper_only;                // 16-bit operands as the upper triangle plus diagonal blocks
     size_t plane_elems;
 };
 void launch_init(const InitArgs& a, int max_n, cudaStream_t s);

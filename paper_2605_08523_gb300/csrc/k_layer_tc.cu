@@ -532,30 +532,49 @@ __device__ __forceinline__ void epi_update_last(const LayerArgs& a, const EpiCtx
 }
 
 // Last layer: D = G + f0 I (or (1 - f0) I - G when flipped) at (r, c) and
-// (c, r), and the FP64 sums of the diagonal and of the squares of G.
+// (c, r), and the sums of the diagonal and of the squares of G.  The diagonal
+// element is added in FP64.  The squares of a group's 8 columns are summed in
+// FP32 (exact doubling for the off-diagonal pair, one FMA each) and the group
+// sum in FP64: FP64 arithmetic on every element would run on the FP64 pipe,
+// the slowest unit of this GPU.  The direct row (r, c .. c + 7) is written as
+// two 16-byte vectors when the whole group lies in the triangle and is
+// aligned; the mirror (c, r) is one element per lane, a contiguous run of row c
+// across the warp.
 __device__ __forceinline__ void epi_last(const LayerArgs& a, const EpiCtx& e, int r, int c0, const float* v,
                                          double& tr, double& sq) {
     if (r >= e.n) return;
+    const bool dout = e.kind == CHAIN_FERMI && a.D;
+    float dv[kGrp];
+    float s8 = 0.f;
 #pragma unroll
     for (int jj = 0; jj < kGrp; ++jj) {
         const int c = c0 + jj;
+        const float g = v[jj];
+        const bool diag = r == c;
+        if (e.flip) dv[jj] = (diag ? (float)e.cdiag : 0.f) - g;
+        else dv[jj] = g + (diag ? (float)e.cdiag : 0.f);
         if (c < e.n && r <= c) {
-            const float g = v[jj];
-            if (e.kind == CHAIN_FERMI && a.D) {
-                float dv;
-                if (e.flip) dv = (r == c ? (float)e.cdiag : 0.f) - g;
-                else dv = g + (r == c ? (float)e.cdiag : 0.f);
-                a.D[e.doff + (int64_t)r * e.n + c] = dv;
-                if (c != r) a.D[e.doff + (int64_t)c * e.n + r] = dv;
-            }
-            const double gd = (double)g;
-            if (r == c) {
-                tr += gd;
-                sq += gd * gd;
-            } else {
-                sq += 2.0 * gd * gd;
-            }
+            if (diag) tr += (double)g;
+            s8 = fmaf(diag ? g : 2.f * g, g, s8);
         }
+    }
+    sq += (double)s8;
+    if (!dout) return;
+    float* drow = a.D + e.doff + (int64_t)r * e.n;
+    if (c0 >= r && c0 + kGrp <= e.n && (reinterpret_cast<uintptr_t>(drow + c0) & 15u) == 0) {
+        reinterpret_cast<float4*>(drow + c0)[0] = make_float4(dv[0], dv[1], dv[2], dv[3]);
+        reinterpret_cast<float4*>(drow + c0)[1] = make_float4(dv[4], dv[5], dv[6], dv[7]);
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < kGrp; ++jj) {
+            const int c = c0 + jj;
+            if (c < e.n && r <= c) drow[c] = dv[jj];
+        }
+    }
+#pragma unroll
+    for (int jj = 0; jj < kGrp; ++jj) {
+        const int c = c0 + jj;
+        if (c < e.n && r < c) a.D[e.doff + (int64_t)c * e.n + r] = dv[jj];
     }
 }
 

@@ -276,29 +276,31 @@ __device__ __forceinline__ void st32(void* dst, const uint32_t* w) {
 }
 
 // The operands of 16 consecutive elements of one row (idx0 % 16 == 0) in
-// format fmt, as 32-byte vectors per plane; z == nullptr writes zeros.
-__device__ __forceinline__ void write_operand16(int fmt, uint8_t* base, size_t plane_elems, size_t idx0,
-                                                const float* z, float scale) {
-    uint32_t w[3][16];
-    int npl = 1, esz = 4;
-    switch (fmt) {
-        case OP_F16X2: npl = 2; esz = 2; break;
-        case OP_BF16X3: npl = 3; esz = 2; break;
-        case OP_TF32X3: npl = 2; esz = 4; break;
-        default: npl = 1; esz = 4; break;
-    }
+// format FMT, as 32-byte vectors per plane; z == nullptr writes zeros.  One
+// instantiation per format keeps only that format's planes in registers.
+template <int FMT>
+__device__ __forceinline__ void write_operand16_t(uint8_t* base, size_t plane_elems, size_t idx0, const float* z,
+                                                  float scale) {
+    constexpr int NPL = FMT == OP_F16X2 ? 2 : FMT == OP_BF16X3 ? 3 : FMT == OP_TF32X3 ? 2 : 1;
+    constexpr int ESZ = (FMT == OP_F16X2 || FMT == OP_BF16X3) ? 2 : 4;
+    constexpr int WORDS = 16 * ESZ / 4;
+    uint32_t w[NPL][WORDS];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-        uint32_t o[3] = {0u, 0u, 0u};
-        if (z) {
+    for (int p = 0; p < NPL; ++p)
+#pragma unroll
+        for (int i = 0; i < WORDS; ++i) w[p][i] = 0u;
+    if (z) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
             const float v = z[u];
-            if (fmt == OP_F16X2) {
+            uint32_t o[NPL];
+            if constexpr (FMT == OP_F16X2) {
                 const float zs = v * scale;
                 const __half h = __float2half_rn(zs);
                 const __half l = __float2half_rn(zs - __half2float(h));
                 o[0] = __half_as_ushort(h);
                 o[1] = __half_as_ushort(l);
-            } else if (fmt == OP_BF16X3) {
+            } else if constexpr (FMT == OP_BF16X3) {
                 const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
                 const float r1 = v - __bfloat162float(b0);
                 const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
@@ -306,7 +308,7 @@ __device__ __forceinline__ void write_operand16(int fmt, uint8_t* base, size_t p
                 o[0] = __bfloat16_as_ushort(b0);
                 o[1] = __bfloat16_as_ushort(b1);
                 o[2] = __bfloat16_as_ushort(b2);
-            } else if (fmt == OP_TF32X3) {
+            } else if constexpr (FMT == OP_TF32X3) {
                 uint32_t hb;
                 asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
                 o[0] = hb;
@@ -314,34 +316,51 @@ __device__ __forceinline__ void write_operand16(int fmt, uint8_t* base, size_t p
             } else {
                 o[0] = __float_as_uint(v);
             }
-        }
 #pragma unroll
-        for (int p = 0; p < 3; ++p) {
-            if (esz == 2) {
-                if (u & 1) w[p][u / 2] |= o[p] << 16;
-                else w[p][u / 2] = o[p];
-            } else {
-                w[p][u] = o[p];
+            for (int p = 0; p < NPL; ++p) {
+                if constexpr (ESZ == 2) w[p][u / 2] |= o[p] << (16 * (u & 1));
+                else w[p][u] = o[p];
             }
         }
     }
-    for (int p = 0; p < npl; ++p) {
-        uint8_t* dst = base + ((size_t)p * plane_elems + idx0) * esz;
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+        uint8_t* dst = base + ((size_t)p * plane_elems + idx0) * ESZ;
         st32(dst, w[p]);
-        if (esz == 4) st32(dst + 32, w[p] + 8);
+        if constexpr (ESZ == 4) st32(dst + 32, w[p] + 8);
     }
 }
 
-// Layer-0 state and operands.  One CTA per (32-row band, instance); lane =
-// row of the band, each warp walks 16-column chunks of the instance's
-// R x R square (R = n rounded up to the largest tile, 256, at most P):
+__device__ __forceinline__ void write_operand16(int fmt, uint8_t* base, size_t plane_elems, size_t idx0,
+                                                const float* z, float scale) {
+    switch (fmt) {
+        case OP_F16X2: write_operand16_t<OP_F16X2>(base, plane_elems, idx0, z, scale); break;
+        case OP_BF16X3: write_operand16_t<OP_BF16X3>(base, plane_elems, idx0, z, scale); break;
+        case OP_TF32X3: write_operand16_t<OP_TF32X3>(base, plane_elems, idx0, z, scale); break;
+        default: write_operand16_t<OP_F32>(base, plane_elems, idx0, z, scale); break;
+    }
+}
+
+// Layer-0 state and operands.  One CTA per (32-row band, instance, 512
+// columns); lane = row of the band, each warp walks 16-column chunks of the
+// band's columns in the instance's R x R square (R = n rounded up to the
+// largest tile, 256, at most P):
 // * Z_0 = z0 X, A = a0 X with X = H0 - mu0 I (times alpha for the entropy
 //   chain), in the blocked state layout, for the rows below n and the chunks
 //   that reach the upper triangle of the band's 32-row block (the only state
 //   the layer epilogues read): four 512-byte runs per warp and chunk;
 // * operands of Z_0 in the format of the instance's first layer (one parity),
 //   zeros outside n x n in every format and parity a layer may read, as one
-//   32-byte vector per lane and plane (row-major planes).
+//   32-byte vector per lane and plane (row-major planes).  With `upper_only`
+//   and a 16-bit first format (FP16X2, BF16X3) a real row r is written only
+//   from the first column of its 256-row block on: the upper triangle plus the
+//   diagonal blocks of either tile shape, the part a layer that loads the rest
+//   as transposed panels reads.  Chunks left of that block are then skipped,
+//   H included, when every chain of the instance takes this form.
+// Z_0 is formed in FP64 and rounded once: scale * (mu - H_rr) on the diagonal,
+// (-scale) * H_rc elsewhere (the same value as scale * (0 - H_rc)).
+constexpr int kInitCols = 512;     // columns per init CTA
+
 __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
     const int b = blockIdx.y;
     const ftsp2_instance in = a.inst[b];
@@ -365,15 +384,41 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
         a0S = M.a0S;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cbeg = blockIdx.z * kInitCols, cend = min(R, cbeg + kInitCols);
+    if (cbeg >= cend) return;
     const int r = band + lane;
     const bool row_in = r < n;
     const double* Hr = a.H + in.offset + (size_t)r * n;
-    for (int cc = warp * 16; cc < R; cc += 8 * 16) {
+    const double nscale = -rec.scale;
+    // chains whose first layer reads the upper triangle plus diagonal blocks
+    unsigned up_mask = 0u;
+    for (int ch = 0; ch < a.nchains; ++ch) {
+        const int start = (sl_packed >> (16 * ch)) & 0xffff;
+        const bool ref = a.main_fmt != OP_F32 && start >= a.refine_from;
+        const int f = ref ? a.refine_fmt : a.main_fmt;
+        if (a.upper_only && (f == OP_F16X2 || f == OP_BF16X3)) up_mask |= 1u << ch;
+    }
+    const bool all_up = up_mask == (1u << a.nchains) - 1u;
+    const int blk = band & ~255;               // first column of the band's 256-row block
+    if (cend <= blk && all_up && band + 32 <= n) return;
+    for (int cc = cbeg + warp * 16; cc < cend; cc += 8 * 16) {
+        const bool low = cc + 16 <= blk;       // the chunk lies left of the diagonal block
+        if (low && all_up && band + 32 <= n) continue;
         float z[16];
+        if (ok && row_in && !(low && all_up)) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int c = cc + u;
-            z[u] = (ok && row_in && c < n) ? (float)(rec.scale * ((r == c ? in.mu : 0.0) - __ldg(Hr + c))) : 0.f;
+            for (int u = 0; u < 16; ++u) {
+                const int c = cc + u;
+                if (c < n) {
+                    const double h = __ldg(Hr + c);
+                    z[u] = (float)(r == c ? rec.scale * (in.mu - h) : nscale * h);
+                } else {
+                    z[u] = 0.f;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) z[u] = 0.f;
         }
         const bool inside = row_in && cc < n;        // the chunk holds elements of the n x n matrix
         const bool state = inside && cc + 15 >= band;
@@ -400,6 +445,7 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
                 }
             }
             const size_t e0 = base + (size_t)r * P + cc;
+            if (inside && low && ((up_mask >> ch) & 1u)) continue;
             if (inside) {
                 // the values (zeros beyond n within the chunk) in the first layer's format
                 const int start = (sl_packed >> (16 * ch)) & 0xffff;
@@ -433,7 +479,7 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
 }
 
 void launch_init(const InitArgs& a, int max_n, cudaStream_t s) {
-    dim3 grid((a.P + 31) / 32, a.nb);
+    dim3 grid((a.P + 31) / 32, a.nb, (a.P + kInitCols - 1) / kInitCols);
     init_kernel<<<grid, 256, 0, s>>>(a);
     count_launch();
 }
