@@ -284,7 +284,8 @@ MEASURED_TRAFFIC = {("fp16x2", 4096, "5a532e9ee5962246"): 420.6208e6 + 233.58259
                     ("fp16x2", 4096, "f28e2970fe6099cb"): 422.81472e6 + 233.330176e6,
                     ("fp16x2", 4096, "f2da72eea28cec7d"): 341.659136e6 + 217.101312e6,
                     ("fp16x2", 4096, "35cc88bb61af8eea"): 344.602112e6 + 217.907712e6,
-                    ("fp16x2", 4096, "ab8a7663926c8945"): 343.843328e6 + 218.012672e6}
+                    ("fp16x2", 4096, "ab8a7663926c8945"): 343.843328e6 + 218.012672e6,
+                    ("fp16x2", 4096, "ced6ca48c1eace3f"): 342.698752e6 + 217.683968e6}
 
 
 def _code_only(src: str) -> str:
