@@ -31,39 +31,74 @@ __device__ __forceinline__ int tiles_of(int n, int BM, int BN) {
     return c;
 }
 
+// Exclusive scan of one value per thread over the block (blockDim.x a multiple
+// of 32, at most 1024): warp scans by shuffles, then the warp totals.
+__device__ int block_exclusive_scan(int v, int& total) {
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) wsum[lane] = w;      // inclusive warp prefix
+    }
+    __syncthreads();
+    total = wsum[nw - 1];
+    const int r = (warp > 0 ? wsum[warp - 1] : 0) + x - v;
+    __syncthreads();
+    return r;
+}
+
+// Per-instance tile ranges (thread t owns a contiguous chunk of instances; the
+// chunk totals are scanned), then the tiles themselves: warp w writes those of
+// instances w, w + 32, ..., its lanes stepping through the instance's list and
+// decoding (I, J) from the position in the column-major triangle.
 __device__ void block_exclusive_scan_fill(const ftsp2_instance* inst, int nb, int BM, int BN, int nchains,
                                           InstWork* iw, Tile* tiles, int table) {
-    __shared__ int tot[1024];
-    __shared__ int chain_total;
     const int T = blockDim.x;
     const int chunk = (nb + T - 1) / T;
     const int b0 = min(nb, threadIdx.x * chunk);
     const int b1 = min(nb, b0 + chunk);
     int s = 0;
     for (int b = b0; b < b1; ++b) s += tiles_of(inst[b].n, BM, BN);
-    tot[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int t = 0; t < T; ++t) {
-            const int v = tot[t];
-            tot[t] = acc;
-            acc += v;
+    int chain_total;
+    const int first = block_exclusive_scan(s, chain_total);
+    for (int c = 0; c < nchains; ++c) {
+        int pos = c * chain_total + first;
+        for (int b = b0; b < b1; ++b) {
+            const int cnt = tiles_of(inst[b].n, BM, BN);
+            iw[b].tile_start[table][c] = pos;
+            iw[b].tile_count[table][c] = cnt;
+            pos += cnt;
         }
-        chain_total = acc;
     }
     __syncthreads();
     const int q = BN / BM;
-    for (int c = 0; c < nchains; ++c) {
-        int pos = c * chain_total + tot[threadIdx.x];
-        for (int b = b0; b < b1; ++b) {
-            const int n = inst[b].n;
-            const int nI = (n + BM - 1) / BM;
-            const int nJ = (n + BN - 1) / BN;
-            iw[b].tile_start[table][c] = pos;
-            iw[b].tile_count[table][c] = tiles_of(n, BM, BN);
-            for (int J = 0; J < nJ; ++J)
-                for (int I = 0; I < min(q * (J + 1), nI); ++I) tiles[pos++] = Tile{b, I, J, c};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+    for (int b = warp; b < nb; b += nw) {
+        const int n = inst[b].n;
+        const int nI = (n + BM - 1) / BM;
+        const int cnt = iw[b].tile_count[table][0];
+        for (int l = lane; l < cnt; l += 32) {
+            int J = 0, rem = l;
+            for (;;) {
+                const int col = min(q * (J + 1), nI);
+                if (rem < col) break;
+                rem -= col;
+                ++J;
+            }
+            for (int c = 0; c < nchains; ++c) tiles[iw[b].tile_start[table][c] + l] = Tile{b, rem, J, c};
         }
     }
     __syncthreads();
@@ -494,13 +529,15 @@ void launch_init(const InitArgs& a, int max_n, cudaStream_t s) {
 // and for the entropy chain F = G + g0 I:
 //   S = 4 ln2 (Tr F - ||F||^2) = 4 ln2 (n g0 (1 - g0) + (1 - 2 g0) Tr G - ||G||^2).
 // ------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a) {
+constexpr int kFinThreads = 1024;
+
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalArgs a) {
     // one block per instance; each chain's partial sums are reduced by a
     // fixed assignment of slots to threads and a fixed tree, so the result
     // does not depend on scheduling
     const int b = blockIdx.x;
     if (b >= a.nb) return;
-    __shared__ double s_tr[256], s_sq[256];
+    __shared__ double s_tr[kFinThreads], s_sq[kFinThreads];
     ftsp2_rescale_rec rec = a.rec[b];
     const int gstat = *a.status;
     const int n = a.inst[b].n;
@@ -515,7 +552,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a) {
         s_tr[threadIdx.x] = tr;
         s_sq[threadIdx.x] = sq;
         __syncthreads();
-        for (int o = 128; o > 0; o >>= 1) {
+        for (int o = kFinThreads / 2; o > 0; o >>= 1) {
             if (threadIdx.x < o) {
                 s_tr[threadIdx.x] += s_tr[threadIdx.x + o];
                 s_sq[threadIdx.x] += s_sq[threadIdx.x + o];
@@ -592,7 +629,7 @@ void launch_mu_update(const MuArgs& a, cudaStream_t s) {
 }
 
 void launch_finalize(const FinalArgs& a, cudaStream_t s) {
-    finalize_kernel<<<a.nb, 256, 0, s>>>(a);
+    finalize_kernel<<<a.nb, kFinThreads, 0, s>>>(a);
     count_launch();
 }
 

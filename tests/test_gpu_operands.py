@@ -54,3 +54,34 @@ def test_upper_triangle_operands_bit_identical(ft, mode, shape, extra):
         assert np.max(np.abs(D - D.T)) == 0.0
         assert np.max(np.abs(D - ex["D"])) < 1e-6, (mode, shape, extra, i)
         assert abs(float(a.S.cpu()[i]) - ex["S"]) / H.shape[0] < 1e-6
+
+
+@pytest.mark.parametrize("mode", ["fp16x2", "bf16x3"])
+@pytest.mark.parametrize("shape", ["pair", "single"])
+def test_late_starting_models_bit_identical(ft, mode, shape):
+    # models with fewer layers start at later global layers: their layer-0
+    # operands, written by init as the upper triangle plus the diagonal blocks,
+    # are first read by a launch in the middle of the sequence
+    import glob
+    import os
+    tdir = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2605_08523_gb300",
+                        "tables")
+    paths = [os.path.join(tdir, "entropy_b1500_L26.json")]
+    paths += sorted(p for p in glob.glob(os.path.join(tdir, "b*.json"))
+                    if int(os.path.basename(p)[1:].split("_")[0]) >= 3000)
+    ms = ft.ModelSet.from_json(paths)
+    batch = wl.ragged_batch(16, 5)
+    Hs = [b["H"] for b in batch]
+    mus, kTs = [b["mu"] for b in batch], [b["kT"] for b in batch]
+    f = ft.PAIR_TILES if shape == "pair" else ft.SINGLE_TILES
+    flat, _ = wl.pack_batch(Hs)
+    out = []
+    for extra in (0, ft.FULL_OPERANDS):
+        s = ft.Solver([H.shape[0] for H in Hs], mus, kTs, ms, mode=mode, want=3, flags=f | extra)
+        s.run(torch.from_numpy(flat).cuda(), sync=True)
+        torch.cuda.synchronize()
+        out.append(s)
+    a, b = out
+    models = {int(r["model"]) for r in a.records() if r["status"] == 0}
+    assert len(models) >= 2, models          # more than one start layer in the batch
+    assert torch.equal(a.D, b.D) and torch.equal(a.S, b.S) and torch.equal(a.trace, b.trace)
