@@ -63,6 +63,9 @@ def parse():
     p.add_argument("--operands", default="upper", choices=["upper", "full"],
                    help="operand storage of the 16-bit tensor-core layers: upper triangle with transposed "
                         "panel loads (default), or full matrices (FTSP2_FULL_OPERANDS)")
+    p.add_argument("--launch", default="auto", choices=["auto", "layer"],
+                   help="consecutive main-format layers in one persistent launch when each layer is a few "
+                        "waves of tiles (default), or one launch per layer (FTSP2_LAYER_LAUNCHES)")
     p.add_argument("--batch", type=int, default=512,
                    help="cfg2: number of instances (512; smaller batches for profiling captures)")
     p.add_argument("--table", default="printed", choices=["printed", "alt", "skip"],
@@ -424,6 +427,7 @@ def run_cfg2(args):
     shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
     shape_flag |= {"auto": 0, "deferred": ft.EPI_DEFERRED, "inline": ft.EPI_INLINE}[args.epilogue]
     shape_flag |= ft.FULL_OPERANDS if args.operands == "full" else 0
+    shape_flag |= ft.LAYER_LAUNCHES if args.launch == "layer" else 0
     if args.bounds == "lanczos":
         shape_flag |= ft.LANCZOS
     if args.policy == "layers":
@@ -523,6 +527,7 @@ def main():
     shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
     shape_flag |= {"auto": 0, "deferred": ft.EPI_DEFERRED, "inline": ft.EPI_INLINE}[args.epilogue]
     shape_flag |= ft.FULL_OPERANDS if args.operands == "full" else 0
+    shape_flag |= ft.LAYER_LAUNCHES if args.launch == "layer" else 0
     refine = 2 if cfg4 and args.refine == 0 else args.refine
     shape_flag |= {0: 0, 1: ft.REFINE1, 2: ft.REFINE2}[refine]
     if args.refine_tc:
@@ -640,6 +645,8 @@ def main():
 
     # ---- dominant kernel roofline ----
     pk, pk_kind = peaks()
+    # time per layer (both chains): the profiler counts the layers of a
+    # multi-layer launch, so flops per layer / time per layer is the launch's rate
     layer_avg = layer_ms / max(1, layer_n) / 1000.0
     alg_per_launch = 2 * float(n) ** 3
     achieved = alg_per_launch / layer_avg / 1e12 if layer_avg > 0 else None
@@ -686,6 +693,7 @@ def main():
                    "l2": "inputs and working set larger than L2 (no flush)", "parallelism": "replicas",
                    "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
                    "epilogue": args.epilogue, "table": args.table, "operands": args.operands,
+                   "launch": args.launch,
                    "autotune_ms": {"single": ms_single, "pair": ms_pair}},
         "tflops_alg": alg_flops / t_step / 1e12 * world,
         "density_only": {"value": world / t_density, "unit": "solves/s", "ms_per_step": t_density * 1e3},

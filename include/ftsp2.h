@@ -127,6 +127,16 @@ typedef enum {
  * operands).  This halves the operand stores of the epilogue.  With this flag
  * every layer writes and reads full matrices (results are identical). */
 #define FTSP2_FULL_OPERANDS 0x800
+/* Layer launches.  When a launch of the tensor-core layer kernel would run a
+ * few waves of tiles (at most 16 per unit), consecutive layers of the main
+ * format run in one persistent cooperative launch.  Its work items are (layer,
+ * tile) in layer order, and an item of layer g starts once every tile of layer
+ * g - 1 of the same chain is finished (device-side counters; bounded waits
+ * that end in FTSP2_E_TIMEOUT).  The last tiles of one layer then overlap the
+ * first tiles of the next chain's layer, instead of leaving units idle at the
+ * end of every launch.  This flag forces one launch per layer (results are
+ * identical). */
+#define FTSP2_LAYER_LAUNCHES 0x1000
 
 /* One Hamiltonian of a (ragged) batch.  H_b starts at dH + offset and is
  * n x n row-major; D_b starts at dD + offset.  Offsets are in elements. */
@@ -461,7 +471,8 @@ ftsp2_status ftsp2_train_normal_equations(const double* dM, int nsamples, int L,
  * pair recorded on the caller's stream (host-side events, created on demand;
  * not usable during stream capture).  ftsp2_profile_read synchronises those
  * events and returns the summed layer-kernel time (ms) and the number of
- * launches measured since the last read, then clears the record. */
+ * layers measured since the last read (a multi-layer launch counts its
+ * layers), then clears the record. */
 ftsp2_status ftsp2_profile_layers(int enable);
 ftsp2_status ftsp2_profile_read(double* total_ms, uint64_t* launches);
 

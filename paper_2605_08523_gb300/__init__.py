@@ -23,7 +23,8 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (BF16X3, CLAMP, EPI_DEFERRED, EPI_INLINE, FP16X2, FP32, FULL_OPERANDS, LANCZOS, MIN_LAYERS, MODES,
+from ._lib import (BF16X3, CLAMP, EPI_DEFERRED, EPI_INLINE, FP16X2, FP32, FULL_OPERANDS, LANCZOS, LAYER_LAUNCHES,
+                   MIN_LAYERS, MODES,
                    PAIR_TILES,
                    REFINE1, REFINE2, REFINE_TC, SINGLE_TILES, SYNC,
                    TARGET_ENTROPY, TARGET_FERMI, TF32X3, Ftsp2Error, Instance, RescaleRec, Table, TrainReport,
@@ -34,7 +35,7 @@ __all__ = ["ModelSet", "Solver", "ftsp2_rescale", "ftsp2_train_coeffs", "ftsp2_t
            "ftsp2_train_residual_jacobian",
            "ftsp2_train_normal_equations", "ftsp2_autotune_clear", "kernel_launch_count", "profile_layers",
            "profile_read", "MODES", "FP32", "TF32X3", "BF16X3", "FP16X2", "SYNC", "CLAMP", "REFINE1", "REFINE2",
-           "PAIR_TILES", "SINGLE_TILES", "LANCZOS", "MIN_LAYERS", "REFINE_TC", "EPI_DEFERRED", "EPI_INLINE", "FULL_OPERANDS", "TARGET_FERMI", "TARGET_ENTROPY", "Ftsp2Error", "status_string", "lib",
+           "PAIR_TILES", "SINGLE_TILES", "LANCZOS", "MIN_LAYERS", "REFINE_TC", "EPI_DEFERRED", "EPI_INLINE", "FULL_OPERANDS", "LAYER_LAUNCHES", "TARGET_FERMI", "TARGET_ENTROPY", "Ftsp2Error", "status_string", "lib",
            "REC_DTYPE"]
 
 REC_DTYPE = np.dtype([("e_min", "f8"), ("e_max", "f8"), ("mu_p", "f8"), ("beta_p", "f8"), ("scale", "f8"),

@@ -20,6 +20,7 @@ MODES = {"fp32": FP32, "tf32x3": TF32X3, "bf16x3": BF16X3, "fp16x2": FP16X2}
 SYNC, CLAMP, REFINE1, REFINE2, PAIR_TILES, SINGLE_TILES, LANCZOS, MIN_LAYERS, REFINE_TC = \
     0x1, 0x2, 0x4, 0x8, 0x10, 0x20, 0x40, 0x80, 0x100
 EPI_DEFERRED, EPI_INLINE, FULL_OPERANDS = 0x200, 0x400, 0x800
+LAYER_LAUNCHES = 0x1000
 FAMILY_MLSP2, FAMILY_SKIP = 0, 1
 TARGET_FERMI, TARGET_ENTROPY = 0, 1
 

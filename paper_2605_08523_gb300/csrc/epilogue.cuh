@@ -17,13 +17,17 @@
 
 namespace ftsp2 {
 
-// Is tile `t` active in this launch?  Returns local layer k and chain kind.
-__device__ __forceinline__ bool tile_active(const LayerArgs& a, const Tile& t, int& k) {
+// Is tile `t` active at global layer g?  Returns the instance's local layer k.
+__device__ __forceinline__ bool tile_active_g(const LayerArgs& a, const Tile& t, int g, int& k) {
     const ftsp2_rescale_rec& rec = a.rec[t.inst];
     if (rec.status != FTSP2_OK || rec.model < 0) return false;
     const int start = (a.iw[t.inst].start_layer >> (16 * t.chain)) & 0xffff;
-    k = a.gl - start;
+    k = g - start;
     return k >= 0;
+}
+// ... at this launch's (first) layer
+__device__ __forceinline__ bool tile_active(const LayerArgs& a, const Tile& t, int& k) {
+    return tile_active_g(a, t, a.gl, k);
 }
 
 // ----------------------------------------------------------------------------------

@@ -3,6 +3,7 @@
 // training path.  Host code only; kernels live in k_*.cu.
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -19,7 +20,13 @@ void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_r
 // event pairs around tensor-core layer launches (measurement support)
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
-static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_events;
+struct ProfEvent {
+    cudaEvent_t e0, e1;
+    int layers;
+};
+static std::vector<ProfEvent> g_prof_events;
+// multi-layer (cooperative) launches: 1 usable, 0 refused once, -1 not tried
+static std::atomic<int> g_coop_ok{-1};
 
 // ------------------------------------------------------------------------------
 // device checks and the CUDA driver API's tensor-map encoder
@@ -398,6 +405,7 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
         return o;
     };
     L.status = take(256);
+    L.done = take(sizeof(int) * kMaxLayers * kMaxChains);
     L.inst_work = take(sizeof(InstWork) * nb);
     L.tiles = take(sizeof(Tile) * nt);
     L.tiles_ref = need_ref ? take(sizeof(Tile) * ntr) : 0;
@@ -568,6 +576,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     // FTSP2_LANCZOS: the FP32 copy of H lives in chain 0's Z plane, which the
     // initialisation overwrites only after the bounds are final
     sa.h32 = (flags & FTSP2_LANCZOS) ? reinterpret_cast<float*>(W + L.Z[0]) : nullptr;
+    sa.done = reinterpret_cast<int*>(W + L.done);
     launch_prep(sa, s);
     launch_gershgorin(sa, maxn, s);
     if (flags & FTSP2_LANCZOS) {
@@ -671,6 +680,12 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     // all of one form, whichever layer wrote them.
     const bool tc16_0 = !is_simt(0) && (is_rtc(0) || fmt == OP_F16X2 || fmt == OP_BF16X3);
     int prev_skips_mirror = (tc16_0 && ia.upper_only) ? 1 : 0;
+    // a tensor-core layer that is not the last and whose successor has its
+    // arithmetic: it writes operands of its own format (one kernel variant for
+    // all such layers), so consecutive ones can share one multi-layer launch
+    auto in_run = [&](int h) {
+        return h < Lmax - 1 && !is_simt(h) && !is_simt(h + 1) && is_rtc(h) == is_rtc(h + 1);
+    };
     for (int g = 0; g < Lmax; ++g) {
         const bool simt = is_simt(g);
         const bool next_simt = g + 1 < Lmax && is_simt(g + 1);
@@ -678,23 +693,29 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         const bool next_rtc = g + 1 < Lmax && is_rtc(g + 1);
         const int lmode = rtc ? (int)FTSP2_BF16X3 : mode;   // arithmetic of this layer
         la.gl = g;
+        la.nlayers = 1;
         la.last = g == Lmax - 1;
         // The last layers run with 64-element accumulation chunks: their rounding
         // reaches the output undamped (earlier errors are contracted by the
-        // saturating layers), and the entropy is linear in it for occupations
+        // saturating later layers), and the entropy is linear in it for occupations
         // near 0 and 1.
         la.chunk_elems = chunk_elems_of(lmode, g, Lmax);
+        la.chunk_tail = la.chunk_elems;
+        la.tail_from = INT_MAX;
         la.next_fmt = next_simt ? OP_F32 : (next_rtc ? OP_BF16X3 : fmt);
         const bool next_tc16 = !la.last && (la.next_fmt == OP_F16X2 || la.next_fmt == OP_BF16X3);
         la.mirror_all = (next_tc16 && !(flags & FTSP2_FULL_OPERANDS)) ? 0 : 1;
         la.lower_t = (!simt && prev_skips_mirror) ? 1 : 0;
         prev_skips_mirror = la.mirror_all ? 0 : 1;
+        la.done = reinterpret_cast<int*>(W + L.done);
         for (int c = 0; c < L.nchains; ++c) {
             const int rp = g & 1, wp = (g + 1) & 1;
             if (simt || rtc) la.opr[c] = all_simt ? W + L.OP[c][rp] : W + L.OPR[c][rp];
             else la.opr[c] = W + L.OP[c][rp];
             if (next_simt || next_rtc) la.opw[c] = all_simt ? W + L.OP[c][wp] : W + L.OPR[c][wp];
             else la.opw[c] = W + L.OP[c][wp];
+            // write operands of layer g + 1 (same kind): parity (g + 2) & 1
+            la.opw_alt[c] = (rtc ? W + L.OPR[c][rp] : W + L.OP[c][rp]);
         }
         if (dD == nullptr && la.last) la.D = nullptr;
         cudaError_t e;
@@ -710,6 +731,34 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
             la.ntiles = pair ? L.ntiles : L.ntiles_ref;
             const int units = std::max(1, std::min(la.ntiles, pair ? di.sms / 2 : di.sms));
             la.escr = pair && L.escr_ctas >= 2 * units ? reinterpret_cast<float*>(W + L.escr) : nullptr;
+            // consecutive layers of this kind in one persistent launch when each
+            // layer alone is only a few waves of tiles and every unit can be
+            // resident at once (the launch's CTAs wait on one another)
+            int m = 1, lunits = units;
+            if (!(flags & FTSP2_LAYER_LAUNCHES) && g_coop_ok.load() != 0 && !(capturing && g_coop_ok.load() != 1) &&
+                la.ntiles <= 16 * units && in_run(g) &&
+                (lmode == FTSP2_TF32X3 || la.lower_t == (la.mirror_all ? 0 : 1))) {
+                while (g + m < Lmax && in_run(g + m)) ++m;
+                if (m > 1) {
+                    // at most the co-resident units (cluster placement may leave an SM out)
+                    const bool defer = pair && la.escr != nullptr;
+                    const int maxu = layer_tc_max_units(lmode, pair, defer);
+                    if (maxu >= units) lunits = units;
+                    else if (maxu >= (units * 9) / 10) lunits = maxu;
+                    else m = 1;
+                }
+            }
+            la.nlayers = m;
+            if (m > 1) {
+                // chunk schedule over the run: chunk_elems up to tail_from, chunk_tail after
+                for (int h = g + 1; h < g + m; ++h) {
+                    if (chunk_elems_of(lmode, h, Lmax) != la.chunk_elems) {
+                        la.tail_from = h;
+                        la.chunk_tail = chunk_elems_of(lmode, h, Lmax);
+                        break;
+                    }
+                }
+            }
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             {
                 std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -720,13 +769,28 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
                     e0 = e1 = nullptr;
                 }
             }
-            e = launch_layer_tc(lmode, la, rtc ? mapsR[g & 1] : maps[g & 1], units, pair, s);
+            const TmaMaps& m0 = rtc ? mapsR[g & 1] : maps[g & 1];
+            const TmaMaps& m1 = rtc ? mapsR[(g + 1) & 1] : maps[(g + 1) & 1];
+            e = launch_layer_tc(lmode, la, m0, m1, m > 1 ? lunits : units, pair, s);
+            if (m > 1) {
+                if (e != cudaSuccess && !capturing) {
+                    // multi-layer launches refused here: one launch per layer from now on
+                    cudaGetLastError();
+                    g_coop_ok.store(0);
+                    la.nlayers = m = 1;
+                    la.tail_from = INT_MAX;
+                    e = launch_layer_tc(lmode, la, m0, m1, units, pair, s);
+                } else if (e == cudaSuccess) {
+                    g_coop_ok.store(1);
+                }
+            }
             if (e0) {
                 cudaEventRecord(e1, s);
                 std::lock_guard<std::mutex> lk(g_prof_mu);
-                g_prof_events.emplace_back(e0, e1);
+                g_prof_events.push_back(ProfEvent{e0, e1, m});
             }
             last_table = pair ? 0 : 1;
+            g += m - 1;     // the run's remaining layers are done
         }
         if (e != cudaSuccess) return FTSP2_E_CUDA;
     }
@@ -855,14 +919,14 @@ ftsp2_status ftsp2_profile_read(double* total_ms, uint64_t* launches) {
     ftsp2_status st = FTSP2_OK;
     for (auto& pr : g_prof_events) {
         float ms = 0.f;
-        if (cudaEventSynchronize(pr.second) != cudaSuccess || cudaEventElapsedTime(&ms, pr.first, pr.second) != cudaSuccess)
+        if (cudaEventSynchronize(pr.e1) != cudaSuccess || cudaEventElapsedTime(&ms, pr.e0, pr.e1) != cudaSuccess)
             st = FTSP2_E_CUDA;
         else {
             sum += ms;
-            ++n;
+            n += (uint64_t)pr.layers;
         }
-        cudaEventDestroy(pr.first);
-        cudaEventDestroy(pr.second);
+        cudaEventDestroy(pr.e0);
+        cudaEventDestroy(pr.e1);
     }
     g_prof_events.clear();
     if (total_ms) *total_ms = sum;

@@ -95,6 +95,7 @@ struct InstWork {
 struct Layout {
     // all offsets in bytes from the workspace base
     size_t inst_work, tiles, tiles_ref, partials, status, lanczos;
+    size_t done;          // kMaxLayers x kMaxChains completion counters (multi-layer launches)
     size_t escr;          // deferred-epilogue scratch (escr_ctas x kEpiScratchFloats floats)
     int escr_ctas;        // 0: the pair tiles run their final epilogue inline
     size_t Z[kMaxChains], A[kMaxChains], OP[kMaxChains][2], OPR[kMaxChains][2];
@@ -118,6 +119,7 @@ struct SetupArgs {
     ftsp2_rescale_rec* rec;
     int* status;
     float* h32;                       // nullable: FP32 copy of H (same element offsets), for FTSP2_LANCZOS
+    int* done;                        // kMaxLayers x kMaxChains counters, zeroed by prep
 };
 
 void launch_prep(const SetupArgs& a, cudaStream_t s);
@@ -222,6 +224,18 @@ struct LayerArgs {
     // mirror_all = this layer writes the mirror (c, r) everywhere (the next
     // layer reads full matrices), else only inside diagonal tiles.
     int lower_t, mirror_all;
+    // Several consecutive layers in one persistent launch (nlayers > 1): the
+    // work items are (global layer gl + l, tile) for l < nlayers, taken in that
+    // order; an item of layer g waits until every epilogue of layer g - 1 of its
+    // chain has finished (done[(g - 1) * kMaxChains + chain] reaches
+    // kEpiWarps x CTAs per tile x tiles per chain).  Layers gl + 1, gl + 3, ...
+    // write their operands through opw_alt and read them through the second
+    // tensor-map set.  Layers >= tail_from accumulate chunk_tail elements per
+    // TMEM chunk instead of chunk_elems.
+    int nlayers;
+    int chunk_tail, tail_from;
+    uint8_t* opw_alt[kMaxChains];
+    int* done;
 };
 
 struct TmaMaps {
@@ -235,8 +249,12 @@ int tc_block_m(int mode, int pair);
 int tc_smem_bytes(int mode);
 // pair = 1: 256 x 256 tiles on CTA pairs (units = pairs); pair = 0: 128 x 128
 // tiles on single CTAs (units = CTAs).  Persistent grid of `units`.
-cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, int units, int pair,
-                            cudaStream_t s);
+cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, const TmaMaps& maps_alt, int units,
+                            int pair, cudaStream_t s);
+// Largest number of units (pairs or CTAs) of the main-format layer kernel that
+// can be resident at once (0 if unknown): the bound for multi-layer launches,
+// whose CTAs wait on one another.
+int layer_tc_max_units(int mode, int pair, bool defer);
 // CUDA-core FP32 layer (k_layer_simt.cu), 128 x 128 tiles.
 cudaError_t launch_layer_simt(const LayerArgs& a, int grid, cudaStream_t s);
 

@@ -372,13 +372,13 @@ struct EpiLite {
 // FMT: operand format written; scaled_in: the products were formed from
 // power-of-two scaled FP16 operands (FP16X2 layers).
 template <int FMT>
-__device__ __forceinline__ void make_lite(const LayerArgs& a, const Tile& t, int k, bool scaled_in, EpiLite& e) {
+__device__ __forceinline__ void make_lite(const LayerArgs& a, const Tile& t, int g, int k, bool scaled_in, EpiLite& e) {
     const ftsp2_rescale_rec& rec = a.rec[t.inst];
     const DevModel& M = a.models[rec.model];
     const DevLayer L = a.layers[(a.chain_kind[t.chain] == CHAIN_ENTROPY ? M.offS : M.off) + k];
     const size_t slab = (size_t)t.inst * a.P * a.P;
     e.Z = a.Z[t.chain] + slab;
-    e.op = a.opw[t.chain] + slab * OpFmtT<FMT>::ESZ;
+    e.op = (((g - a.gl) & 1) ? a.opw_alt : a.opw)[t.chain] + slab * OpFmtT<FMT>::ESZ;
     e.mul = scaled_in ? L.acc_mul : L.a;
     e.bp = L.bp;
     e.d = L.d;
@@ -625,12 +625,57 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // The persistent loop of a unit visits tiles t, t + nunits, ...: is there an
 // active tile after t?  (The last tile of a unit runs its final epilogue inline,
 // so that no store-warp tail follows the last MMAs.)
-__device__ __forceinline__ bool has_next_tile(const LayerArgs& a, int t, int nunits) {
-    for (int u = t + nunits; u < a.ntiles; u += nunits) {
-        int k;
-        if (tile_active(a, a.tiles[u], k)) return true;
+// Work items of a launch: item f is (global layer gl + f / ntiles, tile
+// f % ntiles); a one-layer launch has ntiles items.
+__device__ __forceinline__ int n_items(const LayerArgs& a) { return a.ntiles * a.nlayers; }
+__device__ __forceinline__ void item_of(const LayerArgs& a, int f, int& g, int& t) {
+    const int l = f / a.ntiles;
+    g = a.gl + l;
+    t = f - l * a.ntiles;
+}
+
+// Does the unit have an active item after item f?
+__device__ __forceinline__ bool has_next_tile(const LayerArgs& a, int f, int nunits) {
+    const int nf = n_items(a);
+    for (int u = f + nunits; u < nf; u += nunits) {
+        int g, t, k;
+        item_of(a, u, g, t);
+        if (tile_active_g(a, a.tiles[t], g, k)) return true;
     }
     return false;
+}
+
+// Completion counters of multi-layer launches.  An epilogue warp adds its
+// share after its stores (release: fence, then the atomic); a reader acquires.
+__device__ __forceinline__ void done_add(const LayerArgs& a, int g, int chain, int v) {
+    __threadfence();
+    atomicAdd(a.done + g * kMaxChains + chain, v);
+}
+__device__ __forceinline__ int done_acquire(const LayerArgs& a, int g, int chain) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(a.done + g * kMaxChains + chain) : "memory");
+    return v;
+}
+// Wait, with the barrier waits' time limit, until layer g of `chain` is
+// complete; false on timeout (abort flag and status set) or when another role
+// or CTA has failed.
+__device__ __forceinline__ bool wait_layer_done(const LayerArgs& a, int g, int chain, int target,
+                                                volatile int* abort_flag) {
+    if (done_acquire(a, g, chain) >= target) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        __nanosleep(256);
+        if (done_acquire(a, g, chain) >= target) return true;
+        if (*abort_flag || *reinterpret_cast<volatile int*>(a.status) != 0) {
+            *abort_flag = 1;
+            return false;
+        }
+        if (globaltimer() - t0 > kWaitTimeoutNs) {
+            *abort_flag = 1;
+            atomicExch(a.status, (int)FTSP2_E_TIMEOUT);
+            return false;
+        }
+    }
 }
 
 // Work items of the deferred epilogue: item i (the block of accumulating warp
@@ -669,7 +714,8 @@ __device__ __forceinline__ bool next_entry(const Tile& tl, int rank, int n, int&
 
 template <int MODE, int OUTFMT, bool PAIR, bool DEFER>
 __global__ void __launch_bounds__(threads_of(DEFER), 1)
-    layer_tc_kernel(const __grid_constant__ LayerArgs a, const __grid_constant__ TmaMaps maps) {
+    layer_tc_kernel(const __grid_constant__ LayerArgs a, const __grid_constant__ TmaMaps maps0,
+                    const __grid_constant__ TmaMaps maps1) {
     using C = TcCfg<MODE>;
     using G = Geo<PAIR>;
     static_assert(!(DEFER && OUTFMT == kLastLayer), "the last layer runs its epilogue inline");
@@ -696,9 +742,14 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = PAIR ? cluster_rank() : 0u;
-    // K slices per accumulation chunk: the default 128 elements, or a shorter
-    // chunk requested for this launch (a.chunk_elems)
-    const int ck = max(1, (a.chunk_elems > 0 ? a.chunk_elems : C::CK * BKE) / BKE);
+    // K slices per accumulation chunk at global layer g: the default 128
+    // elements, or a shorter chunk requested for the layer
+    auto ck_of = [&](int g) {
+        const int ce = g >= a.tail_from ? a.chunk_tail : a.chunk_elems;
+        return max(1, (ce > 0 ? ce : C::CK * BKE) / BKE);
+    };
+    // epilogue-warp completions that make a layer of one chain complete
+    const int done_target = kEpiWarps * G::NCTA * (a.ntiles / max(1, a.nchains));
     const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;     // pair or CTA
     const int nunits = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
     if (threadIdx.x == 0) {
@@ -743,10 +794,25 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             // ---------------- TMA producer ----------------
             int stage = 0;
             uint32_t phase = 0;
-            for (int t = unit; t < a.ntiles && !abort_flag; t += nunits) {
+            int known[kMaxChains] = {a.gl, a.gl};    // layers whose predecessor is known complete
+            const int nf = n_items(a);
+            for (int f = unit; f < nf && !abort_flag; f += nunits) {
+                int g, t;
+                item_of(a, f, g, t);
                 const Tile tl = a.tiles[t];
                 int k;
-                if (!tile_active(a, tl, k)) continue;
+                if (!tile_active_g(a, tl, g, k)) {
+                    // an inactive item counts as finished for the layer's completion
+                    if (a.nlayers > 1) atomicAdd(a.done + g * kMaxChains + tl.chain, kEpiWarps);
+                    continue;
+                }
+                if (g > known[tl.chain]) {
+                    // operands and state of this item were written by other CTAs
+                    if (!wait_layer_done(a, g - 1, tl.chain, done_target, &abort_flag)) break;
+                    known[tl.chain] = g;
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                }
+                const TmaMaps& maps = ((g - a.gl) & 1) ? maps1 : maps0;
                 const int n = a.inst[tl.inst].n;
                 const int nk = (n + BKE - 1) / BKE;
                 const int rowA = tl.inst * a.P + tl.I * TILE + (int)rank * kCtaRows;
@@ -826,12 +892,16 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             // address >> 4); all operand slices lie inside this CTA's window
             const uint64_t desc0 = sdesc_sw128(smem_u32(smem));
             const uint64_t descT = sdesc_mn_sw128(smem_u32(smem));   // transposed panels
-            for (int t = unit; t < a.ntiles && ok && !abort_flag; t += nunits) {
+            const int nf = n_items(a);
+            for (int f = unit; f < nf && ok && !abort_flag; f += nunits) {
+                int g, t;
+                item_of(a, f, g, t);
                 const Tile tl = a.tiles[t];
                 int k;
-                if (!tile_active(a, tl, k)) continue;
+                if (!tile_active_g(a, tl, g, k)) continue;
                 const int n = a.inst[tl.inst].n;
                 const int nk = (n + BKE - 1) / BKE;
+                const int ck = ck_of(g);
                 for (int kc = 0; kc < nk && ok; kc += ck) {
                     if (!wait_bar(&tempty_bar[buf], aphase ^ 1u, &abort_flag, a.status)) {
                         ok = false;
@@ -907,19 +977,27 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
         uint32_t sp = 0;
         uint32_t used = 0;                       // entries consumed (ring slot)
         bool ok = true;
-        for (int t = unit; t < a.ntiles && ok; t += nunits) {
+        const int nf = n_items(a);
+        for (int f = unit; f < nf && ok; f += nunits) {
+            int g, t;
+            item_of(a, f, g, t);
             const Tile tl = a.tiles[t];
             int k;
-            if (!tile_active(a, tl, k)) continue;
-            if (!has_next_tile(a, t, nunits)) continue;     // inline in the accumulating warps
+            if (!tile_active_g(a, tl, g, k)) continue;
+            if (!has_next_tile(a, f, nunits)) continue;     // inline in the accumulating warps
             if (!wait_bar(&sfull_bar, sp, &abort_flag, a.status)) {
                 ok = false;
                 break;
             }
             sp ^= 1u;
+            if (a.nlayers > 1 && g > a.gl) {
+                // the state of layer g - 1, written by other CTAs
+                if (lane == 0) done_acquire(a, g - 1, tl.chain);
+                __syncwarp();
+            }
             const int n = a.inst[tl.inst].n;
             EpiLite e;
-            make_lite<OUTFMT>(a, tl, k, MODE == FTSP2_FP16X2, e);
+            make_lite<OUTFMT>(a, tl, g, k, MODE == FTSP2_FP16X2, e);
             // each lane copies exactly the 16-byte runs it reads later (its row
             // of the 8-column halves), so its own cp.async.wait_group suffices
             auto issue = [&](int i, int g, uint32_t slot) {
@@ -968,7 +1046,11 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             }
             if (!ok) break;
             __syncwarp();
-            if (lane == 0) local_arrive(smem_u32(&sempty_bar));
+            if (lane == 0) {
+                // this warp's share of the tile's kEpiWarps completions
+                if (a.nlayers > 1) done_add(a, g, tl.chain, kEpiWarps / kStoreWarps);
+                local_arrive(smem_u32(&sempty_bar));
+            }
         }
         }
         __syncwarp();
@@ -982,7 +1064,10 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
         uint32_t aphase = 0;
         uint32_t sp = 0;                         // scratch parity (deferred epilogue)
         bool ok = true;
-        for (int t = unit; t < a.ntiles && ok; t += nunits) {
+        const int nf = n_items(a);
+        for (int f = unit; f < nf && ok; f += nunits) {
+            int g, t;
+            item_of(a, f, g, t);
             // Only the chunk count and the liveness of the warp's block are
             // carried through the drain loop; the tile's descriptor and the
             // rest of the context are fetched again for the final epilogue
@@ -993,13 +1078,14 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             {
                 const Tile tl = a.tiles[t];
                 int k;
-                if (!tile_active(a, tl, k)) continue;
+                if (!tile_active_g(a, tl, g, k)) continue;
                 const int n = a.inst[tl.inst].n;
                 const int R0 = tl.I * TILE + (int)rank * kCtaRows + q * 32;
                 const int C0 = tl.J * TILE + cq * EPI_COLS;
                 warp_live = C0 < n && C0 + EPI_COLS - 1 >= R0 && R0 < n;
+                const int ck = ck_of(g);
                 nch = ((n + BKE - 1) / BKE + ck - 1) / ck;
-                defer_tile = DEFER && has_next_tile(a, t, nunits);
+                defer_tile = DEFER && has_next_tile(a, f, nunits);
             }
             float acc[EPI_COLS];
 #pragma unroll
@@ -1066,7 +1152,12 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             const uint32_t tfin = tbase + (uint32_t)(buf * TILE);   // the held buffer
             const Tile tl = a.tiles[t];
             int k;
-            tile_active(a, tl, k);
+            tile_active_g(a, tl, g, k);
+            if (a.nlayers > 1 && g > a.gl) {
+                // the state of layer g - 1, written by other CTAs
+                if (lane == 0) done_acquire(a, g - 1, tl.chain);
+                __syncwarp();
+            }
             const int n = a.inst[tl.inst].n;
             const int R0 = tl.I * TILE + (int)rank * kCtaRows + q * 32;   // first row of this warp
             const int r = R0 + lane;
@@ -1090,7 +1181,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                     }
                 } else {
                     EpiLite e;
-                    make_lite<OUTFMT>(a, tl, k, MODE == FTSP2_FP16X2, e);
+                    make_lite<OUTFMT>(a, tl, g, k, MODE == FTSP2_FP16X2, e);
                     // the groups that touch the triangle and the order form one range
                     const int g_lo = R0 > C0 ? min(EPI_COLS / kGrp, (R0 - C0) / kGrp) : 0;
                     const int g_hi = min(EPI_COLS / kGrp, (n - C0 + kGrp - 1) / kGrp);
@@ -1106,6 +1197,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             if (lane == 0) {
                 if constexpr (PAIR) remote_arrive(tempty0 + 8u * (uint32_t)buf);
                 else local_arrive(tempty0 + 8u * (uint32_t)buf);
+                if (a.nlayers > 1) done_add(a, g, tl.chain, 1);
             }
             if (++buf == NBUF) {
                 buf = 0;
@@ -1164,61 +1256,122 @@ int tc_smem_bytes(int mode) {
 }
 
 template <int MODE, int OUTFMT, bool PAIR, bool DEFER>
-static cudaError_t launch_variant(const LayerArgs& a, const TmaMaps& maps, int units, cudaStream_t s) {
-    const int smem = smem_of<MODE>(DEFER);
+static cudaError_t set_smem_attr() {
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(layer_tc_kernel<MODE, OUTFMT, PAIR, DEFER>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_of<MODE>(DEFER));
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
+    return cudaSuccess;
+}
+
+// A multi-layer launch (a.nlayers > 1) is cooperative: its CTAs wait on one
+// another, so all of them must be resident at once.
+template <int MODE, int OUTFMT, bool PAIR, bool DEFER>
+static cudaError_t launch_variant(const LayerArgs& a, const TmaMaps& maps, const TmaMaps& maps_alt, int units,
+                                  cudaStream_t s) {
+    const int smem = smem_of<MODE>(DEFER);
+    cudaError_t e = set_smem_attr<MODE, OUTFMT, PAIR, DEFER>();
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(Geo<PAIR>::NCTA * units, 1, 1);
     cfg.blockDim = dim3(threads_of(DEFER), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    if (PAIR) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = Geo<PAIR>::NCTA;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    if (a.nlayers > 1) {
+        attr[na].id = cudaLaunchAttributeCooperative;
+        attr[na].val.cooperative = 1;
+        ++na;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    e = cudaLaunchKernelEx(&cfg, layer_tc_kernel<MODE, OUTFMT, PAIR, DEFER>, a, maps, maps_alt);
+    count_launch();
+    return e;
+}
+
+template <int MODE, int OUTFMT, bool PAIR, bool DEFER>
+static int max_units_variant() {
+    if (set_smem_attr<MODE, OUTFMT, PAIR, DEFER>() != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(Geo<PAIR>::NCTA, 1, 1);
+    cfg.blockDim = dim3(threads_of(DEFER), 1, 1);
+    cfg.dynamicSmemBytes = smem_of<MODE>(DEFER);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = Geo<PAIR>::NCTA;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = PAIR ? 1 : 0;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, layer_tc_kernel<MODE, OUTFMT, PAIR, DEFER>, a, maps);
-    count_launch();
-    return e;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, layer_tc_kernel<MODE, OUTFMT, PAIR, DEFER>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 template <int MODE, int MAINFMT, bool PAIR>
-static cudaError_t launch_shape(const LayerArgs& a, const TmaMaps& maps, int units, cudaStream_t s) {
-    if (a.last) return launch_variant<MODE, kLastLayer, PAIR, false>(a, maps, units, s);
-    if (a.next_fmt == OP_F32) return launch_variant<MODE, OP_F32, PAIR, false>(a, maps, units, s);
+static cudaError_t launch_shape(const LayerArgs& a, const TmaMaps& maps, const TmaMaps& maps_alt, int units,
+                                cudaStream_t s) {
+    if (a.last) return launch_variant<MODE, kLastLayer, PAIR, false>(a, maps, maps_alt, units, s);
+    if (a.next_fmt == OP_F32) return launch_variant<MODE, OP_F32, PAIR, false>(a, maps, maps_alt, units, s);
     if constexpr (MAINFMT != OP_BF16X3) {
         // the layer before BF16X3 refinement layers (FTSP2_REFINE_TC)
-        if (a.next_fmt == OP_BF16X3) return launch_variant<MODE, OP_BF16X3, PAIR, false>(a, maps, units, s);
+        if (a.next_fmt == OP_BF16X3) return launch_variant<MODE, OP_BF16X3, PAIR, false>(a, maps, maps_alt, units, s);
     }
     // the layers of the main format: the final epilogue inline or deferred to
     // store warps (a.escr set: a scratch slot for each CTA of the grid)
     if constexpr (PAIR) {
-        if (a.escr) return launch_variant<MODE, MAINFMT, PAIR, true>(a, maps, units, s);
+        if (a.escr) return launch_variant<MODE, MAINFMT, PAIR, true>(a, maps, maps_alt, units, s);
     }
-    return launch_variant<MODE, MAINFMT, PAIR, false>(a, maps, units, s);
+    return launch_variant<MODE, MAINFMT, PAIR, false>(a, maps, maps_alt, units, s);
 }
 
 template <int MODE, int MAINFMT>
-static cudaError_t launch_mode(const LayerArgs& a, const TmaMaps& maps, int units, int pair, cudaStream_t s) {
-    return pair ? launch_shape<MODE, MAINFMT, true>(a, maps, units, s)
-                : launch_shape<MODE, MAINFMT, false>(a, maps, units, s);
+static cudaError_t launch_mode(const LayerArgs& a, const TmaMaps& maps, const TmaMaps& maps_alt, int units, int pair,
+                               cudaStream_t s) {
+    return pair ? launch_shape<MODE, MAINFMT, true>(a, maps, maps_alt, units, s)
+                : launch_shape<MODE, MAINFMT, false>(a, maps, maps_alt, units, s);
 }
 
-cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, int units, int pair, cudaStream_t s) {
+cudaError_t launch_layer_tc(int mode, const LayerArgs& a, const TmaMaps& maps, const TmaMaps& maps_alt, int units,
+                            int pair, cudaStream_t s) {
     switch (mode) {
-        case FTSP2_FP16X2: return launch_mode<FTSP2_FP16X2, OP_F16X2>(a, maps, units, pair, s);
-        case FTSP2_BF16X3: return launch_mode<FTSP2_BF16X3, OP_BF16X3>(a, maps, units, pair, s);
-        case FTSP2_TF32X3: return launch_mode<FTSP2_TF32X3, OP_TF32X3>(a, maps, units, pair, s);
+        case FTSP2_FP16X2: return launch_mode<FTSP2_FP16X2, OP_F16X2>(a, maps, maps_alt, units, pair, s);
+        case FTSP2_BF16X3: return launch_mode<FTSP2_BF16X3, OP_BF16X3>(a, maps, maps_alt, units, pair, s);
+        case FTSP2_TF32X3: return launch_mode<FTSP2_TF32X3, OP_TF32X3>(a, maps, maps_alt, units, pair, s);
     }
     return cudaErrorInvalidValue;
+}
+
+template <int MODE, int MAINFMT>
+static int max_units_mode(int pair, bool defer) {
+    if (pair) {
+        return defer ? max_units_variant<MODE, MAINFMT, true, true>() : max_units_variant<MODE, MAINFMT, true, false>();
+    }
+    return max_units_variant<MODE, MAINFMT, false, false>();
+}
+
+int layer_tc_max_units(int mode, int pair, bool defer) {
+    switch (mode) {
+        case FTSP2_FP16X2: return max_units_mode<FTSP2_FP16X2, OP_F16X2>(pair, defer);
+        case FTSP2_BF16X3: return max_units_mode<FTSP2_BF16X3, OP_BF16X3>(pair, defer);
+        case FTSP2_TF32X3: return max_units_mode<FTSP2_TF32X3, OP_TF32X3>(pair, defer);
+    }
+    return 0;
 }
 
 }  // namespace ftsp2

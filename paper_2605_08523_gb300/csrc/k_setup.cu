@@ -112,6 +112,8 @@ __global__ void prep_kernel(SetupArgs a) {
         a.iw[b].start_layer = 0;
     }
     if (threadIdx.x == 0) *a.status = 0;
+    if (a.done)
+        for (int i = threadIdx.x; i < kMaxLayers * kMaxChains; i += blockDim.x) a.done[i] = 0;
     if (a.tiles) block_exclusive_scan_fill(a.inst, a.nb, a.BM, a.BN, a.nchains, a.iw, a.tiles, 0);
     if (a.tiles_ref) block_exclusive_scan_fill(a.inst, a.nb, a.BM_ref, a.BN_ref, a.nchains, a.iw, a.tiles_ref, 1);
 }
