@@ -703,7 +703,9 @@ def main():
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": "layer_tc_kernel<%s>" % args.mode.upper(), "kernel_sha": ksha,
-                     "per_launch_alg_flops": alg_per_launch, "avg_launch_ms": layer_avg * 1000,
+                     "per_layer_alg_flops": alg_per_launch, "avg_layer_ms": layer_avg * 1000,
+                     "work_unit": "one layer of both chains (CUDA events around each layer-kernel launch; "
+                                  "a multi-layer launch counts its layers)",
                      "peak_kind": "bf16_tflops_sustained (%s)" % pk_kind,
                      "hw_tensor_tflops": hw_achieved, "hw_frac": (hw_achieved / hw_peak) if hw_achieved else None,
                      "hw_peak": hw_peak, "hw_peak_dtype": dt_of_mode, "hw_peak_ratio_to_bf16": ratio,

@@ -128,7 +128,7 @@ typedef enum {
  * every layer writes and reads full matrices (results are identical). */
 #define FTSP2_FULL_OPERANDS 0x800
 /* Layer launches.  When a launch of the tensor-core layer kernel would run a
- * few waves of tiles (at most 16 per unit), consecutive layers of the main
+ * few waves of tiles (at most 8 per unit), consecutive layers of the main
  * format run in one persistent cooperative launch.  Its work items are (layer,
  * tile) in layer order, and an item of layer g starts once every tile of layer
  * g - 1 of the same chain is finished (device-side counters; bounded waits

@@ -732,11 +732,14 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
             const int units = std::max(1, std::min(la.ntiles, pair ? di.sms / 2 : di.sms));
             la.escr = pair && L.escr_ctas >= 2 * units ? reinterpret_cast<float*>(W + L.escr) : nullptr;
             // consecutive layers of this kind in one persistent launch when each
-            // layer alone is only a few waves of tiles and every unit can be
-            // resident at once (the launch's CTAs wait on one another)
+            // layer alone is only a few waves of tiles (at most 8: with more, the
+            // idle tail of a launch is a small share, and at n = 8192 the busier
+            // GPU ran at a lower power-capped clock, 90.2 against 83.2 ms per
+            // solve) and every unit can be resident at once (the launch's CTAs
+            // wait on one another)
             int m = 1, lunits = units;
             if (!(flags & FTSP2_LAYER_LAUNCHES) && g_coop_ok.load() != 0 && !(capturing && g_coop_ok.load() != 1) &&
-                la.ntiles <= 16 * units && in_run(g) &&
+                la.ntiles <= 8 * units && in_run(g) &&
                 (lmode == FTSP2_TF32X3 || la.lower_t == (la.mirror_all ? 0 : 1))) {
                 while (g + m < Lmax && in_run(g + m)) ++m;
                 if (m > 1) {
