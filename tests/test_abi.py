@@ -106,12 +106,12 @@ def test_flag_constants_match_header():
     src = open(os.path.join(ROOT, "include", "ftsp2.h")).read()
     defs = {m.group(1): int(m.group(2), 0) for m in re.finditer(r"#define FTSP2_(\w+)\s+(0x[0-9a-fA-F]+|\d+)", src)}
     for name in ("SYNC", "CLAMP", "REFINE1", "REFINE2", "PAIR_TILES", "SINGLE_TILES", "LANCZOS", "MIN_LAYERS",
-                 "REFINE_TC", "EPI_DEFERRED", "EPI_INLINE", "FULL_OPERANDS", "TARGET_FERMI",
+                 "REFINE_TC", "EPI_DEFERRED", "EPI_INLINE", "FULL_OPERANDS", "LAYER_LAUNCHES", "TARGET_FERMI",
                  "TARGET_ENTROPY"):
         assert defs[name] == getattr(_lib, name), name
     # flags are distinct bits
     bits = [defs[n] for n in ("SYNC", "CLAMP", "REFINE1", "REFINE2", "PAIR_TILES", "SINGLE_TILES", "LANCZOS", "MIN_LAYERS",
-                              "REFINE_TC", "EPI_DEFERRED", "EPI_INLINE", "FULL_OPERANDS")]
+                              "REFINE_TC", "EPI_DEFERRED", "EPI_INLINE", "FULL_OPERANDS", "LAYER_LAUNCHES")]
     assert all(b & (b - 1) == 0 for b in bits) and len(set(bits)) == len(bits)
 
 
