@@ -1,13 +1,18 @@
-// (a3)-(a6) One layer of the learned recursion (Eq. mlsp2) for every active
-// (instance, chain) of a grouped launch, on the 5th-generation tensor cores.
+// (a3)-(a6) Layers of the learned recursion (Eq. mlsp2) for every active
+// (instance, chain) of a grouped launch, on the 5th-generation tensor cores:
+// one layer per launch, or consecutive layers of the main format in one
+// persistent cooperative launch (below).
 //
 // The product of a layer is the symmetric square Z^2 of the centred state.
 // Output tiles are square (256 x 256 on CTA pairs or 128 x 128 on single CTAs,
 // chosen per call) and only those touching the upper triangle are computed
-// (I <= J); each element (r, c) with r <= c is produced once and written to
-// (r, c) and (c, r).  Since Z is symmetric, (Z^2)_{rc} =
-// sum_k Z_{rk} Z_{ck}: both MMA operands are K-major row panels of the same
-// matrix, loaded by TMA with 128-byte swizzle.
+// (I <= J); each element (r, c) with r <= c is produced once.  Since Z is
+// symmetric, (Z^2)_{rc} = sum_k Z_{rk} Z_{ck}: both MMA operands are row
+// panels of the same matrix, loaded by TMA with 128-byte swizzle.  The next
+// operands are stored for the upper triangle plus the diagonal tile blocks
+// (the mirror (c, r) everywhere only before a layer that reads full
+// matrices); K-slices left of a panel's diagonal block are loaded as
+// transposed 64 x 64 panels of the upper triangle (MN-major operands).
 //
 // Split precision (Sec. IV A, Eq. emulated matmul, generalised): Z is stored as
 // NSPLIT low-precision planes Z = sum_s Z_s and the products Z_s Z_t with
@@ -52,6 +57,16 @@
 // shared ring (cp.async) and write the results while the next tile's MMAs run.
 // A unit's last tile always runs inline, so no store-warp tail follows the
 // last MMAs.
+// Multi-layer launches (a.nlayers > 1).  The work items are (layer, tile) in
+// layer order; every role walks the same item sequence.  An item of layer g
+// waits (producer) until all tiles of layer g - 1 of its chain have finished
+// their epilogues: each CTA counts kEpiWarps completions per tile in
+// a.done[g][chain] (accumulating warps 1 each, store warps
+// kEpiWarps / kStoreWarps each, the producer kEpiWarps for an inactive item),
+// released by a fence before the atomic and acquired by the readers, with a
+// proxy fence before the TMA loads of the new operands.  Dependencies point
+// only to earlier items and a unit takes its items in order, so the waits end;
+// the CTAs of such a launch are co-resident (cooperative launch).
 // Every wait is bounded: on timeout the CTA sets FTSP2_E_TIMEOUT in the status
 // word and all roles leave their loops.
 #include <cuda_bf16.h>
