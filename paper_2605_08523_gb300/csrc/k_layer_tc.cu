@@ -123,6 +123,9 @@ constexpr int kRing = 2;
 constexpr int kEntryBytes = 3 * 2048;
 constexpr int kItemFloats = 2048;
 static_assert(kEpiWarps * kItemFloats == kEpiScratchFloats, "scratch of one CTA");
+// multi-layer launches: the store warps' shares of a tile's completions add up
+// to the kEpiWarps that the accumulating warps give for an inline tile
+static_assert(kEpiWarps % kStoreWarps == 0, "completion shares of the store warps");
 __host__ __device__ constexpr int threads_of(bool deferred) {
     return 64 + 32 * (kEpiWarps + (deferred ? kStoreWarps : 0));
 }
