@@ -44,12 +44,17 @@ def test_bounds_match_oracle(ft):
     rec = ft.ftsp2_rescale(torch.from_numpy(flat).cuda(), ns, [0.0] * len(ns), [0.1] * len(ns), ms,
                            flags=ft.LANCZOS)
     for b, H in enumerate(Hs):
-        # the oracle's recurrence is FP64 throughout; the GPU's products H v read
-        # FP32 copies (FP32 row sums), which moves the Ritz values by ~1e-7 of W
+        # The oracle is the FP64 definition.  The GPU forms the products H v
+        # from an FP32 copy of H (FP32 row sums), which moves the Ritz values by
+        # ~1e-7 of W, and widens its interval by 1e-6 of the Ritz magnitude to
+        # cover that rounding: both belong to the implementation, so they are
+        # allowed here, outward only for the widening.
         lo, hi = lanczos.bounds(H)
         W = max(hi - lo, 1e-30)
-        assert abs(rec["e_min"][b] - lo) <= 2e-6 * max(1.0, W), (b, rec["e_min"][b], lo)
-        assert abs(rec["e_max"][b] - hi) <= 2e-6 * max(1.0, W), (b, rec["e_max"][b], hi)
+        tol = 2e-6 * max(1.0, W)
+        widen = 1e-6 * max(abs(lo), abs(hi))
+        assert lo - tol - widen <= rec["e_min"][b] <= lo + tol, (b, rec["e_min"][b], lo)
+        assert hi - tol <= rec["e_max"][b] <= hi + tol + widen, (b, rec["e_max"][b], hi)
         ev = np.linalg.eigvalsh(H)
         assert rec["e_min"][b] <= ev[0] and rec["e_max"][b] >= ev[-1]
 
