@@ -483,6 +483,30 @@ const char* ftsp2_status_string(ftsp2_status s);
 /* Number of kernels this library launched since load (all entry points). */
 uint64_t ftsp2_kernel_launch_count(void);
 
+/* ---- bounded device-side waits ------------------------------------------------- */
+
+/* Every wait inside a layer kernel is bounded by this limit (ns; default 4e9,
+ * process-wide, read at each call).  The waits are those of the multi-layer
+ * launches (an item waits until every tile of the previous layer of its chain
+ * has finished) and of the kernel's internal pipeline barriers.  When a
+ * dependency wait runs out, the kernel records FTSP2_E_TIMEOUT in the call's
+ * status word and every CTA finishes its work list in a skip mode that keeps
+ * the barrier protocol (no loads, MMAs or stores), so nothing is left in
+ * flight and the context stays usable; the per-instance records then carry
+ * FTSP2_E_TIMEOUT (returned with FTSP2_SYNC) and the outputs are not valid.
+ * The next call starts from a cleared status word.  (No counterpart in the
+ * paper: a property of this implementation's persistent launches.)
+ * FTSP2_E_ARG unless 1e5 <= ns <= 6e10. */
+ftsp2_status ftsp2_set_wait_limit_ns(uint64_t ns);
+uint64_t ftsp2_wait_limit_ns(void);
+
+/* Test hook for the bounded waits: while layer >= 0, items of that global
+ * layer inside a multi-layer launch wait for one completion more than their
+ * predecessor layer can give, so their dependency wait runs out after the
+ * wait limit.  -1 (the default) turns it off.  Process-wide; for tests only.
+ * FTSP2_E_ARG for layer < -1 or >= 64. */
+ftsp2_status ftsp2_debug_stall_layer(int layer);
+
 #ifdef __cplusplus
 }
 #endif

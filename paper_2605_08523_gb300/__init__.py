@@ -34,6 +34,7 @@ __all__ = ["ModelSet", "Solver", "ftsp2_rescale", "ftsp2_train_coeffs", "ftsp2_t
            "ftsp2_train_coeffs_skip",
            "ftsp2_train_residual_jacobian",
            "ftsp2_train_normal_equations", "ftsp2_autotune_clear", "kernel_launch_count", "profile_layers",
+           "set_wait_limit_ns", "wait_limit_ns", "debug_stall_layer",
            "profile_read", "MODES", "FP32", "TF32X3", "BF16X3", "FP16X2", "SYNC", "CLAMP", "REFINE1", "REFINE2",
            "PAIR_TILES", "SINGLE_TILES", "LANCZOS", "MIN_LAYERS", "REFINE_TC", "EPI_DEFERRED", "EPI_INLINE", "FULL_OPERANDS", "LAYER_LAUNCHES", "TARGET_FERMI", "TARGET_ENTROPY", "Ftsp2Error", "status_string", "lib",
            "REC_DTYPE"]
@@ -61,6 +62,21 @@ def _stream(stream=None):
 
 def kernel_launch_count() -> int:
     return int(lib().ftsp2_kernel_launch_count())
+
+
+def set_wait_limit_ns(ns: int):
+    """Limit of every bounded device-side wait of the layer kernels (ftsp2_set_wait_limit_ns)."""
+    check(lib().ftsp2_set_wait_limit_ns(int(ns)), "ftsp2_set_wait_limit_ns")
+
+
+def wait_limit_ns() -> int:
+    return int(lib().ftsp2_wait_limit_ns())
+
+
+def debug_stall_layer(layer: int):
+    """Test hook: items of this global layer of a multi-layer launch wait for a
+    completion that never comes (ftsp2_debug_stall_layer); -1 turns it off."""
+    check(lib().ftsp2_debug_stall_layer(int(layer)), "ftsp2_debug_stall_layer")
 
 
 def profile_layers(enable: bool):

@@ -88,6 +88,9 @@ SIGNATURES = {
     "ftsp2_profile_read": (_I, [C.POINTER(_D), C.POINTER(C.c_uint64)]),
     "ftsp2_status_string": (C.c_char_p, [_I]),
     "ftsp2_kernel_launch_count": (C.c_uint64, []),
+    "ftsp2_set_wait_limit_ns": (_I, [C.c_uint64]),
+    "ftsp2_wait_limit_ns": (C.c_uint64, []),
+    "ftsp2_debug_stall_layer": (_I, [_I]),
 }
 
 _lib = None

@@ -42,8 +42,10 @@ __device__ __forceinline__ void store_operand(int fmt, uint8_t* base, size_t pla
             uint32_t hb;
             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(zs));
             const float h = __uint_as_float(hb);
+            uint32_t lb;   // low part rounded to the TF32 bits the tensor core reads
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(zs - h));
             reinterpret_cast<float*>(base)[idx] = h;
-            reinterpret_cast<float*>(base)[plane + idx] = zs - h;
+            reinterpret_cast<float*>(base)[plane + idx] = __uint_as_float(lb);
             break;
         }
         case OP_BF16X3: {

@@ -27,6 +27,9 @@ struct ProfEvent {
 static std::vector<ProfEvent> g_prof_events;
 // multi-layer (cooperative) launches: 1 usable, 0 refused once, -1 not tried
 static std::atomic<int> g_coop_ok{-1};
+// limit of each bounded device-side wait, and the dependency-stall test hook
+static std::atomic<unsigned long long> g_wait_ns{kDefaultWaitNs};
+static std::atomic<int> g_stall_layer{-1};
 
 // ------------------------------------------------------------------------------
 // device checks and the CUDA driver API's tensor-map encoder
@@ -337,9 +340,16 @@ static int op_bytes(int fmt) {
 //   FP16X2 128 + last 12 at 64: 7.6e-7 / 6.2e-7, +2 to 3 % time
 //   BF16X3 128 + last 6 at 64:  8.3e-7 / 1.08e-6;  64 everywhere: 5.0e-7 / 8.0e-7, +0.2 %
 //   TF32X3 128 + last 6 at 64:  9.7e-7 / 1.25e-6;  64 everywhere: 6.2e-7 / 8.3e-7, +0.6 %
+// Batches of short tiles (mean order n over the launch's tiles below
+// kShortTileK, e.g. ragged batches of n <= 768) run 64-element chunks in every
+// layer: their tiles carry little MMA work against the epilogue's memory
+// traffic, so the extra chunk drains cost almost nothing, and the rounding of
+// the high-beta0 models such batches select stays smaller.
 constexpr int kShortChunkLayers = 12;
-static int chunk_elems_of(int mode, int g, int Lmax) {
+constexpr double kShortTileK = 1024.0;
+static int chunk_elems_of(int mode, int g, int Lmax, double mean_k) {
     if (mode == FTSP2_BF16X3 || mode == FTSP2_TF32X3) return 64;
+    if (mean_k < kShortTileK) return 64;
     return g >= Lmax - kShortChunkLayers ? 64 : 0;    // 0: the kernel's default (128)
 }
 
@@ -663,6 +673,8 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     la.D = dD;
     la.partials = partials;
     la.status = dstatus;
+    la.wait_ns = g_wait_ns.load();
+    la.stall_layer = g_stall_layer.load();
     for (int c = 0; c < kMaxChains; ++c) {
         la.chain_kind[c] = kinds[c];
         la.Z[c] = c < L.nchains ? reinterpret_cast<float*>(W + L.Z[c]) : nullptr;
@@ -671,6 +683,18 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     auto is_simt = [&](int g) { return all_simt || (g >= refine_from && !refine_tc); };
     auto is_rtc = [&](int g) { return refine_tc && g >= refine_from; };
     const int pair = all_simt ? 1 : tile_shape_choice(inst, nb, mode, want, flags, di.sms);
+    // mean order n over the tensor-core tiles of the chosen shape (chunk policy)
+    double mean_k = 0.0;
+    {
+        double wk = 0.0, wt = 0.0;
+        const int T = pair ? 256 : 128;
+        for (int b = 0; b < nb; ++b) {
+            const double t = (double)host_tiles_of(inst[b].n, T, T);
+            wt += t;
+            wk += t * inst[b].n;
+        }
+        mean_k = wt > 0.0 ? wk / wt : 0.0;
+    }
     int last_table = 0;
     // Operands of 16-bit tensor-core layers are stored as the upper triangle
     // plus the diagonal tile blocks when the layer that reads them can load the
@@ -699,7 +723,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         // reaches the output undamped (earlier errors are contracted by the
         // saturating later layers), and the entropy is linear in it for occupations
         // near 0 and 1.
-        la.chunk_elems = chunk_elems_of(lmode, g, Lmax);
+        la.chunk_elems = chunk_elems_of(lmode, g, Lmax, mean_k);
         la.chunk_tail = la.chunk_elems;
         la.tail_from = INT_MAX;
         la.next_fmt = next_simt ? OP_F32 : (next_rtc ? OP_BF16X3 : fmt);
@@ -755,9 +779,9 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
             if (m > 1) {
                 // chunk schedule over the run: chunk_elems up to tail_from, chunk_tail after
                 for (int h = g + 1; h < g + m; ++h) {
-                    if (chunk_elems_of(lmode, h, Lmax) != la.chunk_elems) {
+                    if (chunk_elems_of(lmode, h, Lmax, mean_k) != la.chunk_elems) {
                         la.tail_from = h;
-                        la.chunk_tail = chunk_elems_of(lmode, h, Lmax);
+                        la.chunk_tail = chunk_elems_of(lmode, h, Lmax, mean_k);
                         break;
                     }
                 }
@@ -908,6 +932,20 @@ const char* ftsp2_status_string(ftsp2_status s) {
 }
 
 uint64_t ftsp2_kernel_launch_count(void) { return g_launches.load(); }
+
+ftsp2_status ftsp2_set_wait_limit_ns(uint64_t ns) {
+    if (ns < 100000ull || ns > 60000000000ull) return FTSP2_E_ARG;
+    g_wait_ns.store(ns);
+    return FTSP2_OK;
+}
+
+uint64_t ftsp2_wait_limit_ns(void) { return g_wait_ns.load(); }
+
+ftsp2_status ftsp2_debug_stall_layer(int layer) {
+    if (layer < -1 || layer >= kMaxLayers) return FTSP2_E_ARG;
+    g_stall_layer.store(layer);
+    return FTSP2_OK;
+}
 
 ftsp2_status ftsp2_profile_layers(int enable) {
     std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -32,7 +32,7 @@ constexpr int kPartialSlots = 32;            // FP64 partial-sum slots per tile 
 constexpr int kEpiScratchFloats = 32768;     // deferred epilogue: finished sums of one CTA's tile
 constexpr int kMaxDeferCtas = 192;           // CTAs with a scratch slot in the workspace
 constexpr int kDeferMinK = 3072;             // default: deferred epilogue from this mean tile K
-constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;   // 4 s
+constexpr unsigned long long kDefaultWaitNs = 4000000000ull;   // 4 s: limit of a device-side wait
 
 enum ChainKind : int { CHAIN_FERMI = 0, CHAIN_ENTROPY = 1 };
 
@@ -236,6 +236,15 @@ struct LayerArgs {
     int chunk_tail, tail_from;
     uint8_t* opw_alt[kMaxChains];
     int* done;
+    // Time limit of one device-side wait (ns; ftsp2_set_wait_limit_ns).  A
+    // dependency wait that runs out records FTSP2_E_TIMEOUT and the launch
+    // finishes its work list in skip mode; a pipeline wait records it after
+    // wait_ns and gives up after 2 wait_ns.
+    unsigned long long wait_ns;
+    // Test hook (ftsp2_debug_stall_layer): items of this global layer wait for
+    // one completion more than their predecessor layer can give, so that the
+    // dependency wait runs out; -1 in normal operation.
+    int stall_layer;
 };
 
 struct TmaMaps {
@@ -342,26 +351,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
-}
-
-// Wait on an mbarrier phase with a time limit.  On timeout the CTA-wide abort
-// flag and the global status word are set and false is returned; every role
-// then leaves its loop.  Also returns false when another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* gstatus) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 0) {
-            if (*abort_flag) return false;
-            if (globaltimer() - t0 > kWaitTimeoutNs) {
-                *abort_flag = 1;
-                atomicExch(gstatus, (int)FTSP2_E_TIMEOUT);
-                return false;
-            }
-        }
-    }
 }
 
 }  // namespace ftsp2

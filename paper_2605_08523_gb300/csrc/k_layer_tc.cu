@@ -67,8 +67,15 @@
 // proxy fence before the TMA loads of the new operands.  Dependencies point
 // only to earlier items and a unit takes its items in order, so the waits end;
 // the CTAs of such a launch are co-resident (cooperative launch).
-// Every wait is bounded: on timeout the CTA sets FTSP2_E_TIMEOUT in the status
-// word and all roles leave their loops.
+// Every wait is bounded (a.wait_ns).  A dependency wait that runs out records
+// FTSP2_E_TIMEOUT in the status word of the call; from then on every role of
+// every CTA that sees the failure runs the rest of its work items in skip
+// mode: the same barrier arrivals, waits and commits in the same order, but no
+// TMA loads, MMAs or epilogue stores.  Every barrier phase therefore still
+// completes and nothing is in flight when the work list ends; the MMA issuer
+// also waits for a last commit of its own before the CTAs free TMEM.  A
+// pipeline wait that runs out twice (a broken protocol, not expected) leaves
+// its loop after a bounded grace period for the copies in flight.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -210,18 +217,32 @@ __device__ __forceinline__ bool try_wait_cluster(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* gstatus) {
+// Has the call failed (a wait ran out in this or another CTA)?
+__device__ __forceinline__ bool call_failed(const LayerArgs& a) {
+    return *reinterpret_cast<volatile int*>(a.status) != 0;
+}
+__device__ __forceinline__ void record_timeout(const LayerArgs& a) { atomicCAS(a.status, 0, (int)FTSP2_E_TIMEOUT); }
+
+// Wait on a pipeline mbarrier phase.  A failure elsewhere never ends such a
+// wait: after a failure every role keeps the barrier protocol of its work list
+// (arrivals and commits in the usual order, without loads, MMAs or stores), so
+// every phase still completes.  The wait gives up only on its own clock: after
+// a.wait_ns it records FTSP2_E_TIMEOUT (the call has failed), and after twice
+// that it returns false, which only a broken protocol can cause; the caller
+// then leaves its loop and the kernel drains before it frees TMEM.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, const LayerArgs& a) {
     if (try_wait_cluster(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
+    bool recorded = false;
     for (uint32_t it = 1;; ++it) {
         if (try_wait_cluster(bar, parity)) return true;
         if ((it & 63u) == 0) {
-            if (*abort_flag) return false;
-            if (globaltimer() - t0 > kWaitTimeoutNs) {
-                *abort_flag = 1;
-                atomicExch(gstatus, (int)FTSP2_E_TIMEOUT);
-                return false;
+            const unsigned long long dt = globaltimer() - t0;
+            if (!recorded && dt > a.wait_ns) {
+                record_timeout(a);
+                recorded = true;
             }
+            if (dt > 2 * a.wait_ns) return false;
         }
     }
 }
@@ -261,6 +282,12 @@ __device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
         "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
         "h"(mask)
         : "memory");
+}
+
+// arrive on this CTA's barrier only, when all previously issued MMAs of this
+// thread (on both CTAs of the pair) have completed
+__device__ __forceinline__ void umma_commit_local_pair(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 // 32 lanes x 16 columns of FP32 from TMEM into registers (no wait)
@@ -360,7 +387,9 @@ struct OpFmtT<OP_TF32X3> {
         uint32_t hb;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(z));
         o[0] = hb;
-        o[1] = __float_as_uint(z - __uint_as_float(hb));
+        // the tensor core reads only the TF32 bits of the low part: round it
+        // to TF32 (unbiased) instead of letting the low 13 bits be cut
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(o[1]) : "f"(z - __uint_as_float(hb)));
     }
 };
 template <>
@@ -674,23 +703,19 @@ __device__ __forceinline__ int done_acquire(const LayerArgs& a, int g, int chain
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(a.done + g * kMaxChains + chain) : "memory");
     return v;
 }
-// Wait, with the barrier waits' time limit, until layer g of `chain` is
-// complete; false on timeout (abort flag and status set) or when another role
-// or CTA has failed.
-__device__ __forceinline__ bool wait_layer_done(const LayerArgs& a, int g, int chain, int target,
-                                                volatile int* abort_flag) {
+// Wait until layer g of `chain` is complete.  False when the call has failed
+// (this wait ran out after a.wait_ns, which records FTSP2_E_TIMEOUT, or another
+// wait of this launch did): the producer then runs its remaining items in skip
+// mode, without loads.
+__device__ __forceinline__ bool wait_layer_done(const LayerArgs& a, int g, int chain, int target) {
     if (done_acquire(a, g, chain) >= target) return true;
     const unsigned long long t0 = globaltimer();
     for (;;) {
         __nanosleep(256);
         if (done_acquire(a, g, chain) >= target) return true;
-        if (*abort_flag || *reinterpret_cast<volatile int*>(a.status) != 0) {
-            *abort_flag = 1;
-            return false;
-        }
-        if (globaltimer() - t0 > kWaitTimeoutNs) {
-            *abort_flag = 1;
-            atomicExch(a.status, (int)FTSP2_E_TIMEOUT);
+        if (call_failed(a)) return false;
+        if (globaltimer() - t0 > a.wait_ns) {
+            record_timeout(a);
             return false;
         }
     }
@@ -755,7 +780,11 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
     __shared__ __align__(8) uint64_t tempty_bar[NBUF];
     // deferred epilogue: scratch full / empty
     __shared__ __align__(8) uint64_t sfull_bar, sempty_bar;
+    // drain: the MMA issuer's last commit (all of its MMAs complete)
+    __shared__ __align__(8) uint64_t drain_bar;
     __shared__ uint32_t tmem_slot;
+    // skip mode: set once this CTA has seen the call fail; the roles then keep
+    // the barrier protocol of their work items without loads, MMAs or stores
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -783,6 +812,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             mbar_init(&sfull_bar, kEpiWarps);
             mbar_init(&sempty_bar, kStoreWarps);
         }
+        mbar_init(&drain_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -813,8 +843,10 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             int stage = 0;
             uint32_t phase = 0;
             int known[kMaxChains] = {a.gl, a.gl};    // layers whose predecessor is known complete
+            bool skip = false;                       // the call has failed: no more loads
+            bool broken = false;                     // a pipeline wait ran out twice
             const int nf = n_items(a);
-            for (int f = unit; f < nf && !abort_flag; f += nunits) {
+            for (int f = unit; f < nf && !broken; f += nunits) {
                 int g, t;
                 item_of(a, f, g, t);
                 const Tile tl = a.tiles[t];
@@ -824,12 +856,19 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                     if (a.nlayers > 1) atomicAdd(a.done + g * kMaxChains + tl.chain, kEpiWarps);
                     continue;
                 }
-                if (g > known[tl.chain]) {
+                // only multi-layer launches wait on other CTAs and can fail
+                if (!skip && a.nlayers > 1 && call_failed(a)) skip = true;
+                if (!skip && g > known[tl.chain]) {
                     // operands and state of this item were written by other CTAs
-                    if (!wait_layer_done(a, g - 1, tl.chain, done_target, &abort_flag)) break;
-                    known[tl.chain] = g;
-                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    const int target = done_target + (g == a.stall_layer ? 1 : 0);
+                    if (wait_layer_done(a, g - 1, tl.chain, target)) {
+                        known[tl.chain] = g;
+                        asm volatile("fence.proxy.async.global;" ::: "memory");
+                    } else {
+                        skip = true;
+                    }
                 }
+                if (skip) *reinterpret_cast<volatile int*>(&abort_flag) = 1;
                 const TmaMaps& maps = ((g - a.gl) & 1) ? maps1 : maps0;
                 const int n = a.inst[tl.inst].n;
                 const int nk = (n + BKE - 1) / BKE;
@@ -837,55 +876,65 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                 const int rowB = tl.inst * a.P + tl.J * TILE + (int)rank * kCtaRows;
                 // transposed panels: MN index (column of the stored upper block)
                 const int mnA = tl.I * TILE + (int)rank * kCtaRows, mnB = tl.J * TILE + (int)rank * kCtaRows;
-                bool ok = true;
                 for (int kb = 0; kb < nk; ++kb) {
                     // K-slices left of a panel's diagonal block: not stored below
                     // the diagonal, loaded from the transposed upper block
                     const bool lowA = !C::TF32 && a.lower_t && kb * BKE + BKE <= tl.I * TILE;
                     const bool lowB = !C::TF32 && a.lower_t && kb * BKE + BKE <= tl.J * TILE;
                     const int krow = tl.inst * a.P + kb * BKE;
-                    if (!wait_bar(&empty_bar[stage], phase ^ 1u, &abort_flag, a.status)) {
-                        ok = false;
+                    if (!wait_bar(&empty_bar[stage], phase ^ 1u, a)) {
+                        broken = true;
                         break;
                     }
-                    if (kb == max(0, nk - 3)) prefetch_tile_state<TILE>(a, tl, (int)rank * kCtaRows, n);
                     uint8_t* sbase = smem + stage * STAGE_BYTES;
                     if constexpr (PAIR) {
                         const uint32_t fb = map_to(smem_u32(&full_bar[stage]), 0);
-                        remote_expect_tx(fb, STAGE_BYTES);
+                        if (skip) {
+                            // the stage's arrival without data: the phase completes
+                            // with the peer's loads (if any) and no MMA reads it
+                            remote_arrive(fb);
+                        } else {
+                            if (kb == max(0, nk - 3)) prefetch_tile_state<TILE>(a, tl, (int)rank * kCtaRows, n);
+                            remote_expect_tx(fb, STAGE_BYTES);
 #pragma unroll
-                        for (int s = 0; s < C::NSPLIT; ++s) {
-                            const uint32_t dA = smem_u32(sbase + s * PLANE), dB = smem_u32(sbase + (C::NSPLIT + s) * PLANE);
-                            if (lowA) {
-                                tma_load_pair(dA, &maps.t[tl.chain][s], fb, mnA, krow);
-                                tma_load_pair(dA + PLANE / 2, &maps.t[tl.chain][s], fb, mnA + 64, krow);
-                            } else {
-                                tma_load_pair(dA, &maps.a[tl.chain][s], fb, kb * BKE, rowA);
-                            }
-                            if (lowB) {
-                                tma_load_pair(dB, &maps.t[tl.chain][s], fb, mnB, krow);
-                                tma_load_pair(dB + PLANE / 2, &maps.t[tl.chain][s], fb, mnB + 64, krow);
-                            } else {
-                                tma_load_pair(dB, &maps.a[tl.chain][s], fb, kb * BKE, rowB);
+                            for (int s = 0; s < C::NSPLIT; ++s) {
+                                const uint32_t dA = smem_u32(sbase + s * PLANE), dB = smem_u32(sbase + (C::NSPLIT + s) * PLANE);
+                                if (lowA) {
+                                    tma_load_pair(dA, &maps.t[tl.chain][s], fb, mnA, krow);
+                                    tma_load_pair(dA + PLANE / 2, &maps.t[tl.chain][s], fb, mnA + 64, krow);
+                                } else {
+                                    tma_load_pair(dA, &maps.a[tl.chain][s], fb, kb * BKE, rowA);
+                                }
+                                if (lowB) {
+                                    tma_load_pair(dB, &maps.t[tl.chain][s], fb, mnB, krow);
+                                    tma_load_pair(dB + PLANE / 2, &maps.t[tl.chain][s], fb, mnB + 64, krow);
+                                } else {
+                                    tma_load_pair(dB, &maps.a[tl.chain][s], fb, kb * BKE, rowB);
+                                }
                             }
                         }
                     } else {
                         const uint32_t fb = smem_u32(&full_bar[stage]);
-                        local_expect_tx(fb, STAGE_BYTES);
+                        if (skip) {
+                            local_arrive(fb);
+                        } else {
+                            if (kb == max(0, nk - 3)) prefetch_tile_state<TILE>(a, tl, (int)rank * kCtaRows, n);
+                            local_expect_tx(fb, STAGE_BYTES);
 #pragma unroll
-                        for (int s = 0; s < C::NSPLIT; ++s) {
-                            const uint32_t dA = smem_u32(sbase + s * PLANE), dB = smem_u32(sbase + (C::NSPLIT + s) * PLANE);
-                            if (lowA) {
-                                tma_load_one(dA, &maps.t[tl.chain][s], fb, mnA, krow);
-                                tma_load_one(dA + PLANE / 2, &maps.t[tl.chain][s], fb, mnA + 64, krow);
-                            } else {
-                                tma_load_one(dA, &maps.a[tl.chain][s], fb, kb * BKE, rowA);
-                            }
-                            if (lowB) {
-                                tma_load_one(dB, &maps.t[tl.chain][s], fb, mnB, krow);
-                                tma_load_one(dB + PLANE / 2, &maps.t[tl.chain][s], fb, mnB + 64, krow);
-                            } else {
-                                tma_load_one(dB, &maps.a[tl.chain][s], fb, kb * BKE, rowB);
+                            for (int s = 0; s < C::NSPLIT; ++s) {
+                                const uint32_t dA = smem_u32(sbase + s * PLANE), dB = smem_u32(sbase + (C::NSPLIT + s) * PLANE);
+                                if (lowA) {
+                                    tma_load_one(dA, &maps.t[tl.chain][s], fb, mnA, krow);
+                                    tma_load_one(dA + PLANE / 2, &maps.t[tl.chain][s], fb, mnA + 64, krow);
+                                } else {
+                                    tma_load_one(dA, &maps.a[tl.chain][s], fb, kb * BKE, rowA);
+                                }
+                                if (lowB) {
+                                    tma_load_one(dB, &maps.t[tl.chain][s], fb, mnB, krow);
+                                    tma_load_one(dB + PLANE / 2, &maps.t[tl.chain][s], fb, mnB + 64, krow);
+                                } else {
+                                    tma_load_one(dB, &maps.a[tl.chain][s], fb, kb * BKE, rowB);
+                                }
                             }
                         }
                     }
@@ -894,7 +943,15 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                         phase ^= 1u;
                     }
                 }
-                if (!ok) break;
+            }
+            if (broken) {
+                // The barrier protocol failed, so the completion of the loads
+                // already issued cannot be observed: give them a bounded grace
+                // period (a load of one stage takes microseconds) before the
+                // CTA releases its shared memory.
+                *reinterpret_cast<volatile int*>(&abort_flag) = 1;
+                const unsigned long long t0 = globaltimer();
+                while (globaltimer() - t0 < 2000000ull) __nanosleep(1000);
             }
         }
         __syncwarp();
@@ -911,7 +968,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             const uint64_t desc0 = sdesc_sw128(smem_u32(smem));
             const uint64_t descT = sdesc_mn_sw128(smem_u32(smem));   // transposed panels
             const int nf = n_items(a);
-            for (int f = unit; f < nf && ok && !abort_flag; f += nunits) {
+            for (int f = unit; f < nf && ok; f += nunits) {
                 int g, t;
                 item_of(a, f, g, t);
                 const Tile tl = a.tiles[t];
@@ -921,7 +978,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                 const int nk = (n + BKE - 1) / BKE;
                 const int ck = ck_of(g);
                 for (int kc = 0; kc < nk && ok; kc += ck) {
-                    if (!wait_bar(&tempty_bar[buf], aphase ^ 1u, &abort_flag, a.status)) {
+                    if (!wait_bar(&tempty_bar[buf], aphase ^ 1u, a)) {
                         ok = false;
                         break;
                     }
@@ -929,11 +986,14 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                     const uint32_t dt = tmem + (uint32_t)(buf * TILE);
                     const int kend = min(nk, kc + ck);
                     for (int kb = kc; kb < kend; ++kb) {
-                        if (!wait_bar(&full_bar[stage], phase, &abort_flag, a.status)) {
+                        if (!wait_bar(&full_bar[stage], phase, a)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
+                        // skip mode: the stage holds no new data; the commits below
+                        // keep the protocol
+                        const bool mma = *reinterpret_cast<volatile int*>(&abort_flag) == 0;
                         const uint64_t ds = desc0 + (uint64_t)((stage * STAGE_BYTES) >> 4);
                         const uint64_t dsT = descT + (uint64_t)((stage * STAGE_BYTES) >> 4);
                         const uint32_t first = kb == kc ? 0u : 1u;
@@ -954,7 +1014,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                         for (int q = 0; q < C::NPROD; ++q) {
                             const int p = C::NPROD - 1 - q;
 #pragma unroll
-                            for (int kk = 0; kk < KSTEPS; ++kk) {
+                            for (int kk = 0; kk < KSTEPS && mma; ++kk) {
                                 const uint64_t da = baseA + (uint64_t)((prod_a(p) * PLANE + kk * stepA) >> 4);
                                 const uint64_t db = baseB + (uint64_t)(((C::NSPLIT + prod_b(p)) * PLANE + kk * stepB) >> 4);
                                 if constexpr (PAIR)
@@ -978,6 +1038,15 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                         aphase ^= 1u;
                     }
                 }
+            }
+            // Drain: every MMA this thread issued (they write TMEM of both CTAs
+            // of a pair and read both CTAs' stages) has completed before the
+            // final barrier, after which the CTAs free TMEM and shared memory.
+            if constexpr (PAIR) umma_commit_local_pair(smem_u32(&drain_bar));
+            else umma_commit_one(smem_u32(&drain_bar));
+            if (!wait_bar(&drain_bar, 0, a)) {
+                const unsigned long long t0 = globaltimer();
+                while (globaltimer() - t0 < 2000000ull) __nanosleep(1000);
             }
         }
         __syncwarp();
@@ -1003,11 +1072,14 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             int k;
             if (!tile_active_g(a, tl, g, k)) continue;
             if (!has_next_tile(a, f, nunits)) continue;     // inline in the accumulating warps
-            if (!wait_bar(&sfull_bar, sp, &abort_flag, a.status)) {
+            if (!wait_bar(&sfull_bar, sp, a)) {
                 ok = false;
                 break;
             }
             sp ^= 1u;
+            // skip mode (warp-uniform): hand the scratch back without the work
+            const bool work = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&abort_flag) == 0 ? 1 : 0, 0) != 0;
+            if (work) {
             if (a.nlayers > 1 && g > a.gl) {
                 // the state of layer g - 1, written by other CTAs
                 if (lane == 0) done_acquire(a, g - 1, tl.chain);
@@ -1062,7 +1134,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                     more = next_entry<TILE, EPI_COLS>(tl, (int)rank, n, ii, gi);
                 }
             }
-            if (!ok) break;
+            }
             __syncwarp();
             if (lane == 0) {
                 // this warp's share of the tile's kEpiWarps completions
@@ -1117,7 +1189,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             // tile meanwhile fill the other buffers.
             const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cq * EPI_COLS);
             for (int j = 0; j < nch; ++j) {
-                if (!wait_bar(&tfull_bar[buf], aphase, &abort_flag, a.status)) {
+                if (!wait_bar(&tfull_bar[buf], aphase, a)) {
                     ok = false;
                     break;
                 }
@@ -1153,12 +1225,14 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
                 }
             }
             if (!ok) break;
+            // skip mode (warp-uniform): the protocol without the memory work
+            const bool work = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&abort_flag) == 0 ? 1 : 0, 0) != 0;
             if (defer_tile) {
                 // hand the finished sums to the store warps through the scratch
                 // (its previous tile must have been read), then go on to the next tile
-                if (!wait_bar(&sempty_bar, sp ^ 1u, &abort_flag, a.status)) break;
+                if (!wait_bar(&sempty_bar, sp ^ 1u, a)) break;
                 sp ^= 1u;
-                if (warp_live) {
+                if (warp_live && work) {
                     float* const dst = a.escr + (size_t)blockIdx.x * kEpiScratchFloats + (warp - 2) * kItemFloats + lane * 4;
 #pragma unroll
                     for (int g = 0; g < EPI_COLS / 8; ++g) store_state8(dst + 256 * g, &acc[8 * g]);
@@ -1182,7 +1256,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             const int C0 = tl.J * TILE + cq * EPI_COLS;                   // first column of this warp
             double tr = 0.0, sq = 0.0;
             float sq_lo = 0.f;
-            if (warp_live) {
+            if (warp_live && work) {
                 if constexpr (OUTFMT == kLastLayer) {
                     EpiCtx e;
                     make_ctx(a, tl, k, e, MODE == FTSP2_FP16X2);

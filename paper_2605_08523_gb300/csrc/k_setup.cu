@@ -349,7 +349,9 @@ __device__ __forceinline__ void write_operand16_t(uint8_t* base, size_t plane_el
                 uint32_t hb;
                 asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
                 o[0] = hb;
-                o[1] = __float_as_uint(v - __uint_as_float(hb));
+                // the tensor core reads only the TF32 bits of the low part:
+                // round it to TF32 here (unbiased) instead of letting them be cut
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(o[1]) : "f"(v - __uint_as_float(hb)));
             } else {
                 o[0] = __float_as_uint(v);
             }

@@ -149,3 +149,21 @@ def test_model_set_arguments_checked_on_the_host(built):
     assert create(0, 0) == E_ARG
     assert create(16, 1, beta0=-1.0) == E_ARG
     assert create(16, 0, mu0=1.0) == E_ARG
+
+
+def test_wait_limit_arguments(built):
+    # host-side checks only: the limit is a process-wide setting read at each call
+    default = built.wait_limit_ns()
+    assert default == 4_000_000_000
+    with pytest.raises(built.Ftsp2Error):
+        built.set_wait_limit_ns(10)
+    with pytest.raises(built.Ftsp2Error):
+        built.set_wait_limit_ns(10 ** 11)
+    built.set_wait_limit_ns(1_000_000)
+    assert built.wait_limit_ns() == 1_000_000
+    built.set_wait_limit_ns(default)
+    with pytest.raises(built.Ftsp2Error):
+        built.debug_stall_layer(-2)
+    with pytest.raises(built.Ftsp2Error):
+        built.debug_stall_layer(64)
+    built.debug_stall_layer(-1)
