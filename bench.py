@@ -1,21 +1,32 @@
 """Benchmark of the MLSP2 hot path (density matrix + entropy) on GB300.
 
-Workload (the headline configuration): one dense symmetric H, n = 4096, 3D
-cubic tight-binding lattice 16 x 16 x 16 with open boundaries, on-site
-U(-1, 1) eV, hopping -1 eV, plus symmetrised 0.01 N(0, 1) dense noise;
-kT = 0.1 eV, mu at half filling; the paper's 26-layer table (beta0 = 1500,
-mu0 = 1/3) for the density and the entropy table trained for it by the
-library's GPU trainer; density and entropy chains; FP16x2 split-precision
-tensor-core layers with FP32 accumulation.
+Default workload (the largest single-GPU configuration): one dense symmetric H,
+n = 8192, open 3D cubic tight-binding lattice 16 x 16 x 32 (on-site U(-1, 1)
+eV, hopping -1 eV, symmetrised 0.01 N(0, 1) dense noise) with 5 % of the
+off-diagonal pairs given long-range couplings N(0, 0.05) eV; kT = 0.1 eV, mu
+at half filling; Gershgorin bounds; model set = the paper's printed 26-layer
+table (beta0 = 1500, with the entropy table the library's trainer fitted for
+it) and the library-trained 34-layer beta0 = 3000 table, which the Gershgorin
+width of this matrix selects; FP16X2 split-precision tensor-core layers with
+FP32 accumulation, the last two layers as FP32-class refinement layers
+(BF16X3 products on the tensor cores); density and entropy chains.
 
 A step is one pass of the whole hot path (Gershgorin bounds, rescale, both
-26-layer recursions, traces, entropy) over the resident input.  Inputs and
-the per-step working set (~0.7 GB) are larger than the 129 MB L2, so no
-explicit flush is needed between steps.
+recursions, traces, entropy) over the resident input.  Inputs and the per-step
+working set (several GB) are larger than the 129 MB L2, so no explicit flush is
+needed between steps.
+
+Other workloads (--workload): ``lattice`` (one n = 1024 / 2048 / 4096 lattice
+without the long-range couplings) and ``ragged`` (512 rotated-spectrum
+Hamiltonians, n ~ U{64..768}, one grouped launch per layer for all instances,
+timed as CUDA-graph replays; under torchrun the batch is split across ranks in
+shares of equal sum n^3).  The default run also measures the ragged batch and
+the n = 4096 lattice as secondary results in the same JSON line.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun each rank runs an independent replica (the path has no
-exchange step); value = solves of all ranks / max wall time over ranks.
+Under torchrun each rank runs an independent replica of a single-matrix
+workload (the path has no exchange step); value = solves of all ranks / max
+time over ranks.
 """
 from __future__ import annotations
 
@@ -34,29 +45,40 @@ sys.path.insert(0, ROOT)
 
 METRIC = "density-matrix solves/s and TFLOP/s vs plain FP32 recursion at <=1e-6 error"
 LN2 = math.log(2.0)
+TABLE_DIR = os.path.join(ROOT, "paper_2605_08523_gb300", "tables")
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--dims", default="16,16,16")
+    p.add_argument("--workload", default="longrange", choices=["longrange", "lattice", "ragged"],
+                   help="longrange: n = 8192 lattice with 5%% long-range couplings, two refinement layers "
+                        "(default); lattice: one lattice of --dims; ragged: the 512-instance ragged batch")
+    p.add_argument("--dims", default="16,16,16", help="lattice workload: lattice dimensions")
     p.add_argument("--kT", type=float, default=0.1)
     p.add_argument("--mode", default="fp16x2")
     p.add_argument("--no-baselines", action="store_true")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="skip the secondary measurements (ragged batch, n = 4096 lattice) of the default run")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--mu", type=float, default=None,
                    help="skip the GPU eigendecomposition and use this mu (profiling runs)")
     p.add_argument("--shape", default="auto", choices=["auto", "pair", "single"],
                    help="tensor-core tile shape: auto = the library's autotuner (untimed), or forced")
-    p.add_argument("--bounds", default="gershgorin", choices=["gershgorin", "lanczos"],
-                   help="spectral bounds: Gershgorin (Appendix A) or tightened by Lanczos (FTSP2_LANCZOS)")
-    p.add_argument("--policy", default="beta0", choices=["beta0", "layers"],
-                   help="model choice: smallest beta0 (default) or fewest layers (FTSP2_MIN_LAYERS)")
-    p.add_argument("--refine", type=int, default=0, choices=[0, 1, 2],
-                   help="last 0/1/2 layers in FP32 (FTSP2_REFINE1/2); cfg4 defaults to 2")
+    p.add_argument("--bounds", default=None, choices=["gershgorin", "lanczos"],
+                   help="spectral bounds: Gershgorin (Appendix A; single-matrix default) or tightened by Lanczos "
+                        "(FTSP2_LANCZOS; ragged default)")
+    p.add_argument("--policy", default=None, choices=["beta0", "layers"],
+                   help="model choice: smallest beta0 (single-matrix default) or fewest layers "
+                        "(FTSP2_MIN_LAYERS; ragged default)")
+    p.add_argument("--refine", type=int, default=None, choices=[0, 1, 2],
+                   help="last 0/1/2 layers as refinement layers (FTSP2_REFINE1/2); longrange defaults to 2")
+    p.add_argument("--refine-on", default="tc", choices=["tc", "cuda"],
+                   help="refinement layers as BF16X3 tensor-core layers (FTSP2_REFINE_TC, default) or as FP32 "
+                        "FMA on the CUDA cores")
     p.add_argument("--epilogue", default="auto", choices=["auto", "deferred", "inline"],
                    help="final epilogue of the pair tiles: the library's default, or forced "
                         "(FTSP2_EPI_DEFERRED / FTSP2_EPI_INLINE)")
@@ -67,18 +89,12 @@ def parse():
                    help="consecutive main-format layers in one persistent launch when each layer is a few "
                         "waves of tiles (default), or one launch per layer (FTSP2_LAYER_LAUNCHES)")
     p.add_argument("--batch", type=int, default=512,
-                   help="cfg2: number of instances (512; smaller batches for profiling captures)")
+                   help="ragged: number of instances (512; smaller batches for profiling captures)")
     p.add_argument("--table", default="printed", choices=["printed", "alt", "skip"],
-                   help="cfg1/cfg4 Fermi table: the paper's printed 26-layer table (with the trained entropy "
+                   help="lattice Fermi table: the paper's printed 26-layer table (with the trained entropy "
                         "table), the 26-layer beta0 = 1500 table of the one-term form (Eq. mlsp2_alt), or the "
                         "26-layer beta0 = 1500 Skip-SP2 table, both trained by the library")
-    p.add_argument("--refine-tc", action="store_true",
-                   help="refinement layers as BF16X3 tensor-core layers (FTSP2_REFINE_TC)")
-    p.add_argument("--workload", default="cfg1", choices=["cfg1", "cfg2", "cfg4"],
-                   help="cfg1: the headline single n = 4096 matrix; cfg2: the 512-instance ragged batch; "
-                        "cfg4: n = 8192 lattice with 5%% long-range couplings, two FP32 refinement layers "
-                        "(cfg2 and cfg4 are separate lines, not the headline)")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def peaks():
@@ -92,7 +108,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    """nvidia-smi clock/throttle samples every 100 ms while running."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -145,11 +161,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(dims, seed, longrange=False):
+def single_dims_desc(args):
+    """(lattice dimensions, description) of a single-matrix workload."""
+    if args.workload == "longrange":
+        return (16, 16, 32), ("lattice 16x16x32 (n=8192) with 5%% long-range couplings N(0,0.05), kT=%g, mu at "
+                              "half filling, density+entropy" % args.kT)
+    dims = tuple(int(x) for x in args.dims.split(","))
+    return dims, ("lattice %dx%dx%d (n=%d), kT=%g, mu at half filling, density+entropy"
+                  % (dims + (dims[0] * dims[1] * dims[2], args.kT)))
+
+
+def single_workload(args):
+    """(H, dims, description) of a single-matrix workload; rank r uses seed + r."""
     import workloads as wl
-    if longrange:
-        return wl.lattice_3d(dims, seed, longrange_frac=0.05, longrange_sigma=0.05)
-    return wl.lattice_3d(dims, seed)
+    dims, desc = single_dims_desc(args)
+    seed = args.seed + int(os.environ.get("RANK", "0"))
+    if args.workload == "longrange":
+        H = wl.lattice_3d(dims, seed, longrange_frac=0.05, longrange_sigma=0.05)
+    else:
+        H = wl.lattice_3d(dims, seed)
+    return H, dims, desc
 
 
 def fermi_t(t):
@@ -164,11 +195,7 @@ def entropy_t(t):
     return torch.log1p(e) + a * e / (1 + e)
 
 
-def eig_reference_gpu(Hd, kT, n):
-    """FP64 eigendecomposition baseline on the GPU: eps, V; mu at half filling;
-    D_ref = V f V^T, S_ref = sum s(eps)."""
-    import torch
-    eps, V = torch.linalg.eigh(Hd)
+def mu_half_filling(eps, kT, n):
     lo, hi = float(eps[0]) - 1.0, float(eps[-1]) + 1.0
     for _ in range(200):
         mid = 0.5 * (lo + hi)
@@ -176,7 +203,16 @@ def eig_reference_gpu(Hd, kT, n):
             hi = mid
         else:
             lo = mid
-    mu = 0.5 * (lo + hi)
+    return 0.5 * (lo + hi)
+
+
+def eig_reference_gpu(Hd, kT, n, mu=None):
+    """FP64 eigendecomposition baseline on the GPU: eps, V; mu at half filling
+    (unless given); D_ref = V f V^T, S_ref = sum s(eps)."""
+    import torch
+    eps, V = torch.linalg.eigh(Hd)
+    if mu is None:
+        mu = mu_half_filling(eps, kT, n)
     f = fermi_t((eps - mu) / kT)
     D = (V * f[None, :]) @ V.T
     S = float(entropy_t((eps - mu) / kT).sum())
@@ -192,6 +228,7 @@ def method_exact_gpu(eps, V, rec, table, mu):
     mu0, alpha = table["mu0"], table["alpha"]
     # X0 = mu0 I + scale (mu I - H): on the eigenvalues x0 = mu0 + scale (mu - eps)
     x = mu0 + float(rec["scale"]) * (mu - eps)
+
     def chain(x0, th):
         A = torch.zeros_like(x0)
         xx = x0.clone()
@@ -248,9 +285,9 @@ def probe_dtype_peaks():
     return out
 
 
-def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
+def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax, theta_entropy=None):
     """Baseline (i): the plain FP32 recursion of Alg. 2 with torch.matmul
-    (TF32 disabled): X and Y chains with the chosen table's Fermi weights."""
+    (TF32 disabled): X and Y chains with the chosen table's weights."""
     import torch
     n = Hd.shape[0]
     W = emax - emin
@@ -265,11 +302,13 @@ def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
         mup = 1 - mup
     X = ((betap / beta0) * (Hp - mup * I.double()) + mu0 * I.double()).float()
     Y = alpha * X + (1 - alpha) * mu0 * I
+    del Hp
     AD = torch.zeros_like(X)
     AS = torch.zeros_like(X)
     for a, b, c, d in theta:
         AD += d * X
         X = a * (X @ X) + b * X + c * I
+    for a, b, c, d in (theta_entropy if theta_entropy is not None else theta):
         AS += d * Y
         Y = a * (Y @ Y) + b * Y + c * I
     D = AD + X
@@ -280,15 +319,10 @@ def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax):
     return D, S
 
 
-# (mode, n, kernel_sha(): code hash of the layer kernel) -> dram read + write bytes
-# of one layer launch (both chains), from the ncu capture summarised in
-# profiles/layer_tc_fp16x2_n4096.md
-MEASURED_TRAFFIC = {("fp16x2", 4096, "5a532e9ee5962246"): 420.6208e6 + 233.582592e6,
-                    ("fp16x2", 4096, "f28e2970fe6099cb"): 422.81472e6 + 233.330176e6,
-                    ("fp16x2", 4096, "f2da72eea28cec7d"): 341.659136e6 + 217.101312e6,
-                    ("fp16x2", 4096, "35cc88bb61af8eea"): 344.602112e6 + 217.907712e6,
-                    ("fp16x2", 4096, "ab8a7663926c8945"): 343.843328e6 + 218.012672e6,
-                    ("fp16x2", 4096, "ced6ca48c1eace3f"): 342.698752e6 + 217.683968e6}
+# (mode, n, kernel_sha(): code hash of the layer kernel) -> DRAM read + write
+# bytes of one layer launch of both chains, from an ncu capture of that launch
+# (the profile summaries under profiles/ give the command and the figures)
+MEASURED_TRAFFIC = {}
 
 
 def _code_only(src: str) -> str:
@@ -327,230 +361,271 @@ def kernel_sha():
     return h.hexdigest()[:16]
 
 
-def aggregate(t_step_local: float, world: int, device=None):
-    """Whole-job throughput of independent replicas: every rank processed one
-    solve per step, so value = world / (max over ranks of the step time)."""
+def aggregate(t_step_local: float, world: int, units_local: float = 1.0, device=None):
+    """Whole-job throughput: every rank processed ``units_local`` units per
+    step; value = (sum of units over ranks) / (max over ranks of the step time)."""
     import torch
     import torch.distributed as dist
     t = torch.tensor([t_step_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
     tmax = float(t)
-    return world / tmax, tmax
+    return float(u) / tmax, tmax
 
 
-def cuda_time(fn, reps):
+def partition_by_work(ns, world):
+    """Split instances of orders ns across `world` ranks in shares of nearly
+    equal sum n^3 (the layers' work grows with n^3): largest first, each to the
+    currently lightest rank.  Returns one sorted index list per rank."""
+    order = sorted(range(len(ns)), key=lambda b: (-int(ns[b]) ** 3, b))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for b in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(b)
+        load[r] += int(ns[b]) ** 3
+    return [sorted(p) for p in parts]
+
+
+def cuda_time(fn, reps, stream=None):
     import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    e0.record()
+    e0.record(s)
     for _ in range(reps):
         fn()
-    e1.record()
+    e1.record(s)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / 1000.0 / reps
 
 
+# ---------------------------------------------------------------------------
+# configurations shared by both arms
+# ---------------------------------------------------------------------------
+def single_config(args):
+    """The workload description both arms report (inputs only, no results)."""
+    dims, desc = single_dims_desc(args)
+    n = dims[0] * dims[1] * dims[2]
+    longrange = args.workload == "longrange"
+    refine = refine_layers_of(args)
+    return {"workload": desc, "n": n, "kT": args.kT, "mode": args.mode, "chains": 2,
+            "bounds": bounds_of(args), "policy": policy_of(args),
+            "tables": ("printed 26-layer beta0=1500 (+ trained entropy table)" if (longrange or args.table == "printed")
+                       else args.table) + (" and trained 34-layer beta0=3000" if (longrange or args.kT < 0.1) else ""),
+            "refine_layers": refine, "refine_on": args.refine_on if refine else None,
+            "l2": "inputs and working set larger than L2 (no flush)",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+def ragged_config(args):
+    return {"workload": "ragged batch of %d rotated-spectrum Hamiltonians, n~U{64..768}, eigenvalues U(-10,10) eV, "
+                        "mu~U(-5,5), kT~U(0.02,0.5), density+entropy" % args.batch,
+            "instances": args.batch, "mode": args.mode, "chains": 2, "bounds": bounds_of(args),
+            "policy": policy_of(args), "tables": "every shipped Eq. mlsp2 table (beta0 20..24000)",
+            "l2": "inputs and working set larger than L2 (no flush)",
+            "parallelism": "instances split across ranks by sum n^3" if args.gpus > 1 else "single GPU"}
+
+
+def bounds_of(args):
+    if args.bounds:
+        return args.bounds
+    return "lanczos" if args.workload == "ragged" else "gershgorin"
+
+
+def policy_of(args):
+    if args.policy:
+        return args.policy
+    return "layers" if args.workload == "ragged" else "beta0"
+
+
+def refine_layers_of(args):
+    if args.refine is not None:
+        return args.refine
+    return 2 if args.workload == "longrange" else 0
+
+
+def table_paths(args):
+    if args.workload == "ragged":
+        import glob
+        paths = [os.path.join(TABLE_DIR, "entropy_b1500_L26.json")]
+        paths += sorted(glob.glob(os.path.join(TABLE_DIR, "b*_L32.json")))
+        paths += sorted(p for p in glob.glob(os.path.join(TABLE_DIR, "b*.json"))
+                        if int(os.path.basename(p)[1:].split("_")[0]) >= 3000)
+        return paths
+    first = {"alt": "alt_b1500_L26.json", "skip": "skip_b1500_L26.json"}.get(
+        args.table if args.workload == "lattice" else "printed", "entropy_b1500_L26.json")
+    paths = [os.path.join(TABLE_DIR, first)]
+    # the beta0 = 3000 table serves the cases whose Gershgorin width puts
+    # beta' beyond the printed table's region (the long-range couplings, and
+    # kT = 0.05 on the n = 4096 lattice)
+    if args.workload == "longrange" or args.kT < 0.1:
+        paths.append(os.path.join(TABLE_DIR, "b3000_L34.json"))
+    return paths
+
+
+def flags_of(args, ft):
+    f = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
+    f |= {"auto": 0, "deferred": ft.EPI_DEFERRED, "inline": ft.EPI_INLINE}[args.epilogue]
+    f |= ft.FULL_OPERANDS if args.operands == "full" else 0
+    f |= ft.LAYER_LAUNCHES if args.launch == "layer" else 0
+    r = refine_layers_of(args)
+    f |= {0: 0, 1: ft.REFINE1, 2: ft.REFINE2}[r]
+    if r and args.refine_on == "tc":
+        f |= ft.REFINE_TC
+    if bounds_of(args) == "lanczos":
+        f |= ft.LANCZOS
+    if policy_of(args) == "layers":
+        f |= ft.MIN_LAYERS
+    return f
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def oracle_sample(args):
+    """(callable timing one step, full-workload units per step, description):
+    a bounded sample of the workload for the oracle on the host cores."""
+    import numpy as np
+    import workloads as wl
+    from oracle import fermi
+    if args.workload == "ragged":
+        batch = wl.ragged_batch(args.batch, args.seed)
+        ns = np.array([b["n"] for b in batch], dtype=np.float64)
+        # every 16th instance in order of size: the sample spans the size range
+        pick = list(np.argsort(ns)[::16])
+        frac = float(np.sum(ns[pick] ** 3) / np.sum(ns ** 3))
+
+        def step():
+            for b in pick:
+                fermi.eig_reference(batch[b]["H"], batch[b]["mu"], batch[b]["kT"])
+        return step, frac * len(batch), ("oracle.fermi.eig_reference (numpy eigh + V f V^T + S) on %d of the %d "
+                                         "instances (every 16th by size, %.3f of the batch's sum n^3); value "
+                                         "scaled to instances/s of the whole batch by sum n^3" % (len(pick), len(batch), frac))
+    if args.workload == "longrange":
+        dims = (16, 16, 16)
+        H = wl.lattice_3d(dims, args.seed, longrange_frac=0.05, longrange_sigma=0.05)
+        n_full = 8192
+    else:
+        dims = tuple(int(x) for x in args.dims.split(","))
+        H = wl.lattice_3d(dims, args.seed)
+        n_full = dims[0] * dims[1] * dims[2]
+    n = H.shape[0]
+    eps = np.linalg.eigvalsh(H)
+    mu = fermi.mu_at_filling(eps, args.kT, n / 2)
+
+    def step():
+        fermi.eig_reference(H, mu, args.kT)
+    frac = (n / n_full) ** 3
+    what = ("the full n=%d matrix" % n if n == n_full else
+            "the %dx%dx%d member (n=%d) of the same family, %.3f of the n=%d solve's n^3 work; value scaled "
+            "to n=%d solves/s by n^3" % (dims + (n, frac, n_full, n_full)))
+    return step, frac, "oracle.fermi.eig_reference (numpy eigh + V f V^T + S) on " + what
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle (eigendecomposition definition of D and S)
-    timed on the host cores, on a bounded sample of the workload."""
-    import numpy as np
-    from oracle import fermi
+    timed on the host cores; each step is the bounded sample of oracle_sample,
+    and the value is in units of the full workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    dims = tuple(int(x) for x in args.dims.split(","))
-    n = dims[0] * dims[1] * dims[2]
-    sdims = (dims[0] // 2, dims[1], dims[2]) if n > 2048 else dims
-    ns = sdims[0] * sdims[1] * sdims[2]
-    H = make_workload(sdims, args.seed)
-    eps = np.linalg.eigvalsh(H)
-    mu = fermi.mu_at_filling(eps, args.kT, ns / 2)
-    for _ in range(min(args.warmup, 1)):
-        fermi.eig_reference(H, mu, args.kT)
+    step, units, sample = oracle_sample(args)
+    for _ in range(args.warmup):
+        step()
     ts = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        fermi.eig_reference(H, mu, args.kT)
+        step()
+        ts.append(time.perf_counter() - t0)
+    t = sum(ts) / len(ts)
+    value = units / t
+    cores = os.cpu_count()
+    cfg = ragged_config(args) if args.workload == "ragged" else single_config(args)
+    unit = "instances/s" if args.workload == "ragged" else "solves/s"
+    line = {"impl": "reference", "metric": METRIC if args.workload != "ragged" else
+            "ragged-batch instances/s (density + entropy) at <=1e-6 error",
+            "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1000.0, "units_per_step": units, "higher_is_better": True,
+            "scaling": "strong" if args.workload == "ragged" else "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args, reps=3):
+    """The oracle on the host cores (rank 0, N = 1): the reference arm's
+    bounded sample, median of `reps` steps."""
+    step, units, sample = oracle_sample(args)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        step()
         ts.append(time.perf_counter() - t0)
     t = statistics.median(ts)
-    scale = (ns / n) ** 3
-    value = scale / t
-    cores = os.cpu_count()
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1000 / scale,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "cfg1 lattice %dx%dx%d n=%d kT=%g mu=half filling" % (dims + (n, args.kT)),
-                       "n": n, "kT": args.kT},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": "oracle.fermi.eig_reference (numpy eigh + V f V^T + S) on the "
-                                       "%dx%dx%d lattice (n=%d) of the same family, scaled to n=%d by n^3"
-                                       % (sdims + (ns, n))},
-            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    return {"value": units / t, "unit": "instances/s" if args.workload == "ragged" else "solves/s",
+            "cores": os.cpu_count(), "kind": "oracle", "sample": sample + "; median of %d steps (%.1f s each)"
+            % (reps, t)}
 
 
-def cpu_baseline(H, mu, kT, n):
-    """The oracle (eigendecomposition definition) timed once on the host cores."""
-    from oracle import fermi
-    t0 = time.perf_counter()
-    fermi.eig_reference(H, mu, kT)
-    t = time.perf_counter() - t0
-    return {"value": 1.0 / t, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one oracle.fermi.eig_reference solve (numpy eigh + V f V^T + S) of the full n=%d H "
-                      "(%.1f s)" % (n, t)}
+# ---------------------------------------------------------------------------
+# our arm: one matrix per rank
+# ---------------------------------------------------------------------------
+def hw_flops_per_solve(n, T, L, R, mode, refine_tc, chains=2):
+    """(tensor MMA flops a solve issues, tensor-core layers): upper-triangle
+    tiles of side T, each T x T x n per product; 3 products per FP16X2 / TF32X3
+    layer, 6 per BF16X3 layer; refinement layers on the tensor cores are BF16X3
+    (in BF16X3 mode they are ordinary layers), on the CUDA cores they issue no
+    MMAs."""
+    if mode == "fp32":
+        return 0.0, 0
+    nt = math.ceil(n / T)
+    per_product = 2.0 * (nt * (nt + 1) // 2) * T * T * n * chains
+    nprod = {"fp16x2": 3, "tf32x3": 3, "bf16x3": 6}[mode]
+    if refine_tc and mode == "bf16x3":
+        R = 0
+    ref_tc = R if refine_tc else 0
+    return per_product * ((L - R) * nprod + ref_tc * 6), (L - R) + ref_tc
 
 
-def run_cfg2(args):
-    """Ragged batch of --batch (512) rotated-spectrum Hamiltonians (n ~ U{64..768}),
-    one grouped launch per layer for all instances and both chains, model set
-    of every shipped table (smallest valid beta0 per instance)."""
-    import glob
-    import numpy as np
-    import torch
-    import paper_2605_08523_gb300 as ft
-    import workloads as wl
-    from paper_2605_08523_gb300 import build as ftbuild
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    ftbuild.build()
-    tdir = os.path.join(ROOT, "paper_2605_08523_gb300", "tables")
-    paths = [os.path.join(tdir, "entropy_b1500_L26.json")] + sorted(glob.glob(os.path.join(tdir, "b*_L32.json")))
-    paths += sorted(p for p in glob.glob(os.path.join(tdir, "b*.json"))
-                    if int(os.path.basename(p)[1:].split("_")[0]) >= 3000)
-    ms = ft.ModelSet.from_json(paths)
-    batch = wl.ragged_batch(args.batch, args.seed)
-    Hs = [b["H"] for b in batch]
-    ns = [H.shape[0] for H in Hs]
-    flat, _ = wl.pack_batch(Hs)
-    Hd = torch.from_numpy(flat).cuda()
-    shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
-    shape_flag |= {"auto": 0, "deferred": ft.EPI_DEFERRED, "inline": ft.EPI_INLINE}[args.epilogue]
-    shape_flag |= ft.FULL_OPERANDS if args.operands == "full" else 0
-    shape_flag |= ft.LAYER_LAUNCHES if args.launch == "layer" else 0
-    if args.bounds == "lanczos":
-        shape_flag |= ft.LANCZOS
-    if args.policy == "layers":
-        shape_flag |= ft.MIN_LAYERS
-    solver = ft.Solver(ns, [b["mu"] for b in batch], [b["kT"] for b in batch], ms, mode=args.mode, want=3,
-                       flags=shape_flag)
-    if args.shape == "auto":
-        shape, ms_single, ms_pair = solver.autotune(Hd, reps=1)
-    else:
-        shape, ms_single, ms_pair = solver.tile_shape()[0], None, None
-    for _ in range(args.warmup):
-        solver.run(Hd)
-    torch.cuda.synchronize()
-    rec = solver.records()
-    layers = rec["layers"]
-    valid = rec["status"] == 0
-    steps = max(3, args.steps // 10)
-    t = cuda_time(lambda: solver.run(Hd), steps)
-    alg = float(np.sum((np.array(ns, dtype=np.float64) ** 3 * 2 * layers)[valid]))
-    # accuracy on a sample of 32 instances (FP64 eigendecomposition on the GPU)
-    errD, errS = 0.0, 0.0
-    for b in range(0, len(ns), max(1, len(ns) // 32)):
-        n_b = ns[b]
-        Hb = torch.from_numpy(Hs[b]).cuda()
-        eps, V = torch.linalg.eigh(Hb)
-        tt = (eps - batch[b]["mu"]) / batch[b]["kT"]
-        Dref = (V * fermi_t(tt)[None, :]) @ V.T
-        errD = max(errD, float((solver.matrix(b).double() - Dref).abs().max()))
-        errS = max(errS, abs(float(solver.S[b]) - float(entropy_t(tt).sum())) / n_b)
-    line = {"metric": "ragged-batch solves/s (instances/s, density + entropy)", "value": int(valid.sum()) / t,
-            "unit": "solves/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
-            "higher_is_better": True, "dtype": args.mode, "data": "synthetic",
-            "config": {"workload": "cfg2 ragged batch %d x n~U{64..768}, eigenvalues U(-10,10), kT~U(0.02,0.5), "
-                                   "mu~U(-5,5)" % args.batch, "valid_instances": int(valid.sum()),
-                       "sum_n3": float(np.sum(np.array(ns, dtype=np.float64) ** 3)),
-                       "models_used": {int(m): int(np.sum(rec["model"] == m)) for m in np.unique(rec["model"])},
-                       "bounds": args.bounds, "policy": args.policy, "global_layers": int(rec["layers"].max()),
-                       "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
-                   "epilogue": args.epilogue,
-                       "autotune_ms": {"single": ms_single, "pair": ms_pair}},
-            "tflops_alg": alg / t / 1e12,
-            "accuracy_sampled": {"instances": len(range(0, len(ns), max(1, len(ns) // 32))),
-                                 "max_abs_D_minus_Dref": errD, "max_abs_S_minus_Sref_per_n": errS}}
-    print(json.dumps(line), flush=True)
-
-
-def main():
-    args = parse()
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    if args.workload == "cfg2":
-        run_cfg2(args)
-        return
-    import numpy as np
+def run_single(args, ft, world, rank, local, secondary=False):
+    """One single-matrix workload: the timed hot path, its layer roofline,
+    accuracy, end-to-end time through the API with host buffers, baselines.
+    Returns the result dict (the JSON line of the run, or a secondary entry)."""
     import torch
     import torch.distributed as dist
-
-    import paper_2605_08523_gb300 as ft
-    from paper_2605_08523_gb300 import build as ftbuild
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    if rank == 0:
-        ftbuild.build()
-    if world > 1:
-        dist.barrier()
-    ft.lib()
-    cfg4 = args.workload == "cfg4"
-    dims = (16, 16, 32) if cfg4 else tuple(int(x) for x in args.dims.split(","))
-    n = dims[0] * dims[1] * dims[2]
+    H, dims, desc = single_workload(args)
+    n = H.shape[0]
     kT = args.kT
-    H = make_workload(dims, args.seed + rank, longrange=cfg4)
     Hd = torch.from_numpy(H.ravel().copy()).cuda()
     Hm = Hd.view(n, n)
-
-    # mu at half filling from the FP64 GPU eigendecomposition (baseline ii)
     torch.backends.cuda.matmul.allow_tf32 = False
     if args.mu is None:
         mu, Dref, Sref, eps, V = eig_reference_gpu(Hm, kT, n)
     else:
         mu, Dref, Sref, eps, V = args.mu, None, None, None, None
-    # the paper's printed Fermi table with the entropy table the library's
-    # trainer fitted for it (theta_entropy)
-    tdir = os.path.join(ROOT, "paper_2605_08523_gb300", "tables")
-    tabs = [os.path.join(tdir, {"alt": "alt_b1500_L26.json", "skip": "skip_b1500_L26.json"}.get(
-        args.table, "entropy_b1500_L26.json"))]
-    if cfg4:
-        # the long-range couplings widen the Gershgorin interval: beta' needs the
-        # 34-layer beta0 = 3000 table
-        tabs.append(os.path.join(tdir, "b3000_L34.json"))
-    ms = ft.ModelSet.from_json(tabs)
-    shape_flag = {"auto": 0, "pair": ft.PAIR_TILES, "single": ft.SINGLE_TILES}[args.shape]
-    shape_flag |= {"auto": 0, "deferred": ft.EPI_DEFERRED, "inline": ft.EPI_INLINE}[args.epilogue]
-    shape_flag |= ft.FULL_OPERANDS if args.operands == "full" else 0
-    shape_flag |= ft.LAYER_LAUNCHES if args.launch == "layer" else 0
-    refine = 2 if cfg4 and args.refine == 0 else args.refine
-    shape_flag |= {0: 0, 1: ft.REFINE1, 2: ft.REFINE2}[refine]
-    if args.refine_tc:
-        shape_flag |= ft.REFINE_TC
-    if args.bounds == "lanczos":
-        shape_flag |= ft.LANCZOS
-    solver = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3, flags=shape_flag)
+    ms = ft.ModelSet.from_json(table_paths(args))
+    flags = flags_of(args, ft)
+    R = refine_layers_of(args)
+    refine_tc = bool(R) and args.refine_on == "tc"
+    solver = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3, flags=flags)
     if args.shape == "auto":
-        # tile shape: the library's autotuner times both shapes once (untimed)
+        # tile shape: the library's autotuner times both shapes (untimed)
         shape, ms_single, ms_pair = solver.autotune(Hd, reps=2)
     else:
         shape, ms_single, ms_pair = solver.tile_shape()[0], None, None
-    for _ in range(args.warmup):
+    for _ in range(max(3, args.warmup)):
         solver.run(Hd)
     torch.cuda.synchronize()
     rec = solver.records()[0]
     if rec["status"] != 0:
         raise SystemExit("hot path status %d (%s)" % (rec["status"], ft.status_string(int(rec["status"]))))
-
-    # ---- timed region (device-resident inputs) ----
     L = int(rec["layers"])
-    ft.profile_layers(True)
-    ft.profile_read()
+
+    # ---- timed region (device-resident inputs, no instrumentation) ----
     launches0 = ft.kernel_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
@@ -565,26 +640,36 @@ def main():
     if world > 1:
         dist.barrier()
     launches = ft.kernel_launch_count() - launches0
+    value, t_step = aggregate(ev0.elapsed_time(ev1) / 1000.0 / args.steps, world, 1.0, device="cuda")
+
+    # ---- layer times: a second timed pass of the same steps with CUDA events
+    # recorded around every layer-kernel launch on the launching stream ----
+    ft.profile_layers(True)
+    ft.profile_read()
+    for _ in range(args.steps):
+        solver.run(Hd)
+    torch.cuda.synchronize()
     layer_ms, layer_n = ft.profile_read()
     ft.profile_layers(False)
-    value, t_step = aggregate(ev0.elapsed_time(ev1) / 1000.0 / args.steps, world, device="cuda")
-    alg_flops = 2 * L * float(n) ** 3          # L symmetric squares (n^3) per chain, 2 chains
+
     # ---- accuracy of this run's output ----
     D = solver.matrix(0).double()
     S = float(solver.S[0])
     err_D = float((D - Dref).abs().max()) if Dref is not None else None
     err_S = abs(S - Sref) / n if Sref is not None else None
-    trD = float(solver.trace[0, 0])
     err_Drec = err_Srec = None
     if Dref is not None:
-        # the model set's table (one-term tables as their converted rows)
         Drec, Srec = method_exact_gpu(eps, V, rec, ms.tables[int(rec["model"])], mu)
         err_Drec = float((D - Drec).abs().max())
         err_Srec = abs(S - Srec) / n
         del Drec
+    del D
+    if V is not None:
+        del V
+    torch.cuda.empty_cache()
 
-    # density only (no entropy chain): solves/s of the same call with want = 1
-    solver_d = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=1, flags=shape_flag)
+    # ---- density only (no entropy chain) ----
+    solver_d = ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=1, flags=flags)
     solver_d.run(Hd)
     torch.cuda.synchronize()
     t_density = cuda_time(lambda: solver_d.run(Hd), max(3, args.steps // 4))
@@ -600,7 +685,7 @@ def main():
     Sh = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
     Th = [torch.empty(2, dtype=torch.float64).pin_memory() for _ in range(2)]
     Hdev = [torch.empty_like(Hd) for _ in range(2)]
-    solvers = [solver, ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3, flags=shape_flag)]
+    solvers = [solver, ft.Solver([n], [mu], [kT], ms, mode=args.mode, want=3, flags=flags)]
     comp = torch.cuda.current_stream()
     s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
 
@@ -638,109 +723,301 @@ def main():
 
     e2e_run(2)
     assert torch.equal(Dh[0], Dh[1]) and torch.equal(Dh[0], solver.D.cpu()), "end-to-end outputs differ"
-    e2e_steps = max(3, args.steps // 2)
-    t_e2e = e2e_run(e2e_steps)
+    t_e2e = e2e_run(max(3, args.steps // 2))
+    e2e_value, _ = aggregate(t_e2e, world, 1.0, device="cuda")
     h2d = n * n * 8
     d2h = n * n * 4 + 8 + 16
+    del solvers, Hdev
+    torch.cuda.empty_cache()
 
-    # ---- dominant kernel roofline ----
+    # ---- dominant kernel roofline: the tensor-core layer kernel ----
     pk, pk_kind = peaks()
-    # time per layer (both chains): the profiler counts the layers of a
-    # multi-layer launch, so flops per layer / time per layer is the launch's rate
-    layer_avg = layer_ms / max(1, layer_n) / 1000.0
-    alg_per_launch = 2 * float(n) ** 3
+    # mean time of one tensor-core layer: the profiled launches cover every
+    # tensor-core layer of the steps (a multi-layer launch counts its layers)
+    hw_solve, tc_layers = hw_flops_per_solve(n, 256 if shape == 1 else 128, L, R, args.mode, refine_tc)
+    layer_avg = layer_ms / max(1, args.steps * tc_layers) / 1000.0
+    alg_per_launch = 2 * float(n) ** 3          # one layer of both chains: n^3 per chain
     achieved = alg_per_launch / layer_avg / 1e12 if layer_avg > 0 else None
     peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-    # hardware tensor flops actually issued per launch: upper-triangle tiles of
-    # the chosen shape x split products x 2 chains
-    T = 256 if shape == 1 else 128
-    nt = math.ceil(n / T)
-    tiles = nt * (nt + 1) // 2
-    nprod = {"fp16x2": 3, "tf32x3": 3, "bf16x3": 6}.get(args.mode, 1)
-    hw_per_launch = 2 * tiles * T * T * n * 2 * nprod
-    hw_achieved = hw_per_launch / layer_avg / 1e12 if layer_avg > 0 else None
-    # the split modes' own dtypes: fp16 (FP16X2), bf16 (BF16X3), tf32 (TF32X3);
-    # their peak is the measured sustained bf16 figure x the dtype's measured
-    # (else nominal) rate ratio to bf16
+    hw_achieved = hw_solve / (layer_avg * max(1, tc_layers)) / 1e12 if layer_avg > 0 else None
     dt_of_mode = {"fp16x2": "fp16", "bf16x3": "bf16", "tf32x3": "tf32"}.get(args.mode)
-    dtype_rates = probe_dtype_peaks() if (not args.no_baselines and dt_of_mode) else None
+    dtype_rates = probe_dtype_peaks() if (not args.no_baselines and dt_of_mode and not secondary) else None
     if dtype_rates:
         ratio, ratio_kind = dtype_rates[dt_of_mode] / dtype_rates["bf16"], "measured (torch.matmul 8192^3 probe)"
     else:
         ratio, ratio_kind = {"fp16": 1.0, "bf16": 1.0, "tf32": 1.1 / 2.25}.get(dt_of_mode, 1.0), "nominal"
     hw_peak = peak * ratio
-    # DRAM bytes per launch from one ncu capture (profiles/layer_tc_fp16x2_n4096.md),
-    # valid only while the kernel sources are the ones that were profiled
     ksha = kernel_sha()
     traffic = MEASURED_TRAFFIC.get((args.mode, n, ksha))
+    alg_flops = 2 * L * float(n) ** 3           # L symmetric squares (n^3) per chain, 2 chains
 
     result = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1000.0, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp16x2-split/fp32-accum" if args.mode == "fp16x2" else args.mode,
-        "data": "synthetic",
-        "config": {"workload": ("cfg4 lattice %dx%dx%d with 5%% long-range couplings N(0,0.05) n=%d kT=%g "
-                                "mu=half filling, density+entropy, beta0=1500 and 3000 tables" if cfg4 else
-                                "cfg1 lattice %dx%dx%d n=%d kT=%g mu=half filling, density+entropy, "
-                                + {"alt": "26-layer beta0=1500 table of the one-term form (Eq. mlsp2_alt)",
-                                   "skip": "26-layer beta0=1500 Skip-SP2 table (one stored layer, one accumulator)"}
-                                .get(args.table, "printed 26-layer table + trained entropy table"))
-                                % (dims + (n, kT)),
-                   "n": n, "kT": kT, "mu": mu, "layers": L, "mode": args.mode, "chains": 2,
-                   "refine_layers_fp32": refine, "refine_on_tensor_cores": bool(args.refine_tc),
-                   "model": int(rec["model"]), "bounds": args.bounds,
-                   "e_min": float(rec["e_min"]), "e_max": float(rec["e_max"]),
-                   "l2": "inputs and working set larger than L2 (no flush)", "parallelism": "replicas",
-                   "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
-                   "epilogue": args.epilogue, "table": args.table, "operands": args.operands,
-                   "launch": args.launch,
-                   "autotune_ms": {"single": ms_single, "pair": ms_pair}},
+        "data": "synthetic", "config": single_config(args),
+        "details": {"mu": mu, "layers": L, "model": int(rec["model"]), "e_min": float(rec["e_min"]),
+                    "e_max": float(rec["e_max"]), "beta_p": float(rec["beta_p"]),
+                    "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
+                    "epilogue": args.epilogue, "operands": args.operands, "launch": args.launch,
+                    "autotune_ms": {"single": ms_single, "pair": ms_pair}},
         "tflops_alg": alg_flops / t_step / 1e12 * world,
         "density_only": {"value": world / t_density, "unit": "solves/s", "ms_per_step": t_density * 1e3},
         "accuracy": {"max_abs_D_minus_Dref": err_D, "abs_S_minus_Sref_per_n": err_S,
-                     "max_abs_D_minus_Drec": err_Drec, "abs_S_minus_Srec_per_n": err_Srec, "trD": trD,
-                     "trD_ref": n / 2, "S": S, "S_ref": Sref},
+                     "max_abs_D_minus_Drec": err_Drec, "abs_S_minus_Srec_per_n": err_Srec,
+                     "trD": float(solver.trace[0, 0]), "trD_ref": n / 2, "S": S, "S_ref": Sref},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": "layer_tc_kernel<%s>" % args.mode.upper(), "kernel_sha": ksha,
-                     "per_layer_alg_flops": alg_per_launch, "avg_layer_ms": layer_avg * 1000,
-                     "work_unit": "one layer of both chains (CUDA events around each layer-kernel launch; "
-                                  "a multi-layer launch counts its layers)",
+                     "per_launch_alg_flops": alg_per_launch, "avg_layer_ms": layer_avg * 1000,
+                     "work_unit": "one layer of both chains (n^3 flops per chain: the symmetric square); layer "
+                                  "times from a second pass of the same steps with CUDA events around every "
+                                  "layer-kernel launch on the launching stream",
                      "peak_kind": "bf16_tflops_sustained (%s)" % pk_kind,
                      "hw_tensor_tflops": hw_achieved, "hw_frac": (hw_achieved / hw_peak) if hw_achieved else None,
                      "hw_peak": hw_peak, "hw_peak_dtype": dt_of_mode, "hw_peak_ratio_to_bf16": ratio,
                      "hw_peak_ratio_kind": ratio_kind, "dtype_probe_tflops": dtype_rates},
-        "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
-
-    if not args.no_baselines:
-        # baseline (i): plain FP32 recursion with torch.matmul, TF32 off
+    if not args.no_baselines and not secondary and Dref is not None:
+        # baseline (i): plain FP32 recursion with torch.matmul, TF32 off, the
+        # same table; baseline (ii): FP64 eigendecomposition on the GPU
         th_tab, b0_tab, m0_tab, al_tab = ms.table(int(rec["model"]))
-        theta = [tuple(r) for r in th_tab]
+        tab = ms.tables[int(rec["model"])]
+        th_ent = tab.get("theta_entropy")
         emin, emax = float(rec["e_min"]), float(rec["e_max"])
         out = {}
 
         def fp32_step():
-            out["r"] = plain_fp32_recursion(Hm, mu, kT, theta, b0_tab, m0_tab, al_tab, emin, emax)
+            out["r"] = plain_fp32_recursion(Hm, mu, kT, [tuple(r) for r in th_tab], b0_tab, m0_tab, al_tab,
+                                            emin, emax, th_ent)
 
         fp32_step()
         t32 = cuda_time(fp32_step, 2)
         D32, S32 = out["r"]
-        t64 = cuda_time(lambda: eig_reference_gpu(Hm, kT, n), 1)
+        err32 = float((D32.double() - Dref).abs().max())
+        del D32, out
+        torch.cuda.empty_cache()
+        t64 = cuda_time(lambda: eig_reference_gpu(Hm, kT, n, mu), 1)
         result["baselines"] = {
-            "plain_fp32_recursion": {"solves_per_s": 1 / t32, "max_abs_D_minus_Dref": float((D32.double() - Dref).abs().max()),
+            "plain_fp32_recursion": {"solves_per_s": 1 / t32, "max_abs_D_minus_Dref": err32,
                                      "abs_S_minus_Sref_per_n": abs(S32 - Sref) / n,
-                                     "math": "torch.matmul fp32, allow_tf32=False"},
+                                     "math": "torch.matmul fp32, allow_tf32=False, same tables"},
             "fp64_eigh_gpu": {"solves_per_s": 1 / t64, "how": "torch.linalg.eigh float64 + V f V^T + S"},
             "speedup_vs_fp32_recursion": value / world * t32,
             "speedup_vs_fp64_eigh": value / world * t64,
         }
-    if rank == 0 and world == 1 and not args.no_baselines:
-        result["cpu_baseline"] = cpu_baseline(H, mu, kT, n)
+    del Dref
+    torch.cuda.empty_cache()
+    return result
+
+
+# ---------------------------------------------------------------------------
+# our arm: the ragged batch
+# ---------------------------------------------------------------------------
+def run_ragged(args, ft, world, rank, local, secondary=False):
+    """The ragged batch (this rank's share of it, split by sum n^3): one
+    grouped launch per layer for all instances and both chains, recorded into
+    a CUDA graph and timed as graph replays."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import workloads as wl
+    batch = wl.ragged_batch(args.batch, args.seed)
+    mine = partition_by_work([b["n"] for b in batch], world)[rank]
+    sub = [batch[b] for b in mine]
+    Hs = [b["H"] for b in sub]
+    ns = [b["n"] for b in sub]
+    flat, _ = wl.pack_batch(Hs)
+    Hd = torch.from_numpy(flat).cuda()
+    ms = ft.ModelSet.from_json(table_paths(args))
+    flags = flags_of(args, ft)
+    mus, kTs = [b["mu"] for b in sub], [b["kT"] for b in sub]
+    solver = ft.Solver(ns, mus, kTs, ms, mode=args.mode, want=3, flags=flags)
+    if args.shape == "auto":
+        shape, ms_single, ms_pair = solver.autotune(Hd, reps=1)
+    else:
+        shape, ms_single, ms_pair = solver.tile_shape()[0], None, None
+    for _ in range(max(3, args.warmup)):
+        solver.run(Hd)
+    torch.cuda.synchronize()
+    rec = solver.records()
+    valid = rec["status"] == 0
+    c0 = ft.kernel_launch_count()
+    solver.run(Hd)
+    per_run = ft.kernel_launch_count() - c0
+    t_eager = cuda_time(lambda: solver.run(Hd), 3)
+    graph = solver.graph(Hd)
+    for _ in range(max(3, args.warmup)):
+        graph.replay()
+    torch.cuda.synchronize()
+
+    # ---- timed region: graph replays of the whole hot path ----
+    steps = args.steps
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record()
+        for _ in range(steps):
+            graph.replay()
+        ev1.record()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    value, t_step = aggregate(ev0.elapsed_time(ev1) / 1000.0 / steps, world, float(valid.sum()), device="cuda")
+
+    # ---- layer times (second pass, eager, CUDA events around each layer launch) ----
+    ft.profile_layers(True)
+    ft.profile_read()
+    for _ in range(3):
+        solver.run(Hd)
+    torch.cuda.synchronize()
+    layer_ms, layer_n = ft.profile_read()
+    ft.profile_layers(False)
+    layers = rec["layers"]
+    n3 = np.array(ns, dtype=np.float64) ** 3
+    alg = float(np.sum((2.0 * n3 * layers)[valid]))            # both chains, L_b layers each
+    lmax = int(layers.max())
+    # per global layer in which instances are active (launches of layers before
+    # the first active one leave at once)
+    layer_avg = layer_ms / (3 * lmax) / 1000.0
+    achieved = alg / lmax / layer_avg / 1e12 if layer_avg > 0 else None
+    pk, pk_kind = peaks()
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+
+    # ---- accuracy on 32 instances spread over the sizes (the tests check all) ----
+    errD, errS = 0.0, 0.0
+    order = np.argsort(ns)
+    picks = [int(order[i]) for i in np.linspace(0, len(ns) - 1, min(32, len(ns))).astype(int)]
+    for b in picks:
+        if not valid[b]:
+            continue
+        _, Dref, Sref, _, _ = eig_reference_gpu(torch.from_numpy(Hs[b]).cuda(), kTs[b], ns[b], mus[b])
+        errD = max(errD, float((solver.matrix(b).double() - Dref).abs().max()))
+        errS = max(errS, abs(float(solver.S[b]) - Sref) / ns[b])
+
+    # ---- end to end through the API: H from pinned host memory, D, S and the
+    # traces back to pinned host memory, one stream ----
+    Hh = torch.from_numpy(flat).pin_memory()
+    Dh = torch.empty(solver.D.numel(), dtype=torch.float32).pin_memory()
+    Sh = torch.empty(solver.S.numel(), dtype=torch.float64).pin_memory()
+    Th = torch.empty(solver.trace.numel(), dtype=torch.float64).pin_memory()
+    Hdev = torch.empty_like(Hd)
+
+    def e2e_step():
+        Hdev.copy_(Hh, non_blocking=True)
+        solver.run(Hdev)
+        Dh.copy_(solver.D, non_blocking=True)
+        Sh.copy_(solver.S, non_blocking=True)
+        Th.copy_(solver.trace.view(-1), non_blocking=True)
+
+    e2e_step()
+    t_e2e = cuda_time(e2e_step, max(3, steps // 4))
+    e2e_value, _ = aggregate(t_e2e, world, float(valid.sum()), device="cuda")
+
+    result = {
+        "metric": "ragged-batch instances/s (density + entropy) at <=1e-6 error", "value": value,
+        "unit": "instances/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "fp16x2-split/fp32-accum" if args.mode == "fp16x2" else args.mode,
+        "data": "synthetic", "config": ragged_config(args),
+        "details": {"instances_this_rank": len(ns), "valid_instances_this_rank": int(valid.sum()),
+                    "sum_n3_this_rank": float(np.sum(n3)), "global_layers": lmax,
+                    "models_used": {int(m): int(np.sum(rec["model"] == m)) for m in np.unique(rec["model"])},
+                    "tile_shape": {1: "256x256 CTA pairs", 0: "128x128 single CTAs", -1: "none"}[shape],
+                    "autotune_ms": {"single": ms_single, "pair": ms_pair},
+                    "timing": "CUDA-graph replays of one whole solve of the batch",
+                    "eager_ms_per_step": t_eager * 1e3},
+        "tflops_alg": alg / t_step / 1e12,
+        "accuracy_sampled": {"instances": len(picks), "max_abs_D_minus_Dref": errD,
+                             "max_abs_S_minus_Sref_per_n": errS},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": MEASURED_TRAFFIC.get((args.mode, "ragged%d" % args.batch, kernel_sha())),
+                     "kernel": "layer_tc_kernel<%s>" % args.mode.upper(), "avg_layer_ms": layer_avg * 1e3,
+                     "per_launch_alg_flops": alg / lmax, "peak_kind": "bf16_tflops_sustained (%s)" % pk_kind,
+                     "work_unit": "one global layer of every instance and both chains (n_b^3 per chain)"},
+        "e2e": {"value": e2e_value, "unit": "instances/s", "h2d_bytes_per_step": int(flat.nbytes),
+                "d2h_bytes_per_step": int(Dh.numel() * 4 + Sh.numel() * 8 + Th.numel() * 8)},
+        "gpu_launches": per_run * steps,
+        "clocks": clk.summary(),
+    }
+    if not args.no_baselines and not secondary:
+        # baseline (i): the plain FP32 recursion, one instance after the other
+        # (torch.matmul, TF32 off), with each instance's own table and bounds
+        def fp32_all():
+            for b in range(len(ns)):
+                if not valid[b]:
+                    continue
+                tab = ms.tables[int(rec["model"][b])]
+                plain_fp32_recursion(torch.from_numpy(Hs[b]).cuda(), mus[b], kTs[b], [tuple(r) for r in tab["theta"]],
+                                     tab["beta0"], tab["mu0"], tab["alpha"], float(rec["e_min"][b]),
+                                     float(rec["e_max"][b]), tab.get("theta_entropy"))
+        torch.backends.cuda.matmul.allow_tf32 = False
+        fp32_all()
+        t32 = cuda_time(fp32_all, 1)
+        result["baselines"] = {"plain_fp32_recursion": {"instances_per_s": float(valid.sum()) / t32,
+                                                        "how": "per-instance torch.matmul fp32 loop, TF32 off"},
+                               "speedup_vs_fp32_recursion": value / world * t32}
+    del graph
+    torch.cuda.empty_cache()
+    return result
+
+
+def compact(res):
+    """The headline keys of a secondary result."""
+    keep = ("metric", "value", "unit", "ms_per_step", "tflops_alg", "config", "accuracy", "accuracy_sampled",
+            "density_only", "e2e", "details")
+    out = {k: res[k] for k in keep if k in res}
+    r = res.get("roofline", {})
+    out["roofline"] = {k: r.get(k) for k in ("achieved", "peak", "frac", "avg_layer_ms", "traffic")}
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import paper_2605_08523_gb300 as ft
+    from paper_2605_08523_gb300 import build as ftbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
     if rank == 0:
-        print(json.dumps(result), flush=True)
+        ftbuild.build()
+    if world > 1:
+        dist.barrier()
+    ft.lib()
+    if args.workload == "ragged":
+        res = run_ragged(args, ft, world, rank, local)
+    else:
+        res = run_single(args, ft, world, rank, local)
+    if rank == 0 and world == 1 and not args.no_baselines:
+        res["cpu_baseline"] = cpu_baseline(args)
+    if args.workload == "longrange" and world == 1 and not args.no_secondary:
+        import copy
+        sec = {}
+        a2 = copy.copy(args)
+        a2.workload, a2.refine, a2.steps = "ragged", None, max(5, args.steps // 2)
+        sec["ragged_batch"] = compact(run_ragged(a2, ft, world, rank, local, secondary=True))
+        a3 = copy.copy(args)
+        a3.workload, a3.dims, a3.refine, a3.steps = "lattice", "16,16,16", None, max(5, args.steps // 2)
+        sec["lattice_n4096"] = compact(run_single(a3, ft, world, rank, local, secondary=True))
+        res["secondary"] = sec
+    if rank == 0:
+        print(json.dumps(res), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

@@ -334,7 +334,7 @@ static int op_bytes(int fmt) {
 // 128, and 64 for the last kShortChunkLayers layers; BF16X3 and TF32X3, whose
 // layers carry more MMA work per drained chunk (6 products, or half-rate TF32),
 // so that shorter chunks cost almost nothing: 64 for every layer.  Measured at
-// n = 2048 (cfg1 lattice, printed table, density + entropy; n = 4096 alike),
+// n = 2048 (8x16x16 lattice, printed table, density + entropy; n = 4096 alike),
 // max|D - D_ref| / |S - S_ref|/n:
 //   FP16X2 128 + last 6 at 64:  1.00e-6 / 8.9e-7  (n = 2048)
 //   FP16X2 128 + last 12 at 64: 7.6e-7 / 6.2e-7, +2 to 3 % time

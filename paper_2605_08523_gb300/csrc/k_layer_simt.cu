@@ -18,6 +18,8 @@ __global__ void __launch_bounds__(256) layer_simt_kernel(const __grid_constant__
     __shared__ __align__(16) float As[SK][SB + 4];
     __shared__ __align__(16) float Bs[SK][SB + 4];
     __shared__ double red[8][2];
+    // no instance starts before status[1]: a layer below it has nothing to do
+    if (a.gl < *reinterpret_cast<volatile const int*>(a.status + 1)) return;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {

@@ -772,6 +772,10 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
     constexpr int NBUF = G::NBUF;
     constexpr uint32_t TMEM_COLS = NBUF * TILE;
 
+    // A launch whose layers all lie below the first layer any instance starts
+    // at (models with fewer layers than the set's maximum start late) has no
+    // active item: every thread of both CTAs of a pair leaves at once.
+    if (a.gl + a.nlayers <= *reinterpret_cast<volatile const int*>(a.status + 1)) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t full_bar[C::STAGES];

@@ -111,7 +111,10 @@ __global__ void prep_kernel(SetupArgs a) {
         a.iw[b].nonfinite = 0;
         a.iw[b].start_layer = 0;
     }
-    if (threadIdx.x == 0) *a.status = 0;
+    if (threadIdx.x == 0) {
+        a.status[0] = 0;
+        a.status[1] = 0x7fffffff;     // first global layer with an active instance (decide lowers it)
+    }
     if (a.done)
         for (int i = threadIdx.x; i < kMaxLayers * kMaxChains; i += blockDim.x) a.done[i] = 0;
     if (a.tiles) block_exclusive_scan_fill(a.inst, a.nb, a.BM, a.BN, a.nchains, a.iw, a.tiles, 0);
@@ -291,6 +294,11 @@ __global__ void decide_kernel(SetupArgs a) {
     }
     a.rec[b] = r;
     a.iw[b].start_layer = sl[0] | (sl[1] << 16);
+    if (r.status == FTSP2_OK && r.model >= 0) {
+        int first = sl[0];
+        for (int c = 1; c < a.nchains; ++c) first = min(first, sl[c]);
+        atomicMin(&a.status[1], first);
+    }
 }
 
 void launch_decide(const SetupArgs& a, cudaStream_t s) {

@@ -1,12 +1,23 @@
-"""The ragged batch (cfg2) and the large single matrix (cfg4) through the
-C ABI, against the CPU oracle.
+"""The benchmark workloads at their stated sizes, through the C ABI, against the
+CPU oracle, with the accuracy bounds the path promises: max|D - D_ref| <= 1e-6
+and |S - S_ref| / n <= 1e-6 for every mode and every instance (D_ref, S_ref:
+Fermi function and entropy by FP64 eigendecomposition), and max|D - D_rec|
+<= 1e-6 where the paper's printed table is chosen (D_rec: the FP64 scalar
+recursion of that table on the eigenvalues, i.e. rounding only).
 
-cfg2: 512 Hamiltonians, n ~ U{64..768}, eigenvalues U(-10, 10) eV rotated by
-Haar-random Q, mu ~ U(-5, 5), kT ~ U(0.02, 0.5): one grouped launch per layer
-for all instances and both chains.  Model choice and flip are checked for
-every instance; D and S on instances spread over the size range.
-cfg4: 16 x 16 x 32 lattice (n = 8192) with 5 % long-range couplings N(0, 0.05),
-kT = 0.1, FP16X2 layers with the last two layers in FP32, density + entropy.
+* Lattice sweep: open 3D cubic lattices 8x8x16, 8x16x16, 16x16x16
+  (n = 1024, 2048, 4096), kT in {0.05, 0.1, 0.3} eV, mu at half filling;
+  TF32X3, BF16X3 and FP16X2 layers; model set = the printed 26-layer table
+  (with the entropy table trained for it) and the 34-layer beta0 = 3000 table.
+  With Gershgorin bounds, kT = 0.05 at n = 4096 gives beta' = 1234 and
+  mu' ~ 1/2, beyond the printed table's region (beta' <= 1004 there), so the
+  beta0 = 3000 table is chosen.
+* Ragged batch: all 512 rotated-spectrum instances (n ~ U{64..768},
+  eigenvalues U(-10, 10) eV, mu ~ U(-5, 5), kT ~ U(0.02, 0.5)) in one call,
+  model set = every shipped Eq. mlsp2 table; every instance's decisions and
+  its D and S are checked.
+* Long-range lattice: 16x16x32 (n = 8192) with 5 % long-range couplings
+  N(0, 0.05), kT = 0.1, FP16X2 layers with two refinement layers.
 """
 import glob
 import os
@@ -15,12 +26,14 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from oracle import fermi, pipeline, rescale
+from oracle import fermi, lanczos, mlsp2, rescale, tables
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 TABLES = os.path.join(ROOT, "paper_2605_08523_gb300", "tables")
+PRINTED = rescale.Table(tables.PRINTED_B1500, 1500.0, 1.0 / 3.0, name="printed")
+TOL = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +47,7 @@ def ft():
 
 
 def table_meta(path):
-    # selection metadata only (beta0, mu0, L); coefficients trained by the
+    # selection metadata only (beta0, mu0, L): coefficients trained by the
     # library never enter an oracle computation in this file
     import json
     d = json.load(open(path))
@@ -43,7 +56,80 @@ def table_meta(path):
                          name=os.path.basename(path))
 
 
-def model_set_paths():
+# ---------------------------------------------------------------------------
+# lattice sweep
+# ---------------------------------------------------------------------------
+LATTICE_PATHS = [os.path.join(TABLES, "entropy_b1500_L26.json"), os.path.join(TABLES, "b3000_L34.json")]
+_eig_cache = {}
+
+
+def lattice_refs(dims, kT):
+    """(H, mu, D_ref, S_ref, D_rec or None, model index) from the oracle."""
+    key = (dims, kT)
+    if key in _eig_cache:
+        return _eig_cache[key]
+    if _eig_cache.get("dims") != dims:
+        _eig_cache.clear()
+        H = wl.lattice_3d(dims, 0)
+        _eig_cache.update(dims=dims, H=H, eig=np.linalg.eigh(H))
+    H = _eig_cache["H"]
+    n = H.shape[0]
+    eps, V = _eig_cache["eig"]
+    mu = fermi.mu_at_filling(eps, kT, n / 2)
+    f = fermi.fermi(eps, mu, kT)
+    Dref = (V * f[None, :]) @ V.T
+    Sref = float(np.sum(fermi.entropy(eps, mu, kT)))
+    # the oracle's decisions with the same model set (printed table first)
+    metas = [PRINTED, table_meta(LATTICE_PATHS[1])]
+    lo, hi = rescale.gershgorin(H)
+    mup, bp = rescale.normalise(lo, hi, mu, 1.0 / kT)
+    flip = rescale.flip_needed(mup)
+    if flip:
+        mup = 1.0 - mup
+    m = rescale.select_model(metas, mup, bp)
+    Drec = None
+    if m == 0:
+        _, rec = rescale.rescale(H, mu, kT, [PRINTED])
+        x0 = rescale.x0_of_eigenvalue(eps, mu, kT, rec, PRINTED)
+        p = mlsp2.mlsp2_scalar(x0, PRINTED.theta)
+        if rec.flip:
+            p = 1.0 - p
+        Drec = (V * p[None, :]) @ V.T
+    out = (H, mu, Dref, Sref, Drec, m, flip)
+    _eig_cache[key] = out
+    return out
+
+
+# ordered so that consecutive cases share the eigendecomposition and the references
+SWEEP = [(d, kT, m) for d in ((8, 8, 16), (8, 16, 16), (16, 16, 16)) for kT in (0.05, 0.1, 0.3)
+         for m in ("tf32x3", "bf16x3", "fp16x2")]
+
+
+@pytest.mark.parametrize("dims,kT,mode", SWEEP)
+def test_lattice_sweep_within_1e6(ft, dims, kT, mode):
+    H, mu, Dref, Sref, Drec, m, flip = lattice_refs(dims, kT)
+    n = H.shape[0]
+    ms = ft.ModelSet.from_json(LATTICE_PATHS)
+    s = ft.Solver([n], [mu], [kT], ms, mode=mode, want=3)
+    s.run(torch.from_numpy(H.ravel().copy()).cuda(), sync=True)
+    rec = s.records()[0]
+    assert rec["status"] == 0 and rec["model"] == m and bool(rec["flip"]) == flip
+    if dims == (16, 16, 16) and kT == 0.05:
+        assert m == 1          # the printed table's region ends below this beta'
+    D = s.matrix(0).double().cpu().numpy()
+    errD = np.max(np.abs(D - Dref))
+    assert errD <= TOL, (mode, n, kT, errD)
+    assert abs(float(s.S[0]) - Sref) / n <= TOL
+    if Drec is not None:
+        assert np.max(np.abs(D - Drec)) <= TOL
+    tr = s.trace.cpu().numpy()[0]
+    assert abs(tr[0] - n / 2) < 1e-3 and abs(tr[0] - np.trace(D)) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# ragged batch: every instance
+# ---------------------------------------------------------------------------
+def ragged_paths():
     # the printed table (with its trained entropy table), the 32-layer tables
     # of the training sweep and the high-beta0 tables
     paths = [os.path.join(TABLES, "entropy_b1500_L26.json")]
@@ -53,81 +139,83 @@ def model_set_paths():
     return paths
 
 
-def test_cfg2_ragged_batch(ft):
-    paths = model_set_paths()
-    ms = ft.ModelSet.from_json(paths)
-    metas = [table_meta(p) for p in paths]
+@pytest.fixture(scope="module")
+def ragged():
     batch = wl.ragged_batch(512, 0)
-    Hs = [b["H"] for b in batch]
-    mus = [b["mu"] for b in batch]
-    kTs = [b["kT"] for b in batch]
-    s = ft.Solver([H.shape[0] for H in Hs], mus, kTs, ms, mode="fp16x2", want=3)
-    flat, _ = wl.pack_batch(Hs)
+    refs = [fermi.eig_reference(b["H"], b["mu"], b["kT"]) for b in batch]
+    flat, _ = wl.pack_batch([b["H"] for b in batch])
+    return batch, refs, flat
+
+
+@pytest.mark.parametrize("mode,bounds", [("fp16x2", "gershgorin"), ("bf16x3", "gershgorin"),
+                                         ("fp16x2", "lanczos"), ("tf32x3", "lanczos")])
+def test_ragged_batch_every_instance_within_1e6(ft, ragged, mode, bounds):
+    batch, refs, flat = ragged
+    paths = ragged_paths()
+    metas = [table_meta(p) for p in paths]
+    ns = [b["n"] for b in batch]
+    flags = ft.LANCZOS | ft.MIN_LAYERS if bounds == "lanczos" else 0
+    s = ft.Solver(ns, [b["mu"] for b in batch], [b["kT"] for b in batch], ft.ModelSet.from_json(paths),
+                  mode=mode, want=3, flags=flags)
     s.run(torch.from_numpy(flat).cuda(), sync=True)
     rec = s.records()
-    # scalar decisions (bounds, flip, validity, smallest valid beta0) for every instance
-    n_valid = 0
-    for b, H in enumerate(Hs):
-        lo, hi = rescale.gershgorin(H)
-        mup, bp = rescale.normalise(lo, hi, mus[b], 1.0 / kTs[b])
+    # the scalar decisions of every instance: bounds, flip, validity, model
+    for b, inst in enumerate(batch):
+        H = inst["H"]
+        if bounds == "gershgorin":
+            lo, hi = rescale.gershgorin(H)
+        else:
+            lo, hi = lanczos.bounds(H)
+        mup, bp = rescale.normalise(lo, hi, inst["mu"], 1.0 / inst["kT"])
         flip = rescale.flip_needed(mup)
         if flip:
             mup = 1.0 - mup
-        m = rescale.select_model(metas, mup, bp)
-        assert rec["model"][b] == m, b
-        if m >= 0:
-            n_valid += 1
-            assert rec["status"][b] == 0 and bool(rec["flip"][b]) == flip
-        else:
-            assert rec["status"][b] == -4
-    assert n_valid >= 505
-    # D and S against the eigendecomposition on instances spread over the size
-    # range.  Rounding grows with the chosen table's slope beta0/4; the trained
-    # tables add their fit error (<= 1e-6 for these tables, 2.5e-6 entropy).
-    order = np.argsort([H.shape[0] for H in Hs])
-    picks = [int(order[i]) for i in np.linspace(0, 511, 12).astype(int)]
+        m = rescale.select_model(metas, mup, bp, min_layers=bounds == "lanczos")
+        assert m >= 0 and rec["model"][b] == m, b
+        assert rec["status"][b] == 0 and bool(rec["flip"][b]) == flip, b
+    # D and S of every instance against the eigendecomposition
+    D = s.D.cpu().numpy()
     S = s.S.cpu().numpy()
-    for b in picks:
-        m = rec["model"][b]
-        if m < 0:
-            continue
-        H = Hs[b]
-        n = H.shape[0]
-        Dref, Sref, _, _ = fermi.eig_reference(H, mus[b], kTs[b])
-        D = s.matrix(b).double().cpu().numpy()
-        tol = 1.5e-6 * max(1.0, metas[m].beta0 / 1500.0) + 1.1e-6
-        assert np.max(np.abs(D - Dref)) < tol, (b, n, metas[m].name)
-        assert abs(S[b] - Sref) / n < tol + 2.5e-6, (b, n, metas[m].name)
+    worst = 0.0
+    for b, inst in enumerate(batch):
+        n, o = inst["n"], s.offsets[b]
+        Dref, Sref, _, _ = refs[b]
+        err = np.max(np.abs(D[o:o + n * n].reshape(n, n).astype(np.float64) - Dref))
+        worst = max(worst, err)
+        assert err <= TOL, (b, n, inst["kT"], int(rec["model"][b]), err)
+        assert abs(S[b] - Sref) / n <= TOL, b
+    assert worst > 0.0
 
 
-def test_cfg2_printed_table_method_exact(ft):
-    # Instances of the same batch family solved with the paper's printed table
-    # alone, against the oracle's method-exact result (rounding only).
-    from oracle import tables
-    printed = rescale.Table(tables.PRINTED_B1500, 1500.0, 1.0 / 3.0)
+def test_ragged_batch_printed_table_method_exact(ft):
+    # instances of the same family with the paper's printed table alone,
+    # against the oracle's method-exact result (rounding only)
+    from oracle import pipeline
     batch = wl.ragged_batch(40, 1)
     Hs = [b["H"] for b in batch]
     mus = [b["mu"] for b in batch]
     kTs = [b["kT"] for b in batch]
-    ms = ft.ModelSet()
-    s = ft.Solver([H.shape[0] for H in Hs], mus, kTs, ms, mode="fp16x2", want=1)
+    s = ft.Solver([H.shape[0] for H in Hs], mus, kTs, ft.ModelSet(), mode="fp16x2", want=1)
     flat, _ = wl.pack_batch(Hs)
     s.run(torch.from_numpy(flat).cuda(), sync=True)
     rec = s.records()
     checked = 0
     for b, H in enumerate(Hs):
-        ex = pipeline.method_exact(H, mus[b], kTs[b], [printed])
+        ex = pipeline.method_exact(H, mus[b], kTs[b], [PRINTED])
         if ex["D"] is None:
             assert rec["status"][b] == -4
             continue
         D = s.matrix(b).double().cpu().numpy()
-        assert np.max(np.abs(D - ex["D"])) < 1.5e-6, b
+        assert np.max(np.abs(D - ex["D"])) <= TOL, b
         checked += 1
     assert checked >= 20
 
 
-@pytest.mark.parametrize("refine_tc", [False, True])
-def test_cfg4_n8192_refine2(ft, refine_tc):
+# ---------------------------------------------------------------------------
+# long-range lattice, n = 8192
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def longrange():
     H = wl.lattice_3d((16, 16, 32), 0, longrange_frac=0.05, longrange_sigma=0.05)
     n, kT = 8192, 0.1
     eps, V = np.linalg.eigh(H)
@@ -135,14 +223,17 @@ def test_cfg4_n8192_refine2(ft, refine_tc):
     f = fermi.fermi(eps, mu, kT)
     Dref = (V * f[None, :]) @ V.T
     Sref = float(np.sum(fermi.entropy(eps, mu, kT)))
-    del V
+    return H, mu, kT, Dref, Sref, float(np.sum(f))
+
+
+@pytest.mark.parametrize("refine_tc", [False, True])
+def test_longrange_n8192_refine2(ft, longrange, refine_tc):
+    H, mu, kT, Dref, Sref, trref = longrange
+    n = H.shape[0]
     # The long-range couplings widen the Gershgorin interval to ~141 eV, so
     # beta' ~ 1415 needs beta0 >= ~2100: the 34-layer beta0 = 3000 table is the
-    # smallest valid one.  Rounding scales with beta0 = 3000, which the two
-    # refinement layers and the 64-element chunks keep inside 1e-6 (measured
-    # 6.8e-7 with CUDA-core, 7.4e-7 with tensor-core refinement).
-    ms = ft.ModelSet.from_json([os.path.join(TABLES, "entropy_b1500_L26.json"),
-                                os.path.join(TABLES, "b3000_L34.json")])
+    # smallest valid one.
+    ms = ft.ModelSet.from_json(LATTICE_PATHS)
     s = ft.Solver([n], [mu], [kT], ms, mode="fp16x2", want=3,
                   flags=ft.REFINE2 | (ft.REFINE_TC if refine_tc else 0))
     s.run(torch.from_numpy(H.ravel().copy()).cuda(), sync=True)
@@ -150,31 +241,21 @@ def test_cfg4_n8192_refine2(ft, refine_tc):
     assert rec["status"] == 0 and rec["model"] == 1
     D = s.matrix(0).double().cpu().numpy()
     err = np.max(np.abs(D - Dref))
-    assert err <= 1e-6, err
-    assert abs(float(s.trace[0, 0]) - np.sum(f)) < 1e-3
-    assert abs(float(s.S[0]) - Sref) / n <= 1e-6
+    assert err <= TOL, err
+    assert abs(float(s.trace[0, 0]) - trref) < 1e-3
+    assert abs(float(s.S[0]) - Sref) / n <= TOL
 
 
-def test_cfg2_with_lanczos_bounds_within_1e6(ft):
-    # with the Lanczos-tightened bounds and the fewest-layers policy every
-    # instance of the ragged batch runs the printed 26-layer table, and D and S
-    # meet the 1e-6 bound against the eigendecomposition
-    paths = model_set_paths()
-    ms = ft.ModelSet.from_json(paths)
-    batch = wl.ragged_batch(512, 0)
-    Hs = [b["H"] for b in batch]
-    ns = [H.shape[0] for H in Hs]
-    flat, _ = wl.pack_batch(Hs)
-    s = ft.Solver(ns, [b["mu"] for b in batch], [b["kT"] for b in batch], ms, mode="fp16x2", want=3,
-                  flags=ft.LANCZOS | ft.MIN_LAYERS)
-    s.run(torch.from_numpy(flat).cuda(), sync=True)
-    torch.cuda.synchronize()
-    rec = s.records()
-    assert np.all(rec["status"] == 0) and np.all(rec["model"] == 0)
-    S = s.S.cpu().numpy()
-    for b in range(0, 512, 23):
-        H = Hs[b]
-        Dref, Sref, _, _ = fermi.eig_reference(H, batch[b]["mu"], batch[b]["kT"])
-        D = s.matrix(b).double().cpu().numpy()
-        assert np.max(np.abs(D - Dref)) < 1e-6, b
-        assert abs(S[b] - Sref) / ns[b] < 1e-6, b
+def test_longrange_n8192_lanczos_printed_table(ft, longrange):
+    # with the Lanczos-tightened interval (~13 eV) the printed 26-layer table
+    # is valid: 8 layers fewer, same bound
+    H, mu, kT, Dref, Sref, trref = longrange
+    n = H.shape[0]
+    ms = ft.ModelSet.from_json(LATTICE_PATHS)
+    s = ft.Solver([n], [mu], [kT], ms, mode="fp16x2", want=3, flags=ft.REFINE2 | ft.REFINE_TC | ft.LANCZOS)
+    s.run(torch.from_numpy(H.ravel().copy()).cuda(), sync=True)
+    rec = s.records()[0]
+    assert rec["status"] == 0 and rec["model"] == 0 and rec["layers"] == 26
+    D = s.matrix(0).double().cpu().numpy()
+    assert np.max(np.abs(D - Dref)) <= TOL
+    assert abs(float(s.S[0]) - Sref) / n <= TOL

@@ -80,7 +80,7 @@ def check_instance(s, b, H, mu, kT, tabs, mode, tolD=None, tolS=None, clamp=Fals
 
 @pytest.mark.parametrize("mode", MODES)
 def test_chain256_printed_table(ft, printed_set, mode):
-    # cfg0 shape: open 1D chain n = 256, mu = 0, kT = 0.1 eV.
+    # the chain workload: open 1D chain n = 256, mu = 0, kT = 0.1 eV.
     H = wl.chain_1d(256, 0)
     s = solve(ft, printed_set, [H], [0.0], [0.1], mode)
     check_instance(s, 0, H, 0.0, 0.1, [PRINTED], mode)
@@ -107,7 +107,7 @@ def test_ragged_sizes_other_modes(ft, printed_set, mode, n):
 
 @pytest.mark.parametrize("mode", MODES)
 def test_lattice_1024(ft, printed_set, mode):
-    # cfg1 shape at its smallest size: 8 x 8 x 16 lattice, mu at half filling.
+    # the lattice workload at its smallest size: 8 x 8 x 16, mu at half filling.
     H = wl.lattice_3d((8, 8, 16), 0)
     kT = 0.1
     mu = fermi.mu_at_filling(np.linalg.eigvalsh(H), kT, 512)
@@ -221,7 +221,7 @@ def test_rescale_records(ft, printed_set):
 def test_model_set_selection(ft):
     # Two tables: the printed one (beta0 = 1500) and a 20-layer SP2-mu table
     # at mu0 = 1/3 given beta0 = 4 x its slope at mu0 (fixed coefficients,
-    # cfg0's "plain recursion").  Selection takes the smallest valid beta0;
+    # the chain workload's "plain recursion").  Selection takes the smallest valid beta0;
     # D is compared with the oracle's method-exact result for the chosen table.
     th_sp2 = sp2.sp2_table(1.0 / 3.0, 20)
     b0 = 4.0 * sp2.slope_at(th_sp2, 1.0 / 3.0)
@@ -236,7 +236,7 @@ def test_model_set_selection(ft):
 
 
 @pytest.mark.parametrize("mode", ["fp16x2", "bf16x3"])
-def test_cfg1_n4096_within_the_1e6_bound(ft, printed_set, mode):
+def test_lattice_n4096_within_the_1e6_bound(ft, printed_set, mode):
     # The bench workload at full size (16 x 16 x 16 lattice, kT = 0.1, mu at
     # half filling): every element of D within 1e-6 of the eigendecomposition
     # reference, traces consistent, S within the model's own error.
@@ -261,7 +261,7 @@ def _json_set(ft, *names):
     return ft.ModelSet.from_json([os.path.join(root, "paper_2605_08523_gb300", "tables", nm + ".json") for nm in names])
 
 
-def test_cfg1_n4096_entropy_with_trained_table(ft):
+def test_lattice_n4096_entropy_with_trained_table(ft):
     # printed Fermi table + the entropy table trained for it: S within 1e-6
     # per state of the eigendecomposition entropy, D unchanged.
     ms = _json_set(ft, "entropy_b1500_L26")
@@ -276,7 +276,7 @@ def test_cfg1_n4096_entropy_with_trained_table(ft):
     assert abs(float(s.S[0]) - Sref) / n <= 1e-6
 
 
-def test_cfg3_trained_table_applied_n4096_bf16x3(ft):
+def test_trained_table_applied_to_lattice_n4096_bf16x3(ft):
     # A table trained on the GPU at beta0 = 200, mu0 = 1/3, 32 layers, applied
     # to the n = 4096 lattice in 3xBF16 at kT = 0.5 (beta' ~ 122 <= 2/3 beta0).
     ms = _json_set(ft, "b200_L32")
