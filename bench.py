@@ -960,9 +960,10 @@ def run_ragged(args, ft, world, rank, local, secondary=False):
         torch.backends.cuda.matmul.allow_tf32 = False
         fp32_all()
         t32 = cuda_time(fp32_all, 1)
-        result["baselines"] = {"plain_fp32_recursion": {"instances_per_s": float(valid.sum()) / t32,
+        base = float(valid.sum()) / t32
+        result["baselines"] = {"plain_fp32_recursion": {"instances_per_s": base,
                                                         "how": "per-instance torch.matmul fp32 loop, TF32 off"},
-                               "speedup_vs_fp32_recursion": value / world * t32}
+                               "speedup_vs_fp32_recursion": value / world / base}
     del graph
     torch.cuda.empty_cache()
     return result

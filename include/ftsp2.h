@@ -399,20 +399,67 @@ typedef struct {
 #define FTSP2_TARGET_ENTROPY 1  /* s(beta0 (x - mu0)) of Eq. entropy, model
                                    4 ln2 F (1 - F) with x0 = alpha (x - mu0) + mu0 */
 
-/* Levenberg-Marquardt with optional geodesic acceleration (Sec. II C 2) on
- * nsamples scalar samples.  dX (device, nsamples doubles) holds the sample
- * points in [0, 1] (fixed for the whole fit, Sec. II C 1); dWork must hold
- * ftsp2_train_workspace_size(nsamples, L) bytes.  theta_init (host, L*4) is
- * the starting table; theta_out (host, L*4) receives the result.  Residuals,
- * Jacobian rows and the reductions J^T J, J^T r run on the GPU in FP64; the
- * damped normal equations are solved on the host by Cholesky in FP64.
- * accel != 0 enables geodesic acceleration.  Synchronous on `stream`. */
+/* Levenberg-Marquardt with optional geodesic acceleration (Sec. II C 2) of
+ * an L-layer Eq. mlsp2 table on nsamples scalar samples.
+ *   - Samples (Sec. II C 1): the library builds them (ftsp2_train_samples with
+ *     the same beta0, mu0, nsamples, seed) and keeps them fixed for the whole
+ *     fit; seed 0 gives the deterministic quantile grid.
+ *   - theta_init (host, L*4, nullable): the starting table; NULL starts from
+ *     ftsp2_train_init(L, beta0, mu0) (the SP2 sequence at mu0 with its slope
+ *     matched to beta0/4).  theta_out (host, L*4) receives the result.
+ *   - target FTSP2_TARGET_FERMI or FTSP2_TARGET_ENTROPY (then the model input
+ *     is alpha (x - mu0) + mu0, Eq. entropy expansion); iterations >= 0 LM
+ *     steps; accel != 0 enables geodesic acceleration.
+ *   - Residuals, Jacobian rows and the reductions J^T J, J^T r run on the GPU
+ *     in FP64; the damped normal equations are solved on the host by Cholesky
+ *     in FP64.
+ *   - dWork (device) must hold ftsp2_train_workspace_size(nsamples, L) bytes
+ *     (the samples live there too).  Synchronous on `stream`.
+ * Errors: FTSP2_E_ARG for L outside 1..64, nsamples < 1, beta0 <= 0, mu0
+ * outside (0, 1), a bad target, NULL outputs or non-finite start entries;
+ * FTSP2_E_WORKSPACE for a short workspace. */
 size_t ftsp2_train_workspace_size(int nsamples, int L);
 ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, double alpha,
-                                const double* dX, int nsamples, int iterations, int accel,
+                                int nsamples, uint64_t seed, int iterations, int accel,
                                 const double* theta_init, double* theta_out,
                                 ftsp2_train_report* rep, void* dWork, size_t work_bytes,
                                 void* stream);
+
+/* The training sample set (Sec. II C 1), host only: x_out[nsamples] in [0, 1]
+ * at the quantiles of the density p(x) = 1 + |f'(x)|, f the increasing
+ * logistic 1/(1 + exp(-beta0 (x - mu0))): the CDF of p is integrated by the
+ * trapezoid rule on 2,000,001 evenly spaced points and inverted by linear
+ * interpolation at q_s = (s + 1/2)/nsamples (seed 0) or
+ * q_s = (s + u_s)/nsamples with u_s the top 53 bits of splitmix64(seed + s)
+ * scaled to [0, 1) (one point in each equal-probability cell). */
+ftsp2_status ftsp2_train_samples(double beta0, double mu0, int nsamples, uint64_t seed, double* x_out);
+
+/* Starting tables, host only (reading of the "scaled and truncated SP2"
+ * initial guess of Sec. II A 1):
+ *   ftsp2_train_init: the SP2 sequence for a known chemical potential
+ *     (Eq. sp2-mu) at mu0 as Eq. mlsp2 rows (Appendix C: X^2 -> (1, 0, 0, 0),
+ *     2X - X^2 -> (-1, 2, 0, 0)), with the contraction x -> mu0 + kappa
+ *     (x - mu0) folded into layer 0, kappa = min(1, (beta0/4) / slope), the
+ *     slope of the sequence at mu0 being the product of the layers'
+ *     derivatives along the trajectory of mu0 (L*4 doubles out);
+ *   ftsp2_train_init_alt: the same SP2 sequence in the one-term form
+ *     (Eq. mlsp2_alt; (L + 1)*2 doubles out);
+ *   ftsp2_mlsp2_to_skip: the Appendix embedding of L Eq. mlsp2 rows (every
+ *     a_i != 0) as a Skip-SP2 table with one stored layer and one accumulator
+ *     ((L + 1)*4 doubles out; L <= 63).
+ * ftsp2_layer_count: Eq. layer count, ln(beta'/4) / ln(2 / varphi), the
+ * fewest layers a table needs to reach the slope beta'/4 (NaN for beta' <= 0). */
+ftsp2_status ftsp2_train_init(int L, double beta0, double mu0, double* theta_out);
+ftsp2_status ftsp2_train_init_alt(int L, double mu0, double* alt_out);
+ftsp2_status ftsp2_mlsp2_to_skip(int L, const double* theta, double* skip_out);
+double ftsp2_layer_count(double beta_p);
+
+/* Residuals model - target of a table (family FTSP2_FAMILY_MLSP2: L rows of
+ * 4; FTSP2_FAMILY_SKIP: L + 1 rows of 4) at npoints device points dX, into
+ * dR (device), FP64, no Jacobian: used to measure a table's error on a grid. */
+ftsp2_status ftsp2_train_residuals(int family, int target, double beta0, double mu0, int L, double alpha,
+                                   const double* table, const double* dX, int npoints, double* dR,
+                                   void* stream);
 
 /* The one-term form of the recursion (Eq. mlsp2_alt).  A table of this form
  * holds L + 1 rows (t_i1, t_i2), (L + 1) * 2 doubles: layers
@@ -428,24 +475,26 @@ ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, dou
 ftsp2_status ftsp2_alt_to_mlsp2(int L, const double* alt, double* theta_out);
 
 /* Levenberg-Marquardt training in the one-term form: as ftsp2_train_coeffs,
- * with alt_init / alt_out (host) of (L + 1) * 2 doubles.  The GPU computes the
+ * with alt_init / alt_out (host) of (L + 1) * 2 doubles (alt_init NULL:
+ * ftsp2_train_init_alt(L, mu0)).  The GPU computes the
  * Eq. mlsp2 Jacobian of the mapped table and its reductions J^T J, J^T r; the
  * host applies the chain rule of ftsp2_alt_to_mlsp2 (P^T J^T J P, P^T J^T r,
  * P = d theta / d t) and solves for the 2L + 2 parameters.  Same workspace
  * (ftsp2_train_workspace_size(nsamples, L)). */
 ftsp2_status ftsp2_train_coeffs_alt(int target, double beta0, double mu0, int L, double alpha,
-                                    const double* dX, int nsamples, int iterations, int accel,
+                                    int nsamples, uint64_t seed, int iterations, int accel,
                                     const double* alt_init, double* alt_out, ftsp2_train_report* rep,
                                     void* dWork, size_t work_bytes, void* stream);
 
 /* Levenberg-Marquardt training of a Skip-SP2 table (FTSP2_FAMILY_SKIP, one
  * stored layer and one accumulator): as ftsp2_train_coeffs, with skip_init /
  * skip_out (host) of (L + 1) * 4 doubles (layer rows, then the output row
- * (A_0, gamma_L, 0, 0)); the 4L + 2 parameters get their own forward and
- * reverse sweep on the GPU.  dWork must hold
+ * (A_0, gamma_L, 0, 0)); skip_init NULL starts from the embedding of
+ * ftsp2_train_init(L, beta0, mu0).  The 4L + 2 parameters get their own
+ * forward and reverse sweep on the GPU.  dWork must hold
  * ftsp2_train_workspace_size(nsamples, L + 1) bytes; L <= 63. */
 ftsp2_status ftsp2_train_coeffs_skip(int target, double beta0, double mu0, int L, double alpha,
-                                     const double* dX, int nsamples, int iterations, int accel,
+                                     int nsamples, uint64_t seed, int iterations, int accel,
                                      const double* skip_init, double* skip_out, ftsp2_train_report* rep,
                                      void* dWork, size_t work_bytes, void* stream);
 

@@ -51,14 +51,22 @@ def _density(x, beta0, mu0, weighting):
 
 
 def sample_grid(N: int, beta0: float, mu0: float, weighting: str = "derivative",
-                fine: int = 2_000_001):
-    """Deterministic quantile grid of p on [0, 1] (trapezoid CDF on a fine grid,
-    then linear interpolation of the inverse)."""
+                fine: int = 2_000_001, seed: int = 0):
+    """Quantile grid of p on [0, 1] (trapezoid CDF on a fine grid, then linear
+    interpolation of the inverse): x_s = F^-1(q_s) with q_s = (s + 1/2)/N for
+    seed 0 (deterministic), or q_s = (s + u_s)/N with u_s the top 53 bits of
+    splitmix64(seed + s) scaled to [0, 1) (one point drawn in each of the N
+    equal-probability cells; splitmix64 as in ``lanczos.splitmix64``)."""
     g = np.linspace(0.0, 1.0, fine)
     p = _density(g, beta0, mu0, weighting)
     cdf = np.concatenate([[0.0], np.cumsum(0.5 * (p[1:] + p[:-1]) * np.diff(g))])
     cdf /= cdf[-1]
-    q = (np.arange(N) + 0.5) / N
+    if seed == 0:
+        q = (np.arange(N) + 0.5) / N
+    else:
+        from .lanczos import MASK64, splitmix64
+        u = np.array([(splitmix64((seed + s) & MASK64) >> 11) * 2.0 ** -53 for s in range(N)])
+        q = (np.arange(N) + u) / N
     return np.interp(q, cdf, g)
 
 
@@ -183,10 +191,16 @@ def init_from_sp2(L: int, beta0: float, mu0: float):
     Sec. II A 1): the SP2-mu sequence at mu0 (Eq. sp2-mu, Appendix C
     embedding) with an affine contraction x -> mu0 + kappa (x - mu0) folded
     into layer 0 so that the slope at mu0 equals the target's beta0/4
-    (kappa <= 1; kappa = 1 when L is below the layer count of Eq. layer count)."""
-    from .sp2 import sp2_table, slope_at
+    (kappa <= 1; kappa = 1 when L is below the layer count of Eq. layer count).
+    The slope of the composition at mu0 is the product of the layers'
+    derivatives 2 a m_i + b along the trajectory m_0 = mu0,
+    m_{i+1} = a m_i^2 + b m_i + c (chain rule)."""
+    from .sp2 import sp2_table
     th = np.array(sp2_table(mu0, L), dtype=np.float64)
-    s = slope_at(th, mu0)
+    m, s = mu0, 1.0
+    for a, b, c, _ in th:
+        s *= 2.0 * a * m + b
+        m = a * m * m + b * m + c
     kappa = min(1.0, (beta0 / 4.0) / s)
     m = mu0 * (1.0 - kappa)
     a, b, c, d = th[0]

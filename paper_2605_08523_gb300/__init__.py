@@ -414,62 +414,99 @@ def ftsp2_alt_to_mlsp2(alt):
     return out
 
 
-def ftsp2_train_coeffs_alt(target, beta0, mu0, alt_init, x, iterations=100, accel=True, alpha=1.0, stream=None):
-    """Levenberg-Marquardt fit of a one-term table (Eq. mlsp2_alt) on the GPU.
-    x: CUDA float64 samples.  Returns (alt (L + 1, 2) numpy, report dict)."""
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _train(fn, target, beta0, mu0, L, init, width, nrows, nsamples, seed, iterations, accel, alpha, ws_rows, stream):
     torch = _torch()
-    a0 = np.ascontiguousarray(np.asarray(alt_init, dtype=np.float64).reshape(-1, 2))
-    L = a0.shape[0] - 1
-    ns = x.numel()
-    out = np.zeros_like(a0)
-    wb = lib().ftsp2_train_workspace_size(ns, L)
-    ws = torch.empty(wb, dtype=torch.uint8, device=x.device)
+    p0 = None if init is None else np.ascontiguousarray(np.asarray(init, dtype=np.float64).reshape(-1, width))
+    out = np.zeros((nrows, width))
+    wb = lib().ftsp2_train_workspace_size(int(nsamples), ws_rows)
+    ws = torch.empty(wb, dtype=torch.uint8, device="cuda")
     rep = TrainReport()
-    check(lib().ftsp2_train_coeffs_alt(int(target), float(beta0), float(mu0), L, float(alpha), _ptr(x), ns,
-                                       int(iterations), int(bool(accel)),
-                                       a0.ctypes.data_as(C.POINTER(C.c_double)),
-                                       out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep), _ptr(ws), wb,
-                                       _stream(stream)), "ftsp2_train_coeffs_alt")
+    check(fn(int(target), float(beta0), float(mu0), int(L), float(alpha), int(nsamples), int(seed), int(iterations),
+             int(bool(accel)), None if p0 is None else _dp(p0), _dp(out), C.byref(rep), _ptr(ws), wb,
+             _stream(stream)), fn.__name__)
     return out, dict(iterations=rep.iterations, accepted=rep.accepted, cost0=rep.cost0, cost=rep.cost,
                      max_err=rep.max_err, lam=rep.lam)
 
 
-def ftsp2_train_coeffs_skip(target, beta0, mu0, skip_init, x, iterations=100, accel=True, alpha=1.0, stream=None):
-    """Levenberg-Marquardt fit of a Skip-SP2 table (one stored layer, one
-    accumulator) on the GPU.  x: CUDA float64 samples.  Returns (table
-    (L + 1, 4) numpy, report dict)."""
-    torch = _torch()
-    t0 = np.ascontiguousarray(np.asarray(skip_init, dtype=np.float64).reshape(-1, 4))
-    L = t0.shape[0] - 1
-    ns = x.numel()
-    out = np.zeros_like(t0)
-    wb = lib().ftsp2_train_workspace_size(ns, L + 1)
-    ws = torch.empty(wb, dtype=torch.uint8, device=x.device)
-    rep = TrainReport()
-    check(lib().ftsp2_train_coeffs_skip(int(target), float(beta0), float(mu0), L, float(alpha), _ptr(x), ns,
-                                        int(iterations), int(bool(accel)),
-                                        t0.ctypes.data_as(C.POINTER(C.c_double)),
-                                        out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep), _ptr(ws), wb,
-                                        _stream(stream)), "ftsp2_train_coeffs_skip")
-    return out, dict(iterations=rep.iterations, accepted=rep.accepted, cost0=rep.cost0, cost=rep.cost,
-                     max_err=rep.max_err, lam=rep.lam)
-
-
-def ftsp2_train_coeffs(target, beta0, mu0, theta_init, x, iterations=100, accel=True, alpha=1.0, stream=None):
-    """Levenberg-Marquardt fit on the GPU (Sec. II C).  x: CUDA float64 samples.
+def ftsp2_train_coeffs(target, beta0, mu0, L=None, theta_init=None, nsamples=100_000, seed=0, iterations=100,
+                       accel=True, alpha=1.0, stream=None):
+    """Levenberg-Marquardt fit of an Eq. mlsp2 table on the GPU (Sec. II C) on
+    the library's own sample set (ftsp2_train_samples(beta0, mu0, nsamples,
+    seed)).  theta_init None starts from ftsp2_train_init(L, beta0, mu0).
     Returns (theta (L, 4) numpy, report dict)."""
+    if theta_init is not None:
+        L = np.asarray(theta_init).reshape(-1, 4).shape[0]
+    return _train(lib().ftsp2_train_coeffs, target, beta0, mu0, L, theta_init, 4, L, nsamples, seed, iterations,
+                  accel, alpha, L, stream)
+
+
+def ftsp2_train_coeffs_alt(target, beta0, mu0, L=None, alt_init=None, nsamples=100_000, seed=0, iterations=100,
+                           accel=True, alpha=1.0, stream=None):
+    """Levenberg-Marquardt fit of a one-term table (Eq. mlsp2_alt) on the GPU.
+    Returns (alt (L + 1, 2) numpy, report dict)."""
+    if alt_init is not None:
+        L = np.asarray(alt_init).reshape(-1, 2).shape[0] - 1
+    return _train(lib().ftsp2_train_coeffs_alt, target, beta0, mu0, L, alt_init, 2, L + 1, nsamples, seed,
+                  iterations, accel, alpha, L, stream)
+
+
+def ftsp2_train_coeffs_skip(target, beta0, mu0, L=None, skip_init=None, nsamples=100_000, seed=0, iterations=100,
+                            accel=True, alpha=1.0, stream=None):
+    """Levenberg-Marquardt fit of a Skip-SP2 table (one stored layer, one
+    accumulator) on the GPU.  Returns (table (L + 1, 4) numpy, report dict)."""
+    if skip_init is not None:
+        L = np.asarray(skip_init).reshape(-1, 4).shape[0] - 1
+    return _train(lib().ftsp2_train_coeffs_skip, target, beta0, mu0, L, skip_init, 4, L + 1, nsamples, seed,
+                  iterations, accel, alpha, L + 1, stream)
+
+
+def ftsp2_train_samples(beta0, mu0, nsamples, seed=0):
+    """The training samples the library builds (numpy, host-only call)."""
+    x = np.zeros(int(nsamples))
+    check(lib().ftsp2_train_samples(float(beta0), float(mu0), int(nsamples), int(seed), _dp(x)),
+          "ftsp2_train_samples")
+    return x
+
+
+def ftsp2_train_init(L, beta0, mu0):
+    """The library's starting Eq. mlsp2 table ((L, 4) numpy, host-only call)."""
+    th = np.zeros((int(L), 4))
+    check(lib().ftsp2_train_init(int(L), float(beta0), float(mu0), _dp(th)), "ftsp2_train_init")
+    return th
+
+
+def ftsp2_train_init_alt(L, mu0):
+    """The library's starting one-term table ((L + 1, 2) numpy, host-only call)."""
+    a = np.zeros((int(L) + 1, 2))
+    check(lib().ftsp2_train_init_alt(int(L), float(mu0), _dp(a)), "ftsp2_train_init_alt")
+    return a
+
+
+def ftsp2_mlsp2_to_skip(theta):
+    """Appendix embedding of Eq. mlsp2 rows as a Skip-SP2 table ((L + 1, 4) numpy)."""
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1, 4))
+    L = th.shape[0]
+    out = np.zeros((L + 1, 4))
+    check(lib().ftsp2_mlsp2_to_skip(L, _dp(th), _dp(out)), "ftsp2_mlsp2_to_skip")
+    return out
+
+
+def ftsp2_layer_count(beta_p):
+    """Eq. layer count (host-only call)."""
+    return float(lib().ftsp2_layer_count(float(beta_p)))
+
+
+def ftsp2_train_residuals(target, beta0, mu0, table, x, alpha=1.0, family=0, stream=None):
+    """Residuals model - target of a table at the CUDA float64 points x
+    (family 0: Eq. mlsp2 rows; 1: Skip-SP2 rows with the output row)."""
     torch = _torch()
-    th0 = np.ascontiguousarray(np.asarray(theta_init, dtype=np.float64).reshape(-1, 4))
-    L = th0.shape[0]
-    ns = x.numel()
-    out = np.zeros_like(th0)
-    wb = lib().ftsp2_train_workspace_size(ns, L)
-    ws = torch.empty(wb, dtype=torch.uint8, device=x.device)
-    rep = TrainReport()
-    check(lib().ftsp2_train_coeffs(int(target), float(beta0), float(mu0), L, float(alpha), _ptr(x), ns,
-                                   int(iterations), int(bool(accel)),
-                                   th0.ctypes.data_as(C.POINTER(C.c_double)),
-                                   out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep), _ptr(ws), wb,
-                                   _stream(stream)), "ftsp2_train_coeffs")
-    return out, dict(iterations=rep.iterations, accepted=rep.accepted, cost0=rep.cost0, cost=rep.cost,
-                     max_err=rep.max_err, lam=rep.lam)
+    tb = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 4))
+    L = tb.shape[0] - (1 if family == 1 else 0)
+    r = torch.empty(x.numel(), dtype=torch.float64, device=x.device)
+    check(lib().ftsp2_train_residuals(int(family), int(target), float(beta0), float(mu0), L, float(alpha), _dp(tb),
+                                      _ptr(x), x.numel(), _ptr(r), _stream(stream)), "ftsp2_train_residuals")
+    return r

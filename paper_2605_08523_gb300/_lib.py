@@ -75,13 +75,19 @@ SIGNATURES = {
     "ftsp2_tile_shape": (_I, [_PINST, _I, _I, _I, _I, C.POINTER(_I), C.POINTER(_I)]),
     "ftsp2_autotune_clear": (_I, []),
     "ftsp2_train_workspace_size": (_SZ, [_I, _I]),
-    "ftsp2_train_coeffs": (_I, [_I, _D, _D, _I, _D, _VP, _I, _I, _I, C.POINTER(_D), C.POINTER(_D),
+    "ftsp2_train_coeffs": (_I, [_I, _D, _D, _I, _D, _I, C.c_uint64, _I, _I, C.POINTER(_D), C.POINTER(_D),
                                 C.POINTER(TrainReport), _VP, _SZ, _VP]),
-    "ftsp2_train_coeffs_alt": (_I, [_I, _D, _D, _I, _D, _VP, _I, _I, _I, C.POINTER(_D), C.POINTER(_D),
+    "ftsp2_train_coeffs_alt": (_I, [_I, _D, _D, _I, _D, _I, C.c_uint64, _I, _I, C.POINTER(_D), C.POINTER(_D),
                                     C.POINTER(TrainReport), _VP, _SZ, _VP]),
     "ftsp2_alt_to_mlsp2": (_I, [_I, C.POINTER(_D), C.POINTER(_D)]),
-    "ftsp2_train_coeffs_skip": (_I, [_I, _D, _D, _I, _D, _VP, _I, _I, _I, C.POINTER(_D), C.POINTER(_D),
+    "ftsp2_train_coeffs_skip": (_I, [_I, _D, _D, _I, _D, _I, C.c_uint64, _I, _I, C.POINTER(_D), C.POINTER(_D),
                                      C.POINTER(TrainReport), _VP, _SZ, _VP]),
+    "ftsp2_train_samples": (_I, [_D, _D, _I, C.c_uint64, C.POINTER(_D)]),
+    "ftsp2_train_init": (_I, [_I, _D, _D, C.POINTER(_D)]),
+    "ftsp2_train_init_alt": (_I, [_I, _D, C.POINTER(_D)]),
+    "ftsp2_mlsp2_to_skip": (_I, [_I, C.POINTER(_D), C.POINTER(_D)]),
+    "ftsp2_layer_count": (_D, [_D]),
+    "ftsp2_train_residuals": (_I, [_I, _I, _D, _D, _I, _D, C.POINTER(_D), _VP, _I, _VP, _VP]),
     "ftsp2_train_residual_jacobian": (_I, [_I, _D, _D, _I, _D, C.POINTER(_D), _VP, _I, _VP, _VP, _VP]),
     "ftsp2_train_normal_equations": (_I, [_VP, _I, _I, _VP, _VP, _SZ, _VP]),
     "ftsp2_profile_layers": (_I, [_I]),

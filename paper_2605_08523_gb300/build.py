@@ -17,7 +17,8 @@ LIB = os.path.join(HERE, "libftsp2.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]
-SOURCES = ["k_setup.cu", "k_layer_tc.cu", "k_layer_simt.cu", "k_train.cu", "k_lanczos.cu", "ftsp2_api.cu"]
+SOURCES = ["k_setup.cu", "k_layer_tc.cu", "k_layer_simt.cu", "k_train.cu", "k_lanczos.cu", "train_inputs.cu",
+           "ftsp2_api.cu"]
 
 
 def nvcc() -> str:

@@ -855,6 +855,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
 // ------------------------------------------------------------------------------
 struct TrainLayout {
     size_t M, R, Rh, G, part, apart, v, out, amax;
+    size_t X;             // the sample points (built by the library)
     size_t total;
     int nchunks;
 };
@@ -878,6 +879,7 @@ static TrainLayout train_layout(int ns, int L) {
     t.v = take(sizeof(double) * np);
     t.out = take(sizeof(double) * np);
     t.amax = take(sizeof(double) * 80);
+    t.X = take(sizeof(double) * ns);
     t.total = off;
     return t;
 }
@@ -1608,36 +1610,126 @@ static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int
     return FTSP2_OK;
 }
 
-ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, double alpha, const double* dX,
-                                int nsamples, int iterations, int accel, const double* theta_init,
-                                double* theta_out, ftsp2_train_report* rep, void* dWork, size_t work_bytes,
-                                void* stream) {
-    return lm_train(FORM_MLSP2, target, beta0, mu0, L, alpha, dX, nsamples, iterations, accel, theta_init, theta_out,
-                    rep, dWork, work_bytes, stream);
-}
-
-ftsp2_status ftsp2_train_coeffs_alt(int target, double beta0, double mu0, int L, double alpha, const double* dX,
-                                    int nsamples, int iterations, int accel, const double* alt_init, double* alt_out,
-                                    ftsp2_train_report* rep, void* dWork, size_t work_bytes, void* stream) {
-    return lm_train(FORM_ALT, target, beta0, mu0, L, alpha, dX, nsamples, iterations, accel, alt_init, alt_out, rep,
-                    dWork, work_bytes, stream);
-}
-
-ftsp2_status ftsp2_train_coeffs_skip(int target, double beta0, double mu0, int L, double alpha, const double* dX,
-                                     int nsamples, int iterations, int accel, const double* skip_init,
-                                     double* skip_out, ftsp2_train_report* rep, void* dWork, size_t work_bytes,
-                                     void* stream) {
-    if (L < 1 || L > kMaxLayers - 1) return FTSP2_E_ARG;
+// The sample set (built on the host, copied into the workspace) and the
+// default start of each form, then the LM fit on the device.
+static ftsp2_status train_entry(int form, int target, double beta0, double mu0, int L, double alpha, int nsamples,
+                                uint64_t seed, int iterations, int accel, const double* p_init, double* p_out,
+                                ftsp2_train_report* rep, void* dWork, size_t work_bytes, void* stream) {
+    if (nsamples < 1 || !dWork || !p_out || !(beta0 > 0.0) || !(mu0 > 0.0 && mu0 < 1.0)) return FTSP2_E_ARG;
+    if (L < 1 || L > (form == FORM_SKIP ? kMaxLayers - 1 : kMaxLayers)) return FTSP2_E_ARG;
+    const int train_L = form == FORM_SKIP ? L + 1 : L;       // rows of the Jacobian buffers
+    const TrainLayout tl = train_layout(nsamples, train_L);
+    if (work_bytes < tl.total) return FTSP2_E_WORKSPACE;
+    std::vector<double> x((size_t)nsamples);
+    train_sample_grid(beta0, mu0, nsamples, seed, x.data());
+    double* dX = reinterpret_cast<double*>(static_cast<uint8_t*>(dWork) + tl.X);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(dX, x.data(), sizeof(double) * nsamples, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return FTSP2_E_CUDA;
+    std::vector<double> init;
+    if (!p_init) {
+        if (form == FORM_MLSP2) {
+            init.resize(4 * L);
+            train_init_mlsp2(L, beta0, mu0, init.data());
+        } else if (form == FORM_ALT) {
+            init.resize(2 * L + 2);
+            train_init_alt(L, mu0, init.data());
+        } else {
+            std::vector<double> th(4 * L);
+            train_init_mlsp2(L, beta0, mu0, th.data());
+            init.resize(4 * L + 4);
+            mlsp2_to_skip(L, th.data(), init.data());
+        }
+        p_init = init.data();
+    }
+    if (form != FORM_SKIP)
+        return lm_train(form, target, beta0, mu0, L, alpha, dX, nsamples, iterations, accel, p_init, p_out, rep,
+                        dWork, work_bytes, stream);
     // the table's (L + 1) x 4 rows: the output row's last two entries are unused
     std::vector<double> p(4 * L + 2), out(4 * L + 2);
-    if (!skip_init || !skip_out) return FTSP2_E_ARG;
-    std::copy(skip_init, skip_init + 4 * L + 2, p.begin());
+    std::copy(p_init, p_init + 4 * L + 2, p.begin());
     const ftsp2_status st = lm_train(FORM_SKIP, target, beta0, mu0, L, alpha, dX, nsamples, iterations, accel,
                                      p.data(), out.data(), rep, dWork, work_bytes, stream);
     if (st != FTSP2_OK) return st;
-    std::copy(out.begin(), out.end(), skip_out);
-    skip_out[4 * L + 2] = skip_out[4 * L + 3] = 0.0;
+    std::copy(out.begin(), out.end(), p_out);
+    p_out[4 * L + 2] = p_out[4 * L + 3] = 0.0;
     return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_train_coeffs(int target, double beta0, double mu0, int L, double alpha, int nsamples,
+                                uint64_t seed, int iterations, int accel, const double* theta_init,
+                                double* theta_out, ftsp2_train_report* rep, void* dWork, size_t work_bytes,
+                                void* stream) {
+    return train_entry(FORM_MLSP2, target, beta0, mu0, L, alpha, nsamples, seed, iterations, accel, theta_init,
+                       theta_out, rep, dWork, work_bytes, stream);
+}
+
+ftsp2_status ftsp2_train_coeffs_alt(int target, double beta0, double mu0, int L, double alpha, int nsamples,
+                                    uint64_t seed, int iterations, int accel, const double* alt_init,
+                                    double* alt_out, ftsp2_train_report* rep, void* dWork, size_t work_bytes,
+                                    void* stream) {
+    return train_entry(FORM_ALT, target, beta0, mu0, L, alpha, nsamples, seed, iterations, accel, alt_init, alt_out,
+                       rep, dWork, work_bytes, stream);
+}
+
+ftsp2_status ftsp2_train_coeffs_skip(int target, double beta0, double mu0, int L, double alpha, int nsamples,
+                                     uint64_t seed, int iterations, int accel, const double* skip_init,
+                                     double* skip_out, ftsp2_train_report* rep, void* dWork, size_t work_bytes,
+                                     void* stream) {
+    return train_entry(FORM_SKIP, target, beta0, mu0, L, alpha, nsamples, seed, iterations, accel, skip_init,
+                       skip_out, rep, dWork, work_bytes, stream);
+}
+
+ftsp2_status ftsp2_train_residuals(int family, int target, double beta0, double mu0, int L, double alpha,
+                                   const double* table, const double* dX, int npoints, double* dR, void* stream) {
+    if ((target != FTSP2_TARGET_FERMI && target != FTSP2_TARGET_ENTROPY) || !table || !dX || !dR || npoints < 1)
+        return FTSP2_E_ARG;
+    if (family != FTSP2_FAMILY_MLSP2 && family != FTSP2_FAMILY_SKIP) return FTSP2_E_ARG;
+    const int nv = family == FTSP2_FAMILY_SKIP ? 4 * L + 2 : 4 * L;
+    if (L < 1 || L > (family == FTSP2_FAMILY_SKIP ? kMaxLayers - 1 : kMaxLayers)) return FTSP2_E_ARG;
+    ThetaParam tp;
+    std::memset(&tp, 0, sizeof(tp));
+    for (int i = 0; i < nv; ++i) {
+        if (!std::isfinite(table[i])) return FTSP2_E_ARG;
+        tp.v[i] = table[i];
+    }
+    return from_cuda(launch_train_residual(target, beta0, mu0, L, alpha, tp, dX, npoints, dR,
+                                           static_cast<cudaStream_t>(stream), family));
+}
+
+ftsp2_status ftsp2_train_samples(double beta0, double mu0, int nsamples, uint64_t seed, double* x_out) {
+    if (nsamples < 1 || !x_out || !(beta0 > 0.0) || !(mu0 > 0.0 && mu0 < 1.0)) return FTSP2_E_ARG;
+    train_sample_grid(beta0, mu0, nsamples, seed, x_out);
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_train_init(int L, double beta0, double mu0, double* theta_out) {
+    if (L < 1 || L > kMaxLayers || !theta_out || !(beta0 > 0.0) || !(mu0 > 0.0 && mu0 < 1.0)) return FTSP2_E_ARG;
+    train_init_mlsp2(L, beta0, mu0, theta_out);
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_train_init_alt(int L, double mu0, double* alt_out) {
+    if (L < 1 || L > kMaxLayers || !alt_out || !(mu0 > 0.0 && mu0 < 1.0)) return FTSP2_E_ARG;
+    train_init_alt(L, mu0, alt_out);
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_mlsp2_to_skip(int L, const double* theta, double* skip_out) {
+    if (L < 1 || L > kMaxLayers - 1 || !theta || !skip_out) return FTSP2_E_ARG;
+    for (int i = 0; i < 4 * L; ++i)
+        if (!std::isfinite(theta[i])) return FTSP2_E_ARG;
+    for (int i = 0; i < L; ++i)
+        if (theta[4 * i] == 0.0) return FTSP2_E_ARG;        // a linear layer has no square form
+    mlsp2_to_skip(L, theta, skip_out);
+    return FTSP2_OK;
+}
+
+double ftsp2_layer_count(double beta_p) {
+    // Eq. layer count: n_l = ln(beta'/4) / ln(2 phi), phi = 1/varphi (Sec. IV B)
+    if (!(beta_p > 0.0)) return NAN;
+    const double phi = 2.0 / (1.0 + std::sqrt(5.0));
+    return std::log(beta_p / 4.0) / std::log(2.0 * phi);
 }
 
 ftsp2_status ftsp2_alt_to_mlsp2(int L, const double* alt, double* theta_out) {

@@ -289,6 +289,18 @@ cudaError_t launch_train_absmax(const double* dR, int ns, double* dPart, double*
 
 void count_launch(int n = 1);
 
+// --- inputs of the training built by the library (train_inputs.cu, host) ----------
+// N sample points of [0, 1] at the quantiles of p = 1 + |f'| (seed 0: cell
+// midpoints; else splitmix64-drawn positions inside the N cells)
+void train_sample_grid(double beta0, double mu0, int N, uint64_t seed, double* x);
+// starting tables: the SP2-mu sequence at mu0 with the slope-matching
+// contraction in layer 0 (L rows of 4), the same sequence in the one-term form
+// (L + 1 rows of 2), and the Appendix embedding of Eq. mlsp2 rows in Skip-SP2
+// (L + 1 rows of 4)
+void train_init_mlsp2(int L, double beta0, double mu0, double* theta);
+void train_init_alt(int L, double mu0, double* alt);
+void mlsp2_to_skip(int L, const double* theta, double* tab);
+
 // Element offset of (r, c) inside one P x P slab of the FP32 state Z, A (P a
 // multiple of 128).  The slab is cut into blocks of 32 rows x 8 columns (1 KB),
 // stored block row by block row; a block holds two 32 x 4 halves, each with the

@@ -20,8 +20,9 @@ Two groups of tables:
   L = ceil(layer count (Eq. layer count)) + 2 layers, which ragged batches of
   rotated spectra need once the Gershgorin width inflates beta'.
 
-Every fit uses 1e5 fixed samples from p ~ 1 + |f'| (training.sample_points) and
-Levenberg-Marquardt with geodesic acceleration (ftsp2_train_coeffs).  The max
+Every fit uses the library's 1e5 fixed samples from p ~ 1 + |f'|
+(ftsp2_train_samples, seed 0) and Levenberg-Marquardt with geodesic
+acceleration (ftsp2_train_coeffs).  The max
 error of each table is measured on a uniform grid of 2e6 points in [0, 1].
 """
 from __future__ import annotations
@@ -39,10 +40,12 @@ ALPHA = 0.842704
 MU0 = 1.0 / 3.0
 
 
-def max_error(ft, target, beta0, mu0, theta, alpha, grid=2_000_001):
+def max_error(ft, target, beta0, mu0, theta, alpha, grid=2_000_001, family=0):
+    """max |model - target| of a table on a uniform grid of [0, 1], evaluated
+    by the library (ftsp2_train_residuals)."""
     import torch
     x = torch.linspace(0.0, 1.0, grid, dtype=torch.float64, device="cuda")
-    r, _ = ft.ftsp2_train_residual_jacobian(target, beta0, mu0, theta, x, alpha=alpha, with_jacobian=False)
+    r = ft.ftsp2_train_residuals(target, beta0, mu0, theta, x, alpha=alpha, family=family)
     return float(r.abs().max())
 
 
@@ -108,13 +111,9 @@ def main_alt(outdir: str, iterations: int = 3000):
 
 
 def skip_max_error(target, beta0, mu0, tab, alpha, grid=400_001):
-    """max |model - target| of a Skip-SP2 table on a uniform grid, evaluated
-    with the library's own training kernel (residuals only)."""
-    import torch
+    """max |model - target| of a Skip-SP2 table on a uniform grid."""
     import paper_2605_08523_gb300 as ft
-    x = torch.linspace(0.0, 1.0, grid, dtype=torch.float64, device="cuda")
-    _, rep = ft.ftsp2_train_coeffs_skip(target, beta0, mu0, tab, x, iterations=0, accel=False, alpha=alpha)
-    return rep["max_err"]
+    return max_error(ft, target, beta0, mu0, tab, alpha, grid=grid, family=1)
 
 
 def main_skip(outdir: str, iterations: int = 3000):

@@ -72,11 +72,13 @@ def test_training_in_one_term_form_matches_oracle(ft):
     x = train.sample_grid(4000, beta0, mu0)
     a0 = altform.sp2_alt(mu0, L)
     ref, hist = altform.lm_fit(a0, x, "fermi", beta0, mu0, iters=8, accel=False)
-    got, rep = ft.ftsp2_train_coeffs_alt(0, beta0, mu0, a0, torch.from_numpy(x).cuda(), iterations=8, accel=False)
+    # the library's own samples and start (nsamples = 4000, seed 0, no start
+    # table: ftsp2_train_init_alt) are the oracle's, to 1e-15 (tests/test_train_inputs.py)
+    got, rep = ft.ftsp2_train_coeffs_alt(0, beta0, mu0, L=L, nsamples=4000, iterations=8, accel=False)
     assert rep["accepted"] == sum(1 for h in hist if h[2])
     assert np.max(np.abs(got - ref)) < 1e-6 * max(1.0, np.max(np.abs(ref)))
     assert abs(rep["cost"] - hist[-1][0]) <= 1e-6 * hist[-1][0]
     # with geodesic acceleration the cost falls at least as far as without
-    got_a, rep_a = ft.ftsp2_train_coeffs_alt(0, beta0, mu0, a0, torch.from_numpy(x).cuda(), iterations=8, accel=True)
+    got_a, rep_a = ft.ftsp2_train_coeffs_alt(0, beta0, mu0, alt_init=a0, nsamples=4000, iterations=8, accel=True)
     assert rep_a["cost"] <= 1.05 * rep["cost"]
     assert abs(rep_a["max_err"] - altform.max_error(got_a, "fermi", beta0, mu0, grid=4001)) < 0.5 * rep_a["max_err"] + 1e-9

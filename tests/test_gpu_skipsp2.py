@@ -123,11 +123,12 @@ def test_skip_training_matches_oracle(ft):
     x = train.sample_grid(4000, beta0, mu0)
     t0 = skipsp2.from_mlsp2(train.init_from_sp2(L, beta0, mu0))
     ref, hist = skipsp2.lm_fit(t0, x, "fermi", beta0, mu0, iters=8, accel=False)
-    got, rep = ft.ftsp2_train_coeffs_skip(0, beta0, mu0, t0, torch.from_numpy(x).cuda(), iterations=8, accel=False)
+    # no start table: the library embeds its own SP2 start (= the oracle's, to 1e-15)
+    got, rep = ft.ftsp2_train_coeffs_skip(0, beta0, mu0, L=L, nsamples=4000, iterations=8, accel=False)
     assert rep["accepted"] == sum(1 for h in hist if h[2])
     assert np.max(np.abs(got - ref)) < 1e-6 * max(1.0, np.max(np.abs(ref)))
     assert abs(rep["cost"] - hist[-1][0]) <= 1e-6 * hist[-1][0]
-    got_e, rep_e = ft.ftsp2_train_coeffs_skip(1, beta0, mu0, got, torch.from_numpy(x).cuda(), iterations=4,
+    got_e, rep_e = ft.ftsp2_train_coeffs_skip(1, beta0, mu0, skip_init=got, nsamples=4000, iterations=4,
                                               accel=True, alpha=0.842704)
     ref_e = skipsp2.max_error(got_e, "entropy", beta0, mu0, alpha=0.842704, grid=4001)
     assert abs(rep_e["max_err"] - ref_e) < 0.5 * ref_e + 1e-9

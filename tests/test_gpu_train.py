@@ -52,12 +52,15 @@ def test_gram_matches_numpy(ft):
     assert np.max(np.abs(G - G.T)) == 0.0
 
 
-def test_one_lm_step_matches_oracle(ft):
+@pytest.mark.parametrize("seed", [0, 5])
+def test_one_lm_step_matches_oracle(ft, seed):
+    # theta_init = NULL: the library builds the samples (nsamples, seed) and
+    # the SP2 start itself; the oracle takes the same steps from its own
     L, beta0, mu0 = 12, 40.0, 1 / 3
-    x = train.sample_grid(4000, beta0, mu0)
+    x = train.sample_grid(4000, beta0, mu0, seed=seed)
     th0 = train.init_from_sp2(L, beta0, mu0)
     th_or, hist = train.lm_fit(th0, x, beta0=beta0, mu0=mu0, iters=1, accel=False)
-    th_gpu, rep = ft.ftsp2_train_coeffs(ft.TARGET_FERMI, beta0, mu0, th0, torch.from_numpy(x).cuda(),
+    th_gpu, rep = ft.ftsp2_train_coeffs(ft.TARGET_FERMI, beta0, mu0, L=L, nsamples=4000, seed=seed,
                                         iterations=1, accel=False)
     assert rep["accepted"] == int(hist[0][2])
     assert np.max(np.abs(th_gpu - th_or)) < 1e-8 * max(1.0, np.max(np.abs(th_or)))
@@ -71,8 +74,7 @@ def test_training_gain_over_sp2(ft):
     L, beta0, mu0 = 12, 40.0, 1 / 3
     x = train.sample_grid(20000, beta0, mu0)
     th0 = train.init_from_sp2(L, beta0, mu0)
-    th, rep = ft.ftsp2_train_coeffs(ft.TARGET_FERMI, beta0, mu0, th0, torch.from_numpy(x).cuda(),
-                                    iterations=150, accel=True)
+    th, rep = ft.ftsp2_train_coeffs(ft.TARGET_FERMI, beta0, mu0, L=L, nsamples=20000, iterations=150, accel=True)
     e_sp2 = train.max_error(np.array(sp2.sp2_table(mu0, L)), beta0=beta0, mu0=mu0, grid=20001)
     e_tr = train.max_error(th, beta0=beta0, mu0=mu0, grid=20001)
     assert e_sp2 > 1e-1 and e_tr < 1e-4

@@ -112,3 +112,52 @@ def test_training_improves_on_sp2_beta40():
                             iters=150, accel=True)
     e1 = train.max_error(th, beta0=beta0, mu0=mu0, grid=20001)
     assert e0 > 5e-2 and e1 < 1e-4
+
+
+def _cdf_closed_form(x, beta0, mu0):
+    # F(x) for p ~ 1 + f' (f the increasing logistic, f' > 0): integral of p
+    # from 0 to x over its value at 1
+    f = lambda t: 1.0 / (1.0 + np.exp(-beta0 * (t - mu0)))
+    return (x + f(x) - f(0.0)) / (1.0 + f(1.0) - f(0.0))
+
+
+@pytest.mark.parametrize("seed", [0, 7, 12345])
+def test_sample_grid_points_in_their_quantile_cells(seed):
+    # Point s lies in the s-th of N equal-probability cells of p (closed-form
+    # CDF); seed 0 puts it at the cell's middle, a seed draws its position.
+    N, beta0, mu0 = 2000, 200.0, 1 / 3
+    x = train.sample_grid(N, beta0, mu0, seed=seed)
+    q = _cdf_closed_form(x, beta0, mu0) * N - np.arange(N)
+    assert np.all(q > -1e-6) and np.all(q < 1 + 1e-6)
+    if seed == 0:
+        assert np.max(np.abs(q - 0.5)) < 1e-4
+    else:
+        assert np.std(q) > 0.2          # positions spread over the cells
+        assert np.array_equal(x, train.sample_grid(N, beta0, mu0, seed=seed))
+
+
+def test_seeded_grid_uses_splitmix64():
+    # the cell offsets are the generator's published outputs (first value of
+    # splitmix64 for state 1: 0x910a2dec89025cc1)
+    from oracle import lanczos
+    assert lanczos.splitmix64(1) == 0x910A2DEC89025CC1
+    x = train.sample_grid(4, 50.0, 0.4, weighting="uniform", seed=1)
+    u0 = (lanczos.splitmix64(1) >> 11) * 2.0 ** -53
+    assert abs(x[0] - u0 / 4) < 1e-6
+
+
+@pytest.mark.parametrize("L,beta0", [(12, 40.0), (24, 200.0), (30, 3000.0)])
+def test_sp2_init_slope_is_beta0_over_4(L, beta0):
+    # the contraction folded into layer 0 makes the slope at mu0 equal to the
+    # target's beta0 / 4 whenever the SP2 sequence alone is steeper (central
+    # differences of the composed polynomial, independent of the chain rule)
+    mu0 = 1 / 3
+    th = train.init_from_sp2(L, beta0, mu0)
+    s_sp2 = sp2.slope_at(np.array(sp2.sp2_table(mu0, L)), mu0, h=1e-9)
+    s = sp2.slope_at(th, mu0, h=1e-9)
+    if s_sp2 > beta0 / 4:
+        assert abs(s - beta0 / 4) < 1e-5 * beta0
+    else:
+        assert np.array_equal(th, np.array(sp2.sp2_table(mu0, L)))
+    # mu0 stays a point of the SP2 trajectory: the same image as without contraction
+    assert abs(mlsp2.mlsp2_scalar([mu0], th)[0] - mlsp2.mlsp2_scalar([mu0], sp2.sp2_table(mu0, L))[0]) < 1e-12
