@@ -310,7 +310,9 @@ ftsp2_status ftsp2_density_entropy(const double* dH, const ftsp2_instance* inst,
  *     FTSP2_SYNC is refused (FTSP2_E_ARG); read dRec instead.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  A first call made while `stream` is being
+ *     captured is refused with FTSP2_E_ARG, before the lookup and before any
+ *     launch.
  *   - Every call uses the same array and leaves its contents behind; each call
  *     rewrites everything it reads before reading it.  Calls that overlap on
  *     the GPU (other streams, other host threads) race on the array: serialise

@@ -1304,8 +1304,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 // Device address of the array on the current device.  In host code the name
 // g_noalloc_scratch is only a host-side stand-in, so the address is looked up
 // with cudaGetSymbolAddress once per device (with that device current) and
-// cached; the lookup allocates nothing.
-static ftsp2_status noalloc_scratch(void** ws, size_t* bytes) {
+// cached; the lookup allocates nothing.  The lookup may load the module, which
+// must not happen inside a stream capture: a first call on a device made while
+// `stream` is capturing is refused (FTSP2_E_ARG) before the lookup.
+static ftsp2_status noalloc_scratch(void** ws, size_t* bytes, cudaStream_t stream) {
     constexpr int kMaxDevices = 64;
     static std::mutex mu;
     static void* addr[kMaxDevices] = {nullptr};
@@ -1314,6 +1316,9 @@ static ftsp2_status noalloc_scratch(void** ws, size_t* bytes) {
     if (dev < 0 || dev >= kMaxDevices) return FTSP2_E_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(mu);
     if (!addr[dev]) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return FTSP2_E_CUDA;
+        if (cap != cudaStreamCaptureStatusNone) return FTSP2_E_ARG;
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FTSP2_E_CUDA;
         addr[dev] = p;
@@ -1337,7 +1342,7 @@ ftsp2_status ftsp2_density_noalloc(const double* dH, const ftsp2_instance* inst,
     if (flags & FTSP2_SYNC) return FTSP2_E_ARG;
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    const ftsp2_status st = noalloc_scratch(&ws, &ws_bytes);
+    const ftsp2_status st = noalloc_scratch(&ws, &ws_bytes, static_cast<cudaStream_t>(stream));
     if (st != FTSP2_OK) return st;
     // run() checks the plan against ws_bytes and returns FTSP2_E_WORKSPACE,
     // before launching anything, when the batch needs more scratch than the array.

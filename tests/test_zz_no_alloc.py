@@ -67,11 +67,13 @@ def test_noalloc_matches_workspace_entry_point(ft, mode):
         assert torch.allclose(tr, ref.trace, rtol=0, atol=1e-9)
 
 
-def test_noalloc_single_instance_largest_supported(ft):
+@pytest.mark.parametrize("n", [512, 640])
+def test_noalloc_single_instance_up_to_the_limit(ft, n):
+    # n = 640 is the largest FP16X2 instance the 8 MiB array holds
     ms = ft.ModelSet()
-    H = wl.chain_1d(512, 3)
+    H = wl.chain_1d(n, 3)
     host, d_inst, Hd, total = _inputs(ft, [H], [0.0], [0.1])
-    ref = ft.Solver([512], [0.0], [0.1], ms, mode="fp16x2", want=1)
+    ref = ft.Solver([n], [0.0], [0.1], ms, mode="fp16x2", want=1)
     ref.run(Hd, sync=True)
     for call in range(2):
         st, D, tr, rec = _run_noalloc(ft, ms, host, d_inst, Hd, 1, total, "fp16x2")
@@ -79,9 +81,10 @@ def test_noalloc_single_instance_largest_supported(ft):
         assert torch.equal(D, ref.D)
 
 
-def test_noalloc_rejects_oversize_and_sync(ft):
+@pytest.mark.parametrize("n", [641, 1024])
+def test_noalloc_rejects_oversize_and_sync(ft, n):
+    # n = 641 pads to 768 and needs more than the array: refused before any launch
     ms = ft.ModelSet()
-    n = 1024
     H = np.eye(n)
     host, d_inst, Hd, total = _inputs(ft, [H], [0.5], [0.1])
     st, D, _, _ = _run_noalloc(ft, ms, host, d_inst, Hd, 1, total, "fp16x2")
@@ -91,3 +94,51 @@ def test_noalloc_rejects_oversize_and_sync(ft):
     st = ft.lib().ftsp2_density_noalloc(_p(Hd), host, _p(d_inst), 1, ms.handle, ft.FP16X2, ft.SYNC, _p(D), None,
                                         _p(rec), None)
     assert st == ft._lib.E_ARG
+
+
+_FIRST_CALL_WHILE_CAPTURING = r"""
+import ctypes as C, json, sys
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import paper_2605_08523_gb300 as ft
+import workloads as wl
+from paper_2605_08523_gb300 import _instances
+ms = ft.ModelSet()
+H = wl.chain_1d(128, 5)
+host, _, _ = _instances([128], [0.0], [0.1])
+d_inst = torch.from_numpy(np.frombuffer(bytes(host), dtype=np.uint8).copy()).cuda()
+Hd = torch.from_numpy(H.ravel().copy()).cuda()
+D = torch.full((128 * 128,), float("nan"), dtype=torch.float32, device="cuda")
+rec = torch.zeros(64, dtype=torch.uint8, device="cuda")
+p = lambda t: C.c_void_p(t.data_ptr())
+s = torch.cuda.Stream()
+torch.cuda.synchronize()
+g = torch.cuda.CUDAGraph()
+with torch.cuda.graph(g, stream=s):
+    st_cap = ft.lib().ftsp2_density_noalloc(p(Hd), host, p(d_inst), 1, ms.handle, ft.FP16X2, 0, p(D), None, p(rec),
+                                            C.c_void_p(s.cuda_stream))
+untouched = bool(torch.isnan(D).all())
+st = ft.lib().ftsp2_density_noalloc(p(Hd), host, p(d_inst), 1, ms.handle, ft.FP16X2, 0, p(D), None, p(rec),
+                                    C.c_void_p(torch.cuda.current_stream().cuda_stream))
+torch.cuda.synchronize()
+print(json.dumps({"st_cap": st_cap, "untouched": untouched, "st": st, "finite": bool(torch.isfinite(D).all())}))
+"""
+
+
+def test_noalloc_first_call_while_capturing_is_refused(ft, tmp_path):
+    # In a fresh process the array's address is not known yet: a first call
+    # made while the stream is being captured is refused before the lookup
+    # (which could load the module inside the capture), and the next ordinary
+    # call works.
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    prog = tmp_path / "first_call.py"
+    prog.write_text(_FIRST_CALL_WHILE_CAPTURING)
+    r = subprocess.run([sys.executable, str(prog), root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    assert out["st_cap"] == ft._lib.E_ARG and out["untouched"]
+    assert out["st"] == 0 and out["finite"]
