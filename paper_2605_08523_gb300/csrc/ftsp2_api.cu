@@ -595,7 +595,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         lz.inst = dInst;
         lz.iw = iw;
         lanczos_bind(lz, W + L.lanczos, nb, L.P);
-        launch_lanczos(lz, maxn, s);
+        launch_lanczos(lz, maxn, di.sms, s);
     }
     launch_decide(sa, s);
 
@@ -1094,9 +1094,8 @@ ftsp2_status ftsp2_rescale(const double* dH, const ftsp2_instance* inst, const f
         maxn = std::max(maxn, inst[b].n);
     }
     const int P = (int)align_up((size_t)maxn, kPad);
-    // FTSP2_LANCZOS: Lanczos buffers, then the FP32 copy of H (same element offsets)
-    size_t h32_elems = 0;
-    for (int b = 0; b < nb; ++b) h32_elems = std::max(h32_elems, (size_t)inst[b].offset + (size_t)inst[b].n * inst[b].n);
+    // FTSP2_LANCZOS: Lanczos buffers, then the FP32 copy of H (P x P slab per instance)
+    const size_t h32_elems = (size_t)nb * P * P;
     const size_t lz_off = rescale_ws_bytes(nb), h32_off = lz_off + lanczos_ws_bytes(nb, P);
     if ((flags & FTSP2_LANCZOS) && ws_bytes < h32_off + sizeof(float) * h32_elems) return FTSP2_E_WORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1106,6 +1105,7 @@ ftsp2_status ftsp2_rescale(const double* dH, const ftsp2_instance* inst, const f
     sa.H = dH;
     sa.inst = dInst;
     sa.nb = nb;
+    sa.P = P;
     sa.Lmax = set->Lmax;
     sa.nchains = 1;
     sa.BN = 128;
@@ -1128,7 +1128,7 @@ ftsp2_status ftsp2_rescale(const double* dH, const ftsp2_instance* inst, const f
         lz.inst = dInst;
         lz.iw = sa.iw;
         lanczos_bind(lz, W + lz_off, nb, P);
-        launch_lanczos(lz, maxn, s);
+        launch_lanczos(lz, maxn, di.sms, s);
     }
     launch_decide(sa, s);
     if (cudaGetLastError() != cudaSuccess) return FTSP2_E_CUDA;

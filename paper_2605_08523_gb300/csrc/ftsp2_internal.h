@@ -118,7 +118,7 @@ struct SetupArgs {
     Tile* tiles_ref;
     ftsp2_rescale_rec* rec;
     int* status;
-    float* h32;                       // nullable: FP32 copy of H (same element offsets), for FTSP2_LANCZOS
+    float* h32;                       // nullable: FP32 copy of H for FTSP2_LANCZOS, slab b at b P^2, row pitch P
     int* done;                        // kMaxLayers x kMaxChains counters, zeroed by prep
 };
 
@@ -166,7 +166,7 @@ constexpr int kLzSteps = 24;          // Lanczos steps (fewer when n is smaller)
 constexpr int kLzRows = 8;            // matrix rows per block of the matvec (one warp each)
 constexpr int kLzStopped = 0x10000;   // state flag: invariant subspace reached
 struct LanczosArgs {
-    const float* H32;                 // FP32 copy of H written by the Gershgorin pass
+    const float* H32;                 // FP32 copy of H written by the Gershgorin pass (slab b at b P^2, pitch P)
     const ftsp2_instance* inst;
     InstWork* iw;                     // Gershgorin keys in, tightened keys out
     int nb, P, RB;                    // RB = ceil(P / kLzRows) partial sums per instance
@@ -178,7 +178,7 @@ struct LanczosArgs {
     double* part;                     // [nb][RB]
     int* state;                       // [nb] steps done | kLzStopped
 };
-void launch_lanczos(const LanczosArgs& a, int max_n, cudaStream_t s);
+void launch_lanczos(const LanczosArgs& a, int max_n, int sms, cudaStream_t s);
 // bytes of the Lanczos buffers for nb instances of pitch P (1024-aligned pieces)
 size_t lanczos_ws_bytes(int nb, int P);
 // carve the buffers out of ws (at least lanczos_ws_bytes(nb, P) bytes)

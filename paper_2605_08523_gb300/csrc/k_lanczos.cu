@@ -22,9 +22,17 @@
 //          lo = theta_min - r_min - delta, hi = theta_max + r_max + delta,
 //          delta = 0.01 (theta_max - theta_min) + 1e-6 max(|theta_min|, |theta_max|),
 //          intersected with Gershgorin (each end kept inside it).
+// Two launch shapes: batches whose instances all have n <= kLzSmallN run every
+// step of an instance inside one CTA (vectors in shared memory, one CTA per
+// SM so that the rows each CTA re-reads at every step can stay in L2); larger
+// instances run each step as a multi-block matrix-vector launch plus an update
+// launch.  The FP32 copy of H is stored per instance as a P x P slab with row
+// pitch P, so every row starts 16-byte aligned.
 // Reductions are in fixed order (deterministic).  The interval is not a
 // rigorous enclosure; its safety terms (residual bound and the 1 % margin) are
 // checked against the eigenvalues of the workload families in the tests.
+#include <algorithm>
+
 #include "ftsp2_internal.h"
 
 namespace ftsp2 {
@@ -38,7 +46,8 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
     return z ^ (z >> 31);
 }
 
-// fixed-order block sum of one double per thread (kLzThreads threads)
+// fixed-order block sum of one double per thread (T threads)
+template <int T = kLzThreads>
 __device__ double block_sum(double v, double* sh) {
     const int t = threadIdx.x;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -46,11 +55,11 @@ __device__ double block_sum(double v, double* sh) {
     __syncthreads();
     double s = 0.0;
     if (t == 0) {
-        for (int w = 0; w < kLzThreads / 32; ++w) s += sh[w];
-        sh[kLzThreads / 32] = s;
+        for (int w = 0; w < T / 32; ++w) s += sh[w];
+        sh[T / 32] = s;
     }
     __syncthreads();
-    s = sh[kLzThreads / 32];
+    s = sh[T / 32];
     __syncthreads();
     return s;
 }
@@ -104,7 +113,7 @@ __global__ void __launch_bounds__(kLzRows * 32) lanczos_matvec_kernel(LanczosArg
     const double bprev = j > 0 ? a.ab[((size_t)b * kLzSteps + (j - 1)) * 2 + 1] : 0.0;
     double part = 0.0;
     if (row < n) {
-        const float* Hr = a.H32 + a.inst[b].offset + (size_t)row * n;
+        const float* Hr = a.H32 + ((size_t)b * a.P + row) * a.P;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
         int c = lane;
         for (; c + 96 < n; c += 128) {
@@ -168,6 +177,132 @@ __global__ void __launch_bounds__(kLzThreads) lanczos_update_kernel(LanczosArgs 
     }
 }
 
+// Small instances (every n <= kLzSmallN): one CTA runs all steps of one
+// instance at a time, with the Lanczos vectors in shared memory and the first
+// rows of H (as many as the dynamic shared memory holds) cached there too; the
+// CTAs loop over the instances.  The launch asks for enough shared memory that
+// one CTA runs per SM, so the rows of H that the resident CTAs re-read at every
+// step (one instance each, at most kLzSmallN^2 floats) stay in L2 instead of
+// streaming the whole batch from HBM 24 times.  Arithmetic as in the
+// multi-block kernels: FP32 products and row sums, FP64 vectors, dot
+// products and norms, reductions in a fixed order.
+constexpr int kLzSmallN = 1024;
+constexpr int kLzSmallThreads = 1024;
+constexpr int kLzSmallCacheBytes = 160 * 1024;
+
+__global__ void __launch_bounds__(kLzSmallThreads, 1) lanczos_small_kernel(LanczosArgs a) {
+    __shared__ double vprev[kLzSmallN], vcur[kLzSmallN], w[kLzSmallN];
+    __shared__ __align__(16) float v32[kLzSmallN];
+    __shared__ double sh[kLzSmallThreads / 32 + 1];
+    extern __shared__ float4 hcache4[];             // rows 0 .. rc - 1 of H (FP32), pitch pc
+    float* const hcache = reinterpret_cast<float*>(hcache4);
+    constexpr int NW = kLzSmallThreads / 32;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
+        const int n = a.inst[b].n;
+        const float* Hb = a.H32 + (size_t)b * a.P * a.P;
+        const int pc = (n + 3) & ~3;                 // cached row pitch (16-byte rows)
+        const int rc = min(n, (int)(kLzSmallCacheBytes / (4 * pc)));
+        for (int i = t; i < rc * pc; i += kLzSmallThreads) {
+            const int r = i / pc, c = i - r * pc;
+            hcache[i] = c < n ? Hb[(size_t)r * a.P + c] : 0.f;
+        }
+        // v_1 from the counter-based generator, v_0 = 0
+        double s = 0.0;
+        for (int i = t; i < n; i += kLzSmallThreads) {
+            const double q = 2.0 * ((double)(splitmix64((unsigned long long)i) >> 11) * 0x1.0p-53) - 1.0;
+            vcur[i] = q;
+            vprev[i] = 0.0;
+            s += q * q;
+        }
+        const double nrm = sqrt(block_sum<kLzSmallThreads>(s, sh));
+        for (int i = t; i < n; i += kLzSmallThreads) {
+            vcur[i] /= nrm;
+            v32[i] = (float)vcur[i];
+        }
+        __syncthreads();
+        double* ab = a.ab + (size_t)b * kLzSteps * 2;
+        const int steps = min(n, kLzSteps);
+        const int n4 = n >> 2;                       // whole float4 columns; the rest per lane
+        double a1 = 0.0, b1 = 0.0, bprev = 0.0;
+        int m = 0;
+        bool stop = false;
+        for (int j = 0; j < steps && !stop; ++j) {
+            // w = H v_j - beta_{j-1} v_{j-1}: two rows per warp at a time,
+            // 16-byte loads (rows of H are 16-byte aligned in both copies)
+            const float4* v4 = reinterpret_cast<const float4*>(v32);
+            for (int row = warp; row < n; row += 2 * NW) {
+                const int row2 = row + NW;
+                const bool two = row2 < n;
+                const float* Ra = row < rc ? hcache + (size_t)row * pc : Hb + (size_t)row * a.P;
+                const float* Rb = two ? (row2 < rc ? hcache + (size_t)row2 * pc : Hb + (size_t)row2 * a.P) : Ra;
+                const float4* A4 = reinterpret_cast<const float4*>(Ra);
+                const float4* B4 = reinterpret_cast<const float4*>(Rb);
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+#pragma unroll 4
+                for (int q = lane; q < n4; q += 32) {
+                    const float4 x = A4[q], y = B4[q], v = v4[q];
+                    s0 = fmaf(x.x, v.x, s0);
+                    s1 = fmaf(x.y, v.y, s1);
+                    s2 = fmaf(x.z, v.z, s2);
+                    s3 = fmaf(x.w, v.w, s3);
+                    t0 = fmaf(y.x, v.x, t0);
+                    t1 = fmaf(y.y, v.y, t1);
+                    t2 = fmaf(y.z, v.z, t2);
+                    t3 = fmaf(y.w, v.w, t3);
+                }
+                const int c = 4 * n4 + lane;
+                if (c < n) {
+                    s0 = fmaf(Ra[c], v32[c], s0);
+                    t0 = fmaf(Rb[c], v32[c], t0);
+                }
+                float sa = (s0 + s1) + (s2 + s3), sb = (t0 + t1) + (t2 + t3);
+                for (int o = 16; o > 0; o >>= 1) {
+                    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+                }
+                if (lane == 0) {
+                    w[row] = (double)sa - bprev * vprev[row];
+                    if (two) w[row2] = (double)sb - bprev * vprev[row2];
+                }
+            }
+            __syncthreads();
+            double p = 0.0;
+            for (int i = t; i < n; i += kLzSmallThreads) p += w[i] * vcur[i];
+            const double alpha = block_sum<kLzSmallThreads>(p, sh);
+            p = 0.0;
+            for (int i = t; i < n; i += kLzSmallThreads) {
+                const double wi = w[i] - alpha * vcur[i];
+                w[i] = wi;
+                p += wi * wi;
+            }
+            const double beta = sqrt(block_sum<kLzSmallThreads>(p, sh));
+            if (j == 0) {
+                a1 = alpha;
+                b1 = beta;
+            }
+            if (t == 0) {
+                ab[2 * j] = alpha;
+                ab[2 * j + 1] = beta;
+            }
+            m = j + 1;
+            stop = beta <= 1e-12 * (fabs(a1) + b1 + 1.0);      // the same on every thread
+            if (!stop) {
+                for (int i = t; i < n; i += kLzSmallThreads) {
+                    const double v = w[i] / beta;
+                    vprev[i] = vcur[i];
+                    vcur[i] = v;
+                    v32[i] = (float)v;
+                }
+                bprev = beta;
+            }
+            __syncthreads();
+        }
+        if (t == 0) a.state[b] = m | (stop ? kLzStopped : 0);
+        __syncthreads();
+    }
+}
+
 // number of eigenvalues of the m x m tridiagonal (al, be) below x (Sturm)
 __device__ int sturm_count(const double* al, const double* be, int m, double x) {
     int cnt = 0;
@@ -211,12 +346,14 @@ __device__ double edge_vector_last(const double* al, const double* be, int m, do
 
 // eigenvalue of T_m at the lower (upper) edge by multisection: the 32 lanes
 // count the eigenvalues below 32 points of the bracket, which shrinks 33-fold
-// per round
+// per round; 8 rounds leave the edge within 33^-8 < 1e-12 of the bracket (the
+// Gershgorin interval of T), far below the 1 % margin, and inside the 1e-10
+// shift of the residual bound's inverse iteration
 __device__ double edge_eigenvalue(const double* al, const double* be, int m, double lo, double hi, bool upper,
                                   int lane) {
     const int target = upper ? m : 1;
     double l = lo, h = hi;
-    for (int it = 0; it < 16; ++it) {
+    for (int it = 0; it < 8; ++it) {
         const double x = l + (h - l) * (double)(lane + 1) / 33.0;
         const bool hit = sturm_count(al, be, m, x) >= target;
         const unsigned mask = __ballot_sync(0xffffffffu, hit);
@@ -310,7 +447,19 @@ void lanczos_bind(LanczosArgs& a, uint8_t* ws, int nb, int P) {
     a.state = reinterpret_cast<int*>(ws + off);
 }
 
-void launch_lanczos(const LanczosArgs& a, int max_n, cudaStream_t s) {
+void launch_lanczos(const LanczosArgs& a, int max_n, int sms, cudaStream_t s) {
+    if (max_n <= kLzSmallN) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(lanczos_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kLzSmallCacheBytes);
+            attr = true;
+        }
+        lanczos_small_kernel<<<std::min(a.nb, std::max(1, sms)), kLzSmallThreads, kLzSmallCacheBytes, s>>>(a);
+        lanczos_bounds_kernel<<<(a.nb + 3) / 4, 128, 0, s>>>(a);
+        count_launch(2);
+        return;
+    }
     lanczos_start_kernel<<<a.nb, kLzThreads, 0, s>>>(a);
     count_launch();
     const int steps = max_n < kLzSteps ? max_n : kLzSteps;

@@ -147,8 +147,10 @@ __global__ void __launch_bounds__(kGWarps * 32) gershgorin_kernel(SetupArgs a) {
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int j = lane;
         if (a.h32) {
-            // same pass, plus the FP32 copy the Lanczos matrix-vector products read
-            float* hr = a.h32 + a.inst[b].offset + (size_t)row * n;
+            // same pass, plus the FP32 copy the Lanczos matrix-vector products
+            // read: instance b's slab of P x P floats, row pitch P (16-byte
+            // aligned rows for vector loads)
+            float* hr = a.h32 + ((size_t)b * a.P + row) * a.P;
             for (; j < n; j += 32) {
                 const double h = __ldg(Hr + j);
                 s0 += fabs(h);
