@@ -415,7 +415,7 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
         return o;
     };
     L.status = take(256);
-    L.done = take(sizeof(int) * kMaxLayers * kMaxChains);
+    L.done = take(sizeof(int) * kMaxLayers * kMaxChains * (size_t)nb);
     L.inst_work = take(sizeof(InstWork) * nb);
     L.tiles = take(sizeof(Tile) * nt);
     L.tiles_ref = need_ref ? take(sizeof(Tile) * ntr) : 0;
@@ -587,6 +587,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     // initialisation overwrites only after the bounds are final
     sa.h32 = (flags & FTSP2_LANCZOS) ? reinterpret_cast<float*>(W + L.Z[0]) : nullptr;
     sa.done = reinterpret_cast<int*>(W + L.done);
+    sa.done_layers = Lmax;
     launch_prep(sa, s);
     launch_gershgorin(sa, maxn, s);
     if (flags & FTSP2_LANCZOS) {
@@ -731,7 +732,8 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         la.mirror_all = (next_tc16 && !(flags & FTSP2_FULL_OPERANDS)) ? 0 : 1;
         la.lower_t = (!simt && prev_skips_mirror) ? 1 : 0;
         prev_skips_mirror = la.mirror_all ? 0 : 1;
-        la.done = reinterpret_cast<int*>(W + L.done);
+        la.done_inst = reinterpret_cast<int*>(W + L.done);
+        la.nb = nb;
         for (int c = 0; c < L.nchains; ++c) {
             const int rp = g & 1, wp = (g + 1) & 1;
             if (simt || rtc) la.opr[c] = all_simt ? W + L.OP[c][rp] : W + L.OPR[c][rp];
@@ -753,14 +755,18 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
         } else {
             la.tiles = pair ? tiles : tiles_ref;
             la.ntiles = pair ? L.ntiles : L.ntiles_ref;
+            la.dtab = pair ? 0 : 1;
             const int units = std::max(1, std::min(la.ntiles, pair ? di.sms / 2 : di.sms));
             la.escr = pair && L.escr_ctas >= 2 * units ? reinterpret_cast<float*>(W + L.escr) : nullptr;
             // consecutive layers of this kind in one persistent launch when each
-            // layer alone is only a few waves of tiles (at most 8: with more, the
-            // idle tail of a launch is a small share, and at n = 8192 the busier
-            // GPU ran at a lower power-capped clock, 90.2 against 83.2 ms per
-            // solve) and every unit can be resident at once (the launch's CTAs
-            // wait on one another)
+            // layer is only a few waves of tiles (at most 8), and every unit can
+            // be resident at once (the launch's CTAs wait on one another).  With
+            // more waves the idle tail of a launch is a small share, and runs
+            // measured slower: at n = 8192 the busier GPU ran at a lower
+            // power-capped clock (90.2 against 83.2 ms per solve), and on the
+            // 512-instance ragged batch (71 waves) the units drifted apart
+            // without a barrier per layer, the instances in flight at once
+            // outgrew the L2, and the batch took 34.2 against 31.0 ms.
             int m = 1, lunits = units;
             if (!(flags & FTSP2_LAYER_LAUNCHES) && g_coop_ok.load() != 0 && !(capturing && g_coop_ok.load() != 1) &&
                 la.ntiles <= 8 * units && in_run(g) &&

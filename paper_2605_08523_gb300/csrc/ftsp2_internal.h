@@ -95,7 +95,7 @@ struct InstWork {
 struct Layout {
     // all offsets in bytes from the workspace base
     size_t inst_work, tiles, tiles_ref, partials, status, lanczos;
-    size_t done;          // kMaxLayers x kMaxChains completion counters (multi-layer launches)
+    size_t done;          // completion counters of multi-layer launches: kMaxLayers x nb x kMaxChains
     size_t escr;          // deferred-epilogue scratch (escr_ctas x kEpiScratchFloats floats)
     int escr_ctas;        // 0: the pair tiles run their final epilogue inline
     size_t Z[kMaxChains], A[kMaxChains], OP[kMaxChains][2], OPR[kMaxChains][2];
@@ -119,7 +119,8 @@ struct SetupArgs {
     ftsp2_rescale_rec* rec;
     int* status;
     float* h32;                       // nullable: FP32 copy of H for FTSP2_LANCZOS, slab b at b P^2, row pitch P
-    int* done;                        // kMaxLayers x kMaxChains counters, zeroed by prep
+    int* done;                        // per-instance completion counters, zeroed by prep
+    int done_layers;                  // layers whose counters prep zeroes (done_layers x nb x kMaxChains)
 };
 
 void launch_prep(const SetupArgs& a, cudaStream_t s);
@@ -235,7 +236,12 @@ struct LayerArgs {
     int nlayers;
     int chunk_tail, tail_from;
     uint8_t* opw_alt[kMaxChains];
-    int* done;
+    // completion counters of multi-layer launches, one per (layer, instance,
+    // chain): done_inst[(g * nb + instance) * kMaxChains + chain]; an item waits
+    // for its own instance's previous layer
+    int* done_inst;
+    int nb;
+    int dtab;                         // tile table of this launch in InstWork (0 main, 1 128 x 128)
     // Time limit of one device-side wait (ns; ftsp2_set_wait_limit_ns).  A
     // dependency wait that runs out records FTSP2_E_TIMEOUT and the launch
     // finishes its work list in skip mode; a pipeline wait records it after

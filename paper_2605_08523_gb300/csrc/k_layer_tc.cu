@@ -59,9 +59,9 @@
 // last MMAs.
 // Multi-layer launches (a.nlayers > 1).  The work items are (layer, tile) in
 // layer order; every role walks the same item sequence.  An item of layer g
-// waits (producer) until all tiles of layer g - 1 of its chain have finished
-// their epilogues: each CTA counts kEpiWarps completions per tile in
-// a.done[g][chain] (accumulating warps 1 each, store warps
+// waits (producer) until all tiles of layer g - 1 of its instance and chain
+// have finished their epilogues: each CTA counts kEpiWarps completions per tile
+// in the instance's counter (accumulating warps 1 each, store warps
 // kEpiWarps / kStoreWarps each, the producer kEpiWarps for an inactive item),
 // released by a fence before the atomic and acquired by the readers, with a
 // proxy fence before the TMA loads of the new operands.  Dependencies point
@@ -692,27 +692,33 @@ __device__ __forceinline__ bool has_next_tile(const LayerArgs& a, int f, int nun
     return false;
 }
 
-// Completion counters of multi-layer launches.  An epilogue warp adds its
-// share after its stores (release: fence, then the atomic); a reader acquires.
-__device__ __forceinline__ void done_add(const LayerArgs& a, int g, int chain, int v) {
-    __threadfence();
-    atomicAdd(a.done + g * kMaxChains + chain, v);
+// Completion counters of multi-layer launches, one per (layer, instance,
+// chain): an epilogue warp adds its share after its stores (release: fence,
+// then the atomic); a reader acquires.  (A counter shared by a whole layer
+// took 16 atomics per tile from every CTA on one address, which serialised
+// ragged batches of ten thousand tiles per layer.)
+__device__ __forceinline__ int* inst_counter(const LayerArgs& a, int g, int inst, int chain) {
+    return a.done_inst + ((size_t)g * a.nb + inst) * kMaxChains + chain;
 }
-__device__ __forceinline__ int done_acquire(const LayerArgs& a, int g, int chain) {
+__device__ __forceinline__ void done_add(const LayerArgs& a, int g, int inst, int chain, int v) {
+    __threadfence();
+    atomicAdd(inst_counter(a, g, inst, chain), v);
+}
+__device__ __forceinline__ int acquire_load(const int* p) {
     int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(a.done + g * kMaxChains + chain) : "memory");
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-// Wait until layer g of `chain` is complete.  False when the call has failed
+// Wait until the counter at p reaches target.  False when the call has failed
 // (this wait ran out after a.wait_ns, which records FTSP2_E_TIMEOUT, or another
 // wait of this launch did): the producer then runs its remaining items in skip
 // mode, without loads.
-__device__ __forceinline__ bool wait_layer_done(const LayerArgs& a, int g, int chain, int target) {
-    if (done_acquire(a, g, chain) >= target) return true;
+__device__ __forceinline__ bool wait_counter(const LayerArgs& a, const int* p, int target) {
+    if (acquire_load(p) >= target) return true;
     const unsigned long long t0 = globaltimer();
     for (;;) {
         __nanosleep(256);
-        if (done_acquire(a, g, chain) >= target) return true;
+        if (acquire_load(p) >= target) return true;
         if (call_failed(a)) return false;
         if (globaltimer() - t0 > a.wait_ns) {
             record_timeout(a);
@@ -775,7 +781,10 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
     // A launch whose layers all lie below the first layer any instance starts
     // at (models with fewer layers than the set's maximum start late) has no
     // active item: every thread of both CTAs of a pair leaves at once.
-    if (a.gl + a.nlayers <= *reinterpret_cast<volatile const int*>(a.status + 1)) return;
+    const int first_layer = *reinterpret_cast<volatile const int*>(a.status + 1);
+    if (a.gl + a.nlayers <= first_layer) return;
+    // the items of layers before the first active one are skipped by every role
+    const int f0 = max(0, first_layer - a.gl) * a.ntiles;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t full_bar[C::STAGES];
@@ -799,8 +808,6 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
         const int ce = g >= a.tail_from ? a.chunk_tail : a.chunk_elems;
         return max(1, (ce > 0 ? ce : C::CK * BKE) / BKE);
     };
-    // epilogue-warp completions that make a layer of one chain complete
-    const int done_target = kEpiWarps * G::NCTA * (a.ntiles / max(1, a.nchains));
     const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;     // pair or CTA
     const int nunits = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
     if (threadIdx.x == 0) {
@@ -846,27 +853,33 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             // ---------------- TMA producer ----------------
             int stage = 0;
             uint32_t phase = 0;
-            int known[kMaxChains] = {a.gl, a.gl};    // layers whose predecessor is known complete
+            // (layer, instance) of each chain whose predecessor is known complete
+            int known_g[kMaxChains] = {-1, -1}, known_i[kMaxChains] = {-1, -1};
             bool skip = false;                       // the call has failed: no more loads
             bool broken = false;                     // a pipeline wait ran out twice
             const int nf = n_items(a);
-            for (int f = unit; f < nf && !broken; f += nunits) {
+            for (int f = f0 + unit; f < nf && !broken; f += nunits) {
                 int g, t;
                 item_of(a, f, g, t);
                 const Tile tl = a.tiles[t];
                 int k;
                 if (!tile_active_g(a, tl, g, k)) {
                     // an inactive item counts as finished for the layer's completion
-                    if (a.nlayers > 1) atomicAdd(a.done + g * kMaxChains + tl.chain, kEpiWarps);
+                    if (a.nlayers > 1) atomicAdd(inst_counter(a, g, tl.inst, tl.chain), kEpiWarps);
                     continue;
                 }
                 // only multi-layer launches wait on other CTAs and can fail
                 if (!skip && a.nlayers > 1 && call_failed(a)) skip = true;
-                if (!skip && g > known[tl.chain]) {
-                    // operands and state of this item were written by other CTAs
-                    const int target = done_target + (g == a.stall_layer ? 1 : 0);
-                    if (wait_layer_done(a, g - 1, tl.chain, target)) {
-                        known[tl.chain] = g;
+                if (!skip && g > a.gl && g - 1 >= first_layer &&
+                    !(g == known_g[tl.chain] && tl.inst == known_i[tl.chain])) {
+                    // Operands and state of this item were written by other CTAs:
+                    // wait for the previous layer of its own instance only, so a
+                    // small instance need not wait for a large one.
+                    const int tgt = kEpiWarps * G::NCTA * a.iw[tl.inst].tile_count[a.dtab][tl.chain] +
+                                    (g == a.stall_layer ? 1 : 0);
+                    if (wait_counter(a, inst_counter(a, g - 1, tl.inst, tl.chain), tgt)) {
+                        known_g[tl.chain] = g;
+                        known_i[tl.chain] = tl.inst;
                         asm volatile("fence.proxy.async.global;" ::: "memory");
                     } else {
                         skip = true;
@@ -972,7 +985,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             const uint64_t desc0 = sdesc_sw128(smem_u32(smem));
             const uint64_t descT = sdesc_mn_sw128(smem_u32(smem));   // transposed panels
             const int nf = n_items(a);
-            for (int f = unit; f < nf && ok; f += nunits) {
+            for (int f = f0 + unit; f < nf && ok; f += nunits) {
                 int g, t;
                 item_of(a, f, g, t);
                 const Tile tl = a.tiles[t];
@@ -1069,7 +1082,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
         uint32_t used = 0;                       // entries consumed (ring slot)
         bool ok = true;
         const int nf = n_items(a);
-        for (int f = unit; f < nf && ok; f += nunits) {
+        for (int f = f0 + unit; f < nf && ok; f += nunits) {
             int g, t;
             item_of(a, f, g, t);
             const Tile tl = a.tiles[t];
@@ -1085,8 +1098,8 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             const bool work = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&abort_flag) == 0 ? 1 : 0, 0) != 0;
             if (work) {
             if (a.nlayers > 1 && g > a.gl) {
-                // the state of layer g - 1, written by other CTAs
-                if (lane == 0) done_acquire(a, g - 1, tl.chain);
+                // the state of layer g - 1 of this instance, written by other CTAs
+                if (lane == 0) acquire_load(inst_counter(a, g - 1, tl.inst, tl.chain));
                 __syncwarp();
             }
             const int n = a.inst[tl.inst].n;
@@ -1142,7 +1155,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             __syncwarp();
             if (lane == 0) {
                 // this warp's share of the tile's kEpiWarps completions
-                if (a.nlayers > 1) done_add(a, g, tl.chain, kEpiWarps / kStoreWarps);
+                if (a.nlayers > 1) done_add(a, g, tl.inst, tl.chain, kEpiWarps / kStoreWarps);
                 local_arrive(smem_u32(&sempty_bar));
             }
         }
@@ -1159,7 +1172,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
         uint32_t sp = 0;                         // scratch parity (deferred epilogue)
         bool ok = true;
         const int nf = n_items(a);
-        for (int f = unit; f < nf && ok; f += nunits) {
+        for (int f = f0 + unit; f < nf && ok; f += nunits) {
             int g, t;
             item_of(a, f, g, t);
             // Only the chunk count and the liveness of the warp's block are
@@ -1250,8 +1263,8 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             int k;
             tile_active_g(a, tl, g, k);
             if (a.nlayers > 1 && g > a.gl) {
-                // the state of layer g - 1, written by other CTAs
-                if (lane == 0) done_acquire(a, g - 1, tl.chain);
+                // the state of layer g - 1 of this instance, written by other CTAs
+                if (lane == 0) acquire_load(inst_counter(a, g - 1, tl.inst, tl.chain));
                 __syncwarp();
             }
             const int n = a.inst[tl.inst].n;
@@ -1293,7 +1306,7 @@ __global__ void __launch_bounds__(threads_of(DEFER), 1)
             if (lane == 0) {
                 if constexpr (PAIR) remote_arrive(tempty0 + 8u * (uint32_t)buf);
                 else local_arrive(tempty0 + 8u * (uint32_t)buf);
-                if (a.nlayers > 1) done_add(a, g, tl.chain, 1);
+                if (a.nlayers > 1) done_add(a, g, tl.inst, tl.chain, 1);
             }
             if (++buf == NBUF) {
                 buf = 0;

@@ -115,8 +115,10 @@ __global__ void prep_kernel(SetupArgs a) {
         a.status[0] = 0;
         a.status[1] = 0x7fffffff;     // first global layer with an active instance (decide lowers it)
     }
-    if (a.done)
-        for (int i = threadIdx.x; i < kMaxLayers * kMaxChains; i += blockDim.x) a.done[i] = 0;
+    if (a.done) {
+        const int cnt = a.done_layers * a.nb * kMaxChains;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) a.done[i] = 0;
+    }
     if (a.tiles) block_exclusive_scan_fill(a.inst, a.nb, a.BM, a.BN, a.nchains, a.iw, a.tiles, 0);
     if (a.tiles_ref) block_exclusive_scan_fill(a.inst, a.nb, a.BM_ref, a.BN_ref, a.nchains, a.iw, a.tiles_ref, 1);
 }
