@@ -54,9 +54,11 @@ def parse(argv=None):
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="longrange", choices=["longrange", "lattice", "ragged"],
+    p.add_argument("--workload", default="longrange", choices=["longrange", "lattice", "ragged", "families"],
                    help="longrange: n = 8192 lattice with 5%% long-range couplings, two refinement layers "
-                        "(default); lattice: one lattice of --dims; ragged: the 512-instance ragged batch")
+                        "(default); lattice: one lattice of --dims; ragged: the 512-instance ragged batch; "
+                        "families: the beta0 = 100 tables of Eq. mlsp2, Max-SP2 and Skip-SP2 (k = K = 2) on "
+                        "one lattice of --dims in FP32 mode (use --kT 0.3)")
     p.add_argument("--dims", default="16,16,16", help="lattice workload: lattice dimensions")
     p.add_argument("--kT", type=float, default=0.1)
     p.add_argument("--mode", default="fp16x2")
@@ -248,7 +250,23 @@ def method_exact_gpu(eps, V, rec, table, mu):
             xx = u * u
         return A + tb[-1][1] * xx
 
-    if table.get("skip") is not None:
+    def chain_max(x0, p):
+        # Max-SP2, flat table: blocks (delta_i, gamma_i, theta_{i,0..i}), then (c, gamma_L)
+        L = next(l for l in range(1, 64) if l * (l + 5) // 2 + 2 == len(p))
+        xs, F, o = [x0], torch.zeros_like(x0), 0
+        for i in range(L):
+            u = torch.full_like(x0, p[o])
+            for j in range(i + 1):
+                u = u + p[o + 2 + j] * xs[j]
+            F = F + p[o + 1] * xs[i]
+            xs.append(u * u)
+            o += i + 3
+        return F + p[o] + p[o + 1] * xs[L]
+
+    if table.get("max") is not None:
+        fermi_f = lambda x0: chain_max(x0, table["max"])
+        ent_f = lambda x0: chain_max(x0, table.get("max_entropy") or table["max"])
+    elif table.get("skip") is not None:
         fermi_f = lambda x0: chain_skip(x0, table["skip"])
         ent_f = lambda x0: chain_skip(x0, table.get("skip_entropy") or table["skip"])
     else:
@@ -969,6 +987,77 @@ def run_ragged(args, ft, world, rank, local, secondary=False):
     return result
 
 
+FAMILY_TABLES = ["b100_L10", "b100_L12", "b100_L14", "max_b100_L8", "max_b100_L10", "max_b100_L12",
+                  "skip22_b100_L10", "skip22_b100_L12", "skip22_b100_L14"]
+
+
+def run_families(args, ft):
+    """Layers against memory: the trained beta0 = 100 tables of the three
+    families (Eq. mlsp2; Max-SP2; Skip-SP2 with two stored layers and two
+    accumulators, run as its Max-SP2 embedding) on one n = 4096 lattice
+    Hamiltonian, FP32 mode (the mode Max-SP2 tables run in), density and
+    entropy.  Per table: its fitted max error on [0, 1], the measured time of
+    a solve, the state planes a chain keeps, the workspace, the algorithmic
+    HBM bytes of the layer epilogues (state planes read and written, FP32
+    operands written) and the density error against the exact Fermi operator
+    and against the table's own exact result."""
+    import torch
+    import workloads as wl
+    dims = tuple(int(x) for x in args.dims.split(","))
+    n = dims[0] * dims[1] * dims[2]
+    kT = args.kT
+    H = wl.lattice_3d(dims, args.seed)
+    Hd = torch.from_numpy(H.ravel().copy()).cuda()
+    torch.backends.cuda.matmul.allow_tf32 = False
+    mu, Dref, Sref, eps, V = eig_reference_gpu(Hd.view(n, n), kT, n)
+    rows = []
+    plane = 4.0 * n * n
+    for name in FAMILY_TABLES:
+        path = os.path.join(TABLE_DIR, name + ".json")
+        with open(path) as f:
+            d = json.load(f)
+        ms = ft.ModelSet.from_json([path])
+        is_max = d.get("max") is not None
+        L = int(d["L"])
+        modes = ["fp32"] + ([] if is_max or L != 14 else ["fp16x2"])
+        for mode in modes:
+            # Lanczos bounds: the Gershgorin width of the noisy lattice would
+            # put beta' beyond the beta0 = 100 tables' region at kT = 0.3
+            solver = ft.Solver([n], [mu], [kT], ms, mode=mode, want=3, flags=ft.LANCZOS)
+            for _ in range(max(3, args.warmup)):
+                solver.run(Hd)
+            torch.cuda.synchronize()
+            rec = solver.records()[0]
+            if rec["status"] != 0:
+                raise SystemExit("%s: status %d" % (name, rec["status"]))
+            t = cuda_time(lambda: solver.run(Hd), args.steps)
+            D = solver.matrix(0).double()
+            Drec, Srec = method_exact_gpu(eps, V, rec, ms.tables[0], mu)
+            planes = L + 1 if is_max else 2
+            # epilogue bytes per chain: Eq. mlsp2 reads and writes Z, A and
+            # writes the operands (5 planes a layer); Max-SP2 layer k reads
+            # k + 1 stored layers, writes one and the operands (k + 3)
+            epi = sum((k + 3) if is_max else 5 for k in range(L)) * plane
+            rows.append({"table": name, "family": ("Max-SP2" if name.startswith("max") else
+                                                   "Skip-SP2 k=2 K=2 (as Max-SP2)" if name.startswith("skip22")
+                                                   else "MLSP2"),
+                         "mode": mode, "L": L, "max_err_fermi_fit": d["fit"]["max_err_fermi"],
+                         "ms_per_solve": t * 1e3, "ms_per_layer": t * 1e3 / L,
+                         "state_planes_per_chain": planes, "state_bytes": 2 * planes * plane,
+                         "workspace_bytes": solver.ws_bytes, "epilogue_hbm_bytes": 2 * epi,
+                         "err_D_vs_exact": float((D - Dref).abs().max()),
+                         "err_D_vs_method_exact": float((D - Drec).abs().max()),
+                         "err_S_vs_method_exact_per_n": abs(float(solver.S[0]) - Srec) / n})
+            del solver, D, Drec
+            torch.cuda.empty_cache()
+    return {"metric": "family_layers_vs_memory", "unit": "ms/solve", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": "lattice %dx%dx%d (n=%d), kT=%g, mu at half filling, density+entropy"
+                                   % (dims + (n, kT)), "tables": "beta0=100 families (trained by the library)",
+                       "bounds": "lanczos"},
+            "rows": rows}
+
+
 def compact(res):
     """The headline keys of a secondary result."""
     keep = ("metric", "value", "unit", "ms_per_step", "tflops_alg", "config", "accuracy", "accuracy_sampled",
@@ -1001,6 +1090,10 @@ def main():
     if world > 1:
         dist.barrier()
     ft.lib()
+    if args.workload == "families":
+        if rank == 0:
+            print(json.dumps(run_families(args, ft)), flush=True)
+        return
     if args.workload == "ragged":
         res = run_ragged(args, ft, world, rank, local)
     else:

@@ -164,6 +164,18 @@ typedef struct {
  * combination (beta_i) is what the family adds; beta = 0 covers Eq. mlsp2
  * through the embedding of the Appendix on model embeddings.
  *
+ * family FTSP2_FAMILY_MAX: Max-SP2 (Sec. II A 2, Eq. maxsp2), every layer the
+ * square of an affine combination of all the layers before it:
+ * u_i = delta_i + sum_{j<=i} theta_{i,j} x_j, x_{i+1} = u_i^2, and
+ * f = c + sum_{j<=L} gamma_j x_j (Eq. maxsp2 has c = 0; Alg. maxsp2 a
+ * constant in place of gamma_0 x_0).  theta is flat: for i = 0 .. L-1 the
+ * block (delta_i, gamma_i, theta_{i,0}, ..., theta_{i,i}), then (c, gamma_L):
+ * L (L + 5) / 2 + 2 doubles, L <= 20.  The layers keep every x_j, so a solve
+ * holds L + 1 FP32 state planes per chain (size workspaces with
+ * ftsp2_workspace_size_set).  These tables run in FTSP2_FP32 mode only
+ * (FTSP2_E_UNSUPPORTED otherwise).  Skip-SP2 tables with k stored layers and
+ * K accumulators run through their Max-SP2 embedding (ftsp2_skip_to_max).
+ *
  * theta_entropy holds the entropy recursion's rows (Eq. entropy expansion) in
  * the same family (L_entropy layers) or is NULL to reuse theta (the
  * theta_fermi strategy).  alpha is the entropy input scale of Eq. entropy
@@ -171,6 +183,7 @@ typedef struct {
  * mix families. */
 #define FTSP2_FAMILY_MLSP2 0
 #define FTSP2_FAMILY_SKIP  1
+#define FTSP2_FAMILY_MAX   2
 typedef struct {
     int32_t L;
     int32_t L_entropy;
@@ -218,8 +231,8 @@ ftsp2_status ftsp2_model_set_info(const ftsp2_model_set* set, int* ntab, int* ma
 
 /* Copy of table `idx` of the set: *L layers, theta_out (host, room for 4*64
  * doubles) receives the table's rows as given at creation (Eq. mlsp2: L rows
- * (a, b, c, d); Skip-SP2: L + 1 rows); any output pointer may be NULL.  A
- * Skip-SP2 table has at most 63 layers. */
+ * (a, b, c, d); Skip-SP2: L + 1 rows; Max-SP2: the flat table); any output
+ * pointer may be NULL.  A Skip-SP2 table has at most 63 layers. */
 ftsp2_status ftsp2_model_set_table(const ftsp2_model_set* set, int idx, int* L, double* theta_out,
                                    double* beta0, double* mu0, double* alpha);
 
@@ -231,6 +244,12 @@ ftsp2_status ftsp2_model_set_table(const ftsp2_model_set* set, int idx, int* L, 
  * scratch). */
 ftsp2_status ftsp2_workspace_size(const ftsp2_instance* inst, int nb, ftsp2_mode mode,
                                   int want, size_t* bytes);
+
+/* The same for a given model set: also covers the state planes that Max-SP2
+ * tables of the set keep (L + 1 per chain instead of 2).  Equal to
+ * ftsp2_workspace_size for sets without such tables. */
+ftsp2_status ftsp2_workspace_size_set(const ftsp2_instance* inst, int nb, const ftsp2_model_set* set,
+                                      ftsp2_mode mode, int want, size_t* bytes);
 
 /* ---- the hot path ------------------------------------------------------------ */
 
@@ -457,8 +476,9 @@ ftsp2_status ftsp2_mlsp2_to_skip(int L, const double* theta, double* skip_out);
 double ftsp2_layer_count(double beta_p);
 
 /* Residuals model - target of a table (family FTSP2_FAMILY_MLSP2: L rows of
- * 4; FTSP2_FAMILY_SKIP: L + 1 rows of 4) at npoints device points dX, into
- * dR (device), FP64, no Jacobian: used to measure a table's error on a grid. */
+ * 4; FTSP2_FAMILY_SKIP: L + 1 rows of 4; FTSP2_FAMILY_MAX: the flat table,
+ * L <= 20) at npoints device points dX, into dR (device), FP64, no Jacobian:
+ * used to measure a table's error on a grid. */
 ftsp2_status ftsp2_train_residuals(int family, int target, double beta0, double mu0, int L, double alpha,
                                    const double* table, const double* dX, int npoints, double* dR,
                                    void* stream);
@@ -475,6 +495,28 @@ ftsp2_status ftsp2_train_residuals(int family, int target, double beta0, double 
  * every term of a layer into one pass whichever form the table has).
  * FTSP2_E_ARG for L outside 1..64 or non-finite entries. */
 ftsp2_status ftsp2_alt_to_mlsp2(int L, const double* alt, double* theta_out);
+
+/* Embeddings in Max-SP2 (the Appendix on model embeddings: MLSP2 in Skip-SP2
+ * in Max-SP2), host only; max_out receives the flat Max-SP2 table
+ * (L (L + 5) / 2 + 2 doubles) computing the same function.
+ *   ftsp2_mlsp2_to_max: L Eq. mlsp2 rows (every a_i != 0), through the
+ *     Skip-SP2 embedding of ftsp2_mlsp2_to_skip.
+ *   ftsp2_skip_to_max: a Skip-SP2 table with k stored layers and K
+ *     accumulators (Sec. II A 3): u_i = alpha_{i,k} + sum_{j<min(k,i+1)}
+ *     alpha_{i,j} x_{i-j} + sum_l beta_{i,l} A_{i,l},
+ *     A_{i+1,l} = A_{i,l} + gamma_{i,l} x_i, x_{i+1} = u_i^2,
+ *     f = gamma_L x_L + sum_l A_{L,l} (the paper writes gamma_L = 1; the
+ *     embedding of Eq. mlsp2 needs the weight); alpha is L x (k + 1)
+ *     row-major (the constant alpha_{i,k} last), beta and gamma L x K, A0
+ *     the K initial accumulators (beta, gamma, A0 may be NULL when K = 0).
+ *     With A_{i,l} = A_{0,l} + sum_{j<i} gamma_{j,l} x_j:
+ *     delta_i = alpha_{i,k} + sum_l beta_{i,l} A_{0,l},
+ *     theta_{i,j} = sum_l beta_{i,l} gamma_{j,l} [j < i] + alpha_{i,i-j} [i - j < k],
+ *     c = sum_l A_{0,l}, gamma_j = sum_l gamma_{j,l} (j < L), and gamma_L.
+ * FTSP2_E_ARG for L outside 1..20, k < 1, K < 0, or non-finite entries. */
+ftsp2_status ftsp2_mlsp2_to_max(int L, const double* theta, double* max_out);
+ftsp2_status ftsp2_skip_to_max(int L, int k, int K, const double* alpha, const double* beta, const double* gamma,
+                               const double* A0, double gamma_L, double* max_out);
 
 /* Levenberg-Marquardt training in the one-term form: as ftsp2_train_coeffs,
  * with alt_init / alt_out (host) of (L + 1) * 2 doubles (alt_init NULL:
@@ -499,6 +541,42 @@ ftsp2_status ftsp2_train_coeffs_skip(int target, double beta0, double mu0, int L
                                      int nsamples, uint64_t seed, int iterations, int accel,
                                      const double* skip_init, double* skip_out, ftsp2_train_report* rep,
                                      void* dWork, size_t work_bytes, void* stream);
+
+/* Levenberg-Marquardt training of the families that keep stored layers
+ * (Sec. II A 2 and II A 3), as ftsp2_train_coeffs otherwise (samples, seed,
+ * geodesic acceleration, report, stream).  L <= 20; dWork must hold
+ * ftsp2_train_workspace_size_max(nsamples, L) bytes (room for the
+ * L (L + 5) / 2 + 3 columns of the augmented Max-SP2 Jacobian).
+ * ftsp2_train_coeffs_max: a flat Max-SP2 table (FTSP2_FAMILY_MAX layout);
+ *   max_init NULL starts from ftsp2_mlsp2_to_max of ftsp2_train_init(L,
+ *   beta0, mu0).  The GPU runs the Max-SP2 forward and reverse sweep.
+ * ftsp2_train_coeffs_skipk: a Skip-SP2 table with k stored layers and K
+ *   accumulators (1 <= k <= L, K >= 1) as the vector
+ *   (alpha (L x (k + 1), constant last), beta (L x K), gamma (L x K),
+ *   A_{0,1}, gamma_L): (1 + k + 2K) L + 2 doubles, the paper's count, the
+ *   other initial accumulators zero.  The model is its Max-SP2 embedding
+ *   (ftsp2_skipk_to_max), the GPU forms the Max-SP2 Jacobian and its
+ *   reductions, the host applies the embedding's exact Jacobian
+ *   (P^T J^T J P, P^T J^T r); a parameter whose J^T J diagonal is zero at the
+ *   current point is damped with the smallest positive diagonal entry.
+ *   skip_init NULL starts from ftsp2_train_init_skipk.
+ * ftsp2_train_init_skipk (host): the default start, the one-accumulator
+ *   embedding (ftsp2_mlsp2_to_skip) of ftsp2_train_init(L, beta0, mu0) in
+ *   stored-layer slot 0 and accumulator 1; the further stored layers and
+ *   accumulator inputs gamma zero, the further accumulators' feedback beta
+ *   0.01 (no effect on the function while those accumulators are zero).
+ * ftsp2_skipk_to_max (host): the flat Max-SP2 table of such a vector. */
+size_t ftsp2_train_workspace_size_max(int nsamples, int L);
+ftsp2_status ftsp2_train_coeffs_max(int target, double beta0, double mu0, int L, double alpha, int nsamples,
+                                    uint64_t seed, int iterations, int accel, const double* max_init,
+                                    double* max_out, ftsp2_train_report* rep, void* dWork, size_t work_bytes,
+                                    void* stream);
+ftsp2_status ftsp2_train_coeffs_skipk(int target, double beta0, double mu0, int L, int k, int K, double alpha,
+                                      int nsamples, uint64_t seed, int iterations, int accel,
+                                      const double* skip_init, double* skip_out, ftsp2_train_report* rep,
+                                      void* dWork, size_t work_bytes, void* stream);
+ftsp2_status ftsp2_train_init_skipk(int L, int k, int K, double beta0, double mu0, double* skip_out);
+ftsp2_status ftsp2_skipk_to_max(int L, int k, int K, const double* skip, double* max_out);
 
 /* Building blocks of one LM iteration, exposed for parity tests.
  * ftsp2_train_residual_jacobian: residuals dR[nsamples] = model(theta) - target

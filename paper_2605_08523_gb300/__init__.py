@@ -100,7 +100,11 @@ class ModelSet:
     ftsp2_alt_to_mlsp2.  A Skip-SP2 table (one stored layer, one accumulator;
     FTSP2_FAMILY_SKIP) gives ``skip`` ((L + 1, 4) rows: (delta, alpha, beta,
     gamma) per layer and the output row (A_0, gamma_L, 0, 0)) and optionally
-    ``skip_entropy``."""
+    ``skip_entropy``.  A Max-SP2 table (FTSP2_FAMILY_MAX; FP32 mode only)
+    gives ``max``, the flat table of ``max_nparams(L)`` numbers (blocks
+    (delta_i, gamma_i, theta_{i,0..i}), then (c, gamma_L)), and optionally
+    ``max_entropy``; ftsp2_mlsp2_to_max and ftsp2_skip_to_max build such tables
+    from the other families."""
 
     def __init__(self, tables=None):
         self._h = C.c_void_p()
@@ -118,7 +122,12 @@ class ModelSet:
                 t = dict(t, theta_entropy=ftsp2_alt_to_mlsp2(t["alt_entropy"]).tolist())
             conv.append(t)
             skip = t.get("skip") is not None
-            if skip:
+            mx = t.get("max") is not None
+            if mx:
+                th = np.ascontiguousarray(np.asarray(t["max"], dtype=np.float64).ravel())
+                arr[i].family = 2
+                arr[i].L = max_layers_of(th.size)
+            elif skip:
                 th = np.ascontiguousarray(np.asarray(t["skip"], dtype=np.float64).reshape(-1, 4))
                 arr[i].family = 1
                 arr[i].L = th.shape[0] - 1
@@ -131,8 +140,13 @@ class ModelSet:
             arr[i].mu0 = float(t["mu0"])
             arr[i].alpha = float(t.get("alpha", 0.842704))
             arr[i].theta = th.ctypes.data_as(C.POINTER(C.c_double))
-            te = t.get("skip_entropy") if skip else t.get("theta_entropy")
-            if te is not None:
+            te = t.get("max_entropy") if mx else t.get("skip_entropy") if skip else t.get("theta_entropy")
+            if te is not None and mx:
+                te = np.ascontiguousarray(np.asarray(te, dtype=np.float64).ravel())
+                self._keep.append(te)
+                arr[i].L_entropy = max_layers_of(te.size)
+                arr[i].theta_entropy = te.ctypes.data_as(C.POINTER(C.c_double))
+            elif te is not None:
                 te = np.ascontiguousarray(np.asarray(te, dtype=np.float64).reshape(-1, 4))
                 self._keep.append(te)
                 arr[i].L_entropy = te.shape[0] - (1 if skip else 0)
@@ -146,15 +160,16 @@ class ModelSet:
     @classmethod
     def from_json(cls, paths):
         """Model set from table files written by train_tables (keys beta0, mu0,
-        alpha, theta and optionally theta_entropy)."""
+        alpha, and theta / alt / skip / max with the matching entropy key)."""
         import json
         tabs = []
         for p in paths:
             with open(p) as f:
                 d = json.load(f)
-            tabs.append(dict(theta=d.get("theta"), alt=d.get("alt"), skip=d.get("skip"), beta0=d["beta0"],
-                             mu0=d["mu0"], alpha=d.get("alpha", 0.842704), theta_entropy=d.get("theta_entropy"),
-                             alt_entropy=d.get("alt_entropy"), skip_entropy=d.get("skip_entropy")))
+            tabs.append(dict(theta=d.get("theta"), alt=d.get("alt"), skip=d.get("skip"), max=d.get("max"),
+                             beta0=d["beta0"], mu0=d["mu0"], alpha=d.get("alpha", 0.842704),
+                             theta_entropy=d.get("theta_entropy"), alt_entropy=d.get("alt_entropy"),
+                             skip_entropy=d.get("skip_entropy"), max_entropy=d.get("max_entropy")))
         return cls(tabs)
 
     @property
@@ -167,12 +182,15 @@ class ModelSet:
         return n.value, L.value
 
     def table(self, idx=0):
-        """(theta (L, 4), beta0, mu0, alpha) of table idx (ftsp2_model_set_table)."""
+        """(theta (L, 4), beta0, mu0, alpha) of table idx (ftsp2_model_set_table;
+        the flat table for a Max-SP2 table)."""
         L = C.c_int()
         th = (C.c_double * 256)()
         b0, m0, al = C.c_double(), C.c_double(), C.c_double()
         check(lib().ftsp2_model_set_table(self._h, int(idx), C.byref(L), th, C.byref(b0), C.byref(m0),
                                           C.byref(al)), "ftsp2_model_set_table")
+        if self.tables is not None and self.tables[idx].get("max") is not None:
+            return np.array(th[:max_nparams(L.value)]), b0.value, m0.value, al.value
         return np.array(th[:4 * L.value]).reshape(-1, 4), b0.value, m0.value, al.value
 
     def close(self):
@@ -225,8 +243,8 @@ class Solver:
         raw = np.frombuffer(bytes(self.host_inst), dtype=INST_DTYPE)
         self.d_inst = torch.from_numpy(raw.view(np.uint8).copy()).to(self.device)
         wsz = C.c_size_t()
-        check(lib().ftsp2_workspace_size(self.host_inst, self.nb, self.mode, self.want, C.byref(wsz)),
-              "ftsp2_workspace_size")
+        check(lib().ftsp2_workspace_size_set(self.host_inst, self.nb, model_set.handle, self.mode, self.want,
+                                             C.byref(wsz)), "ftsp2_workspace_size_set")
         self.ws_bytes = wsz.value
         self._ws_raw = torch.empty(self.ws_bytes + 1024, dtype=torch.uint8, device=self.device)
         base = self._ws_raw.data_ptr()
@@ -454,6 +472,77 @@ def ftsp2_train_coeffs_alt(target, beta0, mu0, L=None, alt_init=None, nsamples=1
                   iterations, accel, alpha, L, stream)
 
 
+def _report(rep):
+    return dict(iterations=rep.iterations, accepted=rep.accepted, cost0=rep.cost0, cost=rep.cost,
+                max_err=rep.max_err, lam=rep.lam)
+
+
+def ftsp2_train_coeffs_max(target, beta0, mu0, L=None, max_init=None, nsamples=100_000, seed=0, iterations=100,
+                           accel=True, alpha=1.0, stream=None):
+    """Levenberg-Marquardt fit of a flat Max-SP2 table on the GPU.  max_init
+    None starts from ftsp2_mlsp2_to_max(ftsp2_train_init(L, beta0, mu0)).
+    Returns (flat table numpy, report dict)."""
+    torch = _torch()
+    p0 = None
+    if max_init is not None:
+        p0 = np.ascontiguousarray(np.asarray(max_init, dtype=np.float64).ravel())
+        L = max_layers_of(p0.size)
+    out = np.zeros(max_nparams(L))
+    wb = lib().ftsp2_train_workspace_size_max(int(nsamples), int(L))
+    ws = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    rep = TrainReport()
+    check(lib().ftsp2_train_coeffs_max(int(target), float(beta0), float(mu0), int(L), float(alpha), int(nsamples),
+                                       int(seed), int(iterations), int(bool(accel)), None if p0 is None else _dp(p0),
+                                       _dp(out), C.byref(rep), _ptr(ws), wb, _stream(stream)),
+          "ftsp2_train_coeffs_max")
+    return out, _report(rep)
+
+
+def skipk_nparams(L, k, K):
+    """(1 + k + 2K) L + 2 trainable numbers of a Skip-SP2 table with k stored
+    layers and K accumulators."""
+    return (1 + int(k) + 2 * int(K)) * int(L) + 2
+
+
+def ftsp2_train_coeffs_skipk(target, beta0, mu0, L, k, K, skip_init=None, nsamples=100_000, seed=0, iterations=100,
+                             accel=True, alpha=1.0, stream=None):
+    """Levenberg-Marquardt fit of a Skip-SP2 table with k stored layers and K
+    accumulators on the GPU (vector layout of ftsp2_train_coeffs_skipk).
+    Returns (vector numpy, report dict)."""
+    torch = _torch()
+    npar = skipk_nparams(L, k, K)
+    p0 = None if skip_init is None else np.ascontiguousarray(np.asarray(skip_init, dtype=np.float64).ravel())
+    if p0 is not None and p0.size != npar:
+        raise ValueError("skip_init must hold (1 + k + 2K) L + 2 numbers")
+    out = np.zeros(npar)
+    wb = lib().ftsp2_train_workspace_size_max(int(nsamples), int(L))
+    ws = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    rep = TrainReport()
+    check(lib().ftsp2_train_coeffs_skipk(int(target), float(beta0), float(mu0), int(L), int(k), int(K), float(alpha),
+                                         int(nsamples), int(seed), int(iterations), int(bool(accel)),
+                                         None if p0 is None else _dp(p0), _dp(out), C.byref(rep), _ptr(ws), wb,
+                                         _stream(stream)), "ftsp2_train_coeffs_skipk")
+    return out, _report(rep)
+
+
+def ftsp2_train_init_skipk(L, k, K, beta0, mu0):
+    """The library's default start of a Skip-SP2 (k, K) fit (host-only call)."""
+    out = np.zeros(skipk_nparams(L, k, K))
+    check(lib().ftsp2_train_init_skipk(int(L), int(k), int(K), float(beta0), float(mu0), _dp(out)),
+          "ftsp2_train_init_skipk")
+    return out
+
+
+def ftsp2_skipk_to_max(vec, L, k, K):
+    """Flat Max-SP2 table of a Skip-SP2 (k, K) vector (host-only call)."""
+    v = np.ascontiguousarray(np.asarray(vec, dtype=np.float64).ravel())
+    if v.size != skipk_nparams(L, k, K):
+        raise ValueError("vector must hold (1 + k + 2K) L + 2 numbers")
+    out = np.zeros(max_nparams(L))
+    check(lib().ftsp2_skipk_to_max(int(L), int(k), int(K), _dp(v), _dp(out)), "ftsp2_skipk_to_max")
+    return out
+
+
 def ftsp2_train_coeffs_skip(target, beta0, mu0, L=None, skip_init=None, nsamples=100_000, seed=0, iterations=100,
                             accel=True, alpha=1.0, stream=None):
     """Levenberg-Marquardt fit of a Skip-SP2 table (one stored layer, one
@@ -495,6 +584,45 @@ def ftsp2_mlsp2_to_skip(theta):
     return out
 
 
+def max_nparams(L):
+    """Length of a flat Max-SP2 table of L layers: L (L + 5) / 2 + 2."""
+    return int(L) * (int(L) + 5) // 2 + 2
+
+
+def max_layers_of(size):
+    """Layer count of a flat Max-SP2 table of `size` numbers."""
+    for L in range(1, 64):
+        if max_nparams(L) == size:
+            return L
+    raise ValueError(f"{size} numbers are no flat Max-SP2 table")
+
+
+def ftsp2_mlsp2_to_max(theta):
+    """Flat Max-SP2 table computing the same function as Eq. mlsp2 rows
+    (through their Skip-SP2 embedding; host-only call)."""
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1, 4))
+    L = th.shape[0]
+    out = np.zeros(max_nparams(L))
+    check(lib().ftsp2_mlsp2_to_max(L, _dp(th), _dp(out)), "ftsp2_mlsp2_to_max")
+    return out
+
+
+def ftsp2_skip_to_max(alpha, beta, gamma, A0, gL=1.0):
+    """Flat Max-SP2 table of a Skip-SP2 table with k stored layers and K
+    accumulators: alpha (L, k + 1) with the constant last, beta and gamma
+    (L, K), A0 (K,), output weight gL of the last layer (host-only call)."""
+    al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
+    L, k = al.shape[0], al.shape[1] - 1
+    be = np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(L, -1))
+    K = be.shape[1]
+    ga = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64).reshape(L, K))
+    a0 = np.ascontiguousarray(np.asarray(A0, dtype=np.float64).reshape(K))
+    out = np.zeros(max_nparams(L))
+    check(lib().ftsp2_skip_to_max(L, k, K, _dp(al), _dp(be) if K else None, _dp(ga) if K else None,
+                                  _dp(a0) if K else None, float(gL), _dp(out)), "ftsp2_skip_to_max")
+    return out
+
+
 def ftsp2_layer_count(beta_p):
     """Eq. layer count (host-only call)."""
     return float(lib().ftsp2_layer_count(float(beta_p)))
@@ -502,10 +630,15 @@ def ftsp2_layer_count(beta_p):
 
 def ftsp2_train_residuals(target, beta0, mu0, table, x, alpha=1.0, family=0, stream=None):
     """Residuals model - target of a table at the CUDA float64 points x
-    (family 0: Eq. mlsp2 rows; 1: Skip-SP2 rows with the output row)."""
+    (family 0: Eq. mlsp2 rows; 1: Skip-SP2 rows with the output row; 2: a
+    flat Max-SP2 table)."""
     torch = _torch()
-    tb = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 4))
-    L = tb.shape[0] - (1 if family == 1 else 0)
+    if family == 2:
+        tb = np.ascontiguousarray(np.asarray(table, dtype=np.float64).ravel())
+        L = max_layers_of(tb.size)
+    else:
+        tb = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 4))
+        L = tb.shape[0] - (1 if family == 1 else 0)
     r = torch.empty(x.numel(), dtype=torch.float64, device=x.device)
     check(lib().ftsp2_train_residuals(int(family), int(target), float(beta0), float(mu0), L, float(alpha), _dp(tb),
                                       _ptr(x), x.numel(), _ptr(r), _stream(stream)), "ftsp2_train_residuals")

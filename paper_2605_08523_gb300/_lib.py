@@ -21,7 +21,7 @@ SYNC, CLAMP, REFINE1, REFINE2, PAIR_TILES, SINGLE_TILES, LANCZOS, MIN_LAYERS, RE
     0x1, 0x2, 0x4, 0x8, 0x10, 0x20, 0x40, 0x80, 0x100
 EPI_DEFERRED, EPI_INLINE, FULL_OPERANDS = 0x200, 0x400, 0x800
 LAYER_LAUNCHES = 0x1000
-FAMILY_MLSP2, FAMILY_SKIP = 0, 1
+FAMILY_MLSP2, FAMILY_SKIP, FAMILY_MAX = 0, 1, 2
 TARGET_FERMI, TARGET_ENTROPY = 0, 1
 
 
@@ -62,6 +62,7 @@ SIGNATURES = {
     "ftsp2_model_set_table": (_I, [_VP, _I, C.POINTER(_I), C.POINTER(_D), C.POINTER(_D), C.POINTER(_D),
                                    C.POINTER(_D)]),
     "ftsp2_workspace_size": (_I, [_PINST, _I, _I, _I, C.POINTER(_SZ)]),
+    "ftsp2_workspace_size_set": (_I, [_PINST, _I, _VP, _I, _I, C.POINTER(_SZ)]),
     "ftsp2_rescale_workspace_size": (_I, [_I, C.POINTER(_SZ)]),
     "ftsp2_rescale": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _VP, _VP, _SZ, _VP]),
     "ftsp2_density": (_I, [_VP, _PINST, _VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _SZ, _VP]),
@@ -82,10 +83,20 @@ SIGNATURES = {
     "ftsp2_alt_to_mlsp2": (_I, [_I, C.POINTER(_D), C.POINTER(_D)]),
     "ftsp2_train_coeffs_skip": (_I, [_I, _D, _D, _I, _D, _I, C.c_uint64, _I, _I, C.POINTER(_D), C.POINTER(_D),
                                      C.POINTER(TrainReport), _VP, _SZ, _VP]),
+    "ftsp2_train_workspace_size_max": (_SZ, [_I, _I]),
+    "ftsp2_train_coeffs_max": (_I, [_I, _D, _D, _I, _D, _I, C.c_uint64, _I, _I, C.POINTER(_D), C.POINTER(_D),
+                                    C.POINTER(TrainReport), _VP, _SZ, _VP]),
+    "ftsp2_train_coeffs_skipk": (_I, [_I, _D, _D, _I, _I, _I, _D, _I, C.c_uint64, _I, _I, C.POINTER(_D),
+                                      C.POINTER(_D), C.POINTER(TrainReport), _VP, _SZ, _VP]),
+    "ftsp2_train_init_skipk": (_I, [_I, _I, _I, _D, _D, C.POINTER(_D)]),
+    "ftsp2_skipk_to_max": (_I, [_I, _I, _I, C.POINTER(_D), C.POINTER(_D)]),
     "ftsp2_train_samples": (_I, [_D, _D, _I, C.c_uint64, C.POINTER(_D)]),
     "ftsp2_train_init": (_I, [_I, _D, _D, C.POINTER(_D)]),
     "ftsp2_train_init_alt": (_I, [_I, _D, C.POINTER(_D)]),
     "ftsp2_mlsp2_to_skip": (_I, [_I, C.POINTER(_D), C.POINTER(_D)]),
+    "ftsp2_mlsp2_to_max": (_I, [_I, C.POINTER(_D), C.POINTER(_D)]),
+    "ftsp2_skip_to_max": (_I, [_I, _I, _I, C.POINTER(_D), C.POINTER(_D), C.POINTER(_D), C.POINTER(_D), _D,
+                               C.POINTER(_D)]),
     "ftsp2_layer_count": (_D, [_D]),
     "ftsp2_train_residuals": (_I, [_I, _I, _D, _D, _I, _D, C.POINTER(_D), _VP, _I, _VP, _VP]),
     "ftsp2_train_residual_jacobian": (_I, [_I, _D, _D, _I, _D, C.POINTER(_D), _VP, _I, _VP, _VP, _VP]),

@@ -147,6 +147,90 @@ __device__ __forceinline__ void epi_segment(const LayerArgs& a, const EpiCtx& e,
     }
 }
 
+// Max-SP2 layer k (FP32 mode, CUDA-core layers only).  State plane j of the
+// chain holds the centred stored layer x^_j = X_j - chi_j I (chi_j the layer
+// values along the trajectory of mu0, sigma_k the combination's value there);
+// the operands of layer k are the centred combination
+// U^_k = sum_{j<=k} theta_{k,j} x^_j, and with v = (U^_k^2)_{rc}:
+//   x^_{k+1} = v + 2 sigma_k U^_k          (bp = 2 sigma_k, mul = 1)
+// is stored as plane k + 1 and the operands of layer k + 1,
+// U^_{k+1} = sum_{j<=k+1} theta_{k+1,j} x^_j, are written at (r, c) and (c, r);
+// the last layer forms G = sum_{j<=L} gamma_j x^_j instead (D = G + f0 I).
+// U^_k is re-formed here from the planes in the order its operands were
+// formed, so it equals the operand value the product used.
+template <int W>
+__device__ __forceinline__ void epi_segment_max(const LayerArgs& a, const EpiCtx& e, int r, int c0,
+                                                const float* v, double& tr, double& sq) {
+    if (r >= e.n) return;
+    float* X = a.Z[e.chain] + e.slab;
+    const int k1 = e.L.nplanes;                    // k + 1 stored layers are read
+    const float* th = a.coef + e.L.coef;           // theta_{k,0..k}
+    const float* tn = th + k1;                     // theta_{k+1,0..k+1}
+    const float* gm = tn + k1 + 1;                 // gamma_{0..L} (last layer)
+    float ui[W], un[W], g[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) ui[j] = un[j] = g[j] = 0.f;
+    for (int p = 0; p < k1; ++p) {
+        const float tk = th[p], tq = tn[p], gp = e.last ? gm[p] : 0.f;
+        const float* Xp = X + (size_t)p * a.plane_elems;
+#pragma unroll
+        for (int i = 0; i < W / 4; ++i) {
+            const float4 xx = *reinterpret_cast<const float4*>(Xp + state_off(e.P, r, c0 + 4 * i));
+            const float xv[4] = {xx.x, xx.y, xx.z, xx.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ui[4 * i + q] = fmaf(tk, xv[q], ui[4 * i + q]);
+                un[4 * i + q] = fmaf(tq, xv[q], un[4 * i + q]);
+                g[4 * i + q] = fmaf(gp, xv[q], g[4 * i + q]);
+            }
+        }
+    }
+    float xn[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) xn[j] = fmaf(e.mul, v[j], e.L.bp * ui[j]);
+    if (!e.last) {
+        float* Xn = X + (size_t)k1 * a.plane_elems;
+#pragma unroll
+        for (int i = 0; i < W / 4; ++i)
+            *reinterpret_cast<float4*>(Xn + state_off(e.P, r, c0 + 4 * i)) =
+                make_float4(xn[4 * i], xn[4 * i + 1], xn[4 * i + 2], xn[4 * i + 3]);
+        const float tl = tn[k1];
+        uint8_t* ob = a.opw[e.chain];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int c = c0 + j;
+            if (c < e.n && r <= c) {
+                const float zs = fmaf(tl, xn[j], un[j]);
+                store_operand(e.next_fmt, ob, a.plane_elems, e.slab + (size_t)r * e.P + c, zs);
+                if (c != r) store_operand(e.next_fmt, ob, a.plane_elems, e.slab + (size_t)c * e.P + r, zs);
+            }
+        }
+    } else {
+        const float gl = gm[k1];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int c = c0 + j;
+            if (c < e.n && r <= c) {
+                const float gv = fmaf(gl, xn[j], g[j]);
+                if (e.kind == CHAIN_FERMI && a.D) {
+                    float dv;
+                    if (e.flip) dv = (r == c ? (float)e.cdiag : 0.f) - gv;
+                    else dv = gv + (r == c ? (float)e.cdiag : 0.f);
+                    a.D[e.doff + (int64_t)r * e.n + c] = dv;
+                    if (c != r) a.D[e.doff + (int64_t)c * e.n + r] = dv;
+                }
+                const double gd = (double)gv;
+                if (r == c) {
+                    tr += gd;
+                    sq += gd * gd;
+                } else {
+                    sq += 2.0 * gd * gd;
+                }
+            }
+        }
+    }
+}
+
 // `scaled_in`: the products were formed from power-of-two scaled FP16 operands.
 __device__ __forceinline__ void make_ctx(const LayerArgs& a, const Tile& t, int k, EpiCtx& e, bool scaled_in) {
     const ftsp2_instance in = a.inst[t.inst];

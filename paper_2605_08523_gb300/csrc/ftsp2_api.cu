@@ -106,7 +106,10 @@ struct ftsp2_model_set {
     ftsp2::DevModel* d_models[2] = {nullptr, nullptr};   // [plain, fp16-scaled]
     ftsp2::DevLayer* d_layers[2] = {nullptr, nullptr};
     void* d_mem = nullptr;
+    float* d_coef = nullptr;       // Max-SP2 coefficient pool (nullable)
     int Lmax = 0;
+    int planes = 2;                // FP32 state planes per chain a solve needs
+    bool has_max = false;
     int device = -1;
 };
 
@@ -172,6 +175,8 @@ static void chain_constants_skip(const std::vector<double>& tb, int L, double mu
             dl.out_scale = 1.f;
         }
         dl.pad0 = dl.pad1 = 0.f;
+        dl.coef = -1;
+        dl.nplanes = 0;
         out[k] = dl;
     }
     scale0 = (float)std::ldexp(1.0, e[0]);
@@ -223,15 +228,65 @@ static void chain_constants(const std::vector<double>& th, int L, double mu0, do
         dl.d2 = 0.f;
         dl.g = 1.f;
         dl.pad0 = dl.pad1 = 0.f;
+        dl.coef = -1;
+        dl.nplanes = 0;
         out[k] = dl;
     }
     scale0 = (float)std::ldexp(1.0, e[0]);
+}
+
+// Max-SP2 chain (FTSP2_FAMILY_MAX, FP32 mode): the centre trajectory at
+// x0 = mu0 (chi_j of x_j, sigma_i of u_i), f0 = c + sum_j gamma_j chi_j, and per
+// layer the coefficient block of the pool (DevLayer.coef): theta_{i,0..i},
+// theta_{i+1,0..i+1} (zeros after the last layer), and gamma_{0..L} for the
+// last layer.  In the centred variables x^_j = x_j - chi_j the layer i computes
+// Z^_i = sum_j theta_{i,j} x^_j, x^_{i+1} = S + 2 sigma_i Z^_i (S = Z^_i^2), and
+// Z^_{i+1} = sum_{j <= i+1} theta_{i+1,j} x^_j (the constants cancel).
+int max_nparams(int L) { return L * (L + 5) / 2 + 2; }
+static void chain_constants_max(const std::vector<double>& p, int L, double mu0, std::vector<DevLayer>& out,
+                                std::vector<float>& pool, double& f0, float& op0) {
+    std::vector<int> off(L);
+    int o = 0;
+    for (int i = 0; i < L; ++i) {
+        off[i] = o;
+        o += i + 3;
+    }
+    const double c = p[o], gL = p[o + 1];
+    auto theta = [&](int i, int j) { return p[off[i] + 2 + j]; };
+    auto gamma = [&](int j) { return j < L ? p[off[j] + 1] : gL; };
+    std::vector<double> chi(L + 1), sig(L);
+    chi[0] = mu0;
+    for (int i = 0; i < L; ++i) {
+        double u = p[off[i]];
+        for (int j = 0; j <= i; ++j) u += theta(i, j) * chi[j];
+        sig[i] = u;
+        chi[i + 1] = u * u;
+    }
+    f0 = c;
+    for (int j = 0; j <= L; ++j) f0 += gamma(j) * chi[j];
+    out.resize(L);
+    for (int i = 0; i < L; ++i) {
+        DevLayer dl;
+        std::memset(&dl, 0, sizeof(dl));
+        dl.a = dl.acc_mul = 1.f;
+        dl.bp = (float)(2.0 * sig[i]);
+        dl.in_scale = dl.out_scale = 1.f;
+        dl.coef = (int)pool.size();
+        dl.nplanes = i + 1;
+        for (int j = 0; j <= i; ++j) pool.push_back((float)theta(i, j));
+        for (int j = 0; j <= i + 1; ++j) pool.push_back(i + 1 < L ? (float)theta(i + 1, j) : 0.f);
+        if (i == L - 1)
+            for (int j = 0; j <= L; ++j) pool.push_back((float)gamma(j));
+        out[i] = dl;
+    }
+    op0 = (float)theta(0, 0);
 }
 
 static ftsp2_status upload_models(ftsp2_model_set* s) {
     const int nm = (int)s->host.size();
     std::vector<DevModel> dm[2];
     std::vector<DevLayer> dl[2];
+    std::vector<float> pool[2];
     for (int v = 0; v < 2; ++v) {
         const bool scaled = v == 1;
         for (int m = 0; m < nm; ++m) {
@@ -245,16 +300,25 @@ static ftsp2_status upload_models(ftsp2_model_set* s) {
             std::vector<DevLayer> lf, ls;
             const double ylo = h.mu0 + h.alpha * (0.0 - h.mu0), yhi = h.mu0 + h.alpha * (1.0 - h.mu0);
             const std::vector<double>& thE = h.thS.empty() ? h.th : h.thS;
-            if (h.family == FTSP2_FAMILY_SKIP) {
+            if (h.family == FTSP2_FAMILY_MAX) {
+                // FP32 mode only: no FP16 scales; state plane 0 = x^_0 (z0 = 1)
+                chain_constants_max(h.th, h.L, h.mu0, lf, pool[v], M.f0, M.op0);
+                chain_constants_max(thE, h.LS, h.mu0, ls, pool[v], M.g0, M.op0S);
+                M.scale0 = M.scale0S = 1.f;
+                M.z0 = M.z0S = 1.f;
+                M.a0 = M.a0S = 0.f;
+            } else if (h.family == FTSP2_FAMILY_SKIP) {
                 chain_constants_skip(h.th, h.L, h.mu0, 0.0, 1.0, scaled, lf, M.f0, M.scale0, M.z0, M.a0);
                 chain_constants_skip(thE, h.LS, h.mu0, std::min(ylo, yhi), std::max(ylo, yhi), scaled, ls, M.g0,
                                      M.scale0S, M.z0S, M.a0S);
+                M.op0 = M.op0S = 1.f;
             } else {
                 chain_constants(h.th, h.L, h.mu0, 0.0, 1.0, scaled, lf, M.f0, M.scale0);
                 chain_constants(thE, h.LS, h.mu0, std::min(ylo, yhi), std::max(ylo, yhi), scaled, ls, M.g0,
                                 M.scale0S);
                 M.z0 = M.z0S = 1.f;
                 M.a0 = M.a0S = 0.f;
+                M.op0 = M.op0S = 1.f;
             }
             M.off = (int)dl[v].size();
             dl[v].insert(dl[v].end(), lf.begin(), lf.end());
@@ -264,16 +328,26 @@ static ftsp2_status upload_models(ftsp2_model_set* s) {
         }
     }
     const size_t bm = sizeof(DevModel) * nm, bl = sizeof(DevLayer) * dl[0].size();
-    const size_t total = 2 * (bm + bl) + 256;
+    const size_t bp = (sizeof(float) * pool[0].size() + 255) / 256 * 256;
+    const size_t bm_a = (bm + 255) / 256 * 256, bl_a = (bl + 255) / 256 * 256;
+    const size_t total = 2 * (bm_a + bl_a) + bp + 256;
     if (cudaMalloc(&s->d_mem, total) != cudaSuccess) return FTSP2_E_CUDA;
     uint8_t* p = static_cast<uint8_t*>(s->d_mem);
     for (int v = 0; v < 2; ++v) {
         s->d_models[v] = reinterpret_cast<DevModel*>(p);
-        p += bm;
+        p += bm_a;
         s->d_layers[v] = reinterpret_cast<DevLayer*>(p);
-        p += bl;
+        p += bl_a;
         if (cudaMemcpy(s->d_models[v], dm[v].data(), bm, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(s->d_layers[v], dl[v].data(), bl, cudaMemcpyHostToDevice) != cudaSuccess)
+            return FTSP2_E_CUDA;
+    }
+    // the Max-SP2 coefficient pool (FP32 mode uses the unscaled variant)
+    s->d_coef = nullptr;
+    if (!pool[0].empty()) {
+        s->d_coef = reinterpret_cast<float*>(p);
+        if (cudaMemcpy(s->d_coef, pool[0].data(), sizeof(float) * pool[0].size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
             return FTSP2_E_CUDA;
     }
     cudaGetDevice(&s->device);
@@ -366,7 +440,8 @@ static int host_tiles_of(int n, int BM, int BN) {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want, int flags, Layout& L) {
+static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want, int flags, Layout& L,
+                         int planes = 2) {
     if (!inst || nb < 1) return FTSP2_E_ARG;
     if (mode < FTSP2_FP32 || mode > FTSP2_FP16X2) return FTSP2_E_ARG;
     if (want < 1 || want > 3) return FTSP2_E_ARG;
@@ -427,9 +502,12 @@ static ftsp2_status plan(const ftsp2_instance* inst, int nb, int mode, int want,
     for (int c = 0; c < kMaxChains; ++c) {
         L.Z[c] = L.A[c] = L.OP[c][0] = L.OP[c][1] = L.OPR[c][0] = L.OPR[c][1] = 0;
     }
+    L.planes = std::max(2, planes);
     for (int c = 0; c < nch; ++c) {
-        L.Z[c] = take(4 * L.plane_elems);
-        L.A[c] = take(4 * L.plane_elems);
+        // state planes 0 .. planes - 1 back to back: Z, A, then the further
+        // stored layers of Max-SP2 tables (plane j at Z + j plane_elems)
+        L.Z[c] = take(4 * L.plane_elems * (size_t)L.planes);
+        L.A[c] = L.Z[c] + 4 * L.plane_elems;
         L.OP[c][0] = take((size_t)op_bytes(fmt) * L.plane_elems);
         L.OP[c][1] = take((size_t)op_bytes(fmt) * L.plane_elems);
         if (refine) {
@@ -525,8 +603,10 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     DeviceInfo di;
     ftsp2_status st = device_info(di);
     if (st != FTSP2_OK) return st;
+    // Max-SP2 tables keep every layer: FP32 mode (CUDA-core layers) only
+    if (set->has_max && mode != FTSP2_FP32) return FTSP2_E_UNSUPPORTED;
     Layout L;
-    st = plan(inst, nb, mode, want, flags, L);
+    st = plan(inst, nb, mode, want, flags, L, set->planes);
     if (st != FTSP2_OK) return st;
     if (ws_bytes < L.total) return FTSP2_E_WORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -674,6 +754,7 @@ static ftsp2_status run(const double* dH, const ftsp2_instance* inst, const ftsp
     la.D = dD;
     la.partials = partials;
     la.status = dstatus;
+    la.coef = set->d_coef;
     la.wait_ns = g_wait_ns.load();
     la.stall_layer = g_stall_layer.load();
     for (int c = 0; c < kMaxChains; ++c) {
@@ -991,14 +1072,16 @@ ftsp2_status ftsp2_model_set_create(const ftsp2_table* tabs, int ntab, ftsp2_mod
     for (int i = 0; i < ntab; ++i) {
         const ftsp2_table& t = tabs[i];
         const int LS = t.theta_entropy ? t.L_entropy : t.L;
-        // a Skip-SP2 table carries an output row: at most kMaxLayers rows in all
-        const int lmax = t.family == FTSP2_FAMILY_SKIP ? kMaxLayers - 1 : kMaxLayers;
+        // a Skip-SP2 table carries an output row: at most kMaxLayers rows in
+        // all; a Max-SP2 table keeps every layer: at most kMaxMaxLayers
+        const int lmax = t.family == FTSP2_FAMILY_SKIP ? kMaxLayers - 1
+                         : t.family == FTSP2_FAMILY_MAX ? kMaxMaxLayers : kMaxLayers;
         if (t.L < 1 || t.L > lmax || LS < 1 || LS > lmax || !t.theta || !(t.beta0 > 0) ||
             !(t.mu0 > 0 && t.mu0 < 1) || !std::isfinite(t.alpha)) {
             delete s;
             return FTSP2_E_ARG;
         }
-        if (t.family != FTSP2_FAMILY_MLSP2 && t.family != FTSP2_FAMILY_SKIP) {
+        if (t.family != FTSP2_FAMILY_MLSP2 && t.family != FTSP2_FAMILY_SKIP && t.family != FTSP2_FAMILY_MAX) {
             delete s;
             return FTSP2_E_ARG;
         }
@@ -1009,9 +1092,16 @@ ftsp2_status ftsp2_model_set_create(const ftsp2_table* tabs, int ntab, ftsp2_mod
         h.beta0 = t.beta0;
         h.mu0 = t.mu0;
         h.alpha = t.alpha;
-        const int rows = t.family == FTSP2_FAMILY_SKIP ? 1 : 0;   // the output row of Skip-SP2
-        h.th.assign(t.theta, t.theta + 4 * (t.L + rows));
-        if (t.theta_entropy) h.thS.assign(t.theta_entropy, t.theta_entropy + 4 * (LS + rows));
+        if (t.family == FTSP2_FAMILY_MAX) {
+            h.th.assign(t.theta, t.theta + max_nparams(t.L));
+            if (t.theta_entropy) h.thS.assign(t.theta_entropy, t.theta_entropy + max_nparams(LS));
+            s->has_max = true;
+            s->planes = std::max(s->planes, std::max(t.L, LS) + 1);
+        } else {
+            const int rows = t.family == FTSP2_FAMILY_SKIP ? 1 : 0;   // the output row of Skip-SP2
+            h.th.assign(t.theta, t.theta + 4 * (t.L + rows));
+            if (t.theta_entropy) h.thS.assign(t.theta_entropy, t.theta_entropy + 4 * (LS + rows));
+        }
         for (double v : h.th)
             if (!std::isfinite(v)) { delete s; return FTSP2_E_ARG; }
         for (double v : h.thS)
@@ -1064,6 +1154,18 @@ ftsp2_status ftsp2_model_set_table(const ftsp2_model_set* s, int idx, int* L, do
     if (beta0) *beta0 = h.beta0;
     if (mu0) *mu0 = h.mu0;
     if (alpha) *alpha = h.alpha;
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_workspace_size_set(const ftsp2_instance* inst, int nb, const ftsp2_model_set* set,
+                                      ftsp2_mode mode, int want, size_t* bytes) {
+    if (!bytes) return FTSP2_E_ARG;
+    if (!set || set->host.empty()) return FTSP2_E_NOMODEL;
+    Layout L;
+    const ftsp2_status st = plan(inst, nb, mode, want, FTSP2_REFINE2 | FTSP2_REFINE_TC | FTSP2_EPI_DEFERRED, L,
+                                 set->planes);
+    if (st != FTSP2_OK) return st;
+    *bytes = L.total;
     return FTSP2_OK;
 }
 
@@ -1401,13 +1503,78 @@ ftsp2_status ftsp2_train_normal_equations(const double* dM, int nsamples, int L,
 // J_p = J P and the reductions transform as P^T (J^T J) P and P^T (J^T r).
 // Skip-SP2 tables (FORM_SKIP): p = the table itself, 4L + 2 entries (layer
 // rows, then A_0 and gamma_L), with its own forward/Jacobian kernel.
-enum { FORM_MLSP2 = 0, FORM_ALT = 1, FORM_SKIP = 2 };
+// Max-SP2 tables (FORM_MAX): p = the flat table, L (L + 5) / 2 + 2 entries.
+// Skip-SP2 with k stored layers and K accumulators (FORM_SKIPK): p = (alpha
+// (L x (k + 1), the constant last), beta (L x K), gamma (L x K), A_{0,1},
+// gamma_L), (1 + k + 2K) L + 2 entries, the other initial accumulators zero;
+// theta(p) = its Max-SP2 embedding (ftsp2_skip_to_max) and P its exact
+// Jacobian (the embedding is affine in each single parameter).
+enum { FORM_MLSP2 = 0, FORM_ALT = 1, FORM_SKIP = 2, FORM_MAX = 3, FORM_SKIPK = 4 };
 
-static int form_params(int form, int L) {
-    return form == FORM_ALT ? 2 * L + 2 : (form == FORM_SKIP ? 4 * L + 2 : 4 * L);
+struct FormDims {
+    int k = 1, K = 1;          // FORM_SKIPK only
+};
+
+static int form_params(int form, int L, const FormDims& fd = FormDims()) {
+    switch (form) {
+        case FORM_ALT: return 2 * L + 2;
+        case FORM_SKIP: return 4 * L + 2;
+        case FORM_MAX: return max_nparams(L);
+        case FORM_SKIPK: return (1 + fd.k + 2 * fd.K) * L + 2;
+        default: return 4 * L;
+    }
 }
-static int form_theta_dim(int form, int L) { return form == FORM_SKIP ? 4 * L + 2 : 4 * L; }
-static int form_family(int form) { return form == FORM_SKIP ? FTSP2_FAMILY_SKIP : FTSP2_FAMILY_MLSP2; }
+static int form_theta_dim(int form, int L) {
+    return form == FORM_SKIP ? 4 * L + 2 : (form == FORM_MAX || form == FORM_SKIPK) ? max_nparams(L) : 4 * L;
+}
+static int form_family(int form) {
+    return form == FORM_SKIP ? FTSP2_FAMILY_SKIP
+                             : (form == FORM_MAX || form == FORM_SKIPK) ? FTSP2_FAMILY_MAX : FTSP2_FAMILY_MLSP2;
+}
+
+// Max-SP2 embedding of a FORM_SKIPK parameter vector
+static ftsp2_status skipk_theta(int L, const FormDims& fd, const double* p, double* th) {
+    const int k = fd.k, K = fd.K;
+    const double* al = p;
+    const double* be = al + L * (k + 1);
+    const double* ga = be + L * K;
+    std::vector<double> A0(std::max(K, 1), 0.0);
+    A0[0] = ga[L * K];
+    return ftsp2_skip_to_max(L, k, K, al, K ? be : nullptr, K ? ga : nullptr, K ? A0.data() : nullptr,
+                             ga[L * K + 1], th);
+}
+
+// d theta / d p of FORM_SKIPK (nt x np, row-major), written out from the
+// embedding: delta_i = alpha_{i,k} + beta_{i,1} A_{0,1},
+// theta_{i,j} = sum_l beta_{i,l} gamma_{j,l} [j < i] + alpha_{i,i-j} [i - j < k],
+// gamma_j = sum_l gamma_{j,l}, c = A_{0,1}, gamma_L.
+static void skipk_jacobian(int L, const FormDims& fd, const double* p, std::vector<double>& P) {
+    const int k = fd.k, K = fd.K, np = form_params(FORM_SKIPK, L, fd), nt = max_nparams(L);
+    const int pa = 0, pb = L * (k + 1), pg = pb + L * K, pA = pg + L * K, pL = pA + 1;
+    P.assign((size_t)nt * np, 0.0);
+    auto at = [&](int row, int col) -> double& { return P[(size_t)row * np + col]; };
+    int o = 0;
+    for (int i = 0; i < L; ++i) {
+        at(o, pa + i * (k + 1) + k) = 1.0;
+        if (K > 0) {
+            at(o, pb + i * K) += p[pA];
+            at(o, pA) += p[pb + i * K];
+        }
+        for (int l = 0; l < K; ++l) at(o + 1, pg + i * K + l) = 1.0;
+        for (int j = 0; j <= i; ++j) {
+            const int row = o + 2 + j;
+            if (j < i)
+                for (int l = 0; l < K; ++l) {
+                    at(row, pb + i * K + l) += p[pg + j * K + l];
+                    at(row, pg + j * K + l) += p[pb + i * K + l];
+                }
+            if (i - j < k) at(row, pa + i * (k + 1) + (i - j)) += 1.0;
+        }
+        o += i + 3;
+    }
+    at(o, pA) = 1.0;
+    at(o + 1, pL) = 1.0;
+}
 
 static void alt_rows(int L, const double* alt, double* th) {
     for (int i = 0; i < L; ++i) {
@@ -1424,9 +1591,13 @@ static void alt_rows(int L, const double* alt, double* th) {
     last[2] = last[2] * w + u;
 }
 
-// P (4L x np, row-major) at p
-static void form_jacobian(int form, int L, const double* p, std::vector<double>& P) {
-    const int np = form_params(form, L), nt = form_theta_dim(form, L);
+// P (nt x np, row-major) at p
+static void form_jacobian(int form, int L, const double* p, std::vector<double>& P, const FormDims& fd) {
+    if (form == FORM_SKIPK) {
+        skipk_jacobian(L, fd, p, P);
+        return;
+    }
+    const int np = form_params(form, L, fd), nt = form_theta_dim(form, L);
     P.assign((size_t)nt * np, 0.0);
     if (form != FORM_ALT) {
         for (int i = 0; i < nt; ++i) P[(size_t)i * np + i] = 1.0;
@@ -1448,8 +1619,20 @@ static void form_jacobian(int form, int L, const double* p, std::vector<double>&
     P[(size_t)(r + 2) * np + 2 * L] = 1.0;
 }
 
-static ftsp2_status form_theta(int form, int L, const double* p, ThetaParam& tp) {
+static ftsp2_status form_theta(int form, int L, const double* p, ThetaParam& tp, const FormDims& fd) {
     if (form == FORM_MLSP2) return load_theta(L, p, tp);
+    if (form == FORM_MAX || form == FORM_SKIPK) {
+        if (!p || L < 1 || L > kMaxMaxLayers) return FTSP2_E_ARG;
+        std::memset(&tp, 0, sizeof(tp));
+        const int np = form_params(form, L, fd);
+        for (int i = 0; i < np; ++i)
+            if (!std::isfinite(p[i])) return FTSP2_E_ARG;
+        if (form == FORM_MAX) {
+            std::copy(p, p + np, tp.v);
+            return FTSP2_OK;
+        }
+        return skipk_theta(L, fd, p, tp.v);
+    }
     if (form == FORM_SKIP) {
         if (!p || L < 1 || L > kMaxLayers - 1) return FTSP2_E_ARG;
         std::memset(&tp, 0, sizeof(tp));
@@ -1469,20 +1652,27 @@ static ftsp2_status form_theta(int form, int L, const double* p, ThetaParam& tp)
 
 // Levenberg-Marquardt (optionally geodesic-accelerated) on p; residuals, the
 // Jacobian of theta and J^T J, J^T r run on the GPU, the rest on the host.
+// Rows argument of train_layout for a form: room for its nt + 1 columns
+static int form_layout_rows(int form, int L) {
+    if (form == FORM_SKIP) return L + 1;
+    if (form == FORM_MAX || form == FORM_SKIPK) return (max_nparams(L) + 3) / 4;
+    return L;
+}
+
 static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int L, double alpha, const double* dX,
                              int nsamples, int iterations, int accel, const double* p_init, double* p_out,
-                             ftsp2_train_report* rep, void* dWork, size_t work_bytes, void* stream) {
+                             ftsp2_train_report* rep, void* dWork, size_t work_bytes, void* stream,
+                             const FormDims& fd = FormDims()) {
     if ((target != FTSP2_TARGET_FERMI && target != FTSP2_TARGET_ENTROPY) || !dX || nsamples < 1 || !p_out ||
         !dWork || iterations < 0 || !p_init)
         return FTSP2_E_ARG;
-    const int np = form_params(form, L), nt = form_theta_dim(form, L);
+    const int np = form_params(form, L, fd), nt = form_theta_dim(form, L);
     const int fam = form_family(form);
     std::vector<double> p(p_init, p_init + np);
     ThetaParam tp;
-    ftsp2_status st = form_theta(form, L, p.data(), tp);
+    ftsp2_status st = form_theta(form, L, p.data(), tp, fd);
     if (st != FTSP2_OK) return st;
-    // room for nt + 1 columns (the Skip-SP2 form has 4L + 2 parameters)
-    const TrainLayout tl = train_layout(nsamples, form == FORM_SKIP ? L + 1 : L);
+    const TrainLayout tl = train_layout(nsamples, form_layout_rows(form, L));
     if (work_bytes < tl.total) return FTSP2_E_WORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint8_t* W = static_cast<uint8_t*>(dWork);
@@ -1508,7 +1698,7 @@ static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int
         if (cudaMemcpyAsync(Gt.data(), dG, sizeof(double) * mt * mt, cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return FTSP2_E_CUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return FTSP2_E_CUDA;
-        form_jacobian(form, L, pp, Pm);
+        form_jacobian(form, L, pp, Pm, fd);
         cst = 0.5 * Gt[(size_t)nt * mt + nt];
         std::vector<double> GP((size_t)nt * np, 0.0);   // (J^T J) P
         for (int i = 0; i < nt; ++i)
@@ -1539,7 +1729,19 @@ static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int
     std::vector<double> Md((size_t)np * np), v, a, rhs(np), JTJc, gc, Pc, vt(nt);
     for (it = 0; it < iterations; ++it) {
         Md = JTJ;
-        for (int i = 0; i < np; ++i) Md[(size_t)i * np + i] += lam * JTJ[(size_t)i * np + i];
+        // FORM_SKIPK: a zero diagonal entry (a parameter the output does not
+        // depend on at p, e.g. the feedback of an accumulator that is still
+        // zero) is damped with the smallest positive one, so Md stays regular
+        double dmin = 0.0;
+        if (form == FORM_SKIPK)
+            for (int i = 0; i < np; ++i) {
+                const double dv = JTJ[(size_t)i * np + i];
+                if (dv > 0.0 && (dmin == 0.0 || dv < dmin)) dmin = dv;
+            }
+        for (int i = 0; i < np; ++i) {
+            const double dv = JTJ[(size_t)i * np + i];
+            Md[(size_t)i * np + i] += lam * (form == FORM_SKIPK && dv <= 0.0 ? (dmin > 0.0 ? dmin : 1.0) : dv);
+        }
         for (int i = 0; i < np; ++i) rhs[i] = -g[i];
         if (!chol_solve(Md, np, rhs, v)) {
             lam = std::min(lam * 10.0, 1e12);
@@ -1552,7 +1754,7 @@ static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int
             std::vector<double> ph(p);
             for (int i = 0; i < np; ++i) ph[i] += h * v[i];
             ThetaParam th_h;
-            if (form_theta(form, L, ph.data(), th_h) != FTSP2_OK) return FTSP2_E_ARG;
+            if (form_theta(form, L, ph.data(), th_h, fd) != FTSP2_OK) return FTSP2_E_ARG;
             for (int k = 0; k < nt; ++k) {
                 double acc = 0.0;
                 for (int j = 0; j < np; ++j) acc += Pj[(size_t)k * np + j] * v[j];
@@ -1584,7 +1786,7 @@ static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int
         for (int i = 0; i < np; ++i) pc[i] += step[i];
         ThetaParam cand;
         double cc = INFINITY;
-        if (form_theta(form, L, pc.data(), cand) == FTSP2_OK) {
+        if (form_theta(form, L, pc.data(), cand, fd) == FTSP2_OK) {
             st = eval(cand, pc.data(), JTJc, gc, Pc, cc);
             if (st != FTSP2_OK) return st;
         }
@@ -1623,13 +1825,44 @@ static ftsp2_status lm_train(int form, int target, double beta0, double mu0, int
 
 // The sample set (built on the host, copied into the workspace) and the
 // default start of each form, then the LM fit on the device.
+// Default start of a FORM_SKIPK fit: the one-accumulator embedding of the
+// Eq. mlsp2 start (ftsp2_mlsp2_to_skip), its connections in slots 0 and its
+// constant in slot k; the further stored layers and accumulator inputs gamma
+// zero, the further accumulators' feedback beta kSkipkBetaStart (no effect
+// while those accumulators are zero; nonzero, so that their gamma have a
+// derivative and the fit can open them).
+constexpr double kSkipkBetaStart = 0.01;
+
+static void skipk_start(int L, const FormDims& fd, double beta0, double mu0, double* p) {
+    const int k = fd.k, K = fd.K;
+    std::vector<double> th(4 * L), tab(4 * L + 4);
+    train_init_mlsp2(L, beta0, mu0, th.data());
+    mlsp2_to_skip(L, th.data(), tab.data());
+    double* al = p;
+    double* be = al + L * (k + 1);
+    double* ga = be + L * K;
+    std::fill(p, p + form_params(FORM_SKIPK, L, fd), 0.0);
+    for (int i = 0; i < L; ++i) {
+        al[i * (k + 1) + 0] = tab[4 * i + 1];
+        al[i * (k + 1) + k] = tab[4 * i + 0];
+        for (int l = 0; l < K; ++l) {
+            be[i * K + l] = l == 0 ? tab[4 * i + 2] : kSkipkBetaStart;
+            ga[i * K + l] = l == 0 ? tab[4 * i + 3] : 0.0;
+        }
+    }
+    ga[L * K] = tab[4 * L];          // A_{0,1}
+    ga[L * K + 1] = tab[4 * L + 1];  // gamma_L
+}
+
 static ftsp2_status train_entry(int form, int target, double beta0, double mu0, int L, double alpha, int nsamples,
                                 uint64_t seed, int iterations, int accel, const double* p_init, double* p_out,
-                                ftsp2_train_report* rep, void* dWork, size_t work_bytes, void* stream) {
+                                ftsp2_train_report* rep, void* dWork, size_t work_bytes, void* stream,
+                                const FormDims& fd = FormDims()) {
     if (nsamples < 1 || !dWork || !p_out || !(beta0 > 0.0) || !(mu0 > 0.0 && mu0 < 1.0)) return FTSP2_E_ARG;
-    if (L < 1 || L > (form == FORM_SKIP ? kMaxLayers - 1 : kMaxLayers)) return FTSP2_E_ARG;
-    const int train_L = form == FORM_SKIP ? L + 1 : L;       // rows of the Jacobian buffers
-    const TrainLayout tl = train_layout(nsamples, train_L);
+    const bool maxf = form == FORM_MAX || form == FORM_SKIPK;
+    if (L < 1 || L > (form == FORM_SKIP ? kMaxLayers - 1 : maxf ? kMaxMaxLayers : kMaxLayers)) return FTSP2_E_ARG;
+    if (form == FORM_SKIPK && (fd.k < 1 || fd.K < 1 || fd.k > L)) return FTSP2_E_ARG;
+    const TrainLayout tl = train_layout(nsamples, form_layout_rows(form, L));
     if (work_bytes < tl.total) return FTSP2_E_WORKSPACE;
     std::vector<double> x((size_t)nsamples);
     train_sample_grid(beta0, mu0, nsamples, seed, x.data());
@@ -1645,6 +1878,15 @@ static ftsp2_status train_entry(int form, int target, double beta0, double mu0, 
         } else if (form == FORM_ALT) {
             init.resize(2 * L + 2);
             train_init_alt(L, mu0, init.data());
+        } else if (form == FORM_MAX) {
+            std::vector<double> th(4 * L);
+            train_init_mlsp2(L, beta0, mu0, th.data());
+            init.resize(max_nparams(L));
+            const ftsp2_status st = ftsp2_mlsp2_to_max(L, th.data(), init.data());
+            if (st != FTSP2_OK) return st;
+        } else if (form == FORM_SKIPK) {
+            init.resize(form_params(FORM_SKIPK, L, fd));
+            skipk_start(L, fd, beta0, mu0, init.data());
         } else {
             std::vector<double> th(4 * L);
             train_init_mlsp2(L, beta0, mu0, th.data());
@@ -1655,7 +1897,7 @@ static ftsp2_status train_entry(int form, int target, double beta0, double mu0, 
     }
     if (form != FORM_SKIP)
         return lm_train(form, target, beta0, mu0, L, alpha, dX, nsamples, iterations, accel, p_init, p_out, rep,
-                        dWork, work_bytes, stream);
+                        dWork, work_bytes, stream, fd);
     // the table's (L + 1) x 4 rows: the output row's last two entries are unused
     std::vector<double> p(4 * L + 2), out(4 * L + 2);
     std::copy(p_init, p_init + 4 * L + 2, p.begin());
@@ -1691,13 +1933,115 @@ ftsp2_status ftsp2_train_coeffs_skip(int target, double beta0, double mu0, int L
                        skip_out, rep, dWork, work_bytes, stream);
 }
 
+size_t ftsp2_train_workspace_size_max(int nsamples, int L) {
+    if (nsamples < 1 || L < 1 || L > kMaxMaxLayers) return 0;
+    return train_layout(nsamples, form_layout_rows(FORM_MAX, L)).total;
+}
+
+ftsp2_status ftsp2_train_coeffs_max(int target, double beta0, double mu0, int L, double alpha, int nsamples,
+                                    uint64_t seed, int iterations, int accel, const double* max_init, double* max_out,
+                                    ftsp2_train_report* rep, void* dWork, size_t work_bytes, void* stream) {
+    return train_entry(FORM_MAX, target, beta0, mu0, L, alpha, nsamples, seed, iterations, accel, max_init, max_out,
+                       rep, dWork, work_bytes, stream);
+}
+
+ftsp2_status ftsp2_train_coeffs_skipk(int target, double beta0, double mu0, int L, int k, int K, double alpha,
+                                      int nsamples, uint64_t seed, int iterations, int accel, const double* skip_init,
+                                      double* skip_out, ftsp2_train_report* rep, void* dWork, size_t work_bytes,
+                                      void* stream) {
+    FormDims fd;
+    fd.k = k;
+    fd.K = K;
+    return train_entry(FORM_SKIPK, target, beta0, mu0, L, alpha, nsamples, seed, iterations, accel, skip_init,
+                       skip_out, rep, dWork, work_bytes, stream, fd);
+}
+
+ftsp2_status ftsp2_train_init_skipk(int L, int k, int K, double beta0, double mu0, double* skip_out) {
+    if (L < 1 || L > kMaxMaxLayers || k < 1 || K < 1 || k > L || !skip_out || !(beta0 > 0.0) ||
+        !(mu0 > 0.0 && mu0 < 1.0))
+        return FTSP2_E_ARG;
+    FormDims fd;
+    fd.k = k;
+    fd.K = K;
+    skipk_start(L, fd, beta0, mu0, skip_out);
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_skipk_to_max(int L, int k, int K, const double* skip, double* max_out) {
+    if (L < 1 || L > kMaxMaxLayers || k < 1 || K < 1 || !skip || !max_out) return FTSP2_E_ARG;
+    FormDims fd;
+    fd.k = k;
+    fd.K = K;
+    return skipk_theta(L, fd, skip, max_out);
+}
+
+ftsp2_status ftsp2_skip_to_max(int L, int k, int K, const double* alpha, const double* beta, const double* gamma,
+                               const double* A0, double gamma_L, double* max_out) {
+    if (L < 1 || L > kMaxMaxLayers || k < 1 || K < 0 || !alpha || !max_out || (K > 0 && (!beta || !gamma || !A0)) ||
+        !std::isfinite(gamma_L))
+        return FTSP2_E_ARG;
+    for (int i = 0; i < L * (k + 1); ++i)
+        if (!std::isfinite(alpha[i])) return FTSP2_E_ARG;
+    for (int i = 0; i < L * K; ++i)
+        if (!std::isfinite(beta[i]) || !std::isfinite(gamma[i])) return FTSP2_E_ARG;
+    for (int l = 0; l < K; ++l)
+        if (!std::isfinite(A0[l])) return FTSP2_E_ARG;
+    int o = 0;
+    for (int i = 0; i < L; ++i) {
+        double dl = alpha[i * (k + 1) + k];
+        for (int l = 0; l < K; ++l) dl += beta[i * K + l] * A0[l];
+        max_out[o] = dl;
+        double gs = 0.0;
+        for (int l = 0; l < K; ++l) gs += gamma[i * K + l];
+        max_out[o + 1] = gs;
+        for (int j = 0; j <= i; ++j) {
+            double th = 0.0;
+            if (j < i)
+                for (int l = 0; l < K; ++l) th += beta[i * K + l] * gamma[j * K + l];
+            if (i - j < k) th += alpha[i * (k + 1) + (i - j)];
+            max_out[o + 2 + j] = th;
+        }
+        o += i + 3;
+    }
+    double c = 0.0;
+    for (int l = 0; l < K; ++l) c += A0[l];
+    max_out[o] = c;
+    max_out[o + 1] = gamma_L;
+    return FTSP2_OK;
+}
+
+ftsp2_status ftsp2_mlsp2_to_max(int L, const double* theta, double* max_out) {
+    if (L < 1 || L > kMaxMaxLayers || !theta || !max_out) return FTSP2_E_ARG;
+    std::vector<double> sk(4 * (L + 1));
+    const ftsp2_status st = ftsp2_mlsp2_to_skip(L, theta, sk.data());
+    if (st != FTSP2_OK) return st;
+    // Skip-SP2 rows (delta, alpha, beta, gamma) with output row (A_0, gamma_L):
+    // u_i = delta_i + alpha_i x_i + beta_i (A_0 + sum_{j<i} gamma_j x_j)
+    int o = 0;
+    const double A0 = sk[4 * L], gL = sk[4 * L + 1];
+    for (int i = 0; i < L; ++i) {
+        max_out[o] = sk[4 * i] + sk[4 * i + 2] * A0;
+        max_out[o + 1] = sk[4 * i + 3];
+        for (int j = 0; j < i; ++j) max_out[o + 2 + j] = sk[4 * i + 2] * sk[4 * j + 3];
+        max_out[o + 2 + i] = sk[4 * i + 1];
+        o += i + 3;
+    }
+    max_out[o] = A0;
+    max_out[o + 1] = gL;
+    return FTSP2_OK;
+}
+
 ftsp2_status ftsp2_train_residuals(int family, int target, double beta0, double mu0, int L, double alpha,
                                    const double* table, const double* dX, int npoints, double* dR, void* stream) {
     if ((target != FTSP2_TARGET_FERMI && target != FTSP2_TARGET_ENTROPY) || !table || !dX || !dR || npoints < 1)
         return FTSP2_E_ARG;
-    if (family != FTSP2_FAMILY_MLSP2 && family != FTSP2_FAMILY_SKIP) return FTSP2_E_ARG;
-    const int nv = family == FTSP2_FAMILY_SKIP ? 4 * L + 2 : 4 * L;
-    if (L < 1 || L > (family == FTSP2_FAMILY_SKIP ? kMaxLayers - 1 : kMaxLayers)) return FTSP2_E_ARG;
+    if (family != FTSP2_FAMILY_MLSP2 && family != FTSP2_FAMILY_SKIP && family != FTSP2_FAMILY_MAX)
+        return FTSP2_E_ARG;
+    if (L < 1 || L > (family == FTSP2_FAMILY_SKIP  ? kMaxLayers - 1
+                      : family == FTSP2_FAMILY_MAX ? kMaxMaxLayers
+                                                   : kMaxLayers))
+        return FTSP2_E_ARG;
+    const int nv = family == FTSP2_FAMILY_SKIP ? 4 * L + 2 : family == FTSP2_FAMILY_MAX ? max_nparams(L) : 4 * L;
     ThetaParam tp;
     std::memset(&tp, 0, sizeof(tp));
     for (int i = 0; i < nv; ++i) {

@@ -25,6 +25,8 @@
 namespace ftsp2 {
 
 constexpr int kMaxLayers = 64;
+constexpr int kMaxMaxLayers = 20;            // Max-SP2 tables keep every layer: at most 20
+int max_nparams(int L);                      // L (L + 5) / 2 + 2 numbers of a flat Max-SP2 table
 constexpr int kMaxChains = 2;
 constexpr int kTileM = 128;                  // tensor-core tile rows (UMMA M)
 constexpr int kPad = 128;                    // matrix pitch granularity (elements)
@@ -58,6 +60,12 @@ struct DevLayer {
     float a;          // mul for unscaled products
     float p, q, d2, g;
     float pad0, pad1;
+    // Max-SP2 layers (family FTSP2_FAMILY_MAX; FP32 mode): the layer reads the
+    // nplanes stored centred layers x^_0 .. x^_{k} (state planes 0 .. k of the
+    // chain) and its coefficients start at coef in the model set's pool:
+    // theta_{k,0..k}, then theta_{k+1,0..k+1} (zeros after the last layer),
+    // then, for the last layer, gamma_{0..L}.  nplanes = 0 for the other families.
+    int coef, nplanes;
 };
 
 struct DevModel {
@@ -71,8 +79,11 @@ struct DevModel {
     float scale0;     // 2^(e_0) of the Fermi chain (FP16 operands of Z_0)
     float scale0S;    // 2^(e_0) of the entropy chain
     // layer-0 state from the centred input X0 - mu0 I of each chain:
-    // Z_0 = z0 (X0 - mu0 I), A = a0 (X0 - mu0 I) (Eq. mlsp2: 1, 0)
+    // Z_0 = z0 (X0 - mu0 I), A = a0 (X0 - mu0 I) (Eq. mlsp2: 1, 0), and the
+    // layer-0 operands op0 Z_0 (op0 = 1, except for Max-SP2, whose state plane
+    // 0 holds x^_0 = X0 - mu0 I and whose operands are theta_00 x^_0)
     float z0, a0, z0S, a0S;
+    float op0, op0S;
 };
 
 // One output tile of one grouped layer launch.
@@ -102,6 +113,7 @@ struct Layout {
     size_t total;
     size_t plane_elems;   // nb * P * P
     int P, nb, nchains, ntiles, ntiles_ref, BN, BM;
+    int planes;           // FP32 state planes per chain: 2 (Z, A), or L + 1 for Max-SP2 tables
 };
 
 // --- setup / bandwidth kernels (k_setup.cu) --------------------------------
@@ -246,6 +258,7 @@ struct LayerArgs {
     // dependency wait that runs out records FTSP2_E_TIMEOUT and the launch
     // finishes its work list in skip mode; a pipeline wait records it after
     // wait_ns and gives up after 2 wait_ns.
+    const float* coef;                // Max-SP2 coefficient pool of the model set (nullable)
     unsigned long long wait_ns;
     // Test hook (ftsp2_debug_stall_layer): items of this global layer wait for
     // one completion more than their predecessor layer can give, so that the
@@ -279,7 +292,9 @@ struct ThetaParam {
 };
 // family FTSP2_FAMILY_MLSP2: th = L rows (a, b, c, d), 4L Jacobian columns;
 // FTSP2_FAMILY_SKIP: th = L rows (delta, alpha, beta, gamma) + (A_0, gamma_L),
-// 4L + 2 columns.  The residual column follows the Jacobian's.
+// 4L + 2 columns; FTSP2_FAMILY_MAX: th = the flat Max-SP2 table, L (L + 5) / 2
+// + 2 columns (L <= 20: at most 252 entries).  The residual column follows the
+// Jacobian's.
 cudaError_t launch_train_fwd_jac(int target, double beta0, double mu0, int L, double alpha,
                                  const ThetaParam& th, const double* dX, int ns,
                                  double* dR, double* dM, cudaStream_t s, int family = FTSP2_FAMILY_MLSP2);

@@ -1,8 +1,9 @@
 // (a3)-(a6) One layer of the centred recursion with FP32 FMA products on the
 // CUDA cores: the FTSP2_FP32 mode and the FP32 refinement layers
 // (FTSP2_REFINE1/2).  Same triangular tile list (128 x 128 tiles), same
-// epilogue as the tensor-core kernel; the operand is the full symmetric FP32
-// matrix Z_k (written for this layer by the previous layer's epilogue).
+// epilogue as the tensor-core kernel (plus the Max-SP2 layers, which only this
+// kernel runs); the operand is the full symmetric FP32 matrix Z_k (written for
+// this layer by the previous layer's epilogue).
 // Classic register-blocked tile product: 256 threads, 8 x 8 outputs each,
 // K-slices of 16 staged through shared memory (transposed, K-major rows),
 // sums taken over 128-element K chunks.
@@ -83,7 +84,10 @@ __global__ void __launch_bounds__(256) layer_simt_kernel(const __grid_constant__
         for (int i = 0; i < 8; ++i) {
             const int r = rowA + ty * 8 + i;
             const int c0 = rowB + tx * 8;
-            if (c0 < n && c0 + 7 >= r) epi_segment<8>(a, e, r, c0, acc[i], tr, sq);
+            if (c0 < n && c0 + 7 >= r) {
+                if (e.L.nplanes > 0) epi_segment_max<8>(a, e, r, c0, acc[i], tr, sq);
+                else epi_segment<8>(a, e, r, c0, acc[i], tr, sq);
+            }
         }
         if (a.last) {
             for (int o = 16; o > 0; o >>= 1) {

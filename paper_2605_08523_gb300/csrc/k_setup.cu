@@ -397,10 +397,12 @@ __device__ __forceinline__ void write_operand16(int fmt, uint8_t* base, size_t p
 // band's columns in the instance's R x R square (R = n rounded up to the
 // largest tile, 256, at most P):
 // * Z_0 = z0 X, A = a0 X with X = H0 - mu0 I (times alpha for the entropy
-//   chain), in the blocked state layout, for the rows below n and the chunks
+//   chain; for Max-SP2 the stored layer x^_0 = X, z0 = 1, a0 = 0, and A is
+//   the plane of x^_1, written by layer 0), in the blocked state layout, for
+//   the rows below n and the chunks
 //   that reach the upper triangle of the band's 32-row block (the only state
 //   the layer epilogues read): four 512-byte runs per warp and chunk;
-// * operands of Z_0 in the format of the instance's first layer (one parity),
+// * operands op0 Z_0 in the format of the instance's first layer (one parity),
 //   zeros outside n x n in every format and parity a layer may read, as one
 //   32-byte vector per lane and plane (row-major planes).  With `upper_only`
 //   and a 16-bit first format (FP16X2, BF16X3) a real row r is written only
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
     const bool ok = rec.status == FTSP2_OK && rec.model >= 0;
     const size_t base = (size_t)b * P * P;
     const int sl_packed = a.iw[b].start_layer;
-    float alpha = 1.f, sc0 = 1.f, sc0S = 1.f, z0 = 1.f, a0 = 0.f, z0S = 1.f, a0S = 0.f;
+    float alpha = 1.f, sc0 = 1.f, sc0S = 1.f, z0 = 1.f, a0 = 0.f, z0S = 1.f, a0S = 0.f, op0 = 1.f, op0S = 1.f;
     if (ok) {
         const DevModel& M = a.models[rec.model];
         alpha = (float)M.alpha;
@@ -433,6 +435,8 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
         a0 = M.a0;
         z0S = M.z0S;
         a0S = M.a0S;
+        op0 = M.op0;
+        op0S = M.op0S;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cbeg = blockIdx.z * kInitCols, cend = min(R, cbeg + kInitCols);
@@ -476,10 +480,13 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
         for (int ch = 0; ch < a.nchains; ++ch) {
             const bool ent = a.chain_kind[ch] == CHAIN_ENTROPY;
             const float xs = ent ? alpha : 1.f;
-            const float zf = (ent ? z0S : z0) * xs, af = (ent ? a0S : a0) * xs;
-            float zc[16];
+            const float zf = (ent ? z0S : z0) * xs, af = (ent ? a0S : a0) * xs, of = ent ? op0S : op0;
+            float zc[16], zo[16];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) zc[u] = zf * z[u];
+            for (int u = 0; u < 16; ++u) {
+                zc[u] = zf * z[u];
+                zo[u] = of * zc[u];      // the operands: zc itself unless op0 != 1 (Max-SP2)
+            }
             if (state) {
 #pragma unroll
                 for (int blk = 0; blk < 2; ++blk) {
@@ -501,8 +508,8 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a) {
                 // the values (zeros beyond n within the chunk) in the first layer's format
                 const int start = (sl_packed >> (16 * ch)) & 0xffff;
                 const bool ref = a.main_fmt != OP_F32 && start >= a.refine_from;
-                if (ref) write_operand16(a.refine_fmt, a.OPR[ch][start & 1], a.plane_elems, e0, zc, 1.f);
-                else write_operand16(a.main_fmt, a.OP[ch][start & 1], a.plane_elems, e0, zc, ent ? sc0S : sc0);
+                if (ref) write_operand16(a.refine_fmt, a.OPR[ch][start & 1], a.plane_elems, e0, zo, 1.f);
+                else write_operand16(a.main_fmt, a.OP[ch][start & 1], a.plane_elems, e0, zo, ent ? sc0S : sc0);
                 if (cc + 15 >= n) {
                     // a chunk across the order: its padding columns must read as zero in
                     // every other format and parity too (its columns below n there are

@@ -1,6 +1,7 @@
 // (a7) Training kernels (Sec. II C): per-sample forward and reverse sweep of the
-// scalar recursion (Eq. mlsp2, or the entropy expansion of Eqs. entropy
-// expansion / entropy expansion-s), and the FP64 reductions of one
+// scalar recursion (Eq. mlsp2, Skip-SP2 with one stored layer and one
+// accumulator, or Max-SP2; each also under the entropy expansion of Eqs.
+// entropy expansion / entropy expansion-s), and the FP64 reductions of one
 // Levenberg-Marquardt iteration.
 //
 // Layout: the augmented Jacobian M = [J | r] is stored parameter-major,
@@ -125,9 +126,70 @@ __global__ void __launch_bounds__(128) fwd_skip_kernel(int target, double beta0,
     M[(size_t)(4 * L) * ns + s] = fac * gA;
 }
 
+// Max-SP2 (Sec. II A 2, Eq. maxsp2) on the flat table th: for i < L the block
+// (delta_i, gamma_i, theta_{i,0..i}) at off_i = i (i + 5) / 2, then (c, gamma_L);
+// u_i = delta_i + sum_{j<=i} theta_{i,j} x_j, x_{i+1} = u_i^2,
+// F = c + sum_{j<=L} gamma_j x_j.  Reverse sweep with g_j = dF/dx_j (from
+// gamma_j; g_{i+1} is final once the layers after i are done):
+// w = 2 u_i g_{i+1}, dF/d delta_i = w, dF/d theta_{i,j} = w x_j,
+// g_j += w theta_{i,j}; dF/d gamma_j = x_j, dF/dc = 1.  Columns in the flat
+// order, the residual after them.
+constexpr int kTrainMaxMaxL = kMaxMaxLayers;
+
+template <bool WITH_J>
+__global__ void __launch_bounds__(128) fwd_max_kernel(int target, double beta0, double mu0, int L, double alpha,
+                                                      const __grid_constant__ ThetaParam thp,
+                                                      const double* __restrict__ X, int ns,
+                                                      double* __restrict__ R, double* __restrict__ M) {
+    const double* th = thp.v;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    const double x = X[s];
+    double xs[kTrainMaxMaxL + 1], us[kTrainMaxMaxL], g[kTrainMaxMaxL + 1];
+    xs[0] = target == FTSP2_TARGET_ENTROPY ? alpha * (x - mu0) + mu0 : x;
+    const int oc = L * (L + 5) / 2;            // offset of (c, gamma_L)
+    double F = th[oc];
+    for (int i = 0; i < L; ++i) {
+        const int o = i * (i + 5) / 2;
+        double u = th[o];
+        for (int j = 0; j <= i; ++j) u = fma(th[o + 2 + j], xs[j], u);
+        us[i] = u;
+        xs[i + 1] = u * u;
+        F = fma(th[o + 1], xs[i], F);
+    }
+    F = fma(th[oc + 1], xs[L], F);
+    double out = F, fac = 1.0;
+    if (target == FTSP2_TARGET_ENTROPY) {
+        const double k4 = 4.0 * 0.69314718055994530942;
+        out = k4 * F * (1.0 - F);
+        fac = k4 * (1.0 - 2.0 * F);
+    }
+    const double r = out - target_value(target, x, beta0, mu0);
+    R[s] = r;
+    if (!WITH_J) return;
+    const int np = oc + 2;
+    M[(size_t)np * ns + s] = r;
+    M[(size_t)oc * ns + s] = fac;
+    M[(size_t)(oc + 1) * ns + s] = fac * xs[L];
+    for (int j = 0; j < L; ++j) g[j] = th[j * (j + 5) / 2 + 1];
+    g[L] = th[oc + 1];
+    for (int i = L - 1; i >= 0; --i) {
+        const int o = i * (i + 5) / 2;
+        const double w = 2.0 * us[i] * g[i + 1];
+        M[(size_t)o * ns + s] = fac * w;
+        M[(size_t)(o + 1) * ns + s] = fac * xs[i];
+        for (int j = 0; j <= i; ++j) {
+            M[(size_t)(o + 2 + j) * ns + s] = fac * w * xs[j];
+            g[j] = fma(w, th[o + 2 + j], g[j]);
+        }
+    }
+}
+
 cudaError_t launch_train_fwd_jac(int target, double beta0, double mu0, int L, double alpha, const ThetaParam& th,
                                  const double* dX, int ns, double* dR, double* dM, cudaStream_t s, int family) {
-    if (family == FTSP2_FAMILY_SKIP)
+    if (family == FTSP2_FAMILY_MAX)
+        fwd_max_kernel<true><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR, dM);
+    else if (family == FTSP2_FAMILY_SKIP)
         fwd_skip_kernel<true><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR, dM);
     else fwd_kernel<true><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR, dM);
     count_launch();
@@ -136,7 +198,10 @@ cudaError_t launch_train_fwd_jac(int target, double beta0, double mu0, int L, do
 
 cudaError_t launch_train_residual(int target, double beta0, double mu0, int L, double alpha, const ThetaParam& th,
                                   const double* dX, int ns, double* dR, cudaStream_t s, int family) {
-    if (family == FTSP2_FAMILY_SKIP)
+    if (family == FTSP2_FAMILY_MAX)
+        fwd_max_kernel<false><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR,
+                                                               nullptr);
+    else if (family == FTSP2_FAMILY_SKIP)
         fwd_skip_kernel<false><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR,
                                                                 nullptr);
     else fwd_kernel<false><<<(ns + 127) / 128, 128, 0, s>>>(target, beta0, mu0, L, alpha, th, dX, ns, dR, nullptr);

@@ -16,6 +16,12 @@ Two groups of tables:
 * ``--skip``: Skip-SP2 tables (one stored layer, one accumulator): (1500, 26)
   from the embedding of the printed table, (100, 16) from the embedding of
   the SP2 initial guess (ftsp2_train_coeffs_skip), with entropy tables;
+* ``--families``: at beta0 = 100, tables of the three families at several
+  depths for the layers-against-memory comparison: Eq. mlsp2 (L = 10, 12,
+  14), Max-SP2 (L = 8, 10, 12; ftsp2_train_coeffs_max) and Skip-SP2 with two
+  stored layers and two accumulators (L = 10, 12, 14;
+  ftsp2_train_coeffs_skipk, stored with its Max-SP2 embedding, the form the
+  layer kernels run), each with an entropy table started from it;
 * ``--high``: tables at beta0 in {3000, 6000, 12000, 24000} with
   L = ceil(layer count (Eq. layer count)) + 2 layers, which ragged batches of
   rotated spectra need once the Gershgorin width inflates beta'.
@@ -147,6 +153,53 @@ def main_skip(outdir: str, iterations: int = 3000):
     return out
 
 
+def main_families(outdir: str, iterations: int = 1000):
+    import paper_2605_08523_gb300 as ft
+    from .build import build
+    build()
+    os.makedirs(outdir, exist_ok=True)
+    out = {}
+    beta0 = 100.0
+    for L in (10, 12, 14):
+        th, rep = fit(ft, ft.TARGET_FERMI, beta0, L, None, iterations)
+        ths, reps = fit(ft, ft.TARGET_ENTROPY, beta0, L, th, iterations, alpha=ALPHA)
+        out["b100_L%d" % L] = dict(beta0=beta0, mu0=MU0, alpha=ALPHA, L=L, theta=th.tolist(),
+                                   theta_entropy=ths.tolist(),
+                                   fit=dict(max_err_fermi=rep["max_err_grid"], max_err_entropy=reps["max_err_grid"]),
+                                   train=dict(fermi=rep, entropy=reps, samples=100_000, density="1+|f'|"))
+    for L in (8, 10, 12):
+        t0 = time.time()
+        p, rep = ft.ftsp2_train_coeffs_max(ft.TARGET_FERMI, beta0, MU0, L=L, iterations=iterations)
+        rep["seconds"] = time.time() - t0
+        pe, reps = ft.ftsp2_train_coeffs_max(ft.TARGET_ENTROPY, beta0, MU0, max_init=p, iterations=iterations,
+                                             alpha=ALPHA)
+        fitd = dict(max_err_fermi=max_error(ft, ft.TARGET_FERMI, beta0, MU0, p, 1.0, family=2),
+                    max_err_entropy=max_error(ft, ft.TARGET_ENTROPY, beta0, MU0, pe, ALPHA, family=2))
+        out["max_b100_L%d" % L] = dict(beta0=beta0, mu0=MU0, alpha=ALPHA, L=L, family="Max-SP2", max=p.tolist(),
+                                       max_entropy=pe.tolist(), fit=fitd,
+                                       train=dict(fermi=rep, entropy=reps, samples=100_000, density="1+|f'|"))
+    k, K = 2, 2
+    for L in (10, 12, 14):
+        t0 = time.time()
+        v, rep = ft.ftsp2_train_coeffs_skipk(ft.TARGET_FERMI, beta0, MU0, L, k, K, iterations=iterations)
+        rep["seconds"] = time.time() - t0
+        ve, reps = ft.ftsp2_train_coeffs_skipk(ft.TARGET_ENTROPY, beta0, MU0, L, k, K, skip_init=v,
+                                               iterations=iterations, alpha=ALPHA)
+        p, pe = ft.ftsp2_skipk_to_max(v, L, k, K), ft.ftsp2_skipk_to_max(ve, L, k, K)
+        fitd = dict(max_err_fermi=max_error(ft, ft.TARGET_FERMI, beta0, MU0, p, 1.0, family=2),
+                    max_err_entropy=max_error(ft, ft.TARGET_ENTROPY, beta0, MU0, pe, ALPHA, family=2))
+        out["skip22_b100_L%d" % L] = dict(beta0=beta0, mu0=MU0, alpha=ALPHA, L=L, k=k, K=K,
+                                          family="Skip-SP2, two stored layers, two accumulators (as Max-SP2)",
+                                          skipk=v.tolist(), skipk_entropy=ve.tolist(), max=p.tolist(),
+                                          max_entropy=pe.tolist(), fit=fitd,
+                                          train=dict(fermi=rep, entropy=reps, samples=100_000, density="1+|f'|"))
+    for name, d in out.items():
+        print(name, d["fit"], flush=True)
+        with open(os.path.join(outdir, name + ".json"), "w") as f:
+            json.dump(d, f, indent=1)
+    return out
+
+
 def main(outdir: str, iterations: int = 800, quick: bool = False):
     import paper_2605_08523_gb300 as ft
     from .build import build
@@ -191,6 +244,8 @@ if __name__ == "__main__":
         main_skip(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)
     elif "--alt" in sys.argv:
         main_alt(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)
+    elif "--families" in sys.argv:
+        main_families(outdir, iterations=int(args[1]) if len(args) > 1 else 1000)
     elif "--high" in sys.argv:
         main_high(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)
     else:

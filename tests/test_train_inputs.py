@@ -60,3 +60,49 @@ def test_argument_checks(ft):
         ft.ftsp2_train_init(65, 100.0, 1 / 3)
     with pytest.raises(ft.Ftsp2Error):
         ft.ftsp2_mlsp2_to_skip(np.array([[0.0, 1.0, 0.0, 0.0]]))      # a linear layer has no square form
+
+
+@pytest.mark.parametrize("L", [1, 5, 20])
+def test_mlsp2_to_max_matches_oracle(ft, L):
+    from oracle import maxsp2
+    rng = np.random.default_rng(L)
+    th = rng.normal(size=(L, 4)) * 0.5
+    th[:, 0] = np.where(np.abs(th[:, 0]) < 0.2, 0.7, th[:, 0])
+    got = ft.ftsp2_mlsp2_to_max(th)
+    assert got.size == ft.max_nparams(L)
+    assert np.max(np.abs(got - maxsp2.mlsp2_to_max(th))) <= 1e-13 * max(1.0, np.max(np.abs(got)))
+
+
+@pytest.mark.parametrize("L,k,K", [(1, 1, 1), (6, 2, 2), (9, 3, 1), (4, 1, 3), (7, 2, 0), (20, 2, 2)])
+def test_skip_to_max_matches_oracle(ft, L, k, K):
+    from oracle import maxsp2
+    rng = np.random.default_rng(100 * L + 10 * k + K)
+    t = dict(alpha=rng.normal(size=(L, k + 1)), beta=rng.normal(size=(L, K)), gamma=rng.normal(size=(L, K)),
+             A0=rng.normal(size=K), gL=float(rng.normal()))
+    got = ft.ftsp2_skip_to_max(t["alpha"], t["beta"], t["gamma"], t["A0"], t["gL"])
+    assert np.max(np.abs(got - maxsp2.skip_to_max(t))) <= 1e-13 * max(1.0, np.max(np.abs(got)))
+
+
+def test_max_conversions_reject_bad_arguments(ft):
+    with pytest.raises(Exception):
+        ft.ftsp2_mlsp2_to_max(np.ones((21, 4)))          # more than 20 layers
+    with pytest.raises(Exception):
+        ft.ftsp2_skip_to_max(np.ones((3, 1)), np.ones((3, 1)), np.ones((3, 1)), np.ones(1))   # k = 0
+    with pytest.raises(Exception):
+        ft.ftsp2_skip_to_max(np.full((3, 2), np.nan), np.ones((3, 1)), np.ones((3, 1)), np.ones(1))
+    assert [ft.max_layers_of(ft.max_nparams(L)) for L in (1, 7, 20)] == [1, 7, 20]
+
+
+@pytest.mark.parametrize("L,k,K,beta0", [(12, 2, 2, 100.0), (8, 1, 1, 40.0), (10, 3, 2, 200.0)])
+def test_skipk_start_and_embedding_match_oracle(ft, L, k, K, beta0):
+    from oracle import maxsp2
+    v = ft.ftsp2_train_init_skipk(L, k, K, beta0, 1 / 3)
+    t = maxsp2.skip_from_skip1(skipsp2.from_mlsp2(train.init_from_sp2(L, beta0, 1 / 3)), k, K, beta_extra=0.01)
+    assert v.size == (1 + k + 2 * K) * L + 2
+    assert np.max(np.abs(v - maxsp2.skip_pack(t))) <= 1e-14 * max(1.0, np.max(np.abs(v)))
+    # the start computes the Eq. mlsp2 start's function
+    p = ft.ftsp2_skipk_to_max(v, L, k, K)
+    assert np.max(np.abs(p - maxsp2.skip_to_max(t))) <= 1e-13 * max(1.0, np.max(np.abs(p)))
+    x = np.linspace(0.0, 1.0, 1001)
+    ref = train.forward(train.init_from_sp2(L, beta0, 1 / 3), x)
+    assert np.max(np.abs(maxsp2.max_scalar(x, p, L) - ref)) < 1e-11
