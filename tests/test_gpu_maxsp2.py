@@ -168,3 +168,40 @@ def test_workspace_and_refused_modes(ft, golden):
         with pytest.raises(ft.Ftsp2Error) as e:
             run(ft, ms, Hs, [0.0], [0.2], mode=mode, want=1)
         assert e.value.code == ft._lib.E_UNSUPPORTED
+
+
+def _bounded_max_table(rng, L):
+    # u_i = 0.3 + 0.5 x_i + small weights on the earlier layers: x stays in
+    # [0, 1] for x_0 in [0, 1], so every layer is well conditioned
+    delta, gamma, theta = np.full(L, 0.3), rng.uniform(-0.3, 0.3, L + 1), []
+    for i in range(L):
+        th = rng.uniform(-0.05, 0.05, i + 1)
+        th[i] = 0.5
+        theta.append(th)
+    return maxsp2.flat(delta, gamma, theta, 0.1)
+
+
+@pytest.mark.parametrize("L", [1, 2, 20])
+def test_depth_limits_and_tiny_orders(ft, L):
+    # one layer (the first layer is the last), two, and the largest table
+    # (20 layers, 21 state planes per chain); orders 1, 17 and 130 (ragged,
+    # below one tile, across a tile edge)
+    rng = np.random.default_rng(L)
+    p, pe = _bounded_max_table(rng, L), _bounded_max_table(rng, L)
+    d = dict(beta0=100.0, mu0=1.0 / 3.0, alpha=0.842704)
+    ms = ft.ModelSet([dict(max=p, max_entropy=pe, **d)])
+    Hs = [np.array([[0.3]]), wl.chain_1d(17, 2), wl.chain_1d(130, 8)]
+    mus, kTs = [0.0, 0.1, -0.1], [0.5, 0.3, 0.25]
+    s = run(ft, ms, Hs, mus, kTs)
+    for b, H in enumerate(Hs):
+        ex = maxsp2.method_exact(H, mus[b], kTs[b], p, L, d["beta0"], d["mu0"], d["alpha"], pe, L)
+        if ex["D"] is None:
+            assert s.records()[b]["status"] != 0
+            continue
+        assert s.records()[b]["status"] == 0
+        assert np.max(np.abs(s.matrix(b).double().cpu().numpy() - ex["D"])) < TOL_D, (L, b)
+        assert abs(float(s.S.cpu()[b]) - ex["S"]) / H.shape[0] < 1e-6
+    # the workspace holds L + 1 planes per chain: L = 20 is the limit
+    if L == 20:
+        with pytest.raises(Exception):
+            ft.ModelSet([dict(max=np.zeros(ft.max_nparams(21)), **d)])

@@ -10,7 +10,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import altform, skipsp2, tables, train
+from oracle import altform, maxsp2, skipsp2, tables, train
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 FILES = sorted(glob.glob(os.path.join(ROOT, "paper_2605_08523_gb300", "tables", "*.json")))
@@ -33,7 +33,18 @@ def test_tables_present():
 def test_table_fit_errors(path):
     d = json.load(open(path))
     b0, m0, al = d["beta0"], d["mu0"], d["alpha"]
-    if "skip" in d:
+    if "max" in d:
+        # Max-SP2 (flat table; Skip-SP2 (k, K) tables carry their Max-SP2 embedding)
+        p, pe = np.array(d["max"]), np.array(d["max_entropy"])
+        assert p.size == maxsp2.nparams(d["L"]) and pe.size == maxsp2.nparams(d["L"])
+        if "skipk" in d:
+            # the stored embedding is that of the stored Skip-SP2 vector
+            k, K, L = d["k"], d["K"], d["L"]
+            t = maxsp2.skip_unpack(np.array(d["skipk"]), L, k, K)
+            assert np.max(np.abs(maxsp2.skip_to_max(t) - p)) < 1e-12 * max(1.0, np.max(np.abs(p)))
+        ef = maxsp2.max_error(p, d["L"], "fermi", b0, m0, 1.0, grid=400001)
+        es = maxsp2.max_error(pe, d["L"], "entropy", b0, m0, al, grid=400001)
+    elif "skip" in d:
         # Skip-SP2 (one stored layer, one accumulator): the oracle's recursion of that family
         t, te = np.array(d["skip"]), np.array(d["skip_entropy"])
         assert t.shape == (d["L"] + 1, 4) and te.shape == (d["L"] + 1, 4)
@@ -91,3 +102,15 @@ def test_training_sweep_layer_count():
     for k, f in e.items():
         assert f["max_err_fermi"] < 1e-3 * f["max_err_sp2_init"], k
         assert f["max_err_fermi"] < 3e-5, k
+
+
+def test_family_tables_layers_saved():
+    # beta0 = 100: the 12-layer Max-SP2 table fits as well as the 14-layer
+    # Eq. mlsp2 table; at 10 layers Max-SP2 is far ahead of Eq. mlsp2 and
+    # Skip-SP2 (2, 2) sits between them
+    e = {n: load(n)["fit"]["max_err_fermi"] for n in ("b100_L10", "b100_L12", "b100_L14", "max_b100_L10",
+                                                       "max_b100_L12", "skip22_b100_L10", "skip22_b100_L12")}
+    assert e["max_b100_L12"] < e["b100_L14"]
+    assert e["max_b100_L10"] < 0.1 * e["b100_L10"] and e["max_b100_L10"] < e["b100_L12"]
+    assert e["max_b100_L10"] < e["skip22_b100_L10"] < e["b100_L10"]
+    assert e["skip22_b100_L12"] < e["b100_L12"]
