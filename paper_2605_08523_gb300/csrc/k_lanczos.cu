@@ -180,7 +180,9 @@ __global__ void __launch_bounds__(kLzThreads) lanczos_update_kernel(LanczosArgs 
 // Small instances (every n <= kLzSmallN): one CTA runs all steps of one
 // instance at a time, with the Lanczos vectors in shared memory and the first
 // rows of H (as many as the dynamic shared memory holds) cached there too; the
-// CTAs loop over the instances.  The launch asks for enough shared memory that
+// CTAs take the instances from a queue, largest order first (longest
+// processing time first: a fixed round-robin split left the CTA with the most
+// large instances running about twice the mean).  The launch asks for enough shared memory that
 // one CTA runs per SM, so the rows of H that the resident CTAs re-read at every
 // step (one instance each, at most kLzSmallN^2 floats) stay in L2 instead of
 // streaming the whole batch from HBM 24 times.  Arithmetic as in the
@@ -190,15 +192,50 @@ constexpr int kLzSmallN = 1024;
 constexpr int kLzSmallThreads = 1024;
 constexpr int kLzSmallCacheBytes = 160 * 1024;
 
+// The queue of the small-instance kernel, in the partial-sum buffer (which
+// only the multi-block path uses; nb RB doubles hold nb + 1 ints): queue[0]
+// the next item (zeroed here), queue[1 + k] the instance of item k, by
+// decreasing order n and then increasing index (the rank of b is the number
+// of instances that come before it).  One thread per instance; O(nb^2)
+// comparisons, a few microseconds up to kLzSortMax instances; larger batches
+// keep their own order (the queue still balances the CTAs).
+constexpr int kLzSortMax = 8192;
+__device__ __forceinline__ int* lz_queue(const LanczosArgs& a) { return reinterpret_cast<int*>(a.part); }
+
+__global__ void lanczos_queue_kernel(LanczosArgs a) {
+    int* const queue = lz_queue(a);
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0) queue[0] = 0;
+    if (b >= a.nb) return;
+    int rank = b;
+    if (a.nb <= kLzSortMax) {
+        const int nself = a.inst[b].n;
+        rank = 0;
+        for (int q = 0; q < a.nb; ++q) {
+            const int nq = a.inst[q].n;
+            rank += (nq > nself || (nq == nself && q < b)) ? 1 : 0;
+        }
+    }
+    queue[1 + rank] = b;
+}
+
 __global__ void __launch_bounds__(kLzSmallThreads, 1) lanczos_small_kernel(LanczosArgs a) {
     __shared__ double vprev[kLzSmallN], vcur[kLzSmallN], w[kLzSmallN];
     __shared__ __align__(16) float v32[kLzSmallN];
     __shared__ double sh[kLzSmallThreads / 32 + 1];
+    __shared__ int item;
     extern __shared__ float4 hcache4[];             // rows 0 .. rc - 1 of H (FP32), pitch pc
     float* const hcache = reinterpret_cast<float*>(hcache4);
     constexpr int NW = kLzSmallThreads / 32;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
+    for (;;) {
+        // every thread has read `item` of the previous instance: the loop body
+        // ends with a barrier
+        if (t == 0) item = atomicAdd(lz_queue(a), 1);
+        __syncthreads();
+        const int k = item;
+        if (k >= a.nb) break;
+        const int b = lz_queue(a)[1 + k];
         const int n = a.inst[b].n;
         const float* Hb = a.H32 + (size_t)b * a.P * a.P;
         const int pc = (n + 3) & ~3;                 // cached row pitch (16-byte rows)
@@ -455,9 +492,10 @@ void launch_lanczos(const LanczosArgs& a, int max_n, int sms, cudaStream_t s) {
                                  kLzSmallCacheBytes);
             attr = true;
         }
+        lanczos_queue_kernel<<<(a.nb + 255) / 256, 256, 0, s>>>(a);
         lanczos_small_kernel<<<std::min(a.nb, std::max(1, sms)), kLzSmallThreads, kLzSmallCacheBytes, s>>>(a);
         lanczos_bounds_kernel<<<(a.nb + 3) / 4, 128, 0, s>>>(a);
-        count_launch(2);
+        count_launch(3);
         return;
     }
     lanczos_start_kernel<<<a.nb, kLzThreads, 0, s>>>(a);

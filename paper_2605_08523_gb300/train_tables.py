@@ -22,6 +22,7 @@ Two groups of tables:
   stored layers and two accumulators (L = 10, 12, 14;
   ftsp2_train_coeffs_skipk, stored with its Max-SP2 embedding, the form the
   layer kernels run), each with an entropy table started from it;
+* ``--grid B:L,...``: tables at the given (beta0, L) pairs;
 * ``--high``: tables at beta0 in {3000, 6000, 12000, 24000} with
   L = ceil(layer count (Eq. layer count)) + 2 layers, which ragged batches of
   rotated spectra need once the Gershgorin width inflates beta'.
@@ -153,6 +154,31 @@ def main_skip(outdir: str, iterations: int = 3000):
     return out
 
 
+def main_grid(outdir: str, specs, iterations: int = 3000):
+    """Tables at given (beta0, L) pairs (``--grid 2250:30,3000:32``), each a
+    Fermi table from the SP2 initial guess and an entropy table started from
+    it, written like the ``--high`` tables."""
+    import paper_2605_08523_gb300 as ft
+    from .build import build
+    build()
+    os.makedirs(outdir, exist_ok=True)
+    out = {}
+    for beta0, L in specs:
+        th, rep = fit(ft, ft.TARGET_FERMI, beta0, L, None, iterations)
+        ths, reps = fit(ft, ft.TARGET_ENTROPY, beta0, L, th, iterations, alpha=ALPHA)
+        name = "b%d_L%d" % (int(beta0), L)
+        out[name] = dict(beta0=beta0, mu0=MU0, alpha=ALPHA, L=L, theta=th.tolist(), theta_entropy=ths.tolist(),
+                         fit=dict(max_err_fermi=rep["max_err_grid"], max_err_entropy=reps["max_err_grid"],
+                                  max_err_sp2_init=max_error(ft, ft.TARGET_FERMI, beta0, MU0,
+                                                             training.sp2_init(L, beta0, MU0), 1.0),
+                                  layer_count=training.layer_count(beta0)),
+                         train=dict(fermi=rep, entropy=reps, samples=100_000, density="1+|f'|"))
+        print(name, out[name]["fit"], flush=True)
+        with open(os.path.join(outdir, name + ".json"), "w") as f:
+            json.dump(out[name], f, indent=1)
+    return out
+
+
 def main_families(outdir: str, iterations: int = 1000):
     import paper_2605_08523_gb300 as ft
     from .build import build
@@ -244,6 +270,11 @@ if __name__ == "__main__":
         main_skip(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)
     elif "--alt" in sys.argv:
         main_alt(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)
+    elif "--grid" in sys.argv:
+        spec = sys.argv[sys.argv.index("--grid") + 1]
+        pairs = [(float(b), int(l)) for b, l in (x.split(":") for x in spec.split(","))]
+        args = [a for a in args if a != spec]
+        main_grid(outdir, pairs, iterations=int(args[1]) if len(args) > 1 else 3000)
     elif "--families" in sys.argv:
         main_families(outdir, iterations=int(args[1]) if len(args) > 1 else 1000)
     elif "--high" in sys.argv:
