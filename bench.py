@@ -447,7 +447,7 @@ def ragged_config(args):
     return {"workload": "ragged batch of %d rotated-spectrum Hamiltonians, n~U{64..768}, eigenvalues U(-10,10) eV, "
                         "mu~U(-5,5), kT~U(0.02,0.5), density+entropy" % args.batch,
             "instances": args.batch, "mode": args.mode, "chains": 2, "bounds": bounds_of(args),
-            "policy": policy_of(args), "tables": "every shipped Eq. mlsp2 table (beta0 20..24000)",
+            "policy": policy_of(args), "tables": "printed, 32-layer sweep, high-beta0 and polished low-beta0 tables",
             "l2": "inputs and working set larger than L2 (no flush)",
             "parallelism": "instances split across ranks by sum n^3" if args.gpus > 1 else "single GPU"}
 
@@ -470,14 +470,28 @@ def refine_layers_of(args):
     return 2 if args.workload == "longrange" else 0
 
 
+# polished low-beta0 tables (fewer layers than the printed one where beta'
+# is small); with the fewest-layers policy most instances of the ragged
+# batch take one of them
+RAGGED_LOW = ("b100_L18", "b200_L21", "b400_L24")
+
+
+def ragged_table_paths():
+    """Model set of the ragged batch: the printed table (with its trained
+    entropy table), the 32-layer sweep tables, the high-beta0 tables and the
+    polished low-beta0 tables."""
+    import glob
+    paths = [os.path.join(TABLE_DIR, "entropy_b1500_L26.json")]
+    paths += sorted(glob.glob(os.path.join(TABLE_DIR, "b*_L32.json")))
+    paths += sorted(p for p in glob.glob(os.path.join(TABLE_DIR, "b*.json"))
+                    if int(os.path.basename(p)[1:].split("_")[0]) >= 3000)
+    paths += [os.path.join(TABLE_DIR, nm + ".json") for nm in RAGGED_LOW]
+    return paths
+
+
 def table_paths(args):
     if args.workload == "ragged":
-        import glob
-        paths = [os.path.join(TABLE_DIR, "entropy_b1500_L26.json")]
-        paths += sorted(glob.glob(os.path.join(TABLE_DIR, "b*_L32.json")))
-        paths += sorted(p for p in glob.glob(os.path.join(TABLE_DIR, "b*.json"))
-                        if int(os.path.basename(p)[1:].split("_")[0]) >= 3000)
-        return paths
+        return ragged_table_paths()
     first = {"alt": "alt_b1500_L26.json", "skip": "skip_b1500_L26.json"}.get(
         args.table if args.workload == "lattice" else "printed", "entropy_b1500_L26.json")
     paths = [os.path.join(TABLE_DIR, first)]

@@ -130,13 +130,11 @@ def test_lattice_sweep_within_1e6(ft, dims, kT, mode):
 # ragged batch: every instance
 # ---------------------------------------------------------------------------
 def ragged_paths():
-    # the printed table (with its trained entropy table), the 32-layer tables
-    # of the training sweep and the high-beta0 tables
-    paths = [os.path.join(TABLES, "entropy_b1500_L26.json")]
-    paths += sorted(glob.glob(os.path.join(TABLES, "b*_L32.json")))
-    paths += sorted(p for p in glob.glob(os.path.join(TABLES, "b*.json"))
-                    if int(os.path.basename(p)[1:].split("_")[0]) >= 3000)
-    return paths
+    # the model set the bench's ragged workload uses: the printed table (with
+    # its trained entropy table), the 32-layer sweep tables, the high-beta0
+    # tables and the polished low-beta0 tables
+    import bench
+    return bench.ragged_table_paths()
 
 
 @pytest.fixture(scope="module")
