@@ -472,7 +472,8 @@ def refine_layers_of(args):
 
 # polished low-beta0 tables (fewer layers than the printed one where beta'
 # is small); with the fewest-layers policy most instances of the ragged
-# batch take one of them
+# batch take one of them.  The shallower b200_L19, b400_L22 and b800_L24 fit
+# as well but leave instances of the batch above 1e-6 in TF32X3 mode
 RAGGED_LOW = ("b100_L18", "b200_L21", "b400_L24")
 
 
