@@ -151,8 +151,23 @@ __global__ void __launch_bounds__(kGWarps * 32) gershgorin_kernel(SetupArgs a) {
         if (a.h32) {
             // same pass, plus the FP32 copy the Lanczos matrix-vector products
             // read: instance b's slab of P x P floats, row pitch P (16-byte
-            // aligned rows for vector loads)
+            // aligned rows for vector loads).  Four loads are issued before
+            // the four stores (a store may alias a later load as far as the
+            // compiler knows), and the sums split as in the plain pass, so
+            // both give the same bounds.
             float* hr = a.h32 + ((size_t)b * a.P + row) * a.P;
+            for (; j + 96 < n; j += 128) {
+                const double h0 = __ldg(Hr + j), h1 = __ldg(Hr + j + 32), h2 = __ldg(Hr + j + 64),
+                             h3 = __ldg(Hr + j + 96);
+                s0 += fabs(h0);
+                s1 += fabs(h1);
+                s2 += fabs(h2);
+                s3 += fabs(h3);
+                hr[j] = (float)h0;
+                hr[j + 32] = (float)h1;
+                hr[j + 64] = (float)h2;
+                hr[j + 96] = (float)h3;
+            }
             for (; j < n; j += 32) {
                 const double h = __ldg(Hr + j);
                 s0 += fabs(h);
