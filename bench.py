@@ -427,6 +427,46 @@ def cuda_time(fn, reps, stream=None):
 # ---------------------------------------------------------------------------
 # configurations shared by both arms
 # ---------------------------------------------------------------------------
+def overlapped_e2e(solvers, Hh, Hdev, outs, steps, comp, s_h2d, s_d2h):
+    """End-to-end steps through the public API: every step copies H from
+    pinned host memory (Hh) into Hdev[k], runs solvers[k] (k = step % 2) on the
+    compute stream and reads its outputs back into pinned host memory
+    (outs[k]: list of (host tensor, device tensor)).  The copies of one step
+    run on their own streams while the other solver computes: H of step i + 1
+    goes up and the outputs of step i - 1 come down during step i.  Returns
+    seconds per step (CUDA events on the compute stream, after every copy)."""
+    import torch
+    ev_h2d = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_d2h = [torch.cuda.Event() for _ in range(2)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(comp)
+    s_h2d.wait_event(e0)
+    for i in range(steps):
+        k = i % 2
+        if i >= 2:
+            s_h2d.wait_event(ev_done[k])        # step i-2 has consumed Hdev[k]
+        with torch.cuda.stream(s_h2d):
+            Hdev[k].copy_(Hh, non_blocking=True)
+            ev_h2d[k].record(s_h2d)
+        comp.wait_event(ev_h2d[k])
+        if i >= 2:
+            comp.wait_event(ev_d2h[k])          # step i-2's outputs are on the host
+        solvers[k].run(Hdev[k], stream=comp)
+        ev_done[k].record(comp)
+        s_d2h.wait_event(ev_done[k])
+        with torch.cuda.stream(s_d2h):
+            for host, dev in outs[k]:
+                host.copy_(dev, non_blocking=True)
+            ev_d2h[k].record(s_d2h)
+    comp.wait_event(ev_d2h[(steps - 1) % 2])
+    if steps >= 2:
+        comp.wait_event(ev_d2h[(steps - 2) % 2])
+    e1.record(comp)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0 / steps
+
+
 def single_config(args):
     """The workload description both arms report (inputs only, no results)."""
     dims, desc = single_dims_desc(args)
@@ -730,36 +770,8 @@ def run_single(args, ft, world, rank, local, secondary=False):
     s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
 
     def e2e_run(steps):
-        ev_h2d = [torch.cuda.Event() for _ in range(2)]
-        ev_done = [torch.cuda.Event() for _ in range(2)]
-        ev_d2h = [torch.cuda.Event() for _ in range(2)]
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(comp)
-        s_h2d.wait_event(e0)
-        for i in range(steps):
-            k = i % 2
-            if i >= 2:
-                s_h2d.wait_event(ev_done[k])        # step i-2 has consumed Hdev[k]
-            with torch.cuda.stream(s_h2d):
-                Hdev[k].copy_(Hh, non_blocking=True)
-                ev_h2d[k].record(s_h2d)
-            comp.wait_event(ev_h2d[k])
-            if i >= 2:
-                comp.wait_event(ev_d2h[k])          # step i-2's outputs are on the host
-            solvers[k].run(Hdev[k], stream=comp)
-            ev_done[k].record(comp)
-            s_d2h.wait_event(ev_done[k])
-            with torch.cuda.stream(s_d2h):
-                Dh[k].copy_(solvers[k].D, non_blocking=True)
-                Sh[k].copy_(solvers[k].S, non_blocking=True)
-                Th[k].copy_(solvers[k].trace[0], non_blocking=True)
-                ev_d2h[k].record(s_d2h)
-        comp.wait_event(ev_d2h[(steps - 1) % 2])
-        if steps >= 2:
-            comp.wait_event(ev_d2h[(steps - 2) % 2])
-        e1.record(comp)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / 1000.0 / steps
+        outs = [[(Dh[k], solvers[k].D), (Sh[k], solvers[k].S), (Th[k], solvers[k].trace[0])] for k in range(2)]
+        return overlapped_e2e(solvers, Hh, Hdev, outs, steps, comp, s_h2d, s_d2h)
 
     e2e_run(2)
     assert torch.equal(Dh[0], Dh[1]) and torch.equal(Dh[0], solver.D.cpu()), "end-to-end outputs differ"
@@ -941,23 +953,26 @@ def run_ragged(args, ft, world, rank, local, secondary=False):
         errS = max(errS, abs(float(solver.S[b]) - Sref) / ns[b])
 
     # ---- end to end through the API: H from pinned host memory, D, S and the
-    # traces back to pinned host memory, one stream ----
+    # traces back to pinned host memory; two solvers alternate so that the
+    # copies of one step overlap the other step's solve ----
     Hh = torch.from_numpy(flat).pin_memory()
-    Dh = torch.empty(solver.D.numel(), dtype=torch.float32).pin_memory()
-    Sh = torch.empty(solver.S.numel(), dtype=torch.float64).pin_memory()
-    Th = torch.empty(solver.trace.numel(), dtype=torch.float64).pin_memory()
-    Hdev = torch.empty_like(Hd)
-
-    def e2e_step():
-        Hdev.copy_(Hh, non_blocking=True)
-        solver.run(Hdev)
-        Dh.copy_(solver.D, non_blocking=True)
-        Sh.copy_(solver.S, non_blocking=True)
-        Th.copy_(solver.trace.view(-1), non_blocking=True)
-
-    e2e_step()
-    t_e2e = cuda_time(e2e_step, max(3, steps // 4))
+    Dh = [torch.empty(solver.D.numel(), dtype=torch.float32).pin_memory() for _ in range(2)]
+    Sh = [torch.empty(solver.S.numel(), dtype=torch.float64).pin_memory() for _ in range(2)]
+    Th = [torch.empty(solver.trace.numel(), dtype=torch.float64).pin_memory() for _ in range(2)]
+    Hdev = [torch.empty_like(Hd) for _ in range(2)]
+    solvers = [solver, ft.Solver(ns, mus, kTs, ms, mode=args.mode, want=3, flags=flags)]
+    solvers[1].run(Hd)                        # sets the second solver's kernel attributes
+    torch.cuda.synchronize()
+    comp = torch.cuda.current_stream()
+    s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = [[(Dh[k], solvers[k].D), (Sh[k], solvers[k].S), (Th[k], solvers[k].trace.view(-1))] for k in range(2)]
+    overlapped_e2e(solvers, Hh, Hdev, outs, 2, comp, s_h2d, s_d2h)
+    assert torch.equal(Dh[0], Dh[1]) and torch.equal(Dh[0], solver.D.cpu()), "end-to-end outputs differ"
+    t_e2e = overlapped_e2e(solvers, Hh, Hdev, outs, max(3, steps // 2), comp, s_h2d, s_d2h)
     e2e_value, _ = aggregate(t_e2e, world, float(valid.sum()), device="cuda")
+    Dh, Sh, Th = Dh[0], Sh[0], Th[0]
+    del solvers, Hdev
+    torch.cuda.empty_cache()
 
     result = {
         "metric": "ragged-batch instances/s (density + entropy) at <=1e-6 error", "value": value,
