@@ -60,10 +60,16 @@ __device__ int block_exclusive_scan(int v, int& total) {
     return r;
 }
 
-// Per-instance tile ranges (thread t owns a contiguous chunk of instances; the
-// chunk totals are scanned), then the tiles themselves: warp w writes those of
-// instances w, w + 32, ..., its lanes stepping through the instance's list and
-// decoding (I, J) from the position in the column-major triangle.
+// Batches up to this many instances get their tiles in decreasing order of
+// n (O(nb^2 / 1024) comparisons per thread of the one-block prep kernel).
+constexpr int kTileSortMax = 2048;
+
+// Per-instance tile ranges, then the tiles themselves.  A chain's table holds
+// the instances one after the other, by decreasing n (ties by index) up to
+// kTileSortMax instances, else in index order (thread t owns a contiguous
+// chunk of instances; the chunk totals are scanned).  Warp w writes the tiles
+// of instances w, w + 32, ..., its lanes stepping through the instance's list
+// and decoding (I, J) from the position in the column-major triangle.
 __device__ void block_exclusive_scan_fill(const ftsp2_instance* inst, int nb, int BM, int BN, int nchains,
                                           InstWork* iw, Tile* tiles, int table) {
     const int T = blockDim.x;
@@ -74,13 +80,31 @@ __device__ void block_exclusive_scan_fill(const ftsp2_instance* inst, int nb, in
     for (int b = b0; b < b1; ++b) s += tiles_of(inst[b].n, BM, BN);
     int chain_total;
     const int first = block_exclusive_scan(s, chain_total);
-    for (int c = 0; c < nchains; ++c) {
-        int pos = c * chain_total + first;
+    if (nb <= kTileSortMax) {
+        // instances by decreasing order n (ties by index): the units of a
+        // layer launch take the tiles round-robin, so the long-K tiles are
+        // dealt first and every unit's last tiles are short ones
         for (int b = b0; b < b1; ++b) {
-            const int cnt = tiles_of(inst[b].n, BM, BN);
-            iw[b].tile_start[table][c] = pos;
-            iw[b].tile_count[table][c] = cnt;
-            pos += cnt;
+            const int nself = inst[b].n, cnt = tiles_of(nself, BM, BN);
+            int before = 0;
+            for (int q = 0; q < nb; ++q) {
+                const int nq = inst[q].n;
+                if (nq > nself || (nq == nself && q < b)) before += tiles_of(nq, BM, BN);
+            }
+            for (int c = 0; c < nchains; ++c) {
+                iw[b].tile_start[table][c] = c * chain_total + before;
+                iw[b].tile_count[table][c] = cnt;
+            }
+        }
+    } else {
+        for (int c = 0; c < nchains; ++c) {
+            int pos = c * chain_total + first;
+            for (int b = b0; b < b1; ++b) {
+                const int cnt = tiles_of(inst[b].n, BM, BN);
+                iw[b].tile_start[table][c] = pos;
+                iw[b].tile_count[table][c] = cnt;
+                pos += cnt;
+            }
         }
     }
     __syncthreads();
