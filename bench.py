@@ -476,7 +476,7 @@ def single_config(args):
     return {"workload": desc, "n": n, "kT": args.kT, "mode": args.mode, "chains": 2,
             "bounds": bounds_of(args), "policy": policy_of(args),
             "tables": ("printed 26-layer beta0=1500 (+ trained entropy table)" if (longrange or args.table == "printed")
-                       else args.table) + (" and trained 28-layer beta0=2250, 34-layer beta0=3000"
+                       else args.table) + (" and trained 27-layer beta0=2250, 34-layer beta0=3000"
                                            if (longrange or args.kT < 0.1) else ""),
             "refine_layers": refine, "refine_on": args.refine_on if refine else None,
             "l2": "inputs and working set larger than L2 (no flush)",
@@ -541,7 +541,7 @@ def table_paths(args):
     # and kT = 0.05 on the n = 4096 lattice); the rescale takes the smallest
     # valid beta0
     if args.workload == "longrange" or args.kT < 0.1:
-        paths.append(os.path.join(TABLE_DIR, "b2250_L28.json"))
+        paths.append(os.path.join(TABLE_DIR, "b2250_L27.json"))
         paths.append(os.path.join(TABLE_DIR, "b3000_L34.json"))
     return paths
 

@@ -224,19 +224,30 @@ def longrange():
     return H, mu, kT, Dref, Sref, float(np.sum(f))
 
 
-@pytest.mark.parametrize("refine_tc", [False, True])
-def test_longrange_n8192_refine2(ft, longrange, refine_tc):
+def bench_longrange_paths():
+    # the model set of the bench's default workload
+    import types
+    import bench
+    return bench.table_paths(types.SimpleNamespace(workload="longrange", kT=0.1, table="printed"))
+
+
+@pytest.mark.parametrize("refine_tc,tables", [(False, "b3000"), (True, "b3000"), (True, "bench")])
+def test_longrange_n8192_refine2(ft, longrange, refine_tc, tables):
     H, mu, kT, Dref, Sref, trref = longrange
     n = H.shape[0]
     # The long-range couplings widen the Gershgorin interval to ~141 eV, so
-    # beta' ~ 1415 needs beta0 >= ~2100: the 34-layer beta0 = 3000 table is the
-    # smallest valid one.
-    ms = ft.ModelSet.from_json(LATTICE_PATHS)
+    # beta' ~ 1415 at mu' ~ 1/2 needs beta0 >= ~2100: with the printed and the
+    # 34-layer beta0 = 3000 tables the latter is the smallest valid one; the
+    # bench's set adds a beta0 = 2250 table, which it takes.
+    paths = LATTICE_PATHS if tables == "b3000" else bench_longrange_paths()
+    ms = ft.ModelSet.from_json(paths)
     s = ft.Solver([n], [mu], [kT], ms, mode="fp16x2", want=3,
                   flags=ft.REFINE2 | (ft.REFINE_TC if refine_tc else 0))
     s.run(torch.from_numpy(H.ravel().copy()).cuda(), sync=True)
     rec = s.records()[0]
     assert rec["status"] == 0 and rec["model"] == 1
+    if tables == "bench":
+        assert "b2250" in paths[1] and rec["layers"] < 34
     D = s.matrix(0).double().cpu().numpy()
     err = np.max(np.abs(D - Dref))
     assert err <= TOL, err
