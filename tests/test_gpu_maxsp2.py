@@ -205,3 +205,62 @@ def test_depth_limits_and_tiny_orders(ft, L):
     if L == 20:
         with pytest.raises(Exception):
             ft.ModelSet([dict(max=np.zeros(ft.max_nparams(21)), **d)])
+
+
+@pytest.mark.parametrize("want", [1, 2])
+def test_density_only_and_entropy_only(ft, golden, want):
+    # one chain per call: the Fermi chain alone (D, traces) or the entropy
+    # chain alone (S), each against the oracle and against the two-chain call
+    d = golden
+    Hs = [wl.lattice_3d((8, 8, 8), 2), wl.chain_1d(200, 7)]
+    mus, kTs = [-0.2, 0.1], [0.3, 0.2]
+    ms = max_set(ft, d)
+    both = run(ft, ms, Hs, mus, kTs, want=3)
+    one = run(ft, ms, Hs, mus, kTs, want=want)
+    for b, H in enumerate(Hs):
+        ex = maxsp2.method_exact(H, mus[b], kTs[b], d["max"], d["L"], d["beta0"], d["mu0"], d["alpha"],
+                                 d["max_entropy"], d["L"])
+        if want == 1:
+            D = one.matrix(b)
+            assert torch.equal(D, both.matrix(b))
+            assert np.max(np.abs(D.double().cpu().numpy() - ex["D"])) < TOL_D
+        else:
+            assert float(one.S.cpu()[b]) == float(both.S.cpu()[b])
+            assert abs(float(one.S.cpu()[b]) - ex["S"]) / H.shape[0] < 1e-6
+
+
+def test_ragged_batch_with_lanczos_bounds(ft, golden):
+    # Lanczos-tightened bounds and the fewest-layers policy over a set of the
+    # printed Eq. mlsp2 table and the Max-SP2 table, FP32 mode, against the
+    # oracle's method-exact result with the same bounds and policy
+    d = golden
+    from oracle import mlsp2, rescale
+    ms = ft.ModelSet([dict(theta=tables.PRINTED_B1500, beta0=1500.0, mu0=1.0 / 3.0, alpha=0.842704),
+                      dict(max=d["max"], max_entropy=d["max_entropy"], beta0=d["beta0"], mu0=d["mu0"],
+                           alpha=d["alpha"])])
+    metas = [rescale.Table(tables.PRINTED_B1500, 1500.0, 1.0 / 3.0, 0.842704, name="printed"),
+             rescale.Table(tuple((0.0, 0.0, 0.0, 0.0) for _ in range(d["L"])), d["beta0"], d["mu0"], d["alpha"])]
+    Hs = [wl.chain_1d(150, 1), wl.lattice_3d((8, 8, 8), 3), wl.chain_1d(260, 5)]
+    mus, kTs = [0.0, 0.1, -0.1], [0.15, 0.1, 0.05]
+    s = run(ft, ms, Hs, mus, kTs, flags=ft.LANCZOS | ft.MIN_LAYERS)
+    rec = s.records()
+    used = set()
+    for b, H in enumerate(Hs):
+        _, r = rescale.rescale(H, mus[b], kTs[b], metas, lanczos=True, min_layers=True)
+        assert r.valid and rec["status"][b] == 0 and int(rec["model"][b]) == r.model, b
+        used.add(r.model)
+        eps, V = np.linalg.eigh(H)
+        x0 = rescale.x0_of_eigenvalue(eps, mus[b], kTs[b], r, metas[r.model])
+        if r.model == 1:
+            f = maxsp2.max_scalar(x0, d["max"], d["L"])
+            sv = maxsp2.forward(d["max_entropy"], d["L"], x0, "entropy", d["alpha"], d["mu0"])
+        else:
+            th = np.array(tables.PRINTED_B1500)
+            f = mlsp2.mlsp2_scalar(x0, th)
+            sv = mlsp2.entropy_scalar(x0, th, 0.842704, 1.0 / 3.0)     # the theta_fermi entropy
+        if r.flip:
+            f = 1.0 - f
+        D = s.matrix(b).double().cpu().numpy()
+        assert np.max(np.abs(D - (V * f) @ V.T)) < TOL_D, b
+        assert abs(float(s.S.cpu()[b]) - float(np.sum(sv))) / H.shape[0] < 1e-6, b
+    assert used == {0, 1}

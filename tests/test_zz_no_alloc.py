@@ -142,3 +142,25 @@ def test_noalloc_first_call_while_capturing_is_refused(ft, tmp_path):
     out = json.loads(r.stdout.strip().splitlines()[-1])
     assert out["st_cap"] == ft._lib.E_ARG and out["untouched"]
     assert out["st"] == 0 and out["finite"]
+
+
+def test_noalloc_max_sp2_set(ft):
+    # a Max-SP2 table (FP32 mode; 13 state planes per chain) through the
+    # allocation-free entry: the same result as the workspace entry point; the
+    # tensor-core modes refuse such a set
+    import json
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "tests", "golden", "max_table.json")) as f:
+        d = json.load(f)
+    ms = ft.ModelSet([dict(max=d["max"], max_entropy=d["max_entropy"], beta0=d["beta0"], mu0=d["mu0"],
+                           alpha=d["alpha"])])
+    H = wl.chain_1d(96, 4)
+    host, d_inst, Hd, total = _inputs(ft, [H], [0.05], [0.3])
+    ref = ft.Solver([96], [0.05], [0.3], ms, mode="fp32", want=1)
+    ref.run(Hd, sync=True)
+    st, D, tr, rec = _run_noalloc(ft, ms, host, d_inst, Hd, 1, total, "fp32")
+    assert st == 0, ft.status_string(st)
+    assert torch.equal(D, ref.D)
+    st, _, _, _ = _run_noalloc(ft, ms, host, d_inst, Hd, 1, total, "fp16x2")
+    assert st == ft._lib.E_UNSUPPORTED
