@@ -340,6 +340,15 @@ def plain_fp32_recursion(Hd, mu, kT, theta, beta0, mu0, alpha, emin, emax, theta
 # (mode, n, kernel_sha(): code hash of the layer kernel) -> DRAM read + write
 # bytes of one layer launch of both chains, from an ncu capture of that launch
 # (dram__bytes_read.sum + dram__bytes_write.sum) at that code hash
+# (mode, batch size, kernel_sha()) -> (DRAM read + write bytes, algorithmic
+# bytes) of one ragged-batch layer launch with every instance active, from an
+# ncu capture of that launch at that code hash
+MEASURED_RAGGED_TRAFFIC = {
+    # 512-instance ragged batch, global layer 35 of 44: 1.78 GB read + 1.55 GB
+    # written in 0.937 ms
+    ("fp16x2", 512, "215c1725bf044bed"): (3.33e9, 3.285e9),
+}
+
 MEASURED_TRAFFIC = {
     # n = 8192 long-range lattice, FP16X2 main layer (layer_tc_kernel<FP16X2,
     # FP16X2, pair, deferred>): 3.22 GB read + 1.04 GB written per launch
@@ -940,6 +949,18 @@ def run_ragged(args, ft, world, rank, local, secondary=False):
     achieved = alg / lmax / layer_avg / 1e12 if layer_avg > 0 else None
     pk, pk_kind = peaks()
     peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    # algorithmic bytes of one chain-layer of instance b: the state Z and A on
+    # the upper triangle read and written (8 n^2 B), the next operands written
+    # on the upper triangle (2 n^2 B) and this layer's read as full panels
+    # (4 n^2 B); the layer moves them at a fraction of the HBM roof, well above
+    # its fraction of the tensor roof
+    n2 = np.array(ns, dtype=np.float64) ** 2
+    alg_bytes = float(np.sum((2.0 * 14.0 * n2 * layers)[valid]))
+    achieved_gbs = alg_bytes / lmax / layer_avg / 1e9 if layer_avg > 0 else None
+    hbm_peak = pk.get("hbm_gbs")
+    full_layer_bytes = float(np.sum((2.0 * 14.0 * n2)[valid]))
+    cap = MEASURED_RAGGED_TRAFFIC.get((args.mode, args.batch, kernel_sha()))
+    traffic = cap[0] / cap[1] * alg_bytes / lmax if cap else None
 
     # ---- accuracy on 32 instances spread over the sizes (the tests check all) ----
     errD, errS = 0.0, 0.0
@@ -990,12 +1011,20 @@ def run_ragged(args, ft, world, rank, local, secondary=False):
         "tflops_alg": alg / t_step / 1e12,
         "accuracy_sampled": {"instances": len(picks), "max_abs_D_minus_Dref": errD,
                              "max_abs_S_minus_Sref_per_n": errS},
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if achieved else None,
-                     "traffic": MEASURED_TRAFFIC.get((args.mode, "ragged%d" % args.batch, kernel_sha())),
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved_gbs / hbm_peak if achieved_gbs and hbm_peak else None,
+                     "traffic": traffic,
+                     "traffic_how": ("ncu dram bytes of one launch with every instance active, %.3g B against its "
+                                     "%.3g algorithmic B, scaled to the mean launch by algorithmic bytes"
+                                     % cap if cap else None),
                      "kernel": "layer_tc_kernel<%s>" % args.mode.upper(), "avg_layer_ms": layer_avg * 1e3,
-                     "per_launch_alg_flops": alg / lmax, "peak_kind": "bf16_tflops_sustained (%s)" % pk_kind,
-                     "work_unit": "one global layer of every instance and both chains (n_b^3 per chain)"},
+                     "per_launch_alg_bytes": alg_bytes / lmax, "full_layer_alg_bytes": full_layer_bytes,
+                     "peak_kind": "hbm_gbs (%s)" % pk_kind,
+                     "tensor_achieved_tflops": achieved, "tensor_peak": peak,
+                     "tensor_frac": achieved / peak if achieved else None,
+                     "per_launch_alg_flops": alg / lmax,
+                     "work_unit": "one global layer of every active instance and both chains: 14 n_b^2 B and "
+                                  "n_b^3 flops per chain"},
         "e2e": {"value": e2e_value, "unit": "instances/s", "h2d_bytes_per_step": int(flat.nbytes),
                 "d2h_bytes_per_step": int(Dh.numel() * 4 + Sh.numel() * 8 + Th.numel() * 8)},
         "gpu_launches": per_run * steps,
@@ -1101,7 +1130,8 @@ def compact(res):
             "density_only", "e2e", "details")
     out = {k: res[k] for k in keep if k in res}
     r = res.get("roofline", {})
-    out["roofline"] = {k: r.get(k) for k in ("achieved", "peak", "frac", "avg_layer_ms", "traffic")}
+    out["roofline"] = {k: r.get(k) for k in ("bound", "unit", "achieved", "peak", "frac", "avg_layer_ms", "traffic",
+                                             "tensor_frac")}
     return out
 
 
