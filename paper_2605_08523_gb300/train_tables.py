@@ -174,6 +174,20 @@ def fit_polished(ft, target, beta0, L, init, iterations, alpha=1.0, polish=0):
     return best_th, best_rep
 
 
+def grid_args(argv):
+    """(outdir, [(beta0, L), ...], iterations, polish passes) of a command
+    line ``OUT --grid B:L,B:L [ITER] [--polish N]`` (any order)."""
+    spec = argv[argv.index("--grid") + 1]
+    pairs = [(float(b), int(l)) for b, l in (x.split(":") for x in spec.split(","))]
+    skip = {argv.index("--grid") + 1}
+    npol = 0
+    if "--polish" in argv:
+        npol = int(argv[argv.index("--polish") + 1])
+        skip.add(argv.index("--polish") + 1)
+    pos = [a for i, a in enumerate(argv) if i > 0 and i not in skip and not a.startswith("--")]
+    return (pos[0] if pos else "tables_out"), pairs, (int(pos[1]) if len(pos) > 1 else 3000), npol
+
+
 def main_grid(outdir: str, specs, iterations: int = 3000, polish: int = 0):
     """Tables at given (beta0, L) pairs (``--grid 2250:30,3000:32``), each a
     Fermi table from the SP2 initial guess and an entropy table started from
@@ -292,15 +306,8 @@ if __name__ == "__main__":
     elif "--alt" in sys.argv:
         main_alt(outdir, iterations=int(args[1]) if len(args) > 1 else 3000)
     elif "--grid" in sys.argv:
-        spec = sys.argv[sys.argv.index("--grid") + 1]
-        pairs = [(float(b), int(l)) for b, l in (x.split(":") for x in spec.split(","))]
-        npol = int(sys.argv[sys.argv.index("--polish") + 1]) if "--polish" in sys.argv else 0
-        skip = {sys.argv.index("--grid") + 1}
-        if "--polish" in sys.argv:
-            skip.add(sys.argv.index("--polish") + 1)
-        pos = [a for i, a in enumerate(sys.argv) if i > 0 and i not in skip and not a.startswith("--")]
-        main_grid(pos[0] if pos else "tables_out", pairs, iterations=int(pos[1]) if len(pos) > 1 else 3000,
-                  polish=npol)
+        out, pairs, iters, npol = grid_args(sys.argv)
+        main_grid(out, pairs, iterations=iters, polish=npol)
     elif "--families" in sys.argv:
         main_families(outdir, iterations=int(args[1]) if len(args) > 1 else 1000)
     elif "--high" in sys.argv:

@@ -114,3 +114,20 @@ def test_family_tables_layers_saved():
     assert e["max_b100_L10"] < 0.1 * e["b100_L10"] and e["max_b100_L10"] < e["b100_L12"]
     assert e["max_b100_L10"] < e["skip22_b100_L10"] < e["b100_L10"]
     assert e["skip22_b100_L12"] < e["b100_L12"]
+
+
+def test_grid_command_line():
+    # the command lines that produced the polished tables
+    from paper_2605_08523_gb300.train_tables import grid_args
+    assert grid_args(["x", "OUT", "--grid", "2250:27", "5000", "--polish", "14"]) == ("OUT", [(2250.0, 27)], 5000, 14)
+    assert grid_args(["x", "OUT", "--grid", "100:18,200:21", "5000", "--polish", "6"]) == \
+        ("OUT", [(100.0, 18), (200.0, 21)], 5000, 6)
+    assert grid_args(["x", "--polish", "6", "OUT", "--grid", "400:24"]) == ("OUT", [(400.0, 24)], 3000, 6)
+    assert grid_args(["x", "OUT", "--grid", "2250:32"]) == ("OUT", [(2250.0, 32)], 3000, 0)
+
+
+def test_polished_tables_record_their_passes():
+    for name in ("b2250_L27", "b100_L18", "b200_L21", "b400_L24"):
+        d = load(name)
+        assert d["train"]["fermi"]["polish_passes"] >= 6 and 0 <= d["train"]["fermi"]["kept_pass"] <= \
+            d["train"]["fermi"]["polish_passes"], name
