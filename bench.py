@@ -545,6 +545,11 @@ def table_paths(args):
     first = {"alt": "alt_b1500_L26.json", "skip": "skip_b1500_L26.json"}.get(
         args.table if args.workload == "lattice" else "printed", "entropy_b1500_L26.json")
     paths = [os.path.join(TABLE_DIR, first)]
+    # the polished 24-layer beta0 = 1000 table serves the lattice with the
+    # printed table's weights where beta' is small enough (kT >= 0.1 on the
+    # n = 4096 lattice: beta' ~ 620 at mu' ~ 1/2)
+    if args.workload == "lattice" and args.table == "printed":
+        paths.append(os.path.join(TABLE_DIR, "b1000_L24.json"))
     # the beta0 = 2250 and 3000 tables serve the cases whose Gershgorin width
     # puts beta' beyond the printed table's region (the long-range couplings,
     # and kT = 0.05 on the n = 4096 lattice); the rescale takes the smallest
