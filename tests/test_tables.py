@@ -131,3 +131,21 @@ def test_polished_tables_record_their_passes():
         d = load(name)
         assert d["train"]["fermi"]["polish_passes"] >= 6 and 0 <= d["train"]["fermi"]["kept_pass"] <= \
             d["train"]["fermi"]["polish_passes"], name
+
+
+def test_bench_model_sets_exist():
+    # every table the bench's workloads load is shipped and carries its fit
+    import types
+    import bench
+    sets = [bench.ragged_table_paths()]
+    for wk, kT in (("longrange", 0.1), ("lattice", 0.1), ("lattice", 0.05), ("lattice", 0.3)):
+        sets.append(bench.table_paths(types.SimpleNamespace(workload=wk, kT=kT, table="printed")))
+    for tb in ("skip", "alt"):
+        sets.append(bench.table_paths(types.SimpleNamespace(workload="lattice", kT=0.1, table=tb)))
+    sets.append([os.path.join(bench.TABLE_DIR, nm + ".json") for nm in bench.FAMILY_TABLES])
+    for paths in sets:
+        assert paths
+        for p in paths:
+            assert os.path.exists(p), p
+            d = json.load(open(p))
+            assert "fit" in d or os.path.basename(p) == "entropy_b1500_L26.json", p
