@@ -106,3 +106,16 @@ def test_skipk_start_and_embedding_match_oracle(ft, L, k, K, beta0):
     x = np.linspace(0.0, 1.0, 1001)
     ref = train.forward(train.init_from_sp2(L, beta0, 1 / 3), x)
     assert np.max(np.abs(maxsp2.max_scalar(x, p, L) - ref)) < 1e-11
+
+
+def test_skipk_entry_points_reject_bad_shapes(ft):
+    with pytest.raises(Exception):
+        ft.ftsp2_train_init_skipk(3, 4, 2, 100.0, 1 / 3)          # more stored layers than layers
+    with pytest.raises(Exception):
+        ft.ftsp2_train_init_skipk(5, 2, 0, 100.0, 1 / 3)          # no accumulator
+    with pytest.raises(Exception):
+        ft.ftsp2_train_init_skipk(21, 2, 2, 100.0, 1 / 3)         # beyond the 20-layer limit
+    with pytest.raises(ValueError):
+        ft.ftsp2_skipk_to_max(np.zeros(10), 5, 2, 2)              # wrong vector length
+    v = ft.ftsp2_train_init_skipk(5, 2, 2, 100.0, 1 / 3)
+    assert v.size == ft.skipk_nparams(5, 2, 2) == (1 + 2 + 4) * 5 + 2
